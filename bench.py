@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark of the colour-pair search (Hattori and Hiraki, §2 Methods) on GB300.
+
+One step = one pass of the whole search over the dense colour cube: every colour
+with channels 0, 4, .., 252 (262,144 targets) x 128 radii (0.25..32) x 360
+angles = 1.208e10 candidate pairs: target decode to L*a*b* (FP64), the pair
+chain in FP32 with FP64 re-decision near rounding boundaries, the
+embedding-signal decision (V_th = 50, R_novib = 0.5, all patterns, out-of-gamut
+rejected) and the per-colour reduction (count, largest radius, pattern mask).
+
+Prints one JSON line (rank 0).  `value` is G candidate pairs/s over all ranks
+with inputs resident on the device; `e2e` is the same metric through the C ABI
+entry point that takes host buffers (copies inside the timed region).
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+METRIC = "G candidate pairs/s & 4K images/s, FP32+recheck vs plain FP64 GPU, 1 GB300"
+UNIT = "Gcand/s"
+# Candidates of one 3840x2160 frame with the 64-radius x 180-angle image grid.
+CAND_PER_4K_FRAME = 3840 * 2160 * 64 * 180
+# Algorithmic instruction issues per candidate of the FP32 path (one colour
+# conversion and half a pair decision per candidate; see the roofline section
+# of the design notes): 53.5 FP32/INT lane operations + 6 MUFU operations.
+ALG_ISSUES_PER_CAND = 59.5
+LANES_PER_SM_CLK = 128
+REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x2: "applications_clocks_setting", 0x1: "gpu_idle"}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison arm")
+    p.add_argument("--cpu-sample", type=int, default=2048,
+                   help="colours of the cube timed on the CPU oracle")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "-i", str(self.index),
+               "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+               "--format=csv,noheader,nounits", "-lms", "100"]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                parts = [x.strip() for x in line.split(",")]
+                try:
+                    self.samples.append((float(parts[0]), float(parts[1]), float(parts[2]),
+                                         int(parts[3], 16)))
+                except (ValueError, IndexError):
+                    pass
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        busy = [s for s in self.samples if not (s[3] & 0x1)] or self.samples
+        reasons = set()
+        for s in busy:
+            for bit, name in REASON_BITS.items():
+                if s[3] & bit and name != "gpu_idle":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(s[0] for s in busy),
+                "sm_max_mhz": max(s[1] for s in self.samples),
+                "power_w_max": max(s[2] for s in busy),
+                "reasons": sorted(reasons), "samples": len(busy)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("CVS_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest value over all ranks (the job's wall time is its slowest rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ oracle arms
+def cpu_sample(n: int):
+    from paper_2507_22901_gb300 import workloads as W
+    cube = W.color_cube()
+    idx = np.linspace(0, len(cube) - 1, n).astype(np.int64)
+    return cube[idx]
+
+
+def time_oracle(n_colors: int):
+    """FP64 CPU oracle over a bounded, evenly spaced sample of the cube."""
+    import oracle
+    from paper_2507_22901_gb300 import workloads as W
+    radii, ang = W.grid(2)
+    tt = oracle.trig_table(ang)
+    rgb = cpu_sample(n_colors)
+    threads = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.search_colors(rgb, radii, ang, 50.0, 0.5, threads=threads, trig_tab=tt)
+    dt = time.perf_counter() - t0
+    cand = n_colors * len(radii) * len(ang)
+    return cand / dt / 1e9, threads, cand, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2507_22901_gb300 import workloads as W  # noqa: F401
+    n = max(16, args.cpu_sample // 4)
+    for _ in range(args.warmup):
+        time_oracle(max(8, n // 8))
+    vals, cand_total, dt_total, threads = [], 0, 0.0, 1
+    for _ in range(args.steps):
+        v, threads, cand, dt = time_oracle(n)
+        vals.append(v)
+        cand_total += cand
+        dt_total += dt
+    value = cand_total / dt_total / 1e9
+    sample = f"{n} evenly spaced colours of the 262,144-colour cube x 128 radii x 360 angles per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt_total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "colour cube 262144 x 128 radii x 360 angles (sampled)",
+                   "sample_colors_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2507_22901_gb300 as cvs
+    from paper_2507_22901_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    ctx = cvs.Context(local)
+    radii, ang = W.grid(2)
+    rgb_h = W.color_cube()
+    n = len(rgb_h)
+    cand = n * len(radii) * len(ang)
+    rgb = torch.from_numpy(rgb_h).to(device)
+    out = (torch.empty(n, dtype=torch.float32, device=device),
+           torch.empty(n, dtype=torch.int32, device=device),
+           torch.empty(n, dtype=torch.uint8, device=device))
+    stream = torch.cuda.current_stream(device)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=device)  # > 129 MB L2
+
+    def step(prec):
+        ctx.search_colors(rgb, radii, ang, 50.0, 0.5, precision=prec, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        step(cvs.PREC_FP32_RECHECK)
+    ctx.synchronize(stream)
+
+    # ---- timed region: device-resident inputs, L2 flushed between steps
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    step_ms, kern_ms, flagged, rechecked = [], [], 0, 0
+    barrier(world)
+    torch.cuda.synchronize(device)
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            start.record(stream)
+            step(cvs.PREC_FP32_RECHECK)
+            end.record(stream)
+            ctx.synchronize(stream)
+            step_ms.append(start.elapsed_time(end))
+            st = ctx.stats()
+            kern_ms.append(st["search_ms"])
+            flagged += st["flagged"]
+            rechecked += st["rechecked"]
+    torch.cuda.synchronize(device)
+    barrier(world)
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world, device)
+    value = world * cand * args.steps / total_s / 1e9
+    res32 = tuple(x.clone() for x in out)
+
+    # ---- comparison arm: every candidate in FP64 (one timed step)
+    fp64 = None
+    mismatch = None
+    if not args.no_fp64:
+        step(cvs.PREC_FP64)
+        ctx.synchronize(stream)
+        flush.zero_()
+        start.record(stream)
+        step(cvs.PREC_FP64)
+        end.record(stream)
+        ctx.synchronize(stream)
+        t64 = max_over_ranks(start.elapsed_time(end) / 1e3, world, device)
+        fp64 = world * cand / t64 / 1e9
+        mismatch = int(((res32[0].view(torch.int32) != out[0].view(torch.int32)) |
+                        (res32[1] != out[1]) | (res32[2] != out[2])).sum().item())
+
+    # ---- end to end through the host-buffer C entry point
+    h_out = (np.empty(n, np.float32), np.empty(n, np.int32), np.empty(n, np.uint8))
+    ctx.search_colors_host(rgb_h, radii, ang, 50.0, 0.5, out=h_out)
+    barrier(world)
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        ctx.search_colors_host(rgb_h, radii, ang, 50.0, 0.5, out=h_out)
+        e2e_s += time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, world, device)
+    e2e = world * cand * args.steps / e2e_s / 1e9
+    e2e_match = bool(np.array_equal(h_out[1], res32[1].cpu().numpy()))
+
+    # ---- roofline of the search kernel (issue bound)
+    c = clk.summary()
+    f_mhz = c["sm_mhz"] or 2070.0
+    kern_avg_s = sum(kern_ms) / len(kern_ms) / 1e3
+    achieved = ALG_ISSUES_PER_CAND * cand / kern_avg_s / 1e12
+    num_sms = torch.cuda.get_device_properties(device).multi_processor_count
+    peak = num_sms * LANES_PER_SM_CLK * f_mhz * 1e6 / 1e12
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "colour cube 262144 colours x 128 radii (0.25..32) x 360 angles "
+                               "(1.208e10 candidates per GPU per step)",
+                   "v_th": 50, "r_novib": 0.5, "patterns": "all 7", "gamut": "reject",
+                   "precision": "fp32 + fp64 re-decision", "l2": "flushed between steps "
+                   "(256 MB write)", "parallelism": f"replicas x{world}"},
+        "images_4k_per_s": value * 1e9 / CAND_PER_4K_FRAME,
+        "fp64_gpu": {"value": fp64, "unit": UNIT,
+                     "speedup": (value / fp64) if fp64 else None,
+                     "decision_mismatches": mismatch},
+        "recheck": {"flagged_fraction": flagged / (cand * args.steps),
+                    "rechecked_fraction": rechecked / (cand * args.steps),
+                    "window_code_units": ctx.get_option("fp32_window")},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(rgb_h.nbytes),
+                "d2h_bytes_per_step": int(n * 9), "matches_device_result": e2e_match},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_search<fp32>", "achieved": achieved,
+                     "peak": peak, "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": f"{num_sms} SMs x {LANES_PER_SM_CLK} lanes x "
+                                   f"{f_mhz:.0f} MHz median SM clock under load",
+                     "ops_per_candidate": ALG_ISSUES_PER_CAND,
+                     "kernel_ms": kern_avg_s * 1e3},
+        "clocks": {"sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"],
+                   "reasons": c["reasons"], "samples": c["samples"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, threads, ccand, dt = time_oracle(args.cpu_sample)
+        line["cpu_baseline"] = {
+            "value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{args.cpu_sample} evenly spaced colours of the cube x 128 x 360 "
+                      f"({ccand:.3g} candidates, {dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,248 @@
+/*
+ * cvsearch.h - C ABI of libcvsearch, a GB300 (sm_103a) implementation of the
+ * colour-pair search of "Accelerated and Optimized Search of Imperceptible
+ * Color Vibration for Embedding Information into LCD images" (Hattori and
+ * Hiraki, SIGGRAPH Asia 2022 Posters).
+ *
+ * The operation (paper §2 Methods, Fig. 1b and Fig. 2; §3 Experiments and
+ * Table 1):
+ *   For a target colour, take its CIE L*a*b* coordinates (L, a, b).  For every
+ *   radius i = radii[k] and angle j = angles_deg[m] form the point-symmetric
+ *   pair
+ *       plus  = (L, a + i sin j, b + i cos j)      ("D_a", "D_b" added)
+ *       minus = (L, a - i sin j, b - i cos j)      (subtracted)
+ *   at fixed L* (the colour-vibration condition), convert both back to 8-bit
+ *   sRGB and keep the pair if, in every RGB channel, the difference
+ *   |plus_c - minus_c| is either "high" (> V_th) or "low" (< V_th * R_novib),
+ *   the high/low word (R,G,B) = p is not 000, and p is enabled in the pattern
+ *   mask (the embedding-signal condition; patterns 100 ... 111 of Table 1).
+ *
+ * Number semantics (where the paper is silent):
+ *   - sRGB IEC 61966-2-1, D65 white, CIE 1976 L*a*b*; FP64 in the order of the
+ *     textbook formulas; the target's cube roots are correctly rounded.
+ *   - sin j / cos j are the correctly rounded values of the exact angle in
+ *     degrees, so angle j + 180 gives exactly the swapped pair.
+ *   - 8-bit code = floor(255 * enc(lin) + 1/2) of the FP64 linear value, in
+ *     exact arithmetic.  Gamut: mode 0 rejects a pair with any code outside
+ *     [0, 255]; mode 1 clamps the codes.
+ *   The results are identical to those of a plain FP64 evaluation in that
+ *   order: the FP32 fast path re-decides in FP64 every candidate whose FP32
+ *   codes could be wrong.
+ *
+ * Threading: a cvs_ctx may be used by one host thread at a time.  Its
+ * scratch memory is shared by its calls, so asynchronous calls on one context
+ * must be issued on one stream (or the caller synchronises between streams);
+ * a call with a different grid waits for the device before replacing tables.
+ * Memory: the caller owns every input and output buffer; the context owns its
+ * scratch memory (tables, per-target constants, work counters) and frees it
+ * in cvs_destroy.
+ * Errors: every entry point returns a cvs_status; cvs_last_error() gives a
+ * thread-local message for the last failure.  Invalid arguments are reported
+ * before any device work is issued.  Asynchronous entry points report CUDA
+ * launch errors immediately and execution errors at the next synchronising
+ * call (cvs_synchronize or a synchronous entry point).
+ */
+#ifndef CVSEARCH_H
+#define CVSEARCH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CVS_OK = 0,
+    CVS_ERR_INVALID_ARG = 1, /* bad pointer, size, NaN, out-of-range parameter */
+    CVS_ERR_NO_MEMORY = 2,   /* device or pinned host allocation failed */
+    CVS_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    CVS_ERR_TRUNCATED = 4,   /* output capacity too small; *n_out = required count */
+    CVS_ERR_TIMEOUT = 5,     /* a bounded device-side wait expired */
+    CVS_ERR_NUMERIC = 6      /* a table value could not be certified (never seen) */
+} cvs_status;
+
+typedef enum {
+    CVS_PREC_FP32_RECHECK = 0, /* FP32 bulk, FP64 re-decision near rounding boundaries */
+    CVS_PREC_FP64 = 1          /* every candidate in FP64 (comparison form) */
+} cvs_precision;
+
+typedef struct cvs_ctx cvs_ctx;
+
+/* The (radius i, angle j) grid of §2 Methods.  Host pointers, read during the
+ * call.  radii: finite, >= 0, in L*a*b* units, at most 16384 values.
+ * angles_deg: finite, in degrees, at most 16384 values.  When the angle list
+ * is closed under +180 degrees with angles_deg[m + n/2] = angles_deg[m] + 180
+ * (mod 360), each symmetric pair is evaluated once. */
+typedef struct {
+    const double* radii;
+    int32_t n_radii;
+    const double* angles_deg;
+    int32_t n_angles;
+} cvs_grid;
+
+/* Embedding-signal condition (§3 Experiments, Table 1).
+ * v_th: finite, >= 0.  r_novib: in (0, 1].  A channel difference d is high
+ * if d > v_th and low if d < v_th * r_novib (exact comparisons).
+ * pattern_mask: bit p-1 enables pattern p = (hi_R << 2) | (hi_G << 1) | hi_B,
+ * p = 1..7 (0x7F = all seven patterns of Table 1).
+ * gamut_mode: 0 = reject pairs with a code outside [0,255], 1 = clamp. */
+typedef struct {
+    double v_th;
+    double r_novib;
+    uint32_t pattern_mask;
+    int32_t gamut_mode;
+} cvs_thresholds;
+
+/* One passing candidate (16 bytes).  k, m: radius and angle indices;
+ * plus / minus: the 8-bit sRGB of the two colours; pattern: 1..7;
+ * flags: bit 0 = decided by the FP64 re-decision; target: caller's index. */
+typedef struct {
+    uint16_t k, m;
+    uint8_t plus[3], minus[3];
+    uint8_t pattern, flags;
+    uint32_t target;
+} cvs_pair;
+
+/* Per-target results (Table 2's question, per colour or pixel), device
+ * pointers to n entries each, written by the search:
+ *   max_r: largest radius of a passing candidate, -1.0f if none;
+ *   count: number of passing (k, m) candidates;
+ *   pmask: bit p-1 set if some passing candidate carries pattern p. */
+typedef struct {
+    float* max_r;
+    int32_t* count;
+    uint8_t* pmask;
+} cvs_capacity_map;
+
+/* An 8-bit sRGB image, HWC (R, G, B bytes per pixel), device pointer.
+ * Row y starts at rgb + y * pitch_bytes; pitch_bytes >= 3 * width. */
+typedef struct {
+    const uint8_t* rgb;
+    int32_t width;
+    int32_t height;
+    int64_t pitch_bytes;
+} cvs_image;
+
+/* Counters of the last search call on a context (filled when the call has
+ * completed, i.e. after cvs_synchronize for asynchronous calls). */
+typedef struct {
+    int64_t candidates;      /* (target, k, m) candidates decided */
+    int64_t colors_fp32;     /* colour conversions done in FP32 */
+    int64_t flagged;         /* candidates with a code within the FP32 window */
+    int64_t rechecked;       /* candidates re-decided in FP64 */
+    int64_t targets;         /* targets (colours or pixels) searched */
+    int32_t symmetric;       /* 1 if the angle list was folded by +180 degrees */
+    int32_t precision;       /* cvs_precision of the call */
+    double search_ms;        /* device time of the search kernel (CUDA events on the
+                                call's stream) */
+} cvs_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (the device is made current for
+ * every call on the context).  *ctx receives the handle, owned by the caller
+ * and released with cvs_destroy.  Returns CVS_ERR_CUDA if the device is not
+ * usable. */
+cvs_status cvs_create(cvs_ctx** ctx, int device);
+
+/* Free the context and all scratch memory it owns (waits for its work). */
+void cvs_destroy(cvs_ctx* ctx);
+
+/* Thread-local text of the last error, or "" (never NULL). */
+const char* cvs_last_error(void);
+
+/* Library version as "major.minor.patch". */
+const char* cvs_version(void);
+
+/* Resolve the embedding-signal thresholds (§3 Experiments) to integer bounds
+ * on the channel difference d in [0, 255]: high iff d >= *hi_min, low iff
+ * d <= *lo_max.  Host only; no device work.  Validates *thr. */
+cvs_status cvs_signal_bounds(const cvs_thresholds* thr, int32_t* hi_min, int32_t* lo_max);
+
+/* Correctly rounded sin / cos of the angles in degrees as the search uses
+ * them (§2 Methods: D_a = i sin j, D_b = i cos j), computed on the device.
+ * angles_deg: host, n values; sin_out / cos_out: host, n doubles each.
+ * Synchronous. */
+cvs_status cvs_trig_table(cvs_ctx* ctx, const double* angles_deg, int32_t n,
+                          double* sin_out, double* cos_out);
+
+/* L*a*b* of n 8-bit sRGB colours (step 1 of §2 Methods) on the device.
+ * rgb_dev: device, 3n bytes; lab_dev: device, 3n doubles (L, a, b).
+ * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream). */
+cvs_status cvs_target_lab(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, double* lab_dev,
+                          void* stream);
+
+/* --------------------------------------------------------------- searches */
+
+/* Every passing candidate of one target colour rgb[3] (host), sorted by
+ * (k, m), written to out_host[0 .. min(n, cap)) (host).  *n_out receives the
+ * number of passing candidates; if it exceeds cap, the first cap records are
+ * written and CVS_ERR_TRUNCATED is returned.  target is copied into each
+ * record.  Synchronous.  This is the paper's problem statement (§2 Methods):
+ * generate the array of pairs, extract those meeting the conditions. */
+cvs_status cvs_search_color(cvs_ctx* ctx, const uint8_t rgb[3], uint32_t target,
+                            const cvs_grid* grid, const cvs_thresholds* thr,
+                            cvs_precision prec, cvs_pair* out_host, size_t cap,
+                            size_t* n_out);
+
+/* Per-target results for n colours.  rgb_dev: device, 3n bytes (R,G,B per
+ * colour).  out_dev: device capacity map of n entries.  Asynchronous on
+ * `stream`; the device buffers must stay valid until it completes. */
+cvs_status cvs_search_colors(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
+                             const cvs_grid* grid, const cvs_thresholds* thr,
+                             cvs_precision prec, const cvs_capacity_map* out_dev,
+                             void* stream);
+
+/* As cvs_search_colors with host buffers: rgb_host (3n bytes), max_r_host,
+ * count_host, pmask_host (n entries each).  Copies in, searches and copies
+ * out through the context's pinned staging buffers.  Synchronous. */
+cvs_status cvs_search_colors_host(cvs_ctx* ctx, const uint8_t* rgb_host, int64_t n,
+                                  const cvs_grid* grid, const cvs_thresholds* thr,
+                                  cvs_precision prec, float* max_r_host,
+                                  int32_t* count_host, uint8_t* pmask_host);
+
+/* Per-pixel results for a batch of n images of any sizes, in one persistent
+ * launch over a shared work queue.  batch: host array of n image descriptors
+ * (device pixel pointers).  maps: host array of n capacity maps (device
+ * pointers, width*height entries each, row-major, dense).  Asynchronous. */
+cvs_status cvs_search_images(cvs_ctx* ctx, const cvs_image* batch, int32_t n,
+                             const cvs_grid* grid, const cvs_thresholds* thr,
+                             cvs_precision prec, const cvs_capacity_map* maps,
+                             void* stream);
+
+/* Wait for the context's work on `stream` and report any device error or
+ * device-side timeout.  Fills the counters of the last search. */
+cvs_status cvs_synchronize(cvs_ctx* ctx, void* stream);
+
+/* Counters of the last completed search on this context. */
+cvs_status cvs_get_stats(cvs_ctx* ctx, cvs_stats* out);
+
+/* Precision study: for n colours (rgb_dev: device, 3n bytes) on the grid,
+ * compare every FP32 colour conversion (the "plus" colour of each (k, m))
+ * with its FP64 value.  Outputs (host): *max_code_err = largest |v32 - v64|
+ * in 8-bit code units among values within 0.05 of a rounding boundary
+ * (v = 255 enc(lin) before rounding); *max_lin_err = largest |lin32 - lin64|
+ * of the linear RGB; *n_wrong_codes = number of FP32 codes in [0, 255] that
+ * differ from FP64 before any re-decision.  Synchronous. */
+cvs_status cvs_precision_probe(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
+                               const cvs_grid* grid, double* max_code_err,
+                               double* max_lin_err, int64_t* n_wrong_codes);
+
+/* Tuning options of a context (host only):
+ *   "fp32_window"   W, the half-width in 8-bit code units of the band around
+ *                   a rounding boundary inside which an FP32 code is flagged
+ *                   for FP64 re-decision; (0, 0.25); default 2e-3.  It must
+ *                   exceed the FP32 path's error for results to be exact.
+ *   "block"         threads per block of the search kernel: 64, 128 or 256
+ *   "blocks_per_sm" resident blocks per SM (0 = as many as fit)
+ *   "kchunk"        radii per work item (0 = automatic)
+ * Unknown names or out-of-range values return CVS_ERR_INVALID_ARG. */
+cvs_status cvs_set_option(cvs_ctx* ctx, const char* name, double value);
+cvs_status cvs_get_option(cvs_ctx* ctx, const char* name, double* value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CVSEARCH_H */

@@ -95,6 +95,8 @@ def lib() -> ctypes.CDLL:
             L.orc_cbrt_cr.restype = d
             L.orc_target_lab.argtypes = [P(_Consts), vp, vp]
             L.orc_target_lab.restype = None
+            L.orc_target_lab_many.argtypes = [P(_Consts), vp, i64, vp, ctypes.c_int]
+            L.orc_target_lab_many.restype = None
             L.orc_lin_to_lab.argtypes = [P(_Consts), vp, vp]
             L.orc_lin_to_lab.restype = None
             L.orc_lab_to_lin.argtypes = [P(_Consts), d, d, d, vp]
@@ -161,6 +163,15 @@ def target_lab(rgb) -> np.ndarray:
     src = np.ascontiguousarray(np.asarray(rgb, dtype=np.uint8).reshape(3))
     out = np.zeros(3, np.float64)
     lib().orc_target_lab(ctypes.byref(consts()), _ptr(src), _ptr(out))
+    return out
+
+
+def target_lab_many(rgbs, threads: int = 0) -> np.ndarray:
+    """(n, 3) L*a*b* of an (n, 3) uint8 array."""
+    src = np.ascontiguousarray(np.asarray(rgbs, np.uint8).reshape(-1, 3))
+    out = np.zeros(src.shape, np.float64)
+    lib().orc_target_lab_many(ctypes.byref(consts()), _ptr(src), src.shape[0], _ptr(out),
+                              int(threads or max_threads()))
     return out
 
 

@@ -148,6 +148,16 @@ void orc_target_lab(const orc_consts* C, const uint8_t rgb[3], double lab[3]) {
     orc_lin_to_lab(C, lin, lab);
 }
 
+/* Step 1 for many targets: rgb (3n bytes) -> lab (3n doubles). */
+void orc_target_lab_many(const orc_consts* C, const uint8_t* rgb, int64_t n, double* lab,
+                         int n_threads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(n_threads)
+#endif
+    for (int64_t t = 0; t < n; ++t) orc_target_lab(C, rgb + 3 * t, lab + 3 * t);
+    (void)n_threads;
+}
+
 /* Step 3a: L*, a*, b* -> linear RGB. */
 void orc_lab_to_lin(const orc_consts* C, double L, double a, double b, double lin[3]) {
     double fy = (L + 16.0) / 116.0;

@@ -1,0 +1,314 @@
+"""ctypes binding of libcvsearch (include/cvsearch.h).
+
+Argument marshalling only: every step of the search runs in the CUDA library.
+The raw C functions are available under their C names on ``lib()``; the
+``Context`` class wraps them for PyTorch tensors (device memory and streams)
+and NumPy arrays (host buffers).
+"""
+from __future__ import annotations
+
+import ctypes
+import re
+from pathlib import Path
+
+import numpy as np
+
+from . import _build
+
+CVS_OK, CVS_ERR_INVALID_ARG, CVS_ERR_NO_MEMORY, CVS_ERR_CUDA = 0, 1, 2, 3
+CVS_ERR_TRUNCATED, CVS_ERR_TIMEOUT, CVS_ERR_NUMERIC = 4, 5, 6
+PREC_FP32_RECHECK, PREC_FP64 = 0, 1
+
+STATUS_NAMES = {0: "CVS_OK", 1: "CVS_ERR_INVALID_ARG", 2: "CVS_ERR_NO_MEMORY", 3: "CVS_ERR_CUDA",
+                4: "CVS_ERR_TRUNCATED", 5: "CVS_ERR_TIMEOUT", 6: "CVS_ERR_NUMERIC"}
+
+PAIR_DTYPE = np.dtype(
+    [("k", "<u2"), ("m", "<u2"), ("plus", "u1", 3), ("minus", "u1", 3),
+     ("pattern", "u1"), ("flags", "u1"), ("target", "<u4")]
+)
+
+
+class CvsError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class cvs_grid(ctypes.Structure):
+    _fields_ = [("radii", ctypes.POINTER(ctypes.c_double)), ("n_radii", ctypes.c_int32),
+                ("angles_deg", ctypes.POINTER(ctypes.c_double)), ("n_angles", ctypes.c_int32)]
+
+
+class cvs_thresholds(ctypes.Structure):
+    _fields_ = [("v_th", ctypes.c_double), ("r_novib", ctypes.c_double),
+                ("pattern_mask", ctypes.c_uint32), ("gamut_mode", ctypes.c_int32)]
+
+
+class cvs_pair(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint16), ("m", ctypes.c_uint16), ("plus", ctypes.c_uint8 * 3),
+                ("minus", ctypes.c_uint8 * 3), ("pattern", ctypes.c_uint8),
+                ("flags", ctypes.c_uint8), ("target", ctypes.c_uint32)]
+
+
+class cvs_capacity_map(ctypes.Structure):
+    _fields_ = [("max_r", ctypes.c_void_p), ("count", ctypes.c_void_p), ("pmask", ctypes.c_void_p)]
+
+
+class cvs_image(ctypes.Structure):
+    _fields_ = [("rgb", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("pitch_bytes", ctypes.c_int64)]
+
+
+class cvs_stats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int64), ("colors_fp32", ctypes.c_int64),
+                ("flagged", ctypes.c_int64), ("rechecked", ctypes.c_int64),
+                ("targets", ctypes.c_int64), ("symmetric", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("search_ms", ctypes.c_double)]
+
+
+assert ctypes.sizeof(cvs_pair) == 16 and PAIR_DTYPE.itemsize == 16
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/cvsearch.h."""
+    text = (Path(_build.INCLUDE) / "cvsearch.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cvs_[a-z_0-9]+)\s*\(", text)))
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcvsearch.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not _build.up_to_date():
+        try:
+            path = _build.build()
+        except Exception as exc:  # no compiler: fail loudly, never fall back
+            raise RuntimeError(f"libcvsearch is not built and cannot be built: {exc}") from exc
+    L = ctypes.CDLL(str(path))
+    P, vp = ctypes.POINTER, ctypes.c_void_p
+    i32, i64, u32, d, st = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_int
+    sig = {
+        "cvs_create": ([P(vp), ctypes.c_int], st),
+        "cvs_destroy": ([vp], None),
+        "cvs_last_error": ([], ctypes.c_char_p),
+        "cvs_version": ([], ctypes.c_char_p),
+        "cvs_signal_bounds": ([P(cvs_thresholds), P(i32), P(i32)], st),
+        "cvs_trig_table": ([vp, P(d), i32, P(d), P(d)], st),
+        "cvs_target_lab": ([vp, vp, i64, vp, vp], st),
+        "cvs_search_color": ([vp, P(ctypes.c_uint8), u32, P(cvs_grid), P(cvs_thresholds), st,
+                              vp, ctypes.c_size_t, P(ctypes.c_size_t)], st),
+        "cvs_search_colors": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), st,
+                               P(cvs_capacity_map), vp], st),
+        "cvs_search_colors_host": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), st, vp, vp, vp],
+                                   st),
+        "cvs_search_images": ([vp, P(cvs_image), i32, P(cvs_grid), P(cvs_thresholds), st,
+                               P(cvs_capacity_map), vp], st),
+        "cvs_synchronize": ([vp, vp], st),
+        "cvs_get_stats": ([vp, P(cvs_stats)], st),
+        "cvs_precision_probe": ([vp, vp, i64, P(cvs_grid), P(d), P(d), P(i64)], st),
+        "cvs_set_option": ([vp, ctypes.c_char_p, d], st),
+        "cvs_get_option": ([vp, ctypes.c_char_p, P(d)], st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    return lib().cvs_last_error().decode()
+
+
+def check(status: int, where: str):
+    if status != CVS_OK:
+        raise CvsError(status, where, last_error())
+
+
+def make_grid(radii, angles_deg):
+    """(cvs_grid, keep-alive arrays) from sequences of radii and angles."""
+    r = np.ascontiguousarray(radii, np.float64)
+    a = np.ascontiguousarray(angles_deg, np.float64)
+    g = cvs_grid(r.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(r),
+                 a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(a))
+    return g, (r, a)
+
+
+def make_thresholds(v_th, r_novib, pattern_mask=0x7F, gamut_mode=0):
+    return cvs_thresholds(float(v_th), float(r_novib), int(pattern_mask), int(gamut_mode))
+
+
+def signal_bounds(v_th, r_novib, pattern_mask=0x7F, gamut_mode=0):
+    """(hi_min, lo_max) integer bounds of the embedding-signal condition."""
+    t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+    hi, lo = ctypes.c_int32(), ctypes.c_int32()
+    check(lib().cvs_signal_bounds(ctypes.byref(t), ctypes.byref(hi), ctypes.byref(lo)),
+          "cvs_signal_bounds")
+    return hi.value, lo.value
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Context:
+    """A libcvsearch context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = ctypes.c_void_p()
+        check(lib().cvs_create(ctypes.byref(self._h), int(device)), "cvs_create")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().cvs_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -------------------------------------------------------------- options
+    def set_option(self, name: str, value: float):
+        check(lib().cvs_set_option(self._h, name.encode(), float(value)), "cvs_set_option")
+
+    def get_option(self, name: str) -> float:
+        v = ctypes.c_double()
+        check(lib().cvs_get_option(self._h, name.encode(), ctypes.byref(v)), "cvs_get_option")
+        return v.value
+
+    # -------------------------------------------------------------- helpers
+    def trig_table(self, angles_deg):
+        a = np.ascontiguousarray(angles_deg, np.float64)
+        s = np.zeros_like(a)
+        c = np.zeros_like(a)
+        dp = ctypes.POINTER(ctypes.c_double)
+        check(lib().cvs_trig_table(self._h, a.ctypes.data_as(dp), len(a), s.ctypes.data_as(dp),
+                                   c.ctypes.data_as(dp)), "cvs_trig_table")
+        return s, c
+
+    def target_lab(self, rgb_dev, out=None, stream=None):
+        import torch
+        n = rgb_dev.numel() // 3
+        if out is None:
+            out = torch.empty((n, 3), dtype=torch.float64, device=rgb_dev.device)
+        check(lib().cvs_target_lab(self._h, rgb_dev.data_ptr(), n, out.data_ptr(),
+                                   _stream_ptr(stream)), "cvs_target_lab")
+        return out
+
+    # -------------------------------------------------------------- searches
+    def search_color(self, rgb, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
+                     gamut_mode=0, precision=PREC_FP32_RECHECK, target=0, cap=None):
+        """All passing pairs of one colour, sorted by (k, m): (PAIR_DTYPE array, total)."""
+        g, keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        src = (ctypes.c_uint8 * 3)(*[int(x) for x in rgb])
+        if cap is None:
+            cap = len(keep[0]) * len(keep[1])
+        out = np.zeros(max(cap, 1), PAIR_DTYPE)
+        n = ctypes.c_size_t()
+        st = lib().cvs_search_color(self._h, src, int(target), ctypes.byref(g), ctypes.byref(t),
+                                    int(precision), out.ctypes.data, cap, ctypes.byref(n))
+        if st not in (CVS_OK, CVS_ERR_TRUNCATED):
+            check(st, "cvs_search_color")
+        return out[:min(n.value, cap)], n.value
+
+    def search_colors(self, rgb_dev, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
+                      gamut_mode=0, precision=PREC_FP32_RECHECK, out=None, stream=None):
+        """Per-colour (max_r, count, pmask) device tensors for an (n, 3) uint8 CUDA tensor."""
+        import torch
+        n = rgb_dev.numel() // 3
+        dev = rgb_dev.device
+        if out is None:
+            out = (torch.empty(n, dtype=torch.float32, device=dev),
+                   torch.empty(n, dtype=torch.int32, device=dev),
+                   torch.empty(n, dtype=torch.uint8, device=dev))
+        g, keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        m = cvs_capacity_map(out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
+        check(lib().cvs_search_colors(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g),
+                                      ctypes.byref(t), int(precision), ctypes.byref(m),
+                                      _stream_ptr(stream)), "cvs_search_colors")
+        return out
+
+    def search_colors_host(self, rgb, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
+                           gamut_mode=0, precision=PREC_FP32_RECHECK, out=None):
+        """As search_colors, with host NumPy buffers (copies inside the call)."""
+        rgb = np.ascontiguousarray(np.asarray(rgb, np.uint8).reshape(-1, 3))
+        n = rgb.shape[0]
+        if out is None:
+            out = (np.empty(n, np.float32), np.empty(n, np.int32), np.empty(n, np.uint8))
+        g, keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        check(lib().cvs_search_colors_host(self._h, rgb.ctypes.data, n, ctypes.byref(g),
+                                           ctypes.byref(t), int(precision), out[0].ctypes.data,
+                                           out[1].ctypes.data, out[2].ctypes.data),
+              "cvs_search_colors_host")
+        return out
+
+    def search_images(self, images, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
+                      gamut_mode=0, precision=PREC_FP32_RECHECK, maps=None, stream=None):
+        """Per-pixel maps for a list of (H, W, 3) uint8 CUDA tensors (row pitch from stride)."""
+        import torch
+        n = len(images)
+        descs = (cvs_image * n)()
+        if maps is None:
+            maps = []
+            for im in images:
+                h, w = im.shape[0], im.shape[1]
+                maps.append((torch.empty((h, w), dtype=torch.float32, device=im.device),
+                             torch.empty((h, w), dtype=torch.int32, device=im.device),
+                             torch.empty((h, w), dtype=torch.uint8, device=im.device)))
+        cmaps = (cvs_capacity_map * n)()
+        for i, im in enumerate(images):
+            if im.dtype != torch.uint8 or im.dim() != 3 or im.shape[2] != 3 or im.stride(2) != 1 \
+                    or im.stride(1) != 3:
+                raise ValueError("images must be (H, W, 3) uint8 with packed pixels")
+            descs[i] = cvs_image(im.data_ptr(), im.shape[1], im.shape[0], im.stride(0))
+            cmaps[i] = cvs_capacity_map(maps[i][0].data_ptr(), maps[i][1].data_ptr(),
+                                        maps[i][2].data_ptr())
+        g, keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        check(lib().cvs_search_images(self._h, descs, n, ctypes.byref(g), ctypes.byref(t),
+                                      int(precision), cmaps, _stream_ptr(stream)),
+              "cvs_search_images")
+        return maps
+
+    def synchronize(self, stream=None):
+        check(lib().cvs_synchronize(self._h, _stream_ptr(stream)), "cvs_synchronize")
+
+    def stats(self) -> dict:
+        s = cvs_stats()
+        check(lib().cvs_get_stats(self._h, ctypes.byref(s)), "cvs_get_stats")
+        return {f: getattr(s, f) for f, _ in cvs_stats._fields_}
+
+    def precision_probe(self, rgb_dev, radii, angles_deg):
+        g, keep = make_grid(radii, angles_deg)
+        e1, e2, nw = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        n = rgb_dev.numel() // 3
+        check(lib().cvs_precision_probe(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g),
+                                        ctypes.byref(e1), ctypes.byref(e2), ctypes.byref(nw)),
+              "cvs_precision_probe")
+        return {"max_code_err": e1.value, "max_lin_err": e2.value, "n_wrong_codes": nw.value}

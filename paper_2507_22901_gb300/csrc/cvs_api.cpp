@@ -1,0 +1,596 @@
+// cvs_api.cpp - host side of libcvsearch: the C ABI declared in
+// include/cvsearch.h.  Validates arguments, owns the context's scratch memory
+// and grid tables, and launches the kernels of cvs_kernels.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "cvs_internal.h"
+
+using namespace cvs;
+
+namespace {
+
+thread_local std::string g_err;
+
+cvs_status fail(cvs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CVS_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? CVS_ERR_NO_MEMORY : CVS_ERR_CUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+constexpr int32_t kMaxGrid = 16384;
+
+template <class T>
+cudaError_t grow(T** p, int64_t* cap, int64_t need) {
+    if (*cap >= need && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    int64_t n = need < 1 ? 1 : need;
+    cudaError_t e = cudaMalloc((void**)p, (size_t)n * sizeof(T));
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+}  // namespace
+
+struct cvs_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t own = nullptr;  // stream of the synchronous entry points
+    // grid cache
+    std::vector<double> radii, angles;
+    GridDev grid;
+    double* d_angles = nullptr;
+    int64_t cap_grid = 0;
+    int* d_status = nullptr;
+    // per-target scratch
+    TargetF32* tf = nullptr;
+    TargetF64* td = nullptr;
+    Acc* acc = nullptr;
+    int64_t cap_tf = 0, cap_td = 0, cap_acc = 0;
+    long long* qkey = nullptr;
+    unsigned long long* counters = nullptr;  // [0] work, [1] flagged, [2] rechecked, [3] n_out
+    unsigned long long* h_counters = nullptr;  // pinned copy
+    // list mode
+    cvs_pair* dense = nullptr;
+    cvs_pair* compact = nullptr;
+    int64_t cap_dense = 0, cap_compact = 0;
+    // images
+    ImageDesc* d_imgs = nullptr;
+    int64_t cap_imgs = 0;
+    // host-buffer entry point
+    uint8_t* d_in = nullptr;
+    float* d_maxr = nullptr;
+    int32_t* d_count = nullptr;
+    uint8_t* d_pmask = nullptr;
+    int64_t cap_in = 0, cap_maxr = 0, cap_count = 0, cap_pmask = 0;
+    uint8_t* d_rgb1 = nullptr;  // 3 bytes for cvs_search_color
+    // probe
+    unsigned int* d_probe = nullptr;
+    // options
+    LaunchShape shape;
+    double window = 2e-3;  // FP32 flag window W in code units
+    // last call
+    cvs_stats last{};
+    bool last_pending = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the search kernel
+};
+
+namespace {
+
+cvs_status set_device(cvs_ctx* c) {
+    CVS_CUDA(cudaSetDevice(c->device));
+    return CVS_OK;
+}
+
+cvs_status check_thresholds(const cvs_thresholds* t) {
+    if (!t) return fail(CVS_ERR_INVALID_ARG, "thresholds pointer is NULL");
+    if (!std::isfinite(t->v_th) || t->v_th < 0.0)
+        return fail(CVS_ERR_INVALID_ARG, "v_th must be finite and >= 0 (got %g)", t->v_th);
+    if (!(t->r_novib > 0.0 && t->r_novib <= 1.0))
+        return fail(CVS_ERR_INVALID_ARG, "r_novib must be in (0, 1] (got %g)", t->r_novib);
+    if (t->pattern_mask > 0x7Fu)
+        return fail(CVS_ERR_INVALID_ARG, "pattern_mask has bits above the 7 patterns (0x%x)",
+                    t->pattern_mask);
+    if (t->gamut_mode != 0 && t->gamut_mode != 1)
+        return fail(CVS_ERR_INVALID_ARG, "gamut_mode must be 0 (reject) or 1 (clip)");
+    return CVS_OK;
+}
+
+cvs_status check_grid(const cvs_grid* g) {
+    if (!g) return fail(CVS_ERR_INVALID_ARG, "grid pointer is NULL");
+    if (!g->radii || !g->angles_deg) return fail(CVS_ERR_INVALID_ARG, "grid arrays are NULL");
+    if (g->n_radii <= 0 || g->n_radii > kMaxGrid)
+        return fail(CVS_ERR_INVALID_ARG, "n_radii must be in [1, %d] (got %d)", kMaxGrid, g->n_radii);
+    if (g->n_angles <= 0 || g->n_angles > kMaxGrid)
+        return fail(CVS_ERR_INVALID_ARG, "n_angles must be in [1, %d] (got %d)", kMaxGrid,
+                    g->n_angles);
+    for (int i = 0; i < g->n_radii; ++i)
+        if (!std::isfinite(g->radii[i]) || g->radii[i] < 0.0)
+            return fail(CVS_ERR_INVALID_ARG, "radius %d must be finite and >= 0 (got %g)", i,
+                        g->radii[i]);
+    for (int i = 0; i < g->n_angles; ++i)
+        if (!std::isfinite(g->angles_deg[i]))
+            return fail(CVS_ERR_INVALID_ARG, "angle %d is not finite", i);
+    return CVS_OK;
+}
+
+// Upload the grid and build its tables on the device (cached by content).
+cvs_status ensure_grid(cvs_ctx* c, const cvs_grid* g) {
+    if (c->grid.K == g->n_radii && c->grid.N == g->n_angles &&
+        std::memcmp(c->radii.data(), g->radii, sizeof(double) * g->n_radii) == 0 &&
+        std::memcmp(c->angles.data(), g->angles_deg, sizeof(double) * g->n_angles) == 0)
+        return CVS_OK;
+    GridDev& d = c->grid;
+    const int K = g->n_radii, N = g->n_angles;
+    // earlier asynchronous searches may still read the old tables
+    CVS_CUDA(cudaDeviceSynchronize());
+    d.K = 0;  // invalid until complete
+    if (c->cap_grid < kMaxGrid) {
+        CVS_CUDA(cudaMalloc(&d.r32, sizeof(float) * kMaxGrid));
+        CVS_CUDA(cudaMalloc(&d.sc32, sizeof(float2) * kMaxGrid));
+        CVS_CUDA(cudaMalloc(&d.r64, sizeof(double) * kMaxGrid));
+        CVS_CUDA(cudaMalloc(&d.s64, sizeof(double) * kMaxGrid));
+        CVS_CUDA(cudaMalloc(&d.c64, sizeof(double) * kMaxGrid));
+        CVS_CUDA(cudaMalloc(&c->d_angles, sizeof(double) * kMaxGrid));
+        c->cap_grid = kMaxGrid;
+    }
+    std::vector<float> r32(K);
+    double rmax = 0.0;
+    for (int i = 0; i < K; ++i) {
+        r32[i] = (float)g->radii[i];
+        if (g->radii[i] > rmax) rmax = g->radii[i];
+    }
+    cudaStream_t st = c->own;
+    CVS_CUDA(cudaMemcpyAsync(d.r64, g->radii, sizeof(double) * K, cudaMemcpyHostToDevice, st));
+    CVS_CUDA(cudaMemcpyAsync(d.r32, r32.data(), sizeof(float) * K, cudaMemcpyHostToDevice, st));
+    CVS_CUDA(cudaMemcpyAsync(c->d_angles, g->angles_deg, sizeof(double) * N,
+                             cudaMemcpyHostToDevice, st));
+    CVS_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
+    CVS_CUDA(launch_trig_table(c->d_angles, N, d.s64, d.c64, d.sc32, c->d_status, st));
+    std::vector<double> s(N), co(N);
+    int status = 0;
+    CVS_CUDA(cudaMemcpyAsync(s.data(), d.s64, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    CVS_CUDA(cudaMemcpyAsync(co.data(), d.c64, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    CVS_CUDA(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CVS_CUDA(cudaStreamSynchronize(st));
+    if (status) return fail(CVS_ERR_NUMERIC, "an angle's sine could not be certified");
+    // Fold by +180 degrees when the table is exactly antisymmetric.
+    int sym = (N % 2 == 0) ? 1 : 0;
+    for (int m = 0; sym && m < N / 2; ++m)
+        if (!(s[m + N / 2] == -s[m] && co[m + N / 2] == -co[m])) sym = 0;
+    d.sym = sym;
+    d.H = sym ? N / 2 : N;
+    d.N = N;
+    d.rmax = rmax;
+    c->radii.assign(g->radii, g->radii + K);
+    c->angles.assign(g->angles_deg, g->angles_deg + N);
+    d.K = K;
+    return CVS_OK;
+}
+
+cvs_status ensure_targets(cvs_ctx* c, int64_t n) {
+    if (c->cap_tf < n) {
+        if (c->tf) cudaFree(c->tf);
+        c->tf = nullptr;
+        c->cap_tf = 0;
+        CVS_CUDA(cudaMalloc((void**)&c->tf, target_f32_size() * (size_t)n));
+        c->cap_tf = n;
+    }
+    if (c->cap_td < n) {
+        if (c->td) cudaFree(c->td);
+        c->td = nullptr;
+        c->cap_td = 0;
+        CVS_CUDA(cudaMalloc((void**)&c->td, target_f64_size() * (size_t)n));
+        c->cap_td = n;
+    }
+    CVS_CUDA(grow(&c->acc, &c->cap_acc, n));
+    return CVS_OK;
+}
+
+void thresholds_to_int(const cvs_thresholds* t, int32_t* hi_min, int32_t* lo_max) {
+    // high: d > v_th  <=>  d >= floor(v_th) + 1
+    const double fl = std::floor(t->v_th);
+    *hi_min = fl >= 255.0 ? 256 : (int32_t)fl + 1;
+    // low: d < v_th * r_novib (exact product)  <=>  d <= ceil(product) - 1
+    const double p = t->v_th * t->r_novib;
+    const double e = std::fma(t->v_th, t->r_novib, -p);  // product = p + e exactly
+    double ce = std::ceil(p);
+    if (ce == p && e > 0.0) ce += 1.0;
+    *lo_max = ce > 256.0 ? 255 : (int32_t)ce - 1;
+}
+
+int choose_kchunk(const cvs_ctx* c, int64_t n_targets, int K, int H) {
+    if (c->shape.kchunk > 0) return c->shape.kchunk < K ? c->shape.kchunk : K;
+    // aim for >= 32 work items per SM warp-slot group, but >= 2 warp iterations per item
+    const int64_t want_items = (int64_t)c->num_sms * 512;
+    int64_t n_kc = (want_items + n_targets - 1) / (n_targets > 0 ? n_targets : 1);
+    if (n_kc < 1) n_kc = 1;
+    if (n_kc > K) n_kc = K;
+    int kchunk = (int)((K + n_kc - 1) / n_kc);
+    const int min_k = (64 + H - 1) / H;
+    if (kchunk < min_k) kchunk = min_k < K ? min_k : K;
+    return kchunk;
+}
+
+cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_precision prec,
+                      int list_mode, uint32_t target_id, cudaStream_t st) {
+    SearchArgs a{};
+    a.tf = c->tf;
+    a.td = c->td;
+    a.acc = c->acc;
+    a.n_targets = n;
+    a.grid = c->grid;
+    a.qkey = c->qkey;
+    thresholds_to_int(thr, &a.hi_min, &a.lo_max);
+    a.mask2 = thr->pattern_mask << 1;
+    a.clip = thr->gamut_mode;
+    a.half_w = (float)(0.5 - c->window);
+    a.prec = (int32_t)prec;
+    a.list_mode = list_mode;
+    a.dense = c->dense;
+    a.target_id = target_id;
+    a.work_counter = c->counters;
+    a.stats = c->counters + 1;
+    a.shape = c->shape;
+    a.shape.kchunk = choose_kchunk(c, n, c->grid.K, c->grid.H);
+    a.num_sms = c->num_sms;
+    CVS_CUDA(cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), st));
+    CVS_CUDA(cudaEventRecord(c->ev0, st));
+    CVS_CUDA(launch_search(a, st));
+    CVS_CUDA(cudaEventRecord(c->ev1, st));
+    CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, 4 * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, st));
+    cvs_stats& s = c->last;
+    s = cvs_stats{};
+    s.targets = n;
+    s.candidates = n * (int64_t)c->grid.K * c->grid.N;
+    s.colors_fp32 = prec == CVS_PREC_FP64 ? 0 : s.candidates;
+    s.symmetric = c->grid.sym;
+    s.precision = (int32_t)prec;
+    c->last_pending = true;
+    return CVS_OK;
+}
+
+void collect_stats(cvs_ctx* c) {
+    if (!c->last_pending) return;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->last.search_ms = ms;
+    const int f = c->grid.sym ? 2 : 1;
+    c->last.flagged = (int64_t)c->h_counters[1] * f;
+    c->last.rechecked = (int64_t)c->h_counters[2] * f;
+    c->last_pending = false;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+const char* cvs_last_error(void) { return g_err.c_str(); }
+
+const char* cvs_version(void) { return "0.1.0"; }
+
+cvs_status cvs_create(cvs_ctx** out, int device) {
+    if (!out) return fail(CVS_ERR_INVALID_ARG, "ctx output pointer is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CVS_CUDA(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev)
+        return fail(CVS_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, ndev);
+    cvs_ctx* c = new cvs_ctx();
+    c->device = device;
+    cvs_status st = set_device(c);
+    if (st != CVS_OK) { delete c; return st; }
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->qkey, 257 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->counters, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_rgb1, 16);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_probe, 16);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess) e = copy_qkeys_to(c->qkey, c->own);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->own);
+    if (e != cudaSuccess) {
+        cvs_destroy(c);
+        return fail(CVS_ERR_CUDA, "cvs_create: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return CVS_OK;
+}
+
+void cvs_destroy(cvs_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->own) cudaStreamSynchronize(c->own);
+    cudaDeviceSynchronize();
+    void* ptrs[] = {c->grid.r32, c->grid.sc32, c->grid.r64, c->grid.s64, c->grid.c64,
+                    c->d_angles, c->d_status, c->tf, c->td, c->acc, c->qkey, c->counters,
+                    c->dense, c->compact, c->d_imgs, c->d_in, c->d_maxr, c->d_count, c->d_pmask,
+                    c->d_rgb1, c->d_probe};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_counters) cudaFreeHost(c->h_counters);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+}
+
+cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
+    if (!c || !name) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (!std::strcmp(name, "fp32_window")) {
+        if (!(value > 0.0 && value < 0.25))
+            return fail(CVS_ERR_INVALID_ARG, "fp32_window must be in (0, 0.25)");
+        c->window = value;
+    } else if (!std::strcmp(name, "block")) {
+        const int v = (int)value;
+        if (v != 64 && v != 128 && v != 256)
+            return fail(CVS_ERR_INVALID_ARG, "block must be 64, 128 or 256");
+        c->shape.block = v;
+    } else if (!std::strcmp(name, "blocks_per_sm")) {
+        if (value < 0 || value > 32) return fail(CVS_ERR_INVALID_ARG, "blocks_per_sm in [0, 32]");
+        c->shape.blocks_per_sm = (int)value;
+    } else if (!std::strcmp(name, "kchunk")) {
+        if (value < 0 || value > kMaxGrid) return fail(CVS_ERR_INVALID_ARG, "kchunk in [0, 16384]");
+        c->shape.kchunk = (int)value;
+    } else {
+        return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);
+    }
+    return CVS_OK;
+}
+
+cvs_status cvs_get_option(cvs_ctx* c, const char* name, double* value) {
+    if (!c || !name || !value) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (!std::strcmp(name, "fp32_window")) *value = c->window;
+    else if (!std::strcmp(name, "block")) *value = c->shape.block;
+    else if (!std::strcmp(name, "blocks_per_sm")) *value = c->shape.blocks_per_sm;
+    else if (!std::strcmp(name, "kchunk")) *value = c->shape.kchunk;
+    else return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);
+    return CVS_OK;
+}
+
+cvs_status cvs_signal_bounds(const cvs_thresholds* thr, int32_t* hi_min, int32_t* lo_max) {
+    cvs_status st = check_thresholds(thr);
+    if (st != CVS_OK) return st;
+    if (!hi_min || !lo_max) return fail(CVS_ERR_INVALID_ARG, "output pointer is NULL");
+    thresholds_to_int(thr, hi_min, lo_max);
+    return CVS_OK;
+}
+
+cvs_status cvs_trig_table(cvs_ctx* c, const double* angles, int32_t n, double* s, double* co) {
+    if (!c || !angles || !s || !co) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (n <= 0 || n > kMaxGrid) return fail(CVS_ERR_INVALID_ARG, "n must be in [1, %d]", kMaxGrid);
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(angles[i])) return fail(CVS_ERR_INVALID_ARG, "angle %d not finite", i);
+    cvs_status st0 = set_device(c);
+    if (st0 != CVS_OK) return st0;
+    double *da = nullptr, *ds = nullptr, *dc = nullptr;
+    float2* dsc = nullptr;
+    cudaStream_t st = c->own;
+    CVS_CUDA(cudaMalloc(&da, sizeof(double) * n * 3 + sizeof(float2) * n));
+    ds = da + n;
+    dc = ds + n;
+    dsc = reinterpret_cast<float2*>(dc + n);
+    int status = 0;
+    cudaError_t e = cudaMemcpyAsync(da, angles, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_trig_table(da, n, ds, dc, dsc, c->d_status, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s, ds, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(co, dc, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(da);
+    if (e != cudaSuccess) return fail(CVS_ERR_CUDA, "cvs_trig_table: %s", cudaGetErrorString(e));
+    if (status) return fail(CVS_ERR_NUMERIC, "an angle's sine could not be certified");
+    return CVS_OK;
+}
+
+cvs_status cvs_target_lab(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, double* lab_dev,
+                          void* stream) {
+    if (!c || (n > 0 && (!rgb_dev || !lab_dev))) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0) return fail(CVS_ERR_INVALID_ARG, "n must be >= 0");
+    cvs_status st0 = set_device(c);
+    if (st0 != CVS_OK) return st0;
+    CVS_CUDA(launch_target_lab(rgb_dev, n, lab_dev, (cudaStream_t)stream));
+    return CVS_OK;
+}
+
+cvs_status cvs_search_color(cvs_ctx* c, const uint8_t rgb[3], uint32_t target,
+                            const cvs_grid* grid, const cvs_thresholds* thr, cvs_precision prec,
+                            cvs_pair* out_host, size_t cap, size_t* n_out) {
+    if (!c || !rgb || !n_out || (cap > 0 && !out_host))
+        return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
+        return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    cvs_status st0 = check_grid(grid);
+    if (st0 == CVS_OK) st0 = check_thresholds(thr);
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = ensure_targets(c, 1);
+    if (st0 != CVS_OK) return st0;
+    const int64_t nd = (int64_t)c->grid.K * c->grid.N;
+    CVS_CUDA(grow(&c->dense, &c->cap_dense, nd));
+    CVS_CUDA(grow(&c->compact, &c->cap_compact, nd));
+    cudaStream_t st = c->own;
+    CVS_CUDA(cudaMemcpyAsync(c->d_rgb1, rgb, 3, cudaMemcpyHostToDevice, st));
+    CVS_CUDA(cudaMemsetAsync(c->dense, 0, sizeof(cvs_pair) * (size_t)nd, st));
+    CVS_CUDA(launch_setup_colors(c->d_rgb1, 1, c->grid.rmax, c->tf, c->td, c->acc, st));
+    st0 = run_search(c, 1, thr, prec, 1, target, st);
+    if (st0 != CVS_OK) return st0;
+    CVS_CUDA(launch_compact_pairs(c->dense, nd, c->compact, c->counters + 3, st));
+    unsigned long long n = 0;
+    CVS_CUDA(cudaMemcpyAsync(&n, c->counters + 3, sizeof n, cudaMemcpyDeviceToHost, st));
+    CVS_CUDA(cudaStreamSynchronize(st));
+    collect_stats(c);
+    *n_out = (size_t)n;
+    const size_t ncopy = n < cap ? (size_t)n : cap;
+    if (ncopy)
+        CVS_CUDA(cudaMemcpy(out_host, c->compact, ncopy * sizeof(cvs_pair), cudaMemcpyDeviceToHost));
+    if ((size_t)n > cap)
+        return fail(CVS_ERR_TRUNCATED, "%llu passing pairs, capacity %zu", n, cap);
+    return CVS_OK;
+}
+
+cvs_status cvs_search_colors(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, const cvs_grid* grid,
+                             const cvs_thresholds* thr, cvs_precision prec,
+                             const cvs_capacity_map* out, void* stream) {
+    if (!c || !out) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0 || n > (int64_t)1 << 40) return fail(CVS_ERR_INVALID_ARG, "n out of range");
+    if (n > 0 && (!rgb_dev || !out->max_r || !out->count || !out->pmask))
+        return fail(CVS_ERR_INVALID_ARG, "NULL device buffer");
+    if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
+        return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    cvs_status st0 = check_grid(grid);
+    if (st0 == CVS_OK) st0 = check_thresholds(thr);
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = ensure_targets(c, n);
+    if (st0 != CVS_OK) return st0;
+    if (n == 0) return CVS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
+    st0 = run_search(c, n, thr, prec, 0, 0, st);
+    if (st0 != CVS_OK) return st0;
+    CVS_CUDA(launch_finalize_colors(c->acc, n, out->max_r, out->count, out->pmask, st));
+    return CVS_OK;
+}
+
+cvs_status cvs_search_colors_host(cvs_ctx* c, const uint8_t* rgb_host, int64_t n,
+                                  const cvs_grid* grid, const cvs_thresholds* thr,
+                                  cvs_precision prec, float* max_r_host, int32_t* count_host,
+                                  uint8_t* pmask_host) {
+    if (!c) return fail(CVS_ERR_INVALID_ARG, "NULL context");
+    if (n < 0) return fail(CVS_ERR_INVALID_ARG, "n must be >= 0");
+    if (n > 0 && (!rgb_host || !max_r_host || !count_host || !pmask_host))
+        return fail(CVS_ERR_INVALID_ARG, "NULL host buffer");
+    cvs_status st0 = set_device(c);
+    if (st0 != CVS_OK) return st0;
+    CVS_CUDA(grow(&c->d_in, &c->cap_in, 3 * n));
+    CVS_CUDA(grow(&c->d_maxr, &c->cap_maxr, n));
+    CVS_CUDA(grow(&c->d_count, &c->cap_count, n));
+    CVS_CUDA(grow(&c->d_pmask, &c->cap_pmask, n));
+    cudaStream_t st = c->own;
+    if (n > 0) CVS_CUDA(cudaMemcpyAsync(c->d_in, rgb_host, 3 * n, cudaMemcpyHostToDevice, st));
+    cvs_capacity_map m{c->d_maxr, c->d_count, c->d_pmask};
+    st0 = cvs_search_colors(c, c->d_in, n, grid, thr, prec, &m, st);
+    if (st0 != CVS_OK) return st0;
+    if (n > 0) {
+        CVS_CUDA(cudaMemcpyAsync(max_r_host, c->d_maxr, 4 * n, cudaMemcpyDeviceToHost, st));
+        CVS_CUDA(cudaMemcpyAsync(count_host, c->d_count, 4 * n, cudaMemcpyDeviceToHost, st));
+        CVS_CUDA(cudaMemcpyAsync(pmask_host, c->d_pmask, n, cudaMemcpyDeviceToHost, st));
+    }
+    CVS_CUDA(cudaStreamSynchronize(st));
+    collect_stats(c);
+    return CVS_OK;
+}
+
+cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, const cvs_grid* grid,
+                             const cvs_thresholds* thr, cvs_precision prec,
+                             const cvs_capacity_map* maps, void* stream) {
+    if (!c || !batch || !maps) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (n <= 0 || n > (1 << 20)) return fail(CVS_ERR_INVALID_ARG, "n must be in [1, 2^20]");
+    if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
+        return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    std::vector<ImageDesc> h(n);
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const cvs_image& im = batch[i];
+        if (!im.rgb || im.width <= 0 || im.height <= 0 || im.pitch_bytes < 3LL * im.width)
+            return fail(CVS_ERR_INVALID_ARG, "image %d: bad pointer, size or pitch", i);
+        if (!maps[i].max_r || !maps[i].count || !maps[i].pmask)
+            return fail(CVS_ERR_INVALID_ARG, "map %d: NULL buffer", i);
+        const int64_t px = (int64_t)im.width * im.height;
+        if (px >= ((int64_t)1 << 40)) return fail(CVS_ERR_INVALID_ARG, "image %d too large", i);
+        h[i] = ImageDesc{im.rgb, im.pitch_bytes, im.width, im.height, total,
+                         maps[i].max_r, maps[i].count, maps[i].pmask};
+        total += px;
+    }
+    cvs_status st0 = check_grid(grid);
+    if (st0 == CVS_OK) st0 = check_thresholds(thr);
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = ensure_targets(c, total);
+    if (st0 != CVS_OK) return st0;
+    cudaStream_t st = (cudaStream_t)stream;
+    CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, n));
+    CVS_CUDA(cudaMemcpyAsync(c->d_imgs, h.data(), sizeof(ImageDesc) * n, cudaMemcpyHostToDevice, st));
+    CVS_CUDA(launch_setup_images(c->d_imgs, n, total, c->grid.rmax, c->tf, c->td, c->acc, st));
+    st0 = run_search(c, total, thr, prec, 0, 0, st);
+    if (st0 != CVS_OK) return st0;
+    CVS_CUDA(launch_finalize_images(c->acc, c->td, total, c->d_imgs, st));
+    return CVS_OK;
+}
+
+cvs_status cvs_synchronize(cvs_ctx* c, void* stream) {
+    if (!c) return fail(CVS_ERR_INVALID_ARG, "NULL context");
+    cvs_status st0 = set_device(c);
+    if (st0 != CVS_OK) return st0;
+    CVS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    CVS_CUDA(cudaStreamSynchronize(c->own));
+    collect_stats(c);
+    return CVS_OK;
+}
+
+cvs_status cvs_get_stats(cvs_ctx* c, cvs_stats* out) {
+    if (!c || !out) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (c->last_pending) return fail(CVS_ERR_INVALID_ARG, "last search not synchronised yet");
+    *out = c->last;
+    return CVS_OK;
+}
+
+cvs_status cvs_precision_probe(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n,
+                               const cvs_grid* grid, double* max_code_err, double* max_lin_err,
+                               int64_t* n_wrong_codes) {
+    if (!c || !max_code_err || !max_lin_err || !n_wrong_codes)
+        return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (n <= 0 || !rgb_dev) return fail(CVS_ERR_INVALID_ARG, "need n > 0 colours");
+    cvs_status st0 = check_grid(grid);
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = ensure_targets(c, n);
+    if (st0 != CVS_OK) return st0;
+    cudaStream_t st = c->own;
+    CVS_CUDA(cudaMemsetAsync(c->d_probe, 0, 16, st));
+    CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
+    CVS_CUDA(launch_precision_probe(c->tf, c->td, n, c->grid, c->qkey, c->d_probe, c->d_probe + 1,
+                                    reinterpret_cast<unsigned long long*>(c->d_probe + 2),
+                                    c->num_sms, st));
+    unsigned int h[4] = {0, 0, 0, 0};
+    CVS_CUDA(cudaMemcpyAsync(h, c->d_probe, 16, cudaMemcpyDeviceToHost, st));
+    CVS_CUDA(cudaStreamSynchronize(st));
+    float fv, fl;
+    std::memcpy(&fv, &h[0], 4);
+    std::memcpy(&fl, &h[1], 4);
+    unsigned long long w;
+    std::memcpy(&w, &h[2], 8);
+    *max_code_err = fv;
+    *max_lin_err = fl;
+    *n_wrong_codes = (int64_t)w;
+    return CVS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// cvs_internal.h - interface between the host API (cvs_api.cpp) and the
+// kernels (cvs_kernels.cu) of libcvsearch.  Plain structs, no CUDA device code.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cvsearch.h"
+
+namespace cvs {
+
+// Per-target accumulator of the search (16 bytes): passing count, bits of the
+// largest passing radius as float (-1.0f if none; non-negative floats order as
+// integers), pattern bits, and one spare word.
+struct __align__(16) Acc {
+    int32_t count;
+    int32_t rmax_bits;
+    uint32_t pmask;
+    uint32_t pad;
+};
+
+struct TargetF32;  // cvs_device.cuh
+struct TargetF64;
+
+// Grid tables on the device (owned by the context).
+struct GridDev {
+    int32_t K = 0, N = 0;      // radii, angles
+    int32_t H = 0;             // angle slots per radius (N/2 when folded, else N)
+    int32_t sym = 0;           // 1 if angles fold by +180 degrees
+    double rmax = 0.0;
+    float* r32 = nullptr;      // K
+    float2* sc32 = nullptr;    // N: (sin/500, -cos/200) in FP32
+    double* r64 = nullptr;     // K
+    double* s64 = nullptr;     // N
+    double* c64 = nullptr;     // N
+};
+
+struct ImageDesc {             // device-side image table entry
+    const uint8_t* rgb;
+    int64_t pitch;
+    int32_t width, height;
+    int64_t first;             // index of the image's first pixel in the flat target list
+    float* max_r;
+    int32_t* count;
+    uint8_t* pmask;
+};
+
+struct LaunchShape {
+    int block = 256;           // threads per block
+    int blocks_per_sm = 0;     // 0: as many as fit
+    int kchunk = 0;            // radii per work item (0: automatic)
+};
+
+struct SearchArgs {
+    const TargetF32* tf;
+    const TargetF64* td;
+    Acc* acc;
+    int64_t n_targets;
+    GridDev grid;
+    const long long* qkey;     // 257 threshold keys
+    int32_t hi_min, lo_max;
+    uint32_t mask2;
+    int32_t clip;
+    float half_w;              // 0.5 - W
+    int32_t prec;              // cvs_precision
+    int32_t list_mode;         // 1: write records into `dense`
+    cvs_pair* dense;           // K*N records (list mode)
+    uint32_t target_id;        // list mode: copied into records
+    unsigned long long* work_counter;
+    unsigned long long* stats; // [0] flagged, [1] rechecked
+    LaunchShape shape;
+    int num_sms;
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_trig_table(const double* angles_dev, int n, double* s64, double* c64,
+                              float2* sc32, int* status, cudaStream_t st);
+cudaError_t launch_setup_colors(const uint8_t* rgb, int64_t n, double rmax, TargetF32* tf,
+                                TargetF64* td, Acc* acc, cudaStream_t st);
+cudaError_t launch_setup_images(const ImageDesc* imgs, int n_imgs, int64_t total, double rmax,
+                                TargetF32* tf, TargetF64* td, Acc* acc, cudaStream_t st);
+cudaError_t launch_search(const SearchArgs& a, cudaStream_t st);
+cudaError_t launch_finalize_colors(const Acc* acc, int64_t n, float* max_r, int32_t* count,
+                                   uint8_t* pmask, cudaStream_t st);
+cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t n,
+                                   const ImageDesc* imgs, cudaStream_t st);
+cudaError_t launch_compact_pairs(const cvs_pair* dense, int64_t n_dense, cvs_pair* out,
+                                 unsigned long long* n_out, cudaStream_t st);
+cudaError_t launch_target_lab(const uint8_t* rgb, int64_t n, double* lab, cudaStream_t st);
+cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int64_t n,
+                                   const GridDev& g, const long long* qkey,
+                                   unsigned int* max_v_err_bits, unsigned int* max_lin_err_bits,
+                                   unsigned long long* n_wrong, int num_sms, cudaStream_t st);
+cudaError_t copy_qkeys_to(long long* dst, cudaStream_t st);
+size_t target_f32_size();
+size_t target_f64_size();
+int search_smem_bytes(const GridDev& g, int block);
+const void* search_kernel_ptr(int prec, int list_mode);
+void chain_constants(float Ax[3], float Bz[3]);
+
+}  // namespace cvs
