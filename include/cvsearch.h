@@ -241,6 +241,47 @@ cvs_status cvs_precision_probe(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
 cvs_status cvs_set_option(cvs_ctx* ctx, const char* name, double value);
 cvs_status cvs_get_option(cvs_ctx* ctx, const char* name, double* value);
 
+/* ------------------------------------------- allocation-free entry point */
+
+/* cvs_search_colors_noalloc: the per-colour search of cvs_search_colors, for
+ * callers that cannot allocate device memory.  The paper has no counterpart to
+ * this entry point; it exists for callers such as code hosted inside an
+ * application whose memory manager owns the whole device heap and refuses
+ * outside cudaMalloc calls, or latency-critical loops in which cudaMalloc's
+ * implicit device-wide synchronisation would stall other streams.
+ *
+ * It takes no context and allocates nothing: no cudaMalloc, no cudaFree and
+ * no allocating library routine.  All scratch memory (grid tables, threshold
+ * keys, work counters, per-colour constants and accumulators) lives in one
+ * fixed array of CVS_NOALLOC_SCRATCH_BYTES inside the library, which every
+ * GPU that loads the library holds until the process exits.  The caller
+ * passes the inputs and outputs, as for cvs_search_colors: rgb_dev (device,
+ * 3n bytes), out_dev (device capacity map of n entries).
+ *
+ * Limits: n <= CVS_NOALLOC_MAX_COLORS colours, n_radii <=
+ * CVS_NOALLOC_MAX_RADII, n_angles <= CVS_NOALLOC_MAX_ANGLES; larger sizes
+ * return CVS_ERR_INVALID_ARG with a message naming the limit.
+ *
+ * The first call on a device looks up the array's device address and copies a
+ * constant table into it (a synchronous copy): make that first call before
+ * any stream capture.  Every call uploads the grid and reads the angle table
+ * back to decide the +180 degree folding, which synchronises `stream`; the
+ * search itself then runs asynchronously on `stream`.  All calls share the
+ * one array and it keeps the last call's contents (what must start at zero is
+ * cleared by each call): calls whose device work overlaps - on different
+ * streams or from different threads - race on it, so the caller must
+ * serialise them.  The device `device` is made current for the call and the
+ * caller's current device is restored before returning.  Results are
+ * identical to cvs_search_colors on the same inputs. */
+#define CVS_NOALLOC_SCRATCH_BYTES (512 * 1024)
+#define CVS_NOALLOC_MAX_COLORS 4096
+#define CVS_NOALLOC_MAX_RADII 1024
+#define CVS_NOALLOC_MAX_ANGLES 1024
+cvs_status cvs_search_colors_noalloc(int device, const uint8_t* rgb_dev, int64_t n,
+                                     const cvs_grid* grid, const cvs_thresholds* thr,
+                                     cvs_precision prec, const cvs_capacity_map* out_dev,
+                                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

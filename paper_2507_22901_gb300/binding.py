@@ -113,6 +113,8 @@ def lib() -> ctypes.CDLL:
         "cvs_precision_probe": ([vp, vp, i64, P(cvs_grid), P(d), P(d), P(i64)], st),
         "cvs_set_option": ([vp, ctypes.c_char_p, d], st),
         "cvs_get_option": ([vp, ctypes.c_char_p, P(d)], st),
+        "cvs_search_colors_noalloc": ([ctypes.c_int, vp, i64, P(cvs_grid), P(cvs_thresholds), st,
+                                       P(cvs_capacity_map), vp], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

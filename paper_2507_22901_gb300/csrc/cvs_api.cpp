@@ -52,6 +52,8 @@ cudaError_t grow(T** p, int64_t* cap, int64_t need) {
 
 }  // namespace
 
+void cvs::set_error_message(const char* msg) { g_err = msg; }
+
 struct cvs_ctx {
     int device = 0;
     int num_sms = 0;

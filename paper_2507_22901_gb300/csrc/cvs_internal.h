@@ -91,6 +91,8 @@ cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int
                                    unsigned int* max_v_err_bits, unsigned int* max_lin_err_bits,
                                    unsigned long long* n_wrong, int num_sms, cudaStream_t st);
 cudaError_t copy_qkeys_to(long long* dst, cudaStream_t st);
+// Sets the thread-local text returned by cvs_last_error().
+void set_error_message(const char* msg);
 size_t target_f32_size();
 size_t target_f64_size();
 int search_smem_bytes(const GridDev& g, int block);
