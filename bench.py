@@ -50,6 +50,11 @@ def parse_args():
     p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison arm")
     p.add_argument("--cpu-sample", type=int, default=2048,
                    help="colours of the cube timed on the CPU oracle")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the precision study and the one-pass image measurement")
+    p.add_argument("--cube-step", type=int, default=4, choices=[4, 8, 16],
+                   help="channel step of the colour cube (4 = the 262,144-colour workload; "
+                        "larger steps give the small cases used for profiling)")
     return p.parse_args()
 
 
@@ -193,6 +198,60 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ extras
+def run_extras(ctx, torch, device, W, cvs):
+    """Precision study on the 4096-colour set (256 radii x 720 angles) and one
+    timed pass of the 48-image workload (64 radii x 180 angles per pixel)."""
+    out = {}
+    rgb_h = W.precision_colors()
+    radii, ang = W.grid(4)
+    rgb = torch.from_numpy(rgb_h).to(device)
+    cand = len(rgb_h) * len(radii) * len(ang)
+    res = {}
+    for prec in (cvs.PREC_FP32_RECHECK, cvs.PREC_FP64):
+        ctx.search_colors(rgb, radii, ang, 50.0, 0.5, precision=prec)
+        o = ctx.search_colors(rgb, radii, ang, 50.0, 0.5, precision=prec)
+        ctx.synchronize()
+        st = ctx.stats()
+        res[prec] = (o, st)
+    (o32, st32), (o64, st64) = res[cvs.PREC_FP32_RECHECK], res[cvs.PREC_FP64]
+    mism = int(((o32[0].view(torch.int32) != o64[0].view(torch.int32)) | (o32[1] != o64[1]) |
+                (o32[2] != o64[2])).sum().item())
+    probe = ctx.precision_probe(rgb, radii, ang)
+    out["precision_study"] = {
+        "workload": "4096 colours (3072 uniform, 512 near-grey, 512 near gamut edge) x 256 radii "
+                    "x 720 angles", "candidates": cand,
+        "flagged_fraction": st32["flagged"] / cand, "rechecked_fraction": st32["rechecked"] / cand,
+        "max_code_err_fp32": probe["max_code_err"], "max_lin_err_fp32": probe["max_lin_err"],
+        "raw_fp32_wrong_codes": probe["n_wrong_codes"], "decision_mismatches_vs_fp64": mism,
+        "fp32_gcand_s": cand / (st32["search_ms"] / 1e3) / 1e9,
+        "fp64_gcand_s": cand / (st64["search_ms"] / 1e3) / 1e9,
+    }
+    # one pass over the 48 full-size synthetic images
+    params = W.image_params()
+    imgs = [W.render_image_torch(w, h, terms, ns, device=device) for w, h, terms, ns in params]
+    r3, a3 = W.grid(3)
+    px = sum(im.shape[0] * im.shape[1] for im in imgs)
+    maps = ctx.search_images(imgs, r3, a3, 50.0, 0.5)
+    ctx.synchronize()
+    torch.cuda.synchronize(device)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    ctx.search_images(imgs, r3, a3, 50.0, 0.5, maps=maps)
+    t1.record()
+    ctx.synchronize()
+    torch.cuda.synchronize(device)
+    sec = t0.elapsed_time(t1) / 1e3
+    cand3 = px * len(r3) * len(a3)
+    out["images"] = {"workload": "48 images 256..3840 x 256..2160 (seed 0), 64 radii x 180 angles",
+                     "pixels": px, "seconds": sec, "gcand_s": cand3 / sec / 1e9,
+                     "images_per_s": len(imgs) / sec,
+                     "images_4k_equiv_per_s": cand3 / CAND_PER_4K_FRAME / sec}
+    del imgs, maps
+    return out
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, world, rank, local):
     import torch
@@ -203,7 +262,7 @@ def run_ours(args, world, rank, local):
     device = torch.device("cuda", local)
     ctx = cvs.Context(local)
     radii, ang = W.grid(2)
-    rgb_h = W.color_cube()
+    rgb_h = W.color_cube(args.cube_step)
     n = len(rgb_h)
     cand = n * len(radii) * len(ang)
     rgb = torch.from_numpy(rgb_h).to(device)
@@ -275,6 +334,11 @@ def run_ours(args, world, rank, local):
     e2e = world * cand * args.steps / e2e_s / 1e9
     e2e_match = bool(np.array_equal(h_out[1], res32[1].cpu().numpy()))
 
+    # ---- extras: precision study (4096-colour set) and one pass over the images
+    extras = {}
+    if not args.no_extras and world == 1:
+        extras = run_extras(ctx, torch, device, W, cvs)
+
     # ---- roofline of the search kernel (issue bound)
     c = clk.summary()
     f_mhz = c["sm_mhz"] or 2070.0
@@ -288,8 +352,8 @@ def run_ours(args, world, rank, local):
         "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": "colour cube 262144 colours x 128 radii (0.25..32) x 360 angles "
-                               "(1.208e10 candidates per GPU per step)",
+        "config": {"workload": f"colour cube {n} colours x 128 radii (0.25..32) x 360 angles "
+                               f"({cand:.4g} candidates per GPU per step)",
                    "v_th": 50, "r_novib": 0.5, "patterns": "all 7", "gamut": "reject",
                    "precision": "fp32 + fp64 re-decision", "l2": "flushed between steps "
                    "(256 MB write)", "parallelism": f"replicas x{world}"},
@@ -312,6 +376,7 @@ def run_ours(args, world, rank, local):
         "clocks": {"sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"],
                    "reasons": c["reasons"], "samples": c["samples"]},
     }
+    line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, threads, ccand, dt = time_oracle(args.cpu_sample)
         line["cpu_baseline"] = {

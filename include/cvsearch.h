@@ -62,6 +62,11 @@ typedef enum {
     CVS_ERR_NUMERIC = 6      /* a table value could not be certified (never seen) */
 } cvs_status;
 
+/* Arithmetic of a search.  Both give identical results.  FP32_RECHECK runs
+ * the bulk in FP32 and re-decides in FP64 every candidate whose FP32 codes
+ * could be wrong; its error bound is validated for radii up to 32, so a grid
+ * with a larger radius is searched in FP64 (cvs_stats.precision says which
+ * ran). */
 typedef enum {
     CVS_PREC_FP32_RECHECK = 0, /* FP32 bulk, FP64 re-decision near rounding boundaries */
     CVS_PREC_FP64 = 1          /* every candidate in FP64 (comparison form) */
@@ -70,8 +75,8 @@ typedef enum {
 typedef struct cvs_ctx cvs_ctx;
 
 /* The (radius i, angle j) grid of §2 Methods.  Host pointers, read during the
- * call.  radii: finite, >= 0, in L*a*b* units, at most 16384 values.
- * angles_deg: finite, in degrees, at most 16384 values.  When the angle list
+ * call.  radii: in [0, 1000] L*a*b* units, at most 8192 values.
+ * angles_deg: finite, in degrees, at most 8192 values.  When the angle list
  * is closed under +180 degrees with angles_deg[m + n/2] = angles_deg[m] + 180
  * (mod 360), each symmetric pair is evaluated once. */
 typedef struct {
@@ -234,7 +239,7 @@ cvs_status cvs_precision_probe(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
  *                   a rounding boundary inside which an FP32 code is flagged
  *                   for FP64 re-decision; (0, 0.25); default 2e-3.  It must
  *                   exceed the FP32 path's error for results to be exact.
- *   "block"         threads per block of the search kernel: 64, 128 or 256
+ *   "block"         threads per block of the search kernel: 64 or 128
  *   "blocks_per_sm" resident blocks per SM (0 = as many as fit)
  *   "kchunk"        radii per work item (0 = automatic)
  * Unknown names or out-of-range values return CVS_ERR_INVALID_ARG. */

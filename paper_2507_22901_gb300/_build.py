@@ -56,9 +56,10 @@ def build(force: bool = False, verbose: bool = False) -> Path:
         obj = BUILD / (src.stem + ".o")
         objs.append(obj)
         if src.suffix == ".cu":
+            extra = os.environ.get("CVS_NVCC_FLAGS", "").split()
             cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-Xptxas", "-v" if verbose else "-O3", "-I", str(INCLUDE), "-c", str(src),
-                   "-o", str(obj)]
+                   "-Xptxas", "-v" if verbose else "-O3", "-I", str(INCLUDE), *extra, "-c",
+                   str(src), "-o", str(obj)]
         else:
             cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-I", str(cuda / "include"),
                    "-I", str(INCLUDE), "-c", str(src), "-o", str(obj)]

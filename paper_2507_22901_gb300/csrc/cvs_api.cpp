@@ -36,7 +36,7 @@ cvs_status fail(cvs_status st, const char* fmt, ...) {
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
-constexpr int32_t kMaxGrid = 16384;
+constexpr int32_t kMaxGrid = 8192;  // shared-memory tables: 8 B per radius, 16 B per angle slot
 
 template <class T>
 cudaError_t grow(T** p, int64_t* cap, int64_t need) {
@@ -127,8 +127,8 @@ cvs_status check_grid(const cvs_grid* g) {
         return fail(CVS_ERR_INVALID_ARG, "n_angles must be in [1, %d] (got %d)", kMaxGrid,
                     g->n_angles);
     for (int i = 0; i < g->n_radii; ++i)
-        if (!std::isfinite(g->radii[i]) || g->radii[i] < 0.0)
-            return fail(CVS_ERR_INVALID_ARG, "radius %d must be finite and >= 0 (got %g)", i,
+        if (!std::isfinite(g->radii[i]) || g->radii[i] < 0.0 || g->radii[i] > kMaxRadius)
+            return fail(CVS_ERR_INVALID_ARG, "radius %d must be in [0, %g] (got %g)", i, kMaxRadius,
                         g->radii[i]);
     for (int i = 0; i < g->n_angles; ++i)
         if (!std::isfinite(g->angles_deg[i]))
@@ -244,6 +244,8 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
     a.grid = c->grid;
     a.qkey = c->qkey;
     thresholds_to_int(thr, &a.hi_min, &a.lo_max);
+    // the FP32 path's error is validated for radii up to kFp32MaxRadius
+    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
     a.mask2 = thr->pattern_mask << 1;
     a.clip = thr->gamut_mode;
     a.half_w = (float)(0.5 - c->window);
@@ -349,14 +351,14 @@ cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
         c->window = value;
     } else if (!std::strcmp(name, "block")) {
         const int v = (int)value;
-        if (v != 64 && v != 128 && v != 256)
-            return fail(CVS_ERR_INVALID_ARG, "block must be 64, 128 or 256");
+        if (v != 64 && v != kSearchBlock)
+            return fail(CVS_ERR_INVALID_ARG, "block must be 64 or %d", kSearchBlock);
         c->shape.block = v;
     } else if (!std::strcmp(name, "blocks_per_sm")) {
         if (value < 0 || value > 32) return fail(CVS_ERR_INVALID_ARG, "blocks_per_sm in [0, 32]");
         c->shape.blocks_per_sm = (int)value;
     } else if (!std::strcmp(name, "kchunk")) {
-        if (value < 0 || value > kMaxGrid) return fail(CVS_ERR_INVALID_ARG, "kchunk in [0, 16384]");
+        if (value < 0 || value > kMaxGrid) return fail(CVS_ERR_INVALID_ARG, "kchunk in [0, %d]", kMaxGrid);
         c->shape.kchunk = (int)value;
     } else {
         return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);

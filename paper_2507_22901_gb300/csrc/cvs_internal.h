@@ -44,8 +44,16 @@ struct ImageDesc {             // device-side image table entry
     uint8_t* pmask;
 };
 
+// Threads per block of the search kernel (its launch bound is compiled for it).
+constexpr int kSearchBlock = 128;
+// Largest radius for which the FP32 path's error has been measured to stay far
+// inside its flag window; grids with a larger radius run in FP64.
+constexpr double kFp32MaxRadius = 32.0;
+// Largest radius accepted at all (keeps every FP32 code far below 2^22).
+constexpr double kMaxRadius = 1000.0;
+
 struct LaunchShape {
-    int block = 256;           // threads per block
+    int block = kSearchBlock;  // threads per block (64 or kSearchBlock)
     int blocks_per_sm = 0;     // 0: as many as fit
     int kchunk = 0;            // radii per work item (0: automatic)
 };
@@ -96,7 +104,6 @@ void set_error_message(const char* msg);
 size_t target_f32_size();
 size_t target_f64_size();
 int search_smem_bytes(const GridDev& g, int block);
-const void* search_kernel_ptr(int prec, int list_mode);
 void chain_constants(float Ax[3], float Bz[3]);
 
 }  // namespace cvs

@@ -120,66 +120,152 @@ __global__ void k_setup_images(const ImageDesc* __restrict__ imgs, int n_imgs, i
 
 // ------------------------------------------------------------ FP32 slot
 // Codes of the pair at displacement (u, w) = (r sin j / 500, -r cos j / 200) in
-// f-space, as biased integers y = kMagicBits + q.  Returns true if some code's
-// unrounded value lies within W of a rounding boundary.
+// f-space, as biased integers y = kMagicBits + q.  The plus and minus colours
+// run the same chain, so they travel as one float2 through the packed FP32x2
+// instructions (component-wise IEEE round-to-nearest, as the scalar ops).
+// Returns true if some code's unrounded value lies within W of a rounding
+// boundary.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Per-target constants duplicated into (plus, minus) pairs, built once per
+// work item so that the packed instructions find their operands paired.
+struct PairsT {
+    float2 c1x, c2x, c1z, c2z;
+    float2 fx0, fz0, X30, Z30;
+    float2 lin0[3];
+};
+struct PairsC {
+    float2 Ax[3], Bz[3];
+};
+
+__device__ __forceinline__ PairsT make_pairs(const TargetF32& T) {
+    PairsT P;
+    P.c1x = dup(T.c1x);
+    P.c2x = dup(T.c2x);
+    P.c1z = dup(T.c1z);
+    P.c2z = dup(T.c2z);
+    P.fx0 = dup(T.fx0);
+    P.fz0 = dup(T.fz0);
+    P.X30 = dup(T.X30);
+    P.Z30 = dup(T.Z30);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) P.lin0[c] = dup(T.lin0[c]);
+    return P;
+}
+
+__device__ __forceinline__ PairsC make_pairs(const ChainF32& C) {
+    PairsC P;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        P.Ax[c] = dup(C.Ax[c]);
+        P.Bz[c] = dup(C.Bz[c]);
+    }
+    return P;
+}
+
+// f^-1 displacement of X and Z for the pair: u2 = (u, -u), w2 = (w, -w).
 template <bool FAST>
-__device__ __forceinline__ bool codes32(const TargetF32& T, const float Ax[3], const float Bz[3],
-                                        float u, float w, float half_w, int yp[3], int ym[3]) {
-    float dXp, dXm, dZp, dZm;
+__device__ __forceinline__ void delta_xz(const PairsT& P, float2 u2, float2 w2, float2& dX,
+                                         float2& dZ) {
     if (FAST) {
-        dXp = u * fmaf(u, T.c1x + u, T.c2x);
-        dXm = -u * fmaf(-u, T.c1x - u, T.c2x);
-        dZp = w * fmaf(w, T.c1z + w, T.c2z);
-        dZm = -w * fmaf(-w, T.c1z - w, T.c2z);
+        // (f0 + u)^3 - f0^3 = u (3 f0^2 + u (3 f0 + u)), for +u and -u at once
+        dX = __fmul2_rn(u2, __ffma2_rn(u2, __fadd2_rn(P.c1x, u2), P.c2x));
+        dZ = __fmul2_rn(w2, __ffma2_rn(w2, __fadd2_rn(P.c1z, w2), P.c2z));
     } else {
         const float brk = (float)kFinvBreak, add = (float)kFLinAdd, mul = (float)kFinvLinMul;
-        const float fxp = T.fx0 + u, fxm = T.fx0 - u, fzp = T.fz0 + w, fzm = T.fz0 - w;
-        dXp = (fxp > brk ? fxp * fxp * fxp : (fxp - add) * mul) - T.X30;
-        dXm = (fxm > brk ? fxm * fxm * fxm : (fxm - add) * mul) - T.X30;
-        dZp = (fzp > brk ? fzp * fzp * fzp : (fzp - add) * mul) - T.Z30;
-        dZm = (fzm > brk ? fzm * fzm * fzm : (fzm - add) * mul) - T.Z30;
+        const float2 fx = __fadd2_rn(P.fx0, u2), fz = __fadd2_rn(P.fz0, w2);
+        const float2 cx = __fmul2_rn(__fmul2_rn(fx, fx), fx), cz = __fmul2_rn(__fmul2_rn(fz, fz), fz);
+        const float2 lx = __fmul2_rn(__fadd2_rn(fx, dup(-add)), dup(mul));
+        const float2 lz = __fmul2_rn(__fadd2_rn(fz, dup(-add)), dup(mul));
+        dX = __fadd2_rn(f2(fx.x > brk ? cx.x : lx.x, fx.y > brk ? cx.y : lx.y), neg2(P.X30));
+        dZ = __fadd2_rn(f2(fz.x > brk ? cz.x : lz.x, fz.y > brk ? cz.y : lz.y), neg2(P.Z30));
     }
+}
+
+// Codes of the pair as biased integers y = kMagicBits + q.  The plus and minus
+// colours run the same chain, so they travel as one float2 through the packed
+// FP32x2 instructions (component-wise IEEE round-to-nearest, as the scalar
+// ops).  Returns true if some code's unrounded value lies within W of a
+// rounding boundary.
+template <bool FAST>
+__device__ __forceinline__ bool codes32(const PairsT& P, const PairsC& C, float2 u2, float2 w2,
+                                        float half_w, int yp[3], int ym[3]) {
+    float2 dX, dZ;
+    delta_xz<FAST>(P, u2, w2, dX, dZ);
     bool flag = false;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float lp = fmaf(Bz[c], dZp, fmaf(Ax[c], dXp, T.lin0[c]));
-        const float lm = fmaf(Bz[c], dZm, fmaf(Ax[c], dXm, T.lin0[c]));
-        const float vp = encode_v32(lp), vm = encode_v32(lm);
-        const float yfp = __fadd_rn(vp, kMagic), yfm = __fadd_rn(vm, kMagic);
-        flag |= fabsf(__fsub_rn(vp, __fsub_rn(yfp, kMagic))) >= half_w;
-        flag |= fabsf(__fsub_rn(vm, __fsub_rn(yfm, kMagic))) >= half_w;
-        yp[c] = __float_as_int(yfp);
-        ym[c] = __float_as_int(yfm);
+        const float2 lin = __ffma2_rn(C.Bz[c], dZ, __ffma2_rn(C.Ax[c], dX, P.lin0[c]));
+        float lgp, lgm, pp, pm;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lgp) : "f"(lin.x));
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lgm) : "f"(lin.y));
+        const float2 e = __fmul2_rn(f2(lgp, lgm), dup(5.0f / 12.0f));
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pp) : "f"(e.x));
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pm) : "f"(e.y));
+        const float2 vpow = __ffma2_rn(dup(269.025f), f2(pp, pm), dup(-14.025f));
+        const float2 vlin = __fmul2_rn(lin, dup(3294.6f));
+        const float2 v = f2(lin.x <= 0.0031308f ? vlin.x : vpow.x,
+                            lin.y <= 0.0031308f ? vlin.y : vpow.y);
+        const float2 y = __fadd2_rn(v, dup(kMagic));
+        const float2 rr = __fadd2_rn(y, dup(-kMagic));
+        const float2 d = __ffma2_rn(rr, dup(-1.0f), v);  // v - rr, exact
+        flag |= fabsf(d.x) >= half_w;
+        flag |= fabsf(d.y) >= half_w;
+        yp[c] = __float_as_int(y.x);
+        ym[c] = __float_as_int(y.y);
     }
     return flag;
 }
 
-// Embedding-signal decision on biased codes (exact when no code is flagged).
-__device__ __forceinline__ int decide32(const int yp_in[3], const int ym_in[3], int32_t hi_min,
-                                        int32_t lo_max, uint32_t mask2, int32_t clip) {
+// Embedding-signal decision on biased codes y = kMagicBits + q (exact when no
+// code is flagged).  Per channel the difference d = q+ - q- indexes a 512-entry
+// table in shared memory (index d & 511): bit 3 = neither high nor low, bit
+// (2 - c) = high.  OR-ing the three channels gives the pattern in bits 0..2 and
+// "invalid" in bit 3; okmask has bit p set for each enabled pattern p.
+// Gamut (reject): all six codes lie in [0, 255] exactly when the OR of the
+// six y, XOR kMagicBits, is at most 255 (every |q| here is far below 2^22).
+template <bool CLIP>
+__device__ __forceinline__ int decide32(const int yp_in[3], const int ym_in[3],
+                                        const uint8_t* __restrict__ lut, uint32_t okmask) {
     int yp[3], ym[3];
-    uint32_t out = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         yp[c] = yp_in[c];
         ym[c] = ym_in[c];
-        if (clip) {
+        if (CLIP) {
             yp[c] = min(max(yp[c], kMagicBits), kMagicBits + 255);
             ym[c] = min(max(ym[c], kMagicBits), kMagicBits + 255);
         }
-        out |= ((uint32_t)yp[c] ^ (uint32_t)kMagicBits) | ((uint32_t)ym[c] ^ (uint32_t)kMagicBits);
     }
-    const uint32_t gap = (uint32_t)(hi_min - lo_max - 1);
-    bool invalid = out > 255u;  // a code outside [0, 255] (reject mode)
-    uint32_t pattern = 0;
+    bool in_gamut = true;
+    if (!CLIP) {
+        const uint32_t o = ((uint32_t)yp[0] | (uint32_t)ym[0] | (uint32_t)yp[1]) |
+                           ((uint32_t)ym[1] | (uint32_t)yp[2] | (uint32_t)ym[2]);
+        in_gamut = (o ^ (uint32_t)kMagicBits) <= 255u;
+    }
+    uint32_t comb = 0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int d = abs(yp[c] - ym[c]);
-        invalid |= (uint32_t)(d - lo_max - 1) < gap;
-        pattern |= ((uint32_t)(hi_min - 1 - d) >> 31) << (2 - c);
+    for (int c = 0; c < 3; ++c) comb |= lut[c * 512 + ((yp[c] - ym[c]) & 511)];
+    const bool ok = in_gamut && ((okmask >> comb) & 1u);
+    return ok ? (int)(comb & 7u) : 0;
+}
+
+// Build the three 512-entry channel tables of decide32 in shared memory.
+__device__ __forceinline__ void build_decide_lut(uint8_t* lut, int32_t hi_min, int32_t lo_max) {
+    for (int i = threadIdx.x; i < 3 * 512; i += blockDim.x) {
+        const int c = i >> 9, idx = i & 511;
+        const int d = idx < 256 ? idx : idx - 512;  // idx = d & 511 for d in [-256, 255]
+        const int ad = d < 0 ? -d : d;
+        uint8_t e;
+        if (ad > 255) e = 8;  // cannot happen for codes in [0, 255]
+        else {
+            const bool hi = ad >= hi_min, lo = ad <= lo_max;
+            e = (uint8_t)((hi ? (1u << (2 - c)) : 0u) | ((hi || lo) ? 0u : 8u));
+        }
+        lut[i] = e;
     }
-    const bool ok = !invalid && ((mask2 >> pattern) & 1u);
-    return ok ? (int)pattern : 0;
 }
 
 // Exact analysis of a slot with flagged codes: each flagged code may be one
@@ -190,31 +276,19 @@ template <bool FAST>
 __device__ __noinline__ int certain32(const TargetF32 T, const ChainF32 C, float u, float w,
                                       float half_w, int32_t hi_min, int32_t lo_max,
                                       uint32_t mask2, int32_t clip, int list_mode) {
-    const float* Ax = C.Ax;
-    const float* Bz = C.Bz;
-    // recompute the unrounded values
-    float dXp, dXm, dZp, dZm;
-    if (FAST) {
-        dXp = u * fmaf(u, T.c1x + u, T.c2x);
-        dXm = -u * fmaf(-u, T.c1x - u, T.c2x);
-        dZp = w * fmaf(w, T.c1z + w, T.c2z);
-        dZm = -w * fmaf(-w, T.c1z - w, T.c2z);
-    } else {
-        const float brk = (float)kFinvBreak, add = (float)kFLinAdd, mul = (float)kFinvLinMul;
-        const float fxp = T.fx0 + u, fxm = T.fx0 - u, fzp = T.fz0 + w, fzm = T.fz0 - w;
-        dXp = (fxp > brk ? fxp * fxp * fxp : (fxp - add) * mul) - T.X30;
-        dXm = (fxm > brk ? fxm * fxm * fxm : (fxm - add) * mul) - T.X30;
-        dZp = (fzp > brk ? fzp * fzp * fzp : (fzp - add) * mul) - T.Z30;
-        dZm = (fzm > brk ? fzm * fzm * fzm : (fzm - add) * mul) - T.Z30;
-    }
+    const PairsT P = make_pairs(T);
+    const PairsC PC = make_pairs(C);
+    // recompute the unrounded values, operation for operation as in codes32
+    float2 dX2, dZ2;
+    delta_xz<FAST>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
     int lo[6], hi[6];  // code intervals: values 0..2 plus colour, 3..5 minus colour
     bool any_flag = false;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+        const float2 lin2 = __ffma2_rn(PC.Bz[c], dZ2, __ffma2_rn(PC.Ax[c], dX2, P.lin0[c]));
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
-            const float dX = s ? dXm : dXp, dZ = s ? dZm : dZp;
-            const float lin = fmaf(Bz[c], dZ, fmaf(Ax[c], dX, T.lin0[c]));
+            const float lin = s ? lin2.y : lin2.x;
             const float v = encode_v32(lin);
             const float rr = __fsub_rn(__fadd_rn(v, kMagic), kMagic);
             const int q = (int)rr;
@@ -261,8 +335,9 @@ __device__ __noinline__ int certain32(const TargetF32 T, const ChainF32 C, float
 
 // ------------------------------------------------------------ search kernel
 struct Smem {
-    float* r;       // K
-    float2* sc;     // H used
+    float2* r2;     // K: (r, r)
+    float4* sc4;    // H: (sin/500, -sin/500, -cos/200, cos/200)
+    uint8_t* lut;   // 3 x 512 channel-difference classes
     uint32_t* rq_t; // per warp: kRqCap target indices (low 32 bits)
     uint32_t* rq_kh;
 };
@@ -342,97 +417,186 @@ __device__ __noinline__ void flush_queue(const SearchArgs& A, uint32_t* rq_t, ui
     __syncwarp();
 }
 
-template <int PREC, bool FAST>
+// Queue up to 32 slots for FP64 re-decision; flush when 32 are waiting.
+__device__ __forceinline__ void push_fp64(const SearchArgs& A, bool need64, int64_t t, int k,
+                                          int h, uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
+                                          unsigned long long& n_re) {
+    const unsigned lane = lane_id();
+    const unsigned ball = __ballot_sync(0xFFFFFFFFu, need64);
+    if (!ball) return;
+    if (need64) {
+        const int pos = rq_n + __popc(ball & ((1u << lane) - 1u));
+        rq_t[pos] = (uint32_t)t;
+        rq_kh[pos] = (uint32_t)k | ((uint32_t)h << 16);
+    }
+    rq_n += __popc(ball);
+    __syncwarp();
+    if (rq_n >= 32) {
+        flush_queue(A, rq_t, rq_kh, 32, &n_re);
+        const int rest = rq_n - 32;
+        uint32_t mt = 0, mkh = 0;
+        if ((int)lane < rest) { mt = rq_t[32 + lane]; mkh = rq_kh[32 + lane]; }
+        __syncwarp();
+        if ((int)lane < rest) { rq_t[lane] = mt; rq_kh[lane] = mkh; }
+        __syncwarp();
+        rq_n = rest;
+    }
+}
+
+// Decide up to 32 flagged slots of target t, one per lane: exact interval
+// analysis in FP32, FP64 re-decision where the analysis cannot decide.
+template <bool FAST>
+__device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S,
+                                              const TargetF32& T, const ChainF32& C, int64_t t,
+                                              uint32_t* pq, int n, int& cnt, float& rmax,
+                                              uint32_t& pm, uint32_t* rq_t, uint32_t* rq_kh,
+                                              int& rq_n, unsigned long long& n_re) {
+    const unsigned lane = lane_id();
+    const int inc = A.grid.sym ? 2 : 1;
+    int k = 0, h = 0, pc = 0;
+    if ((int)lane < n) {
+        const uint32_t kh = pq[lane];
+        k = (int)(kh & 0xFFFFu);
+        h = (int)(kh >> 16);
+        const float r = S.r2[k].x;
+        const float4 sc = S.sc4[h];
+        pc = certain32<FAST>(T, C, r * sc.x, r * sc.z, A.half_w, A.hi_min, A.lo_max, A.mask2,
+                             A.clip, A.list_mode);
+        if (pc > 0) {
+            cnt += inc;
+            rmax = fmaxf(rmax, r);
+            pm |= 1u << pc;
+        }
+    }
+    __syncwarp();
+    push_fp64(A, (int)lane < n && pc < 0, t, k, h, rq_t, rq_kh, rq_n, n_re);
+}
+
+// Per-lane accumulators of one work item.
+struct Tally {
+    int cnt;
+    float rmax;
+    uint32_t pm;
+};
+
+// One 32-slot step of a work item: every lane evaluates slot (k, h).  With
+// CHECK, lanes past the item's last slot (active == false) contribute nothing.
+template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST>
+__device__ __forceinline__ void slot_step(const SearchArgs& A, const Smem& S, const TargetF32& T,
+                                          const PairsT& P, const PairsC& PC, const TargetF64& D,
+                                          const ChainF32& C, int64_t t, int k, int h, bool active,
+                                          Tally& acc, uint32_t* pq, int& pq_n, uint32_t* rq_t,
+                                          uint32_t* rq_kh, int& rq_n, unsigned long long& n_flag,
+                                          unsigned long long& n_re) {
+    const unsigned lane = lane_id();
+    const int H = A.grid.H;
+    const int inc = A.grid.sym ? 2 : 1;
+    if (CHECK && !active) { k = 0; h = 0; }
+    const float2 r2 = S.r2[k];
+    const float r = r2.x;
+    if (PREC == CVS_PREC_FP32_RECHECK) {
+        const float4 sc = S.sc4[h];
+        const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));  // (u, -u)
+        const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));  // (w, -w)
+        int yp[3], ym[3];
+        bool flag = codes32<FAST>(P, PC, u2, w2, A.half_w, yp, ym);
+        if (CHECK) flag = flag && active;
+        int pattern = decide32<CLIP>(yp, ym, S.lut, A.mask2);
+        if (flag || (CHECK && !active)) pattern = 0;
+        if (pattern) {
+            if (!LIST) {
+                acc.cnt += inc;
+                acc.rmax = fmaxf(acc.rmax, r);
+                acc.pm |= 1u << pattern;  // bit p for pattern p; shifted down at the end
+            } else {
+                int qp[3], qm[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    int a = yp[c] - kMagicBits, b = ym[c] - kMagicBits;
+                    if (CLIP) { a = min(max(a, 0), 255); b = min(max(b, 0), 255); }
+                    qp[c] = a;
+                    qm[c] = b;
+                }
+                write_records(A.dense, A.grid.N, H, A.grid.sym, k, h, qp, qm, pattern, 0u,
+                              A.target_id);
+            }
+        }
+        const unsigned fball = __ballot_sync(0xFFFFFFFFu, flag);
+        if (fball) {
+            if (flag) {
+                pq[pq_n + __popc(fball & ((1u << lane) - 1u))] = (uint32_t)k | ((uint32_t)h << 16);
+                ++n_flag;
+            }
+            pq_n += __popc(fball);
+            __syncwarp();
+            if (pq_n >= 32) {
+                drain_flagged<FAST>(A, S, T, C, t, pq, 32, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh,
+                                    rq_n, n_re);
+                const int rest = pq_n - 32;
+                const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
+                __syncwarp();
+                if ((int)lane < rest) pq[lane] = mv;
+                __syncwarp();
+                pq_n = rest;
+            }
+        }
+    } else {
+        int qp[3], qm[3];
+        const int pattern = (!CHECK || active) ? decide64_slot(A, D, k, h, qp, qm) : 0;
+        if (pattern) {
+            if (LIST) {
+                write_records(A.dense, A.grid.N, H, A.grid.sym, k, h, qp, qm, pattern, 0u,
+                              A.target_id);
+            } else {
+                acc.cnt += inc;
+                acc.rmax = fmaxf(acc.rmax, r);
+                acc.pm |= 1u << pattern;
+            }
+        }
+    }
+}
+
+template <int PREC, bool FAST, bool CLIP, bool LIST>
 __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int64_t t, int k0,
-                                         int k1, const float Ax[3], const float Bz[3],
+                                         int k1, const ChainF32& C, uint32_t* pq,
                                          uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
                                          unsigned long long& n_flag, unsigned long long& n_re) {
     const unsigned lane = lane_id();
     const int H = A.grid.H;
-    const int inc = A.grid.sym ? 2 : 1;
     const int nslots = (k1 - k0) * H;
     TargetF32 T;
     TargetF64 D;
     if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
     else D = A.td[t];
-    int cnt = 0;
-    float rmax = -1.0f;
-    uint32_t pm = 0;
-    // lane's first slot
+    const PairsT P = make_pairs(T);
+    const PairsC PC = make_pairs(C);
+    Tally acc{0, -1.0f, 0u};
+    int pq_n = 0;  // flagged slots waiting for drain_flagged (warp-uniform)
+    // slot i of the item is (k0 + i / H, i % H); lanes start at i = lane and
+    // step by 32 = q32 H + r32, so one conditional wrap keeps h in [0, H)
+    const int q32 = 32 / H, r32 = 32 - q32 * H;
     int k = k0 + (int)lane / H, h = (int)lane % H;
-    for (int base = 0; base < nslots; base += 32) {
-        const bool active = base + (int)lane < nslots;
-        const int kk = active ? k : k0, hh = active ? h : 0;
-        const float r = S.r[kk];
-        int pattern = 0;
-        bool need64 = false;
-        int qp[3], qm[3];
-        if (PREC == CVS_PREC_FP32_RECHECK) {
-            const float2 sc = S.sc[hh];
-            const float u = r * sc.x, w = r * sc.y;
-            int yp[3], ym[3];
-            const bool flag = codes32<FAST>(T, Ax, Bz, u, w, A.half_w, yp, ym) && active;
-            pattern = decide32(yp, ym, A.hi_min, A.lo_max, A.mask2, A.clip);
-            if (flag) {
-                ++n_flag;
-                ChainF32 C;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) { C.Ax[c] = Ax[c]; C.Bz[c] = Bz[c]; }
-                const int pc = certain32<FAST>(T, C, u, w, A.half_w, A.hi_min, A.lo_max, A.mask2,
-                                               A.clip, A.list_mode);
-                need64 = pc < 0;
-                pattern = pc < 0 ? 0 : pc;
-            }
-            if (A.list_mode && pattern && active) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    int a = yp[c] - kMagicBits, b = ym[c] - kMagicBits;
-                    if (A.clip) { a = min(max(a, 0), 255); b = min(max(b, 0), 255); }
-                    qp[c] = a;
-                    qm[c] = b;
-                }
-            }
-        } else {
-            pattern = active ? decide64_slot(A, D, kk, hh, qp, qm) : 0;
-        }
-        if (!active) pattern = 0;
-        if (pattern) {
-            if (A.list_mode) {
-                write_records(A.dense, A.grid.N, H, A.grid.sym, kk, hh, qp, qm, pattern, 0u,
-                              A.target_id);
-            } else {
-                cnt += inc;
-                rmax = fmaxf(rmax, r);
-                pm |= 1u << (pattern - 1);
-            }
-        }
-        if (PREC == CVS_PREC_FP32_RECHECK) {
-            const unsigned ball = __ballot_sync(0xFFFFFFFFu, need64);
-            if (ball) {
-                if (need64) {
-                    const int pos = rq_n + __popc(ball & ((1u << lane) - 1u));
-                    rq_t[pos] = (uint32_t)t;
-                    rq_kh[pos] = (uint32_t)kk | ((uint32_t)hh << 16);
-                }
-                rq_n += __popc(ball);
-                __syncwarp();
-                if (rq_n >= 32) {
-                    flush_queue(A, rq_t, rq_kh, 32, &n_re);
-                    const int rest = rq_n - 32;
-                    uint32_t mt = 0, mkh = 0;
-                    if ((int)lane < rest) { mt = rq_t[32 + lane]; mkh = rq_kh[32 + lane]; }
-                    __syncwarp();
-                    if ((int)lane < rest) { rq_t[lane] = mt; rq_kh[lane] = mkh; }
-                    __syncwarp();
-                    rq_n = rest;
-                }
-            }
-        }
-        // advance by 32 slots
-        h += 32;
-        while (h >= H) { h -= H; ++k; }
+    const int nfull = nslots >> 5;
+    for (int it = 0; it < nfull; ++it) {
+        slot_step<PREC, FAST, false, CLIP, LIST>(A, S, T, P, PC, D, C, t, k, h, true, acc, pq, pq_n, rq_t,
+                                     rq_kh, rq_n, n_flag, n_re);
+        h += r32;
+        k += q32;
+        const bool wrap = h >= H;
+        h = wrap ? h - H : h;
+        k = wrap ? k + 1 : k;
     }
-    if (!A.list_mode) {
+    if (nslots & 31) {
+        slot_step<PREC, FAST, true, CLIP, LIST>(A, S, T, P, PC, D, C, t, k, h, (int)lane < (nslots & 31), acc,
+                                    pq, pq_n, rq_t, rq_kh, rq_n, n_flag, n_re);
+    }
+    if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0)
+        drain_flagged<FAST>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh, rq_n,
+                            n_re);
+    if (!LIST) {
+        int cnt = acc.cnt;
+        float rmax = acc.rmax;
+        uint32_t pm = acc.pm;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
@@ -443,30 +607,46 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
             Acc* ac = A.acc + t;
             atomicAdd(&ac->count, cnt);
             atomicMax(&ac->rmax_bits, __float_as_int(rmax));
-            atomicOr(&ac->pmask, pm);
+            atomicOr(&ac->pmask, pm >> 1);  // bit p-1 for pattern p
         }
     }
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(256) k_search(const SearchArgs A) {
+// Launch bounds of the search kernel: blocks of up to CVS_SEARCH_MAX_THREADS
+// threads, at least CVS_SEARCH_MIN_BLOCKS of them resident per SM.
+#ifndef CVS_SEARCH_MAX_THREADS
+#define CVS_SEARCH_MAX_THREADS kSearchBlock
+#endif
+#ifndef CVS_SEARCH_MIN_BLOCKS
+#define CVS_SEARCH_MIN_BLOCKS 5
+#endif
+
+template <int PREC, bool CLIP, bool LIST>
+__global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
+    k_search(const SearchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = A.grid.K, H = A.grid.H;
     Smem S;
-    S.r = reinterpret_cast<float*>(smem);
-    S.sc = reinterpret_cast<float2*>(smem + ((K * 4 + 15) & ~15));
-    unsigned char* q = smem + ((K * 4 + 15) & ~15) + ((H * 8 + 15) & ~15);
+    S.r2 = reinterpret_cast<float2*>(smem);
+    S.sc4 = reinterpret_cast<float4*>(smem + ((K * 8 + 15) & ~15));
+    S.lut = smem + ((K * 8 + 15) & ~15) + H * 16;
+    unsigned char* q = S.lut + 3 * 512;
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     S.rq_t = reinterpret_cast<uint32_t*>(q);
     S.rq_kh = S.rq_t + nwarps * kRqCap;
-    for (int i = threadIdx.x; i < K; i += blockDim.x) S.r[i] = A.grid.r32[i];
-    for (int i = threadIdx.x; i < H; i += blockDim.x) S.sc[i] = A.grid.sc32[i];
+    uint32_t* pq = S.rq_kh + nwarps * kRqCap + warp * kRqCap;
+    build_decide_lut(S.lut, A.hi_min, A.lo_max);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) S.r2[i] = dup(A.grid.r32[i]);
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        const float2 sc = A.grid.sc32[i];
+        S.sc4[i] = make_float4(sc.x, -sc.x, sc.y, -sc.y);
+    }
     __syncthreads();
-    float Ax[3], Bz[3];
+    ChainF32 C;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        Ax[c] = __double2float_rn(__dmul_rn(c_MI[3 * c], c_W[0]));
-        Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
+        C.Ax[c] = __double2float_rn(__dmul_rn(c_MI[3 * c], c_W[0]));
+        C.Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
     }
     uint32_t* rq_t = S.rq_t + warp * kRqCap;
     uint32_t* rq_kh = S.rq_kh + warp * kRqCap;
@@ -487,11 +667,14 @@ __global__ void __launch_bounds__(256) k_search(const SearchArgs A) {
         if (PREC == CVS_PREC_FP32_RECHECK) {
             const uint32_t fl = A.tf[t].flags;
             if (fl & 1u)
-                run_item<PREC, true>(A, S, t, k0, k1, Ax, Bz, rq_t, rq_kh, rq_n, n_flag, n_re);
+                run_item<PREC, true, CLIP, LIST>(A, S, t, k0, k1, C, pq, rq_t, rq_kh, rq_n, n_flag,
+                                                 n_re);
             else
-                run_item<PREC, false>(A, S, t, k0, k1, Ax, Bz, rq_t, rq_kh, rq_n, n_flag, n_re);
+                run_item<PREC, false, CLIP, LIST>(A, S, t, k0, k1, C, pq, rq_t, rq_kh, rq_n, n_flag,
+                                                  n_re);
         } else {
-            run_item<PREC, true>(A, S, t, k0, k1, Ax, Bz, rq_t, rq_kh, rq_n, n_flag, n_re);
+            run_item<PREC, true, CLIP, LIST>(A, S, t, k0, k1, C, pq, rq_t, rq_kh, rq_n, n_flag,
+                                             n_re);
         }
     }
     if (PREC == CVS_PREC_FP32_RECHECK && rq_n > 0) flush_queue(A, rq_t, rq_kh, rq_n, &n_re);
@@ -599,28 +782,21 @@ __global__ void k_precision_probe(const TargetF32* __restrict__ tf, const Target
         const TargetF64 D = td[t];
         const float r = g.r32[k];
         const float2 sc = g.sc32[m];
-        int yp[3], ym[3];
-        if (T.flags & 1u) codes32<true>(T, Ax, Bz, r * sc.x, r * sc.y, 0.5f, yp, ym);
-        else codes32<false>(T, Ax, Bz, r * sc.x, r * sc.y, 0.5f, yp, ym);
+        const PairsT P = make_pairs(T);
         // FP64 reference of the plus colour
         const double da = __dmul_rn(g.r64[k], g.s64[m]), db = __dmul_rn(g.r64[k], g.c64[m]);
         double lin[3];
         color_lin64(D.L, __dadd_rn(D.a, da), __dadd_rn(D.b, db), lin);
         // FP32 plus colour, recomputed to get the unrounded values
-        float dX, dZ;
+        float2 dX2, dZ2;
         const float u = r * sc.x, w = r * sc.y;
-        if (T.flags & 1u) {
-            dX = u * fmaf(u, T.c1x + u, T.c2x);
-            dZ = w * fmaf(w, T.c1z + w, T.c2z);
-        } else {
-            const float brk = (float)kFinvBreak, add = (float)kFLinAdd, mul = (float)kFinvLinMul;
-            const float fx = T.fx0 + u, fz = T.fz0 + w;
-            dX = (fx > brk ? fx * fx * fx : (fx - add) * mul) - T.X30;
-            dZ = (fz > brk ? fz * fz * fz : (fz - add) * mul) - T.Z30;
-        }
+        if (T.flags & 1u) delta_xz<true>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
+        else delta_xz<false>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float l32 = fmaf(Bz[c], dZ, fmaf(Ax[c], dX, T.lin0[c]));
+            const float l32 = __ffma2_rn(f2(Bz[c], Bz[c]), dZ2,
+                                         __ffma2_rn(f2(Ax[c], Ax[c]), dX2,
+                                                    f2(T.lin0[c], T.lin0[c]))).x;
             const float v32 = encode_v32(l32);
             const double l64 = lin[c];
             const double v64 = l64 <= 0.0031308 ? 3294.6 * l64 : 269.025 * pow(l64, 1.0 / 2.4) - 14.025;
@@ -632,8 +808,6 @@ __global__ void k_precision_probe(const TargetF32* __restrict__ tf, const Target
             const int q32 = (int)fminf(fmaxf(rintf(v32), -1.0f), 256.0f);
             if (q64 != q32 && q64 >= 0 && q64 <= 255) ++wrong;
         }
-        (void)yp;
-        (void)ym;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -680,18 +854,15 @@ cudaError_t launch_setup_images(const ImageDesc* imgs, int n_imgs, int64_t total
 }
 
 int search_smem_bytes(const GridDev& g, int block) {
-    return ((g.K * 4 + 15) & ~15) + ((g.H * 8 + 15) & ~15) + (block / 32) * kRqCap * 8;
+    // (r, r) pairs, angle quadruples, then per warp: FP64 queue (targets, slots)
+    // and flagged queue
+    return ((g.K * 8 + 15) & ~15) + g.H * 16 + 3 * 512 + (block / 32) * kRqCap * 12;
 }
 
-const void* search_kernel_ptr(int prec, int list_mode) {
-    (void)list_mode;
-    return prec == CVS_PREC_FP64 ? (const void*)k_search<CVS_PREC_FP64>
-                                 : (const void*)k_search<CVS_PREC_FP32_RECHECK>;
-}
-
-cudaError_t launch_search(const SearchArgs& a, cudaStream_t st) {
+template <int PREC, bool CLIP, bool LIST>
+cudaError_t launch_search_t(const SearchArgs& a, cudaStream_t st) {
     const int smem = search_smem_bytes(a.grid, a.shape.block);
-    const void* fn = search_kernel_ptr(a.prec, a.list_mode);
+    const void* fn = (const void*)k_search<PREC, CLIP, LIST>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = a.shape.blocks_per_sm;
@@ -700,12 +871,21 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    const int grid = a.num_sms * per_sm;
-    if (a.prec == CVS_PREC_FP64)
-        k_search<CVS_PREC_FP64><<<grid, a.shape.block, smem, st>>>(a);
-    else
-        k_search<CVS_PREC_FP32_RECHECK><<<grid, a.shape.block, smem, st>>>(a);
+    k_search<PREC, CLIP, LIST><<<a.num_sms * per_sm, a.shape.block, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_search_p(const SearchArgs& a, cudaStream_t st) {
+    if (a.clip) return a.list_mode ? launch_search_t<PREC, true, true>(a, st)
+                                   : launch_search_t<PREC, true, false>(a, st);
+    return a.list_mode ? launch_search_t<PREC, false, true>(a, st)
+                       : launch_search_t<PREC, false, false>(a, st);
+}
+
+cudaError_t launch_search(const SearchArgs& a, cudaStream_t st) {
+    return a.prec == CVS_PREC_FP64 ? launch_search_p<CVS_PREC_FP64>(a, st)
+                                   : launch_search_p<CVS_PREC_FP32_RECHECK>(a, st);
 }
 
 cudaError_t launch_finalize_colors(const Acc* acc, int64_t n, float* max_r, int32_t* count,

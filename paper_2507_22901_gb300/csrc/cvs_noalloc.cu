@@ -162,11 +162,12 @@ cvs_status run(int device, const uint8_t* rgb_dev, int64_t n, const cvs_grid* g,
     a.mask2 = thr->pattern_mask << 1;
     a.clip = thr->gamut_mode;
     a.half_w = (float)(0.5 - 2e-3);
-    a.prec = (int32_t)prec;
+    a.prec = (prec == CVS_PREC_FP32_RECHECK && rmax > cvs::kFp32MaxRadius) ? (int32_t)CVS_PREC_FP64
+                                                                           : (int32_t)prec;
     a.list_mode = 0;
     a.work_counter = counters;
     a.stats = counters + 1;
-    a.shape.block = 256;
+    a.shape.block = cvs::kSearchBlock;
     a.shape.blocks_per_sm = 0;
     // radius chunk: enough work items to spread n targets over every SM
     int64_t n_kc = ((int64_t)num_sms * 512 + n - 1) / n;
@@ -205,8 +206,8 @@ extern "C" cvs_status cvs_search_colors_noalloc(int device, const uint8_t* rgb_d
                     "cvs_search_colors_noalloc: grid %d x %d exceeds the fixed scratch limit %d x %d",
                     grid->n_radii, grid->n_angles, kMaxRadii, kMaxAngles);
     for (int i = 0; i < grid->n_radii; ++i)
-        if (!std::isfinite(grid->radii[i]) || grid->radii[i] < 0.0)
-            return fail(CVS_ERR_INVALID_ARG, "radius %d must be finite and >= 0", i);
+        if (!std::isfinite(grid->radii[i]) || grid->radii[i] < 0.0 || grid->radii[i] > cvs::kMaxRadius)
+            return fail(CVS_ERR_INVALID_ARG, "radius %d must be in [0, %g]", i, cvs::kMaxRadius);
     for (int i = 0; i < grid->n_angles; ++i)
         if (!std::isfinite(grid->angles_deg[i]))
             return fail(CVS_ERR_INVALID_ARG, "angle %d is not finite", i);

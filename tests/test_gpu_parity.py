@@ -315,7 +315,8 @@ def test_empty_and_invalid_inputs(ctx, torch_cuda):
                             50, 0.5)
     assert out[0].numel() == 0
     rgb = dev(torch, cube_sample(4))
-    for r, a in [([float("nan")], ang), ([-1.0], ang), (radii, []), ([1.0], [float("inf")])]:
+    for r, a in [([float("nan")], ang), ([-1.0], ang), (radii, []), ([1.0], [float("inf")]),
+                 ([1000.5], ang)]:
         with pytest.raises(cvs.CvsError) as ei:
             ctx.search_colors(rgb, r, a, 50, 0.5)
         assert ei.value.status == binding.CVS_ERR_INVALID_ARG
@@ -337,3 +338,15 @@ def test_host_entry_point_and_stream(ctx, torch_cuda):
         out = ctx.search_colors(d, radii, ang, 50, 0.5, stream=s)
     ctx.synchronize(s)
     assert_maps_equal(tuple(x.cpu().numpy() for x in out), exp, "side stream")
+
+
+def test_large_radii_run_in_fp64_and_match(ctx, torch_cuda):
+    """Radii beyond the FP32 path's validated range (32) are searched in FP64."""
+    rgb = cube_sample(16, seed=21)
+    radii = np.array([5.0, 31.5, 40.0, 64.0, 120.0])
+    ang = np.arange(72) * 5.0
+    exp = oracle_colors(rgb, radii, ang)
+    got = gpu_colors(ctx, torch_cuda, rgb, radii, ang, binding.PREC_FP32_RECHECK)
+    ctx.synchronize()
+    assert ctx.stats()["precision"] == binding.PREC_FP64
+    assert_maps_equal(got, exp, "large radii")
