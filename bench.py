@@ -35,6 +35,19 @@ CAND_PER_4K_FRAME = 3840 * 2160 * 64 * 180
 # of the design notes): 53.5 FP32/INT lane operations + 6 MUFU operations.
 ALG_ISSUES_PER_CAND = 59.5
 LANES_PER_SM_CLK = 128
+# DRAM bytes of one FP32 search launch on this workload, from the ncu capture
+# summarised in profiles/k_search_fp32_colour_cube_full.md (32,768-colour case
+# scaled by 8, traffic being proportional to the colours).  Valid only for the
+# kernel source it was taken from; otherwise the roofline reports null.
+TRAFFIC_CAPTURE = {"source_sha256_16": "3b7175f5f5b11923", "bytes_per_launch": 8 * 3.15904e6}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    from pathlib import Path
+    csrc = Path(__file__).resolve().parent / "paper_2507_22901_gb300" / "csrc"
+    data = (csrc / "cvs_kernels.cu").read_bytes() + (csrc / "cvs_device.cuh").read_bytes()
+    return hashlib.sha256(data).hexdigest()[:16]
 REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
                0x2: "applications_clocks_setting", 0x1: "gpu_idle"}
@@ -368,7 +381,10 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": int(n * 9), "matches_device_result": e2e_match},
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "alu", "kernel": "k_search<fp32>", "achieved": achieved,
-                     "peak": peak, "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                     "traffic": (TRAFFIC_CAPTURE["bytes_per_launch"]
+                                 if kernel_source_hash() == TRAFFIC_CAPTURE["source_sha256_16"]
+                                 and args.cube_step == 4 else None),
                      "peak_basis": f"{num_sms} SMs x {LANES_PER_SM_CLK} lanes x "
                                    f"{f_mhz:.0f} MHz median SM clock under load",
                      "ops_per_candidate": ALG_ISSUES_PER_CAND,
