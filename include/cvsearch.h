@@ -234,6 +234,26 @@ cvs_status cvs_precision_probe(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
                                const cvs_grid* grid, double* max_code_err,
                                double* max_lin_err, int64_t* n_wrong_codes);
 
+/* A launch shape of the search kernel: threads per block, resident blocks
+ * per SM (0 = as many as fit) and radii per work item (a work item is one
+ * target x kchunk radii x every angle slot, run by one warp). */
+typedef struct {
+    int32_t block;
+    int32_t blocks_per_sm;
+    int32_t kchunk;
+    int32_t reserved;
+    double ms;            /* search-kernel time of the best shape on the tuning sample */
+} cvs_launch_shape;
+
+/* Autotuner: time candidate launch shapes of the per-colour search on these
+ * n colours (rgb_dev: device, 3n bytes; at most ~3e10 candidates of them are
+ * used per timed launch) and remember the fastest for searches on this
+ * context with the same grid, precision, gamut mode and size class (n within
+ * a power of two).  *best receives it.  Synchronous; uses the context's own
+ * stream.  Shapes set by hand with cvs_set_option take precedence. */
+cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const cvs_grid* grid,
+                        const cvs_thresholds* thr, cvs_precision prec, cvs_launch_shape* best);
+
 /* Tuning options of a context (host only):
  *   "fp32_window"   W, the half-width in 8-bit code units of the band around
  *                   a rounding boundary inside which an FP32 code is flagged
@@ -242,6 +262,17 @@ cvs_status cvs_precision_probe(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
  *   "block"         threads per block of the search kernel: 64 or 128
  *   "blocks_per_sm" resident blocks per SM (0 = as many as fit)
  *   "kchunk"        radii per work item (0 = automatic)
+ *   "autotune"      1: the first search of a new kind (grid, precision, gamut
+ *                   mode, size class) times candidate shapes before running,
+ *                   as cvs_autotune does; that call then blocks.  Default 0.
+ *   "graphs"        1: cvs_search_colors / cvs_search_images capture their
+ *                   setup + search + finalize sequence into a CUDA graph the
+ *                   first time a given input signature (pointers, sizes, grid,
+ *                   thresholds, precision, shape) is seen, and replay the graph
+ *                   on later calls with the same signature (up to 8 graphs are
+ *                   kept per context).  Default 0.
+ * Read-only values for cvs_get_option: "graph_launches" (graph replays so
+ * far), "graphs_cached".
  * Unknown names or out-of-range values return CVS_ERR_INVALID_ARG. */
 cvs_status cvs_set_option(cvs_ctx* ctx, const char* name, double value);
 cvs_status cvs_get_option(cvs_ctx* ctx, const char* name, double* value);

@@ -66,6 +66,11 @@ class cvs_stats(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("search_ms", ctypes.c_double)]
 
 
+class cvs_launch_shape(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("kchunk", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
 assert ctypes.sizeof(cvs_pair) == 16 and PAIR_DTYPE.itemsize == 16
 
 _lib = None
@@ -113,6 +118,7 @@ def lib() -> ctypes.CDLL:
         "cvs_precision_probe": ([vp, vp, i64, P(cvs_grid), P(d), P(d), P(i64)], st),
         "cvs_set_option": ([vp, ctypes.c_char_p, d], st),
         "cvs_get_option": ([vp, ctypes.c_char_p, P(d)], st),
+        "cvs_autotune": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), st, P(cvs_launch_shape)], st),
         "cvs_search_colors_noalloc": ([ctypes.c_int, vp, i64, P(cvs_grid), P(cvs_thresholds), st,
                                        P(cvs_capacity_map), vp], st),
     }
@@ -305,6 +311,17 @@ class Context:
         s = cvs_stats()
         check(lib().cvs_get_stats(self._h, ctypes.byref(s)), "cvs_get_stats")
         return {f: getattr(s, f) for f, _ in cvs_stats._fields_}
+
+    def autotune(self, rgb_dev, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
+                 gamut_mode=0, precision=PREC_FP32_RECHECK) -> dict:
+        """Time launch shapes on these colours and keep the fastest (see cvs_autotune)."""
+        g, keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        best = cvs_launch_shape()
+        n = rgb_dev.numel() // 3
+        check(lib().cvs_autotune(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g), ctypes.byref(t),
+                                 int(precision), ctypes.byref(best)), "cvs_autotune")
+        return {f: getattr(best, f) for f, _ in cvs_launch_shape._fields_}
 
     def precision_probe(self, rgb_dev, radii, angles_deg):
         g, keep = make_grid(radii, angles_deg)

@@ -1,10 +1,12 @@
 // cvs_api.cpp - host side of libcvsearch: the C ABI declared in
 // include/cvsearch.h.  Validates arguments, owns the context's scratch memory
 // and grid tables, and launches the kernels of cvs_kernels.cu.
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -95,6 +97,25 @@ struct cvs_ctx {
     cvs_stats last{};
     bool last_pending = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the search kernel
+    // autotuning: best launch shape per (grid, precision, modes, size bucket)
+    int autotune = 0;
+    std::map<std::array<int64_t, 7>, LaunchShape> tuned;
+    Acc* acc_tune = nullptr;
+    int64_t cap_acc_tune = 0;
+    unsigned long long* tune_counters = nullptr;
+    // CUDA graphs: one captured setup+search+finalize sequence per input signature
+    int use_graphs = 0;
+    struct GraphEntry {
+        std::vector<uint64_t> key;
+        cudaGraphExec_t exec = nullptr;
+        ImageDesc* d_imgs = nullptr;
+        uint64_t last_use = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    uint64_t graph_clock = 0;
+    uint64_t grid_gen = 0, scratch_gen = 0;
+    cudaStream_t cap = nullptr;  // capture stream
+    int64_t graph_launches = 0;
 };
 
 namespace {
@@ -187,10 +208,17 @@ cvs_status ensure_grid(cvs_ctx* c, const cvs_grid* g) {
     c->radii.assign(g->radii, g->radii + K);
     c->angles.assign(g->angles_deg, g->angles_deg + N);
     d.K = K;
+    ++c->grid_gen;
     return CVS_OK;
 }
 
+void drop_graphs(cvs_ctx* c);
+
 cvs_status ensure_targets(cvs_ctx* c, int64_t n) {
+    if (c->cap_tf < n || c->cap_td < n || c->cap_acc < n) {
+        drop_graphs(c);  // captured graphs point at the buffers about to be replaced
+        ++c->scratch_gen;
+    }
     if (c->cap_tf < n) {
         if (c->tf) cudaFree(c->tf);
         c->tf = nullptr;
@@ -234,8 +262,85 @@ int choose_kchunk(const cvs_ctx* c, int64_t n_targets, int K, int H) {
     return kchunk;
 }
 
+std::array<int64_t, 7> tune_key(const cvs_ctx* c, int64_t n, int prec, int clip, int list) {
+    int64_t bucket = 0;
+    while ((int64_t(1) << (bucket + 1)) <= n) ++bucket;
+    return {c->grid.K, c->grid.H, c->grid.sym, prec, clip, list, bucket};
+}
+
+// Time candidate launch shapes of the search on (a prefix of) the prepared
+// targets and return the fastest.  Accumulates into a separate buffer, so the
+// caller's accumulators are untouched.  Synchronous on `st`.
+cvs_status tune_shape(cvs_ctx* c, const SearchArgs& base, cudaStream_t st, LaunchShape* best,
+                      double* best_ms) {
+    const int K = c->grid.K, H = c->grid.H;
+    // sample: at most ~3e10 candidates per timed launch
+    int64_t n = base.n_targets;
+    const int64_t per_target = (int64_t)K * H * (c->grid.sym ? 2 : 1);
+    const int64_t cap = (int64_t)3e10 / (per_target > 0 ? per_target : 1);
+    if (n > cap) n = cap < 1 ? 1 : cap;
+    CVS_CUDA(grow(&c->acc_tune, &c->cap_acc_tune, n));
+    if (!c->tune_counters) CVS_CUDA(cudaMalloc(&c->tune_counters, 4 * sizeof(unsigned long long)));
+    std::vector<LaunchShape> cand;
+    const int auto_k = choose_kchunk(c, n, K, H);
+    const int min_k = (64 + H - 1) / H;
+    for (int block : {64, kSearchBlock}) {
+        std::vector<int> ks = {auto_k, K};
+        for (int div = 2; div <= 64; div *= 2) {
+            const int kc = (K + div - 1) / div;
+            if (kc >= min_k && kc >= 1) ks.push_back(kc);
+        }
+        std::vector<int> seen;
+        for (int kc : ks) {
+            bool dup = false;
+            for (int v : seen) dup |= v == kc;
+            if (dup) continue;
+            seen.push_back(kc);
+            LaunchShape sh;
+            sh.block = block;
+            sh.blocks_per_sm = 0;
+            sh.kchunk = kc;
+            cand.push_back(sh);
+        }
+    }
+    cudaEvent_t e0, e1;
+    CVS_CUDA(cudaEventCreate(&e0));
+    CVS_CUDA(cudaEventCreate(&e1));
+    *best_ms = 1e300;
+    cvs_status status = CVS_OK;
+    for (const LaunchShape& sh : cand) {
+        SearchArgs a = base;
+        a.n_targets = n;
+        a.acc = c->acc_tune;
+        a.work_counter = c->tune_counters;
+        a.stats = c->tune_counters + 1;
+        a.list_mode = 0;
+        a.shape = sh;
+        double ms_min = 1e300;
+        for (int rep = 0; rep < 3 && status == CVS_OK; ++rep) {
+            cudaError_t e = cudaMemsetAsync(c->tune_counters, 0, 3 * sizeof(unsigned long long), st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = launch_search(a, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) status = fail(CVS_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+            if (rep > 0 && ms < ms_min) ms_min = ms;  // first run warms up
+        }
+        if (status != CVS_OK) break;
+        if (ms_min < *best_ms) {
+            *best_ms = ms_min;
+            *best = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return status;
+}
+
 cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_precision prec,
-                      int list_mode, uint32_t target_id, cudaStream_t st) {
+                      int list_mode, uint32_t target_id, cudaStream_t st, bool capturing = false) {
     SearchArgs a{};
     a.tf = c->tf;
     a.td = c->td;
@@ -258,10 +363,24 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
     a.shape = c->shape;
     a.shape.kchunk = choose_kchunk(c, n, c->grid.K, c->grid.H);
     a.num_sms = c->num_sms;
+    // a tuned shape applies when the caller has not fixed the shape by hand
+    if (c->shape.kchunk == 0 && c->shape.blocks_per_sm == 0 && c->shape.block == kSearchBlock) {
+        const auto key = tune_key(c, n, (int)prec, a.clip, list_mode);
+        auto it = c->tuned.find(key);
+        if (it == c->tuned.end() && c->autotune && !capturing && !list_mode) {
+            LaunchShape best;
+            double ms = 0.0;
+            cvs_status ts = tune_shape(c, a, st, &best, &ms);
+            if (ts != CVS_OK) return ts;
+            it = c->tuned.emplace(key, best).first;
+        }
+        if (it != c->tuned.end()) a.shape = it->second;
+    }
+    const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     CVS_CUDA(cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), st));
-    CVS_CUDA(cudaEventRecord(c->ev0, st));
+    CVS_CUDA(cudaEventRecordWithFlags(c->ev0, st, ev_flags));
     CVS_CUDA(launch_search(a, st));
-    CVS_CUDA(cudaEventRecord(c->ev1, st));
+    CVS_CUDA(cudaEventRecordWithFlags(c->ev1, st, ev_flags));
     CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, 4 * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, st));
     cvs_stats& s = c->last;
@@ -272,6 +391,74 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
     s.symmetric = c->grid.sym;
     s.precision = (int32_t)prec;
     c->last_pending = true;
+    return CVS_OK;
+}
+
+void drop_graphs(cvs_ctx* c) {
+    for (auto& g : c->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.d_imgs) cudaFree(g.d_imgs);
+    }
+    c->graphs.clear();
+}
+
+uint64_t dbits(double x) {
+    uint64_t u;
+    std::memcpy(&u, &x, sizeof u);
+    return u;
+}
+
+// Launch a captured graph for `key` on `st`, capturing it first with
+// `enqueue(stream)` on the context's capture stream if it is not cached.
+template <class F>
+cvs_status graph_launch(cvs_ctx* c, std::vector<uint64_t> key, cudaStream_t st, F enqueue,
+                        const std::vector<ImageDesc>* imgs = nullptr) {
+    key.push_back(c->grid_gen);
+    key.push_back(c->scratch_gen);
+    cvs_ctx::GraphEntry* hit = nullptr;
+    for (auto& g : c->graphs)
+        if (g.key == key) hit = &g;
+    if (!hit) {
+        if (c->graphs.size() >= 8) {  // evict the least recently used
+            size_t lru = 0;
+            for (size_t i = 1; i < c->graphs.size(); ++i)
+                if (c->graphs[i].last_use < c->graphs[lru].last_use) lru = i;
+            if (c->graphs[lru].exec) cudaGraphExecDestroy(c->graphs[lru].exec);
+            if (c->graphs[lru].d_imgs) cudaFree(c->graphs[lru].d_imgs);
+            c->graphs.erase(c->graphs.begin() + lru);
+        }
+        cvs_ctx::GraphEntry e;
+        e.key = key;
+        if (imgs) {  // the graph's own copy of the image table
+            CVS_CUDA(cudaMalloc(&e.d_imgs, sizeof(ImageDesc) * imgs->size()));
+            CVS_CUDA(cudaMemcpy(e.d_imgs, imgs->data(), sizeof(ImageDesc) * imgs->size(),
+                                cudaMemcpyHostToDevice));
+        }
+        CVS_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        cvs_status est = enqueue(c->cap, e.d_imgs);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(c->cap, &graph);
+        if (est != CVS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            if (e.d_imgs) cudaFree(e.d_imgs);
+            return est;
+        }
+        if (ce != cudaSuccess) {
+            if (e.d_imgs) cudaFree(e.d_imgs);
+            return fail(CVS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+        }
+        ce = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            if (e.d_imgs) cudaFree(e.d_imgs);
+            return fail(CVS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+        }
+        c->graphs.push_back(e);
+        hit = &c->graphs.back();
+    }
+    hit->last_use = ++c->graph_clock;
+    CVS_CUDA(cudaGraphLaunch(hit->exec, st));
+    ++c->graph_launches;
     return CVS_OK;
 }
 
@@ -307,6 +494,7 @@ cvs_status cvs_create(cvs_ctx** out, int device) {
     if (st != CVS_OK) { delete c; return st; }
     cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->qkey, 257 * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->counters, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, 4 * sizeof(unsigned long long));
@@ -336,6 +524,10 @@ void cvs_destroy(cvs_ctx* c) {
                     c->d_rgb1, c->d_probe};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    drop_graphs(c);
+    if (c->acc_tune) cudaFree(c->acc_tune);
+    if (c->tune_counters) cudaFree(c->tune_counters);
+    if (c->cap) cudaStreamDestroy(c->cap);
     if (c->h_counters) cudaFreeHost(c->h_counters);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
@@ -360,6 +552,13 @@ cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
     } else if (!std::strcmp(name, "kchunk")) {
         if (value < 0 || value > kMaxGrid) return fail(CVS_ERR_INVALID_ARG, "kchunk in [0, %d]", kMaxGrid);
         c->shape.kchunk = (int)value;
+    } else if (!std::strcmp(name, "autotune")) {
+        if (value != 0 && value != 1) return fail(CVS_ERR_INVALID_ARG, "autotune is 0 or 1");
+        c->autotune = (int)value;
+    } else if (!std::strcmp(name, "graphs")) {
+        if (value != 0 && value != 1) return fail(CVS_ERR_INVALID_ARG, "graphs is 0 or 1");
+        c->use_graphs = (int)value;
+        if (!c->use_graphs) drop_graphs(c);
     } else {
         return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);
     }
@@ -372,6 +571,10 @@ cvs_status cvs_get_option(cvs_ctx* c, const char* name, double* value) {
     else if (!std::strcmp(name, "block")) *value = c->shape.block;
     else if (!std::strcmp(name, "blocks_per_sm")) *value = c->shape.blocks_per_sm;
     else if (!std::strcmp(name, "kchunk")) *value = c->shape.kchunk;
+    else if (!std::strcmp(name, "autotune")) *value = c->autotune;
+    else if (!std::strcmp(name, "graphs")) *value = c->use_graphs;
+    else if (!std::strcmp(name, "graph_launches")) *value = (double)c->graph_launches;
+    else if (!std::strcmp(name, "graphs_cached")) *value = (double)c->graphs.size();
     else return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);
     return CVS_OK;
 }
@@ -476,11 +679,32 @@ cvs_status cvs_search_colors(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, cons
     if (st0 != CVS_OK) return st0;
     if (n == 0) return CVS_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
-    st0 = run_search(c, n, thr, prec, 0, 0, st);
-    if (st0 != CVS_OK) return st0;
-    CVS_CUDA(launch_finalize_colors(c->acc, n, out->max_r, out->count, out->pmask, st));
-    return CVS_OK;
+    auto enqueue = [&](cudaStream_t s, ImageDesc*) -> cvs_status {
+        CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, s));
+        cvs_status r = run_search(c, n, thr, prec, 0, 0, s, s == c->cap);
+        if (r != CVS_OK) return r;
+        CVS_CUDA(launch_finalize_colors(c->acc, n, out->max_r, out->count, out->pmask, s));
+        return CVS_OK;
+    };
+    if (!c->use_graphs) return enqueue(st, nullptr);
+    if (c->autotune) {  // tune outside the capture, once
+        const auto key = tune_key(c, n, (int)(prec == CVS_PREC_FP32_RECHECK &&
+                                              c->grid.rmax > kFp32MaxRadius ? CVS_PREC_FP64 : prec),
+                                  thr->gamut_mode, 0);
+        if (!c->tuned.count(key)) {
+            st0 = enqueue(st, nullptr);
+            if (st0 != CVS_OK) return st0;
+        }
+    }
+    std::vector<uint64_t> key = {1, (uint64_t)rgb_dev, (uint64_t)n, (uint64_t)out->max_r,
+                                 (uint64_t)out->count, (uint64_t)out->pmask, dbits(thr->v_th),
+                                 dbits(thr->r_novib), thr->pattern_mask,
+                                 (uint64_t)thr->gamut_mode, (uint64_t)prec,
+                                 (uint64_t)c->shape.block, (uint64_t)c->shape.blocks_per_sm,
+                                 (uint64_t)c->shape.kchunk, dbits(c->window)};
+    st0 = graph_launch(c, key, st, enqueue);
+    if (st0 == CVS_OK) c->last_pending = true;
+    return st0;
 }
 
 cvs_status cvs_search_colors_host(cvs_ctx* c, const uint8_t* rgb_host, int64_t n,
@@ -540,12 +764,71 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
     if (st0 == CVS_OK) st0 = ensure_targets(c, total);
     if (st0 != CVS_OK) return st0;
     cudaStream_t st = (cudaStream_t)stream;
-    CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, n));
-    CVS_CUDA(cudaMemcpyAsync(c->d_imgs, h.data(), sizeof(ImageDesc) * n, cudaMemcpyHostToDevice, st));
-    CVS_CUDA(launch_setup_images(c->d_imgs, n, total, c->grid.rmax, c->tf, c->td, c->acc, st));
-    st0 = run_search(c, total, thr, prec, 0, 0, st);
+    auto enqueue = [&](cudaStream_t s, ImageDesc* d_imgs) -> cvs_status {
+        CVS_CUDA(launch_setup_images(d_imgs, n, total, c->grid.rmax, c->tf, c->td, c->acc, s));
+        cvs_status r = run_search(c, total, thr, prec, 0, 0, s, s == c->cap);
+        if (r != CVS_OK) return r;
+        CVS_CUDA(launch_finalize_images(c->acc, c->td, total, d_imgs, s));
+        return CVS_OK;
+    };
+    if (!c->use_graphs) {
+        CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, n));
+        CVS_CUDA(cudaMemcpyAsync(c->d_imgs, h.data(), sizeof(ImageDesc) * n, cudaMemcpyHostToDevice,
+                                 st));
+        return enqueue(st, c->d_imgs);
+    }
+    std::vector<uint64_t> key = {2, (uint64_t)n, dbits(thr->v_th), dbits(thr->r_novib),
+                                 thr->pattern_mask, (uint64_t)thr->gamut_mode, (uint64_t)prec,
+                                 (uint64_t)c->shape.block, (uint64_t)c->shape.blocks_per_sm,
+                                 (uint64_t)c->shape.kchunk, dbits(c->window)};
+    for (const ImageDesc& d : h) {
+        key.insert(key.end(), {(uint64_t)d.rgb, (uint64_t)d.pitch, (uint64_t)d.width,
+                               (uint64_t)d.height, (uint64_t)d.max_r, (uint64_t)d.count,
+                               (uint64_t)d.pmask});
+    }
+    st0 = graph_launch(c, key, st, enqueue, &h);
+    if (st0 == CVS_OK) c->last_pending = true;
+    return st0;
+}
+
+cvs_status cvs_autotune(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, const cvs_grid* grid,
+                        const cvs_thresholds* thr, cvs_precision prec, cvs_launch_shape* best) {
+    if (!c || !rgb_dev || !best) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (n <= 0) return fail(CVS_ERR_INVALID_ARG, "n must be > 0");
+    if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
+        return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    cvs_status st0 = check_grid(grid);
+    if (st0 == CVS_OK) st0 = check_thresholds(thr);
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = ensure_targets(c, n);
     if (st0 != CVS_OK) return st0;
-    CVS_CUDA(launch_finalize_images(c->acc, c->td, total, c->d_imgs, st));
+    cudaStream_t st = c->own;
+    CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
+    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
+    SearchArgs a{};
+    a.tf = c->tf;
+    a.td = c->td;
+    a.acc = c->acc;
+    a.n_targets = n;
+    a.grid = c->grid;
+    a.qkey = c->qkey;
+    thresholds_to_int(thr, &a.hi_min, &a.lo_max);
+    a.mask2 = thr->pattern_mask << 1;
+    a.clip = thr->gamut_mode;
+    a.half_w = (float)(0.5 - c->window);
+    a.prec = (int32_t)prec;
+    a.num_sms = c->num_sms;
+    LaunchShape sh;
+    double ms = 0.0;
+    st0 = tune_shape(c, a, st, &sh, &ms);
+    if (st0 != CVS_OK) return st0;
+    c->tuned[tune_key(c, n, (int)prec, a.clip, 0)] = sh;
+    best->block = sh.block;
+    best->blocks_per_sm = sh.blocks_per_sm;
+    best->kchunk = sh.kchunk;
+    best->reserved = 0;
+    best->ms = ms;
     return CVS_OK;
 }
 

@@ -350,3 +350,62 @@ def test_large_radii_run_in_fp64_and_match(ctx, torch_cuda):
     ctx.synchronize()
     assert ctx.stats()["precision"] == binding.PREC_FP64
     assert_maps_equal(got, exp, "large radii")
+
+
+# ------------------------------------------------------------------ batching machinery
+def test_autotune_keeps_results(ctx, torch_cuda):
+    torch = torch_cuda
+    rgb = cube_sample(300, seed=31)
+    radii, ang = W.grid(2)
+    exp = oracle_colors(rgb, radii, ang)
+    best = ctx.autotune(dev(torch, rgb), radii, ang, 50, 0.5)
+    assert best["block"] in (64, 128) and 1 <= best["kchunk"] <= len(radii) and best["ms"] > 0
+    assert_maps_equal(gpu_colors(ctx, torch, rgb, radii, ang, 0), exp, "after autotune")
+
+
+def test_lazy_autotune_option(torch_cuda):
+    torch = torch_cuda
+    c = cvs.Context(0)
+    c.set_option("autotune", 1)
+    rgb = cube_sample(64, seed=32)
+    radii, ang = W.grid(3)
+    exp = oracle_colors(rgb, radii, ang)
+    for _ in range(2):
+        assert_maps_equal(gpu_colors(c, torch, rgb, radii, ang, 0), exp, "lazy autotune")
+    c.close()
+
+
+def test_graph_replay_colours_and_images(torch_cuda):
+    torch = torch_cuda
+    c = cvs.Context(0)
+    c.set_option("graphs", 1)
+    radii, ang = W.grid(3)
+    a, b = cube_sample(120, seed=33), cube_sample(120, seed=34)
+    d = dev(torch, a)
+    out = (torch.empty(len(a), dtype=torch.float32, device="cuda"),
+           torch.empty(len(a), dtype=torch.int32, device="cuda"),
+           torch.empty(len(a), dtype=torch.uint8, device="cuda"))
+    c.search_colors(d, radii, ang, 50, 0.5, out=out)
+    c.synchronize()
+    assert_maps_equal(tuple(x.cpu().numpy() for x in out), oracle_colors(a, radii, ang), "graph 1")
+    d.copy_(torch.from_numpy(b))  # same buffers, new contents: the replay reads them
+    c.search_colors(d, radii, ang, 50, 0.5, out=out)
+    c.synchronize()
+    assert_maps_equal(tuple(x.cpu().numpy() for x in out), oracle_colors(b, radii, ang), "graph 2")
+    assert c.get_option("graph_launches") == 2 and c.get_option("graphs_cached") == 1
+    st = c.stats()
+    assert st["targets"] == len(b) and st["search_ms"] > 0
+    # images through a graph, twice
+    imgs = [dev(torch, im) for im in small_images()]
+    m1 = [tuple(x.cpu().numpy().copy() for x in m) for m in c.search_images(imgs, radii, ang, 50, 0.5)]
+    c.synchronize()
+    m2 = [tuple(x.cpu().numpy() for x in m) for m in c.search_images(imgs, radii, ang, 50, 0.5)]
+    c.synchronize()
+    ref = cvs.Context(0)
+    m3 = [tuple(x.cpu().numpy() for x in m) for m in ref.search_images(imgs, radii, ang, 50, 0.5)]
+    torch.cuda.synchronize()
+    for x, y, z in zip(m1, m2, m3):
+        for p, q, r in zip(x, y, z):
+            assert np.array_equal(p, r) and np.array_equal(q, r)
+    ref.close()
+    c.close()
