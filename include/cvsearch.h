@@ -216,6 +216,35 @@ cvs_status cvs_search_images(cvs_ctx* ctx, const cvs_image* batch, int32_t n,
                              cvs_precision prec, const cvs_capacity_map* maps,
                              void* stream);
 
+/* ------------------------------------------------ colour-keyed memoisation
+ * A pixel's result is a pure function of its colour (and of the grid and
+ * thresholds).  A capacity table holds the per-colour results of all 2^24
+ * 8-bit sRGB colours, computed once by the per-colour search; afterwards the
+ * maps of any image are a gather from the table, identical to the maps of
+ * cvs_search_images.  The table lives on the context's device (2^24 x 9 bytes
+ * plus a small image table) and is independent of the context afterwards. */
+typedef struct cvs_lut cvs_lut;
+
+/* Search all 2^24 colours on `grid` with `thr` and store the results in a new
+ * table *out (owned by the caller, released with cvs_lut_destroy).  Runs in
+ * chunks of 2^22 colours on `stream` and returns when the table is complete. */
+cvs_status cvs_lut_build(cvs_ctx* ctx, const cvs_grid* grid, const cvs_thresholds* thr,
+                         cvs_precision prec, cvs_lut** out, void* stream);
+
+/* Per-pixel maps of a batch of images from the table (same layout and
+ * ownership as cvs_search_images).  Asynchronous on `stream`; one table
+ * should be used from one stream at a time. */
+cvs_status cvs_lut_lookup_images(cvs_lut* lut, const cvs_image* batch, int32_t n,
+                                 const cvs_capacity_map* maps, void* stream);
+
+/* Per-colour results of n colours (rgb_dev: device, 3n bytes) from the table.
+ * Asynchronous on `stream`. */
+cvs_status cvs_lut_lookup_colors(cvs_lut* lut, const uint8_t* rgb_dev, int64_t n,
+                                 const cvs_capacity_map* out, void* stream);
+
+/* Release a table (waits for the device). */
+void cvs_lut_destroy(cvs_lut* lut);
+
 /* Wait for the context's work on `stream` and report any device error or
  * device-side timeout.  Fills the counters of the last search. */
 cvs_status cvs_synchronize(cvs_ctx* ctx, void* stream);

@@ -118,6 +118,10 @@ def lib() -> ctypes.CDLL:
         "cvs_precision_probe": ([vp, vp, i64, P(cvs_grid), P(d), P(d), P(i64)], st),
         "cvs_set_option": ([vp, ctypes.c_char_p, d], st),
         "cvs_get_option": ([vp, ctypes.c_char_p, P(d)], st),
+        "cvs_lut_build": ([vp, P(cvs_grid), P(cvs_thresholds), st, P(vp), vp], st),
+        "cvs_lut_lookup_images": ([vp, P(cvs_image), i32, P(cvs_capacity_map), vp], st),
+        "cvs_lut_lookup_colors": ([vp, vp, i64, P(cvs_capacity_map), vp], st),
+        "cvs_lut_destroy": ([vp], None),
         "cvs_autotune": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), st, P(cvs_launch_shape)], st),
         "cvs_search_colors_noalloc": ([ctypes.c_int, vp, i64, P(cvs_grid), P(cvs_thresholds), st,
                                        P(cvs_capacity_map), vp], st),
@@ -323,6 +327,16 @@ class Context:
                                  int(precision), ctypes.byref(best)), "cvs_autotune")
         return {f: getattr(best, f) for f, _ in cvs_launch_shape._fields_}
 
+    def build_lut(self, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0,
+                  precision=PREC_FP32_RECHECK, stream=None) -> "CapacityTable":
+        """Capacity table of all 2^24 colours for this grid and thresholds."""
+        g, keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        h = ctypes.c_void_p()
+        check(lib().cvs_lut_build(self._h, ctypes.byref(g), ctypes.byref(t), int(precision),
+                                  ctypes.byref(h), _stream_ptr(stream)), "cvs_lut_build")
+        return CapacityTable(h)
+
     def precision_probe(self, rgb_dev, radii, angles_deg):
         g, keep = make_grid(radii, angles_deg)
         e1, e2, nw = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
@@ -331,3 +345,55 @@ class Context:
                                         ctypes.byref(e1), ctypes.byref(e2), ctypes.byref(nw)),
               "cvs_precision_probe")
         return {"max_code_err": e1.value, "max_lin_err": e2.value, "n_wrong_codes": nw.value}
+
+
+class CapacityTable:
+    """Per-colour results of all 2^24 colours (cvs_lut); images become gathers."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def close(self):
+        if self._h:
+            lib().cvs_lut_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lookup_colors(self, rgb_dev, out=None, stream=None):
+        import torch
+        n = rgb_dev.numel() // 3
+        dev = rgb_dev.device
+        if out is None:
+            out = (torch.empty(n, dtype=torch.float32, device=dev),
+                   torch.empty(n, dtype=torch.int32, device=dev),
+                   torch.empty(n, dtype=torch.uint8, device=dev))
+        m = cvs_capacity_map(out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
+        check(lib().cvs_lut_lookup_colors(self._h, rgb_dev.data_ptr(), n, ctypes.byref(m),
+                                          _stream_ptr(stream)), "cvs_lut_lookup_colors")
+        return out
+
+    def lookup_images(self, images, maps=None, stream=None):
+        import torch
+        n = len(images)
+        descs = (cvs_image * n)()
+        cmaps = (cvs_capacity_map * n)()
+        if maps is None:
+            maps = [(torch.empty(im.shape[:2], dtype=torch.float32, device=im.device),
+                     torch.empty(im.shape[:2], dtype=torch.int32, device=im.device),
+                     torch.empty(im.shape[:2], dtype=torch.uint8, device=im.device))
+                    for im in images]
+        for i, im in enumerate(images):
+            if im.dtype != torch.uint8 or im.dim() != 3 or im.shape[2] != 3 or im.stride(2) != 1 \
+                    or im.stride(1) != 3:
+                raise ValueError("images must be (H, W, 3) uint8 with packed pixels")
+            descs[i] = cvs_image(im.data_ptr(), im.shape[1], im.shape[0], im.stride(0))
+            cmaps[i] = cvs_capacity_map(maps[i][0].data_ptr(), maps[i][1].data_ptr(),
+                                        maps[i][2].data_ptr())
+        check(lib().cvs_lut_lookup_images(self._h, descs, n, cmaps, _stream_ptr(stream)),
+              "cvs_lut_lookup_images")
+        return maps

@@ -832,6 +832,126 @@ cvs_status cvs_autotune(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, const cvs
     return CVS_OK;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------ capacity table
+struct cvs_lut {
+    int device = 0;
+    uint64_t* entry = nullptr;   // 2^24: (count << 32) | max_r bits
+    uint8_t* pmask = nullptr;    // 2^24
+    ImageDesc* d_imgs = nullptr;
+    int64_t* d_block_first = nullptr;
+    int64_t cap_imgs = 0, cap_bf = 0;
+};
+
+extern "C" {
+
+cvs_status cvs_lut_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds* thr,
+                         cvs_precision prec, cvs_lut** out, void* stream) {
+    if (!c || !out) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
+        return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    cvs_status st0 = check_grid(grid);
+    if (st0 == CVS_OK) st0 = check_thresholds(thr);
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    constexpr int64_t kColours = int64_t(1) << 24, kChunk = int64_t(1) << 22;
+    if (st0 == CVS_OK) st0 = ensure_targets(c, kChunk);
+    if (st0 != CVS_OK) return st0;
+    cvs_lut* L = new cvs_lut();
+    L->device = c->device;
+    uint8_t* rgb = nullptr;
+    cudaError_t e = cudaMalloc(&L->entry, sizeof(uint64_t) * kColours);
+    if (e == cudaSuccess) e = cudaMalloc(&L->pmask, kColours);
+    if (e == cudaSuccess) e = cudaMalloc(&rgb, 3 * kChunk);
+    if (e != cudaSuccess) {
+        if (rgb) cudaFree(rgb);
+        cvs_lut_destroy(L);
+        return fail(e == cudaErrorMemoryAllocation ? CVS_ERR_NO_MEMORY : CVS_ERR_CUDA,
+                    "cvs_lut_build: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int64_t first = 0; first < kColours && st0 == CVS_OK; first += kChunk) {
+        e = launch_rgb_iota(rgb, first, kChunk, st);
+        if (e == cudaSuccess) e = launch_setup_colors(rgb, kChunk, c->grid.rmax, c->tf, c->td, c->acc, st);
+        if (e != cudaSuccess) { st0 = fail(CVS_ERR_CUDA, "cvs_lut_build: %s", cudaGetErrorString(e)); break; }
+        st0 = run_search(c, kChunk, thr, prec, 0, 0, st);
+        if (st0 != CVS_OK) break;
+        e = launch_lut_pack(c->acc, kChunk, L->entry + first, L->pmask + first, st);
+        if (e != cudaSuccess) st0 = fail(CVS_ERR_CUDA, "cvs_lut_build: %s", cudaGetErrorString(e));
+    }
+    // the colour buffer is released once the stream has consumed it
+    cudaError_t se = cudaStreamSynchronize(st);
+    cudaFree(rgb);
+    if (st0 == CVS_OK && se != cudaSuccess)
+        st0 = fail(CVS_ERR_CUDA, "cvs_lut_build: %s", cudaGetErrorString(se));
+    if (st0 != CVS_OK) {
+        cvs_lut_destroy(L);
+        return st0;
+    }
+    collect_stats(c);
+    c->last.candidates = kColours * (int64_t)c->grid.K * c->grid.N;
+    c->last.targets = kColours;
+    *out = L;
+    return CVS_OK;
+}
+
+void cvs_lut_destroy(cvs_lut* L) {
+    if (!L) return;
+    cudaSetDevice(L->device);
+    cudaDeviceSynchronize();
+    void* ptrs[] = {L->entry, L->pmask, L->d_imgs, L->d_block_first};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete L;
+}
+
+cvs_status cvs_lut_lookup_colors(cvs_lut* L, const uint8_t* rgb_dev, int64_t n,
+                                 const cvs_capacity_map* out, void* stream) {
+    if (!L || !out) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0) return fail(CVS_ERR_INVALID_ARG, "n must be >= 0");
+    if (n > 0 && (!rgb_dev || !out->max_r || !out->count || !out->pmask))
+        return fail(CVS_ERR_INVALID_ARG, "NULL device buffer");
+    CVS_CUDA(cudaSetDevice(L->device));
+    CVS_CUDA(launch_lut_gather_colors(rgb_dev, n, L->entry, L->pmask, out->max_r, out->count,
+                                      out->pmask, (cudaStream_t)stream));
+    return CVS_OK;
+}
+
+cvs_status cvs_lut_lookup_images(cvs_lut* L, const cvs_image* batch, int32_t n,
+                                 const cvs_capacity_map* maps, void* stream) {
+    if (!L || !batch || !maps) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (n <= 0 || n > (1 << 20)) return fail(CVS_ERR_INVALID_ARG, "n must be in [1, 2^20]");
+    std::vector<ImageDesc> h(n);
+    std::vector<int64_t> bf(n);
+    int64_t blocks = 0, total = 0;
+    for (int i = 0; i < n; ++i) {
+        const cvs_image& im = batch[i];
+        if (!im.rgb || im.width <= 0 || im.height <= 0 || im.pitch_bytes < 3LL * im.width)
+            return fail(CVS_ERR_INVALID_ARG, "image %d: bad pointer, size or pitch", i);
+        if (!maps[i].max_r || !maps[i].count || !maps[i].pmask)
+            return fail(CVS_ERR_INVALID_ARG, "map %d: NULL buffer", i);
+        const int64_t px = (int64_t)im.width * im.height;
+        h[i] = ImageDesc{im.rgb, im.pitch_bytes, im.width, im.height, total,
+                         maps[i].max_r, maps[i].count, maps[i].pmask};
+        bf[i] = blocks;
+        blocks += (px + kGatherBlock - 1) / kGatherBlock;
+        total += px;
+    }
+    if (blocks > 0x7FFFFFFFLL) return fail(CVS_ERR_INVALID_ARG, "batch too large for one launch");
+    CVS_CUDA(cudaSetDevice(L->device));
+    CVS_CUDA(grow(&L->d_imgs, &L->cap_imgs, n));
+    CVS_CUDA(grow(&L->d_block_first, &L->cap_bf, n));
+    cudaStream_t st = (cudaStream_t)stream;
+    CVS_CUDA(cudaMemcpyAsync(L->d_imgs, h.data(), sizeof(ImageDesc) * n, cudaMemcpyHostToDevice, st));
+    CVS_CUDA(cudaMemcpyAsync(L->d_block_first, bf.data(), sizeof(int64_t) * n,
+                             cudaMemcpyHostToDevice, st));
+    CVS_CUDA(launch_lut_gather_images(L->d_imgs, L->d_block_first, n, blocks, L->entry, L->pmask,
+                                      st));
+    return CVS_OK;
+}
+
 cvs_status cvs_synchronize(cvs_ctx* c, void* stream) {
     if (!c) return fail(CVS_ERR_INVALID_ARG, "NULL context");
     cvs_status st0 = set_device(c);

@@ -99,6 +99,17 @@ cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int
                                    unsigned int* max_v_err_bits, unsigned int* max_lin_err_bits,
                                    unsigned long long* n_wrong, int num_sms, cudaStream_t st);
 cudaError_t copy_qkeys_to(long long* dst, cudaStream_t st);
+// Capacity table (all 2^24 colours).
+constexpr int kGatherBlock = 256;
+cudaError_t launch_rgb_iota(uint8_t* rgb, int64_t first, int64_t n, cudaStream_t st);
+cudaError_t launch_lut_pack(const Acc* acc, int64_t n, uint64_t* entry, uint8_t* pmask,
+                            cudaStream_t st);
+cudaError_t launch_lut_gather_images(const ImageDesc* imgs, const int64_t* block_first,
+                                     int n_imgs, int64_t total_blocks, const uint64_t* entry,
+                                     const uint8_t* pmask, cudaStream_t st);
+cudaError_t launch_lut_gather_colors(const uint8_t* rgb, int64_t n, const uint64_t* entry,
+                                     const uint8_t* pmask, float* max_r, int32_t* count,
+                                     uint8_t* pm, cudaStream_t st);
 // Sets the thread-local text returned by cvs_last_error().
 void set_error_message(const char* msg);
 size_t target_f32_size();

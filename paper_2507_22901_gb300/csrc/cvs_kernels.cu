@@ -822,6 +822,72 @@ __global__ void k_precision_probe(const TargetF32* __restrict__ tf, const Target
     }
 }
 
+// ------------------------------------------------------------ capacity table
+// Colours first .. first+n-1 of the 2^24-colour space as (R, G, B) bytes,
+// colour index = (R << 16) | (G << 8) | B.
+__global__ void k_rgb_iota(uint8_t* __restrict__ rgb, int64_t first, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t v = (uint32_t)(first + i);
+    rgb[3 * i] = (uint8_t)(v >> 16);
+    rgb[3 * i + 1] = (uint8_t)(v >> 8);
+    rgb[3 * i + 2] = (uint8_t)v;
+}
+
+// Pack per-colour results into the table: entry = (count << 32) | max_r bits.
+__global__ void k_lut_pack(const Acc* __restrict__ acc, int64_t n, uint64_t* __restrict__ entry,
+                           uint8_t* __restrict__ pmask) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Acc a = acc[i];
+    entry[i] = ((uint64_t)(uint32_t)a.count << 32) | (uint32_t)a.rmax_bits;
+    pmask[i] = (uint8_t)a.pmask;
+}
+
+// Per-pixel maps of a batch of images from the table.  Blocks never straddle
+// images: block b belongs to the image whose block range holds b.
+__global__ void __launch_bounds__(256) k_lut_gather_images(const ImageDesc* __restrict__ imgs,
+                                                           const int64_t* __restrict__ block_first,
+                                                           int n_imgs,
+                                                           const uint64_t* __restrict__ entry,
+                                                           const uint8_t* __restrict__ pmask) {
+    __shared__ int s_img;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_imgs - 1;  // largest i with block_first[i] <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (block_first[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_img = lo;
+    }
+    __syncthreads();
+    const ImageDesc im = imgs[s_img];
+    const int64_t p = ((int64_t)blockIdx.x - block_first[s_img]) * blockDim.x + threadIdx.x;
+    const int64_t npx = (int64_t)im.width * im.height;
+    if (p >= npx) return;
+    const int64_t y = p / im.width, x = p - y * im.width;
+    const uint8_t* px = im.rgb + y * im.pitch + 3 * x;
+    const uint32_t key = ((uint32_t)px[0] << 16) | ((uint32_t)px[1] << 8) | px[2];
+    const uint64_t e = __ldg(entry + key);
+    im.max_r[p] = __uint_as_float((uint32_t)e);
+    im.count[p] = (int32_t)(e >> 32);
+    im.pmask[p] = __ldg(pmask + key);
+}
+
+// Per-colour results of a colour list from the table.
+__global__ void k_lut_gather_colors(const uint8_t* __restrict__ rgb, int64_t n,
+                                    const uint64_t* __restrict__ entry,
+                                    const uint8_t* __restrict__ pmask, float* max_r,
+                                    int32_t* count, uint8_t* pm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t key = ((uint32_t)rgb[3 * i] << 16) | ((uint32_t)rgb[3 * i + 1] << 8) | rgb[3 * i + 2];
+    const uint64_t e = __ldg(entry + key);
+    max_r[i] = __uint_as_float((uint32_t)e);
+    count[i] = (int32_t)(e >> 32);
+    pm[i] = __ldg(pmask + key);
+}
+
 __global__ void k_qkeys(long long* dst) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 257) dst[i] = dkey(g_qthr[i]);
@@ -921,6 +987,36 @@ cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int
     if (n <= 0) return cudaSuccess;
     k_precision_probe<<<num_sms * 8, 256, 0, st>>>(tf, td, n, g, qkey, max_v_err_bits,
                                                     max_lin_err_bits, n_wrong);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rgb_iota(uint8_t* rgb, int64_t first, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_rgb_iota<<<blocks_for(n, 256), 256, 0, st>>>(rgb, first, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lut_pack(const Acc* acc, int64_t n, uint64_t* entry, uint8_t* pmask,
+                            cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_lut_pack<<<blocks_for(n, 256), 256, 0, st>>>(acc, n, entry, pmask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lut_gather_images(const ImageDesc* imgs, const int64_t* block_first,
+                                     int n_imgs, int64_t total_blocks, const uint64_t* entry,
+                                     const uint8_t* pmask, cudaStream_t st) {
+    if (total_blocks <= 0) return cudaSuccess;
+    k_lut_gather_images<<<(unsigned)total_blocks, kGatherBlock, 0, st>>>(imgs, block_first, n_imgs,
+                                                                        entry, pmask);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lut_gather_colors(const uint8_t* rgb, int64_t n, const uint64_t* entry,
+                                     const uint8_t* pmask, float* max_r, int32_t* count,
+                                     uint8_t* pm, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_lut_gather_colors<<<blocks_for(n, 256), 256, 0, st>>>(rgb, n, entry, pmask, max_r, count, pm);
     return cudaGetLastError();
 }
 

@@ -409,3 +409,38 @@ def test_graph_replay_colours_and_images(torch_cuda):
             assert np.array_equal(p, r) and np.array_equal(q, r)
     ref.close()
     c.close()
+
+
+# ------------------------------------------------------------------ capacity table
+@pytest.fixture(scope="module")
+def lut3(ctx):
+    radii, ang = W.grid(3)
+    t = ctx.build_lut(radii, ang, 50, 0.5)
+    yield t
+    t.close()
+
+
+def test_lut_colours_match_oracle(lut3, torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(41)
+    rgb = np.concatenate([rng.integers(0, 256, (1500, 3)), W.precision_colors()[3072:3172],
+                          [[0, 0, 0], [255, 255, 255], [255, 0, 0], [1, 254, 3]]]).astype(np.uint8)
+    radii, ang = W.grid(3)
+    out = lut3.lookup_colors(dev(torch, rgb))
+    torch.cuda.synchronize()
+    assert_maps_equal(tuple(x.cpu().numpy() for x in out), oracle_colors(rgb, radii, ang), "lut")
+
+
+def test_lut_images_match_direct_search(ctx, lut3, torch_cuda):
+    torch = torch_cuda
+    radii, ang = W.grid(3)
+    small = [dev(torch, im) for im in small_images()]
+    params = W.image_params(3, seed=0)
+    big = [W.render_image_torch(w, h, terms, ns) for w, h, terms, ns in params]
+    imgs = small + big
+    direct = ctx.search_images(imgs, radii, ang, 50, 0.5)
+    via = lut3.lookup_images(imgs)
+    torch.cuda.synchronize()
+    for d, v in zip(direct, via):
+        for a, b in zip(d, v):
+            assert torch.equal(a, b)
