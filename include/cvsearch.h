@@ -245,6 +245,90 @@ cvs_status cvs_lut_lookup_colors(cvs_lut* lut, const uint8_t* rgb_dev, int64_t n
 /* Release a table (waits for the device). */
 void cvs_lut_destroy(cvs_lut* lut);
 
+/* ------------------------------------------------------------ serving loop
+ * A request loop with continuous batching (the paper has no serving loop;
+ * this serves its per-pixel search to a stream of frames).  Frames are
+ * submitted from host memory at any time; a scheduler thread admits them in
+ * arrival order as soon as one of max_inflight slots (each a context and a
+ * stream) is free and the device arena has room for the frame and its maps,
+ * so frames that arrive while others are on the GPU overlap with them.  The
+ * maps of a finished frame stay resident in device memory until released.
+ * All device memory (arena, slot scratch for frames up to max_pixels, and the
+ * capacity table when use_table = 1) is allocated by cvs_server_create, never
+ * during serving.  Host waits are bounded by the caller's timeout. */
+typedef struct cvs_server cvs_server;
+
+typedef struct {
+    int32_t device;
+    int32_t max_inflight;        /* concurrent frames on the device, 1..16 */
+    int64_t max_pixels;          /* largest frame accepted (width * height) */
+    int64_t mem_budget_bytes;    /* device arena for frames and maps (12 bytes per pixel) */
+    int32_t use_table;           /* 1: answer from a capacity table built at creation */
+    int32_t reserved;
+} cvs_server_config;
+
+typedef enum {
+    CVS_REQ_QUEUED = 0,
+    CVS_REQ_RUNNING = 1,
+    CVS_REQ_DONE = 2,
+    CVS_REQ_FAILED = 3,
+    CVS_REQ_UNKNOWN = 4
+} cvs_request_state;
+
+typedef struct {
+    int64_t submitted, completed, failed, queued, inflight;
+    int64_t bytes_in_use, peak_bytes_in_use;   /* arena */
+    double p50_ms, p99_ms, mean_ms, max_ms;    /* submit -> maps resident, completed frames */
+    double frames_per_s;                       /* completed / (last completion - first submit) */
+} cvs_server_stats;
+
+/* Create a server for one grid, threshold set and precision (copied).
+ * Synchronous; with use_table it first builds the capacity table. */
+cvs_status cvs_server_create(cvs_server** server, const cvs_server_config* cfg,
+                             const cvs_grid* grid, const cvs_thresholds* thr, cvs_precision prec);
+
+/* Stop the scheduler, wait for the device and free everything. */
+void cvs_server_destroy(cvs_server* server);
+
+/* Queue a frame (rgb_host: host, HWC bytes, row y at rgb_host + y * pitch).
+ * The caller keeps the host frame unchanged until the request is done.
+ * *ticket identifies the request.  Never blocks on the device. */
+cvs_status cvs_server_submit(cvs_server* server, const uint8_t* rgb_host, int32_t width,
+                             int32_t height, int64_t pitch_bytes, uint64_t* ticket);
+
+/* Current cvs_request_state of a ticket. */
+cvs_status cvs_server_state(cvs_server* server, uint64_t ticket, int32_t* state);
+
+/* Wait up to timeout_ms for a request to finish: CVS_OK when its maps are
+ * resident, CVS_ERR_TIMEOUT if it is still queued or running at the
+ * deadline, the request's error if it failed. */
+cvs_status cvs_server_wait(cvs_server* server, uint64_t ticket, int32_t timeout_ms);
+
+/* Device pointers of a finished request's maps (width * height entries each,
+ * row-major), valid until cvs_server_release. */
+cvs_status cvs_server_result(cvs_server* server, uint64_t ticket, cvs_capacity_map* maps,
+                             int32_t* width, int32_t* height);
+
+/* Copy a finished request's maps to host buffers (width * height entries
+ * each).  Synchronous. */
+cvs_status cvs_server_copy_result(cvs_server* server, uint64_t ticket, float* max_r_host,
+                                  int32_t* count_host, uint8_t* pmask_host);
+
+/* Drop a request: frees its device memory (a queued request is cancelled; a
+ * running one must be waited for first, else CVS_ERR_INVALID_ARG). */
+cvs_status cvs_server_release(cvs_server* server, uint64_t ticket);
+
+/* Counters and latency percentiles of the requests so far. */
+cvs_status cvs_server_get_stats(cvs_server* server, cvs_server_stats* out);
+
+/* Allocate ahead of time what later searches on this context need: the grid
+ * tables of `grid` (may be NULL), scratch for up to max_targets colours or
+ * pixels per search, and the image table for batches of up to max_images
+ * images, so that those searches make no device allocation (a device
+ * allocation synchronises the whole device).  Synchronous. */
+cvs_status cvs_reserve(cvs_ctx* ctx, const cvs_grid* grid, int64_t max_targets,
+                       int32_t max_images);
+
 /* Wait for the context's work on `stream` and report any device error or
  * device-side timeout.  Fills the counters of the last search. */
 cvs_status cvs_synchronize(cvs_ctx* ctx, void* stream);

@@ -8,7 +8,8 @@ entry point raises.
 """
 from ._build import build  # noqa: F401
 from .binding import (  # noqa: F401
-    PAIR_DTYPE, PREC_FP32_RECHECK, PREC_FP64, Context, CvsError, header_functions, lib,
+    PAIR_DTYPE, PREC_FP32_RECHECK, PREC_FP64, CapacityTable, Context, CvsError, Server,
+    header_functions, lib,
     signal_bounds,
 )
 

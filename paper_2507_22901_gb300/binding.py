@@ -71,6 +71,23 @@ class cvs_launch_shape(ctypes.Structure):
                 ("kchunk", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ms", ctypes.c_double)]
 
 
+class cvs_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("max_pixels", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_int64),
+                ("use_table", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class cvs_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("inflight", ctypes.c_int64), ("bytes_in_use", ctypes.c_int64),
+                ("peak_bytes_in_use", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("frames_per_s", ctypes.c_double)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_UNKNOWN = 0, 1, 2, 3, 4
+
 assert ctypes.sizeof(cvs_pair) == 16 and PAIR_DTYPE.itemsize == 16
 
 _lib = None
@@ -122,6 +139,16 @@ def lib() -> ctypes.CDLL:
         "cvs_lut_lookup_images": ([vp, P(cvs_image), i32, P(cvs_capacity_map), vp], st),
         "cvs_lut_lookup_colors": ([vp, vp, i64, P(cvs_capacity_map), vp], st),
         "cvs_lut_destroy": ([vp], None),
+        "cvs_reserve": ([vp, P(cvs_grid), i64, i32], st),
+        "cvs_server_create": ([P(vp), P(cvs_server_config), P(cvs_grid), P(cvs_thresholds), st], st),
+        "cvs_server_destroy": ([vp], None),
+        "cvs_server_submit": ([vp, vp, i32, i32, i64, P(ctypes.c_uint64)], st),
+        "cvs_server_state": ([vp, ctypes.c_uint64, P(i32)], st),
+        "cvs_server_wait": ([vp, ctypes.c_uint64, i32], st),
+        "cvs_server_result": ([vp, ctypes.c_uint64, P(cvs_capacity_map), P(i32), P(i32)], st),
+        "cvs_server_copy_result": ([vp, ctypes.c_uint64, vp, vp, vp], st),
+        "cvs_server_release": ([vp, ctypes.c_uint64], st),
+        "cvs_server_get_stats": ([vp, P(cvs_server_stats)], st),
         "cvs_autotune": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), st, P(cvs_launch_shape)], st),
         "cvs_search_colors_noalloc": ([ctypes.c_int, vp, i64, P(cvs_grid), P(cvs_thresholds), st,
                                        P(cvs_capacity_map), vp], st),
@@ -397,3 +424,67 @@ class CapacityTable:
         check(lib().cvs_lut_lookup_images(self._h, descs, n, cmaps, _stream_ptr(stream)),
               "cvs_lut_lookup_images")
         return maps
+
+
+class Server:
+    """Continuous-batching request loop (cvs_server): submit host frames, wait,
+    read the device-resident maps, release."""
+
+    def __init__(self, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0,
+                 precision=PREC_FP32_RECHECK, device=0, max_inflight=2,
+                 max_pixels=7680 * 4320, mem_budget_bytes=4 << 30, use_table=False):
+        g, self._keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        cfg = cvs_server_config(int(device), int(max_inflight), int(max_pixels),
+                                int(mem_budget_bytes), int(bool(use_table)), 0)
+        self._h = ctypes.c_void_p()
+        self._frames = {}
+        check(lib().cvs_server_create(ctypes.byref(self._h), ctypes.byref(cfg), ctypes.byref(g),
+                                      ctypes.byref(t), int(precision)), "cvs_server_create")
+
+    def close(self):
+        if self._h:
+            lib().cvs_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._frames.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, frame) -> int:
+        """Queue an (H, W, 3) uint8 host frame; it is kept alive until released."""
+        frame = np.ascontiguousarray(frame, np.uint8)
+        h, w = frame.shape[:2]
+        tk = ctypes.c_uint64()
+        check(lib().cvs_server_submit(self._h, frame.ctypes.data, w, h, w * 3, ctypes.byref(tk)),
+              "cvs_server_submit")
+        self._frames[tk.value] = frame
+        return tk.value
+
+    def state(self, ticket) -> int:
+        s = ctypes.c_int32()
+        check(lib().cvs_server_state(self._h, ticket, ctypes.byref(s)), "cvs_server_state")
+        return s.value
+
+    def wait(self, ticket, timeout_ms=60000):
+        check(lib().cvs_server_wait(self._h, ticket, int(timeout_ms)), "cvs_server_wait")
+
+    def result_host(self, ticket):
+        frame = self._frames[ticket]
+        h, w = frame.shape[:2]
+        out = (np.empty((h, w), np.float32), np.empty((h, w), np.int32), np.empty((h, w), np.uint8))
+        check(lib().cvs_server_copy_result(self._h, ticket, out[0].ctypes.data, out[1].ctypes.data,
+                                           out[2].ctypes.data), "cvs_server_copy_result")
+        return out
+
+    def release(self, ticket):
+        check(lib().cvs_server_release(self._h, ticket), "cvs_server_release")
+        self._frames.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = cvs_server_stats()
+        check(lib().cvs_server_get_stats(self._h, ctypes.byref(s)), "cvs_server_get_stats")
+        return {f: getattr(s, f) for f, _ in cvs_server_stats._fields_}

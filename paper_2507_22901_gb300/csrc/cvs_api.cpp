@@ -839,9 +839,6 @@ struct cvs_lut {
     int device = 0;
     uint64_t* entry = nullptr;   // 2^24: (count << 32) | max_r bits
     uint8_t* pmask = nullptr;    // 2^24
-    ImageDesc* d_imgs = nullptr;
-    int64_t* d_block_first = nullptr;
-    int64_t cap_imgs = 0, cap_bf = 0;
 };
 
 extern "C" {
@@ -901,7 +898,7 @@ void cvs_lut_destroy(cvs_lut* L) {
     if (!L) return;
     cudaSetDevice(L->device);
     cudaDeviceSynchronize();
-    void* ptrs[] = {L->entry, L->pmask, L->d_imgs, L->d_block_first};
+    void* ptrs[] = {L->entry, L->pmask};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete L;
@@ -923,32 +920,46 @@ cvs_status cvs_lut_lookup_images(cvs_lut* L, const cvs_image* batch, int32_t n,
                                  const cvs_capacity_map* maps, void* stream) {
     if (!L || !batch || !maps) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
     if (n <= 0 || n > (1 << 20)) return fail(CVS_ERR_INVALID_ARG, "n must be in [1, 2^20]");
-    std::vector<ImageDesc> h(n);
-    std::vector<int64_t> bf(n);
-    int64_t blocks = 0, total = 0;
     for (int i = 0; i < n; ++i) {
         const cvs_image& im = batch[i];
         if (!im.rgb || im.width <= 0 || im.height <= 0 || im.pitch_bytes < 3LL * im.width)
             return fail(CVS_ERR_INVALID_ARG, "image %d: bad pointer, size or pitch", i);
         if (!maps[i].max_r || !maps[i].count || !maps[i].pmask)
             return fail(CVS_ERR_INVALID_ARG, "map %d: NULL buffer", i);
-        const int64_t px = (int64_t)im.width * im.height;
-        h[i] = ImageDesc{im.rgb, im.pitch_bytes, im.width, im.height, total,
-                         maps[i].max_r, maps[i].count, maps[i].pmask};
-        bf[i] = blocks;
-        blocks += (px + kGatherBlock - 1) / kGatherBlock;
-        total += px;
+        if ((int64_t)im.width * im.height > ((int64_t)1 << 36))
+            return fail(CVS_ERR_INVALID_ARG, "image %d too large", i);
     }
-    if (blocks > 0x7FFFFFFFLL) return fail(CVS_ERR_INVALID_ARG, "batch too large for one launch");
     CVS_CUDA(cudaSetDevice(L->device));
-    CVS_CUDA(grow(&L->d_imgs, &L->cap_imgs, n));
-    CVS_CUDA(grow(&L->d_block_first, &L->cap_bf, n));
     cudaStream_t st = (cudaStream_t)stream;
-    CVS_CUDA(cudaMemcpyAsync(L->d_imgs, h.data(), sizeof(ImageDesc) * n, cudaMemcpyHostToDevice, st));
-    CVS_CUDA(cudaMemcpyAsync(L->d_block_first, bf.data(), sizeof(int64_t) * n,
-                             cudaMemcpyHostToDevice, st));
-    CVS_CUDA(launch_lut_gather_images(L->d_imgs, L->d_block_first, n, blocks, L->entry, L->pmask,
-                                      st));
+    // descriptors travel by value, kGatherMaxImages images per launch
+    for (int first = 0; first < n; first += kGatherMaxImages) {
+        GatherBatch b{};
+        b.n = n - first < kGatherMaxImages ? n - first : kGatherMaxImages;
+        int64_t blocks = 0;
+        for (int j = 0; j < b.n; ++j) {
+            const cvs_image& im = batch[first + j];
+            const cvs_capacity_map& m = maps[first + j];
+            const int64_t px = (int64_t)im.width * im.height;
+            b.img[j] = ImageDesc{im.rgb, im.pitch_bytes, im.width, im.height, 0, m.max_r, m.count,
+                                 m.pmask};
+            b.block_first[j] = blocks;
+            blocks += (px + kGatherBlock - 1) / kGatherBlock;
+        }
+        if (blocks > 0x7FFFFFFFLL) return fail(CVS_ERR_INVALID_ARG, "batch too large for one launch");
+        CVS_CUDA(launch_lut_gather_images(b, blocks, L->entry, L->pmask, st));
+    }
+    return CVS_OK;
+}
+
+cvs_status cvs_reserve(cvs_ctx* c, const cvs_grid* grid, int64_t max_targets, int32_t max_images) {
+    if (!c) return fail(CVS_ERR_INVALID_ARG, "NULL context");
+    if (max_targets < 0 || max_images < 0) return fail(CVS_ERR_INVALID_ARG, "negative size");
+    cvs_status st0 = grid ? check_grid(grid) : CVS_OK;
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK && grid) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK && max_targets > 0) st0 = ensure_targets(c, max_targets);
+    if (st0 != CVS_OK) return st0;
+    if (max_images > 0) CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, max_images));
     return CVS_OK;
 }
 

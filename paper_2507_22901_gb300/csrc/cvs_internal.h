@@ -101,12 +101,17 @@ cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int
 cudaError_t copy_qkeys_to(long long* dst, cudaStream_t st);
 // Capacity table (all 2^24 colours).
 constexpr int kGatherBlock = 256;
+constexpr int kGatherMaxImages = 32;
+struct GatherBatch {              // kernel parameter (by value)
+    int n;
+    int64_t block_first[kGatherMaxImages];
+    ImageDesc img[kGatherMaxImages];
+};
 cudaError_t launch_rgb_iota(uint8_t* rgb, int64_t first, int64_t n, cudaStream_t st);
 cudaError_t launch_lut_pack(const Acc* acc, int64_t n, uint64_t* entry, uint8_t* pmask,
                             cudaStream_t st);
-cudaError_t launch_lut_gather_images(const ImageDesc* imgs, const int64_t* block_first,
-                                     int n_imgs, int64_t total_blocks, const uint64_t* entry,
-                                     const uint8_t* pmask, cudaStream_t st);
+cudaError_t launch_lut_gather_images(const GatherBatch& b, int64_t total_blocks,
+                                     const uint64_t* entry, const uint8_t* pmask, cudaStream_t st);
 cudaError_t launch_lut_gather_colors(const uint8_t* rgb, int64_t n, const uint64_t* entry,
                                      const uint8_t* pmask, float* max_r, int32_t* count,
                                      uint8_t* pm, cudaStream_t st);

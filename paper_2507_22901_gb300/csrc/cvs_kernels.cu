@@ -844,25 +844,19 @@ __global__ void k_lut_pack(const Acc* __restrict__ acc, int64_t n, uint64_t* __r
     pmask[i] = (uint8_t)a.pmask;
 }
 
-// Per-pixel maps of a batch of images from the table.  Blocks never straddle
-// images: block b belongs to the image whose block range holds b.
-__global__ void __launch_bounds__(256) k_lut_gather_images(const ImageDesc* __restrict__ imgs,
-                                                           const int64_t* __restrict__ block_first,
-                                                           int n_imgs,
-                                                           const uint64_t* __restrict__ entry,
-                                                           const uint8_t* __restrict__ pmask) {
-    __shared__ int s_img;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = n_imgs - 1;  // largest i with block_first[i] <= blockIdx.x
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (block_first[mid] <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
-        }
-        s_img = lo;
-    }
-    __syncthreads();
-    const ImageDesc im = imgs[s_img];
-    const int64_t p = ((int64_t)blockIdx.x - block_first[s_img]) * blockDim.x + threadIdx.x;
+// Per-pixel maps of up to kGatherMaxImages images from the table, descriptors
+// passed by value (no device-side table, so concurrent lookups share nothing).
+// Blocks never straddle images: block b belongs to the image whose block range
+// holds b.
+__global__ void __launch_bounds__(kGatherBlock) k_lut_gather_images(const GatherBatch B,
+                                                                    const uint64_t* __restrict__ entry,
+                                                                    const uint8_t* __restrict__ pmask) {
+    int i = 0;  // largest i with block_first[i] <= blockIdx.x
+#pragma unroll 1
+    for (int j = 1; j < B.n; ++j)
+        if (B.block_first[j] <= (int64_t)blockIdx.x) i = j;
+    const ImageDesc& im = B.img[i];
+    const int64_t p = ((int64_t)blockIdx.x - B.block_first[i]) * blockDim.x + threadIdx.x;
     const int64_t npx = (int64_t)im.width * im.height;
     if (p >= npx) return;
     const int64_t y = p / im.width, x = p - y * im.width;
@@ -1003,12 +997,10 @@ cudaError_t launch_lut_pack(const Acc* acc, int64_t n, uint64_t* entry, uint8_t*
     return cudaGetLastError();
 }
 
-cudaError_t launch_lut_gather_images(const ImageDesc* imgs, const int64_t* block_first,
-                                     int n_imgs, int64_t total_blocks, const uint64_t* entry,
-                                     const uint8_t* pmask, cudaStream_t st) {
+cudaError_t launch_lut_gather_images(const GatherBatch& b, int64_t total_blocks,
+                                     const uint64_t* entry, const uint8_t* pmask, cudaStream_t st) {
     if (total_blocks <= 0) return cudaSuccess;
-    k_lut_gather_images<<<(unsigned)total_blocks, kGatherBlock, 0, st>>>(imgs, block_first, n_imgs,
-                                                                        entry, pmask);
+    k_lut_gather_images<<<(unsigned)total_blocks, kGatherBlock, 0, st>>>(b, entry, pmask);
     return cudaGetLastError();
 }
 
