@@ -290,6 +290,71 @@ def run_extras(ctx, torch, device, W, cvs):
     return out
 
 
+# ------------------------------------------------------------------ serving
+def run_serving(torch, device, W, cvs, n_table=600, n_search=24):
+    """Workload 5: Poisson arrivals (seed 2, 120 frames/s) of 1920x1080 (60%),
+    3840x2160 (30%) and 7680x4320 (10%) frames rendered as in workload 3, sent
+    to the continuous-batching server; latency = submit -> maps resident.  With
+    the capacity table (all 600 requests) and with per-frame search (the first
+    n_search requests: the search alone cannot keep up with 120 frames/s)."""
+    import threading
+    reqs = W.serving_requests(n_table, seed=2, rate=120.0)
+    sizes = sorted({(w, h) for _, w, h, _ in reqs})
+    params = W.image_params(4 * len(sizes), seed=2, sizes=[sz for sz in sizes for _ in range(4)])
+    frames = {}
+    for (w, h, terms, ns) in params:
+        img = W.render_image_torch(w, h, terms, ns, device=device).cpu().numpy()
+        frames.setdefault((w, h), []).append(img)
+    r3, a3 = W.grid(3)
+    out = {}
+    for mode, n in (("table", n_table), ("search", n_search)):
+        srv = cvs.Server(r3, a3, 50.0, 0.5, max_inflight=4, max_pixels=7680 * 4320,
+                         mem_budget_bytes=6 << 30, use_table=(mode == "table"))
+        tickets = []
+        lock = threading.Lock()
+        done_flag = [False]
+
+        def drain():
+            i = 0
+            while True:
+                with lock:
+                    if i < len(tickets):
+                        t = tickets[i]
+                    elif done_flag[0]:
+                        return
+                    else:
+                        t = None
+                if t is None:
+                    time.sleep(0.0005)
+                    continue
+                srv.wait(t, 600000)
+                srv.release(t)
+                i += 1
+        th = threading.Thread(target=drain)
+        th.start()
+        t0 = time.perf_counter()
+        for arrival, w, h, idx in reqs[:n]:
+            delay = t0 + arrival - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            t = srv.submit(frames[(w, h)][idx % 4])
+            with lock:
+                tickets.append(t)
+        with lock:
+            done_flag[0] = True
+        th.join()
+        st = srv.stats()
+        srv.close()
+        px = sum(w * h for _, w, h, _ in reqs[:n])
+        out[mode] = {"requests": n, "completed": st["completed"], "failed": st["failed"],
+                     "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                     "frames_per_s": st["frames_per_s"],
+                     "offered_frames_per_s": n / reqs[n - 1][0],
+                     "pixels": px, "peak_arena_bytes": st["peak_bytes_in_use"]}
+    return {"serving": {"workload": "Poisson 120 frames/s (seed 2): 60% 1080p, 30% 4K, 10% 8K; "
+                                    "64 radii x 180 angles; 4 slots", **out}}
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, world, rank, local):
     import torch
@@ -376,6 +441,7 @@ def run_ours(args, world, rank, local):
     extras = {}
     if not args.no_extras and world == 1:
         extras = run_extras(ctx, torch, device, W, cvs)
+        extras.update(run_serving(torch, device, W, cvs))
 
     # ---- roofline of the search kernel (issue bound)
     c = clk.summary()
