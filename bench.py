@@ -213,36 +213,50 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------ extras
 def run_extras(ctx, torch, device, W, cvs):
-    """Precision study on the 4096-colour set (256 radii x 720 angles) and one
-    timed pass of the 48-image workload (64 radii x 180 angles per pixel)."""
+    """Precision study on workloads 1-4 (FP32 vs FP64 errors, re-decision
+    fractions, decision mismatches) and one timed pass of the 48-image workload
+    (64 radii x 180 angles per pixel), directly and through the capacity table."""
     out = {}
-    rgb_h = W.precision_colors()
-    radii, ang = W.grid(4)
-    rgb = torch.from_numpy(rgb_h).to(device)
-    cand = len(rgb_h) * len(radii) * len(ang)
-    res = {}
-    for prec in (cvs.PREC_FP32_RECHECK, cvs.PREC_FP64):
-        ctx.search_colors(rgb, radii, ang, 50.0, 0.5, precision=prec)
-        o = ctx.search_colors(rgb, radii, ang, 50.0, 0.5, precision=prec)
-        ctx.synchronize()
-        st = ctx.stats()
-        res[prec] = (o, st)
-    (o32, st32), (o64, st64) = res[cvs.PREC_FP32_RECHECK], res[cvs.PREC_FP64]
-    mism = int(((o32[0].view(torch.int32) != o64[0].view(torch.int32)) | (o32[1] != o64[1]) |
-                (o32[2] != o64[2])).sum().item())
-    probe = ctx.precision_probe(rgb, radii, ang)
-    out["precision_study"] = {
-        "workload": "4096 colours (3072 uniform, 512 near-grey, 512 near gamut edge) x 256 radii "
-                    "x 720 angles", "candidates": cand,
-        "flagged_fraction": st32["flagged"] / cand, "rechecked_fraction": st32["rechecked"] / cand,
-        "max_code_err_fp32": probe["max_code_err"], "max_lin_err_fp32": probe["max_lin_err"],
-        "raw_fp32_wrong_codes": probe["n_wrong_codes"], "decision_mismatches_vs_fp64": mism,
-        "fp32_gcand_s": cand / (st32["search_ms"] / 1e3) / 1e9,
-        "fp64_gcand_s": cand / (st64["search_ms"] / 1e3) / 1e9,
-    }
-    # one pass over the 48 full-size synthetic images
     params = W.image_params()
     imgs = [W.render_image_torch(w, h, terms, ns, device=device) for w, h, terms, ns in params]
+    gen = torch.Generator(device="cpu").manual_seed(3)
+    pix = []
+    for im in imgs:  # 1366 random pixels per image
+        ys = torch.randint(0, im.shape[0], (1366,), generator=gen)
+        xs = torch.randint(0, im.shape[1], (1366,), generator=gen)
+        pix.append(im.cpu()[ys, xs])
+    cases = {
+        "1_grey170": (np.array([[170, 170, 170]], np.uint8), W.grid(1)),
+        "2_cube_step8": (W.color_cube(8), W.grid(2)),
+        "3_image_pixels": (torch.cat(pix).numpy(), W.grid(3)),
+        "4_precision_set": (W.precision_colors(), W.grid(4)),
+    }
+    study = {}
+    for name, (rgb_h, (radii, ang)) in cases.items():
+        rgb = torch.from_numpy(np.ascontiguousarray(rgb_h)).to(device)
+        cand = len(rgb_h) * len(radii) * len(ang)
+        res = {}
+        for prec in (cvs.PREC_FP32_RECHECK, cvs.PREC_FP64):
+            ctx.search_colors(rgb, radii, ang, 50.0, 0.5, precision=prec)
+            o = ctx.search_colors(rgb, radii, ang, 50.0, 0.5, precision=prec)
+            ctx.synchronize()
+            res[prec] = (o, ctx.stats())
+        (o32, st32), (o64, st64) = res[cvs.PREC_FP32_RECHECK], res[cvs.PREC_FP64]
+        mism = int(((o32[0].view(torch.int32) != o64[0].view(torch.int32)) |
+                    (o32[1] != o64[1]) | (o32[2] != o64[2])).sum().item())
+        rep = ctx.precision_probe(rgb, radii, ang)
+        study[name] = {
+            "colours": len(rgb_h), "candidates": cand,
+            "flagged_fraction": st32["flagged"] / cand,
+            "rechecked_fraction": st32["rechecked"] / cand,
+            "max_code_err_fp32": rep["max_code_err"], "max_lab_err_fp32": rep["max_lab_err"],
+            "max_lin_err_fp32": rep["max_lin_err"], "raw_fp32_wrong_codes": rep["n_wrong_codes"],
+            "decision_mismatches_vs_fp64": mism,
+            "fp32_gcand_s": cand / (st32["search_ms"] / 1e3) / 1e9,
+            "fp64_gcand_s": cand / (st64["search_ms"] / 1e3) / 1e9,
+        }
+    out["precision_study"] = study
+    # one pass over the 48 full-size synthetic images
     r3, a3 = W.grid(3)
     px = sum(im.shape[0] * im.shape[1] for im in imgs)
     maps = ctx.search_images(imgs, r3, a3, 50.0, 0.5)

@@ -338,14 +338,25 @@ cvs_status cvs_get_stats(cvs_ctx* ctx, cvs_stats* out);
 
 /* Precision study: for n colours (rgb_dev: device, 3n bytes) on the grid,
  * compare every FP32 colour conversion (the "plus" colour of each (k, m))
- * with its FP64 value.  Outputs (host): *max_code_err = largest |v32 - v64|
- * in 8-bit code units among values within 0.05 of a rounding boundary
- * (v = 255 enc(lin) before rounding); *max_lin_err = largest |lin32 - lin64|
- * of the linear RGB; *n_wrong_codes = number of FP32 codes in [0, 255] that
- * differ from FP64 before any re-decision.  Synchronous. */
+ * with its FP64 value.  Synchronous.  Fields of *out:
+ *   max_code_err  largest |v32 - v64| in 8-bit code units among values within
+ *                 0.05 of a rounding boundary (v = 255 enc(lin) unrounded)
+ *   max_lin_err   largest |lin32 - lin64| of the linear RGB
+ *   max_lab_err   largest |a*|, |b*| error of the colour the FP32 chain
+ *                 stands for (its f-values against the exact a +- i sin j,
+ *                 b +- i cos j); L* is exact
+ *   n_wrong_codes FP32 codes in [0, 255] that differ from FP64 before any
+ *                 re-decision (the re-decision corrects every one of them)
+ *   n_values      codes examined */
+typedef struct {
+    double max_code_err;
+    double max_lin_err;
+    double max_lab_err;
+    int64_t n_wrong_codes;
+    int64_t n_values;
+} cvs_precision_report;
 cvs_status cvs_precision_probe(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
-                               const cvs_grid* grid, double* max_code_err,
-                               double* max_lin_err, int64_t* n_wrong_codes);
+                               const cvs_grid* grid, cvs_precision_report* out);
 
 /* A launch shape of the search kernel: threads per block, resident blocks
  * per SM (0 = as many as fit) and radii per work item (a work item is one

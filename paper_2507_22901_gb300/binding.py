@@ -66,6 +66,12 @@ class cvs_stats(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("search_ms", ctypes.c_double)]
 
 
+class cvs_precision_report(ctypes.Structure):
+    _fields_ = [("max_code_err", ctypes.c_double), ("max_lin_err", ctypes.c_double),
+                ("max_lab_err", ctypes.c_double), ("n_wrong_codes", ctypes.c_int64),
+                ("n_values", ctypes.c_int64)]
+
+
 class cvs_launch_shape(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
                 ("kchunk", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ms", ctypes.c_double)]
@@ -132,7 +138,7 @@ def lib() -> ctypes.CDLL:
                                P(cvs_capacity_map), vp], st),
         "cvs_synchronize": ([vp, vp], st),
         "cvs_get_stats": ([vp, P(cvs_stats)], st),
-        "cvs_precision_probe": ([vp, vp, i64, P(cvs_grid), P(d), P(d), P(i64)], st),
+        "cvs_precision_probe": ([vp, vp, i64, P(cvs_grid), P(cvs_precision_report)], st),
         "cvs_set_option": ([vp, ctypes.c_char_p, d], st),
         "cvs_get_option": ([vp, ctypes.c_char_p, P(d)], st),
         "cvs_lut_build": ([vp, P(cvs_grid), P(cvs_thresholds), st, P(vp), vp], st),
@@ -364,14 +370,14 @@ class Context:
                                   ctypes.byref(h), _stream_ptr(stream)), "cvs_lut_build")
         return CapacityTable(h)
 
-    def precision_probe(self, rgb_dev, radii, angles_deg):
+    def precision_probe(self, rgb_dev, radii, angles_deg) -> dict:
+        """FP32-vs-FP64 error report of every plus colour (see cvs_precision_probe)."""
         g, keep = make_grid(radii, angles_deg)
-        e1, e2, nw = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        rep = cvs_precision_report()
         n = rgb_dev.numel() // 3
         check(lib().cvs_precision_probe(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g),
-                                        ctypes.byref(e1), ctypes.byref(e2), ctypes.byref(nw)),
-              "cvs_precision_probe")
-        return {"max_code_err": e1.value, "max_lin_err": e2.value, "n_wrong_codes": nw.value}
+                                        ctypes.byref(rep)), "cvs_precision_probe")
+        return {f: getattr(rep, f) for f, _ in cvs_precision_report._fields_}
 
 
 class CapacityTable:

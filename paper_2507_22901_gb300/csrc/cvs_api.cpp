@@ -500,7 +500,7 @@ cvs_status cvs_create(cvs_ctx** out, int device) {
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_rgb1, 16);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_probe, 16);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_probe, 32);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     if (e == cudaSuccess) e = copy_qkeys_to(c->qkey, c->own);
@@ -981,10 +981,8 @@ cvs_status cvs_get_stats(cvs_ctx* c, cvs_stats* out) {
 }
 
 cvs_status cvs_precision_probe(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n,
-                               const cvs_grid* grid, double* max_code_err, double* max_lin_err,
-                               int64_t* n_wrong_codes) {
-    if (!c || !max_code_err || !max_lin_err || !n_wrong_codes)
-        return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+                               const cvs_grid* grid, cvs_precision_report* out) {
+    if (!c || !out) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
     if (n <= 0 || !rgb_dev) return fail(CVS_ERR_INVALID_ARG, "need n > 0 colours");
     cvs_status st0 = check_grid(grid);
     if (st0 == CVS_OK) st0 = set_device(c);
@@ -992,22 +990,26 @@ cvs_status cvs_precision_probe(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n,
     if (st0 == CVS_OK) st0 = ensure_targets(c, n);
     if (st0 != CVS_OK) return st0;
     cudaStream_t st = c->own;
-    CVS_CUDA(cudaMemsetAsync(c->d_probe, 0, 16, st));
+    CVS_CUDA(cudaMemsetAsync(c->d_probe, 0, 24, st));
     CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
     CVS_CUDA(launch_precision_probe(c->tf, c->td, n, c->grid, c->qkey, c->d_probe, c->d_probe + 1,
-                                    reinterpret_cast<unsigned long long*>(c->d_probe + 2),
+                                    c->d_probe + 2,
+                                    reinterpret_cast<unsigned long long*>(c->d_probe + 4),
                                     c->num_sms, st));
-    unsigned int h[4] = {0, 0, 0, 0};
-    CVS_CUDA(cudaMemcpyAsync(h, c->d_probe, 16, cudaMemcpyDeviceToHost, st));
+    unsigned int h[6] = {0, 0, 0, 0, 0, 0};
+    CVS_CUDA(cudaMemcpyAsync(h, c->d_probe, 24, cudaMemcpyDeviceToHost, st));
     CVS_CUDA(cudaStreamSynchronize(st));
-    float fv, fl;
+    float fv, fl, fa;
     std::memcpy(&fv, &h[0], 4);
     std::memcpy(&fl, &h[1], 4);
+    std::memcpy(&fa, &h[2], 4);
     unsigned long long w;
-    std::memcpy(&w, &h[2], 8);
-    *max_code_err = fv;
-    *max_lin_err = fl;
-    *n_wrong_codes = (int64_t)w;
+    std::memcpy(&w, &h[4], 8);
+    out->max_code_err = fv;
+    out->max_lin_err = fl;
+    out->max_lab_err = fa;
+    out->n_wrong_codes = (int64_t)w;
+    out->n_values = n * (int64_t)c->grid.K * c->grid.N * 3;
     return CVS_OK;
 }
 

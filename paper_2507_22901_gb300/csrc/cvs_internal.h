@@ -97,7 +97,8 @@ cudaError_t launch_target_lab(const uint8_t* rgb, int64_t n, double* lab, cudaSt
 cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int64_t n,
                                    const GridDev& g, const long long* qkey,
                                    unsigned int* max_v_err_bits, unsigned int* max_lin_err_bits,
-                                   unsigned long long* n_wrong, int num_sms, cudaStream_t st);
+                                   unsigned int* max_lab_err_bits, unsigned long long* n_wrong,
+                                   int num_sms, cudaStream_t st);
 cudaError_t copy_qkeys_to(long long* dst, cudaStream_t st);
 // Capacity table (all 2^24 colours).
 constexpr int kGatherBlock = 256;

@@ -763,7 +763,7 @@ __global__ void k_target_lab(const uint8_t* __restrict__ rgb, int64_t n, double*
 __global__ void k_precision_probe(const TargetF32* __restrict__ tf, const TargetF64* __restrict__ td,
                                   int64_t n, const GridDev g, const long long* __restrict__ qkey,
                                   unsigned int* max_v_err_bits, unsigned int* max_lin_err_bits,
-                                  unsigned long long* n_wrong) {
+                                  unsigned int* max_lab_err_bits, unsigned long long* n_wrong) {
     float Ax[3], Bz[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -771,7 +771,7 @@ __global__ void k_precision_probe(const TargetF32* __restrict__ tf, const Target
         Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
     }
     const int64_t total = n * g.K * g.N;
-    float vmax = 0.0f, lmax = 0.0f;
+    float vmax = 0.0f, lmax = 0.0f, amax = 0.0f;
     unsigned long long wrong = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -792,6 +792,14 @@ __global__ void k_precision_probe(const TargetF32* __restrict__ tf, const Target
         const float u = r * sc.x, w = r * sc.y;
         if (T.flags & 1u) delta_xz<true>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
         else delta_xz<false>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
+        // L*a*b* the FP32 chain stands for: f-values fx0 + u and fz0 + w
+        {
+            const double fy = (D.L + 16.0) / 116.0;
+            const double fx_exact = fy + (D.a + da) / 500.0, fz_exact = fy - (D.b + db) / 200.0;
+            const double ea = 500.0 * fabs(((double)T.fx0 + (double)u) - fx_exact);
+            const double eb = 200.0 * fabs(((double)T.fz0 + (double)w) - fz_exact);
+            amax = fmaxf(amax, (float)fmax(ea, eb));
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float l32 = __ffma2_rn(f2(Bz[c], Bz[c]), dZ2,
@@ -813,11 +821,13 @@ __global__ void k_precision_probe(const TargetF32* __restrict__ tf, const Target
     for (int off = 16; off > 0; off >>= 1) {
         vmax = fmaxf(vmax, __shfl_xor_sync(0xFFFFFFFFu, vmax, off));
         lmax = fmaxf(lmax, __shfl_xor_sync(0xFFFFFFFFu, lmax, off));
+        amax = fmaxf(amax, __shfl_xor_sync(0xFFFFFFFFu, amax, off));
         wrong += __shfl_xor_sync(0xFFFFFFFFu, wrong, off);
     }
     if (lane_id() == 0) {
         atomicMax(max_v_err_bits, __float_as_uint(vmax));
         atomicMax(max_lin_err_bits, __float_as_uint(lmax));
+        atomicMax(max_lab_err_bits, __float_as_uint(amax));
         if (wrong) atomicAdd(n_wrong, wrong);
     }
 }
@@ -977,10 +987,11 @@ cudaError_t launch_target_lab(const uint8_t* rgb, int64_t n, double* lab, cudaSt
 cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int64_t n,
                                    const GridDev& g, const long long* qkey,
                                    unsigned int* max_v_err_bits, unsigned int* max_lin_err_bits,
-                                   unsigned long long* n_wrong, int num_sms, cudaStream_t st) {
+                                   unsigned int* max_lab_err_bits, unsigned long long* n_wrong,
+                                   int num_sms, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_precision_probe<<<num_sms * 8, 256, 0, st>>>(tf, td, n, g, qkey, max_v_err_bits,
-                                                    max_lin_err_bits, n_wrong);
+                                                    max_lin_err_bits, max_lab_err_bits, n_wrong);
     return cudaGetLastError();
 }
 

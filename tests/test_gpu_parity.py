@@ -176,7 +176,8 @@ def test_precision_set_full_fp32_equals_fp64_and_probe(ctx, torch_cuda):
     pr = ctx.precision_probe(dev(torch_cuda, rgb), radii, ang)
     w = ctx.get_option("fp32_window")
     print("probe", pr, "window", w)
-    assert pr["max_code_err"] < w
+    assert pr["max_code_err"] < w / 2  # the window keeps a margin over the measured error
+    assert pr["max_lab_err"] < 1e-4 and pr["n_values"] == len(rgb) * 256 * 720 * 3
 
 
 # ------------------------------------------------------------------ images
