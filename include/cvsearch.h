@@ -207,6 +207,21 @@ cvs_status cvs_search_colors_host(cvs_ctx* ctx, const uint8_t* rgb_host, int64_t
                                   cvs_precision prec, float* max_r_host,
                                   int32_t* count_host, uint8_t* pmask_host);
 
+/* Per-colour results for n colours under n_thr threshold sets at once: the
+ * experiment of §3 Experiments (Table 1 colours x every (V_th, R_novib)
+ * combination), computed in one pass that forms each candidate's pair codes
+ * once and decides them against every set.
+ *   thr:     host array of n_thr sets, 1 <= n_thr <= 16; all sets must share
+ *            gamut_mode (CVS_ERR_INVALID_ARG otherwise).
+ *   out_dev: device capacity map of n * n_thr entries; entry t * n_thr + s
+ *            holds colour t under set s, equal to what cvs_search_colors
+ *            returns for that colour with thr[s] alone.
+ * Asynchronous on `stream`; not captured in CUDA graphs. */
+cvs_status cvs_search_colors_multi(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
+                                   const cvs_grid* grid, const cvs_thresholds* thr,
+                                   int32_t n_thr, cvs_precision prec,
+                                   const cvs_capacity_map* out_dev, void* stream);
+
 /* Per-pixel results for a batch of n images of any sizes, in one persistent
  * launch over a shared work queue.  batch: host array of n image descriptors
  * (device pixel pointers).  maps: host array of n capacity maps (device

@@ -134,6 +134,8 @@ def lib() -> ctypes.CDLL:
                                P(cvs_capacity_map), vp], st),
         "cvs_search_colors_host": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), st, vp, vp, vp],
                                    st),
+        "cvs_search_colors_multi": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), i32, st,
+                                     P(cvs_capacity_map), vp], st),
         "cvs_search_images": ([vp, P(cvs_image), i32, P(cvs_grid), P(cvs_thresholds), st,
                                P(cvs_capacity_map), vp], st),
         "cvs_synchronize": ([vp, vp], st),
@@ -296,6 +298,31 @@ class Context:
         check(lib().cvs_search_colors(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g),
                                       ctypes.byref(t), int(precision), ctypes.byref(m),
                                       _stream_ptr(stream)), "cvs_search_colors")
+        return out
+
+    def search_colors_multi(self, rgb_dev, radii, angles_deg, thresholds, gamut_mode=0,
+                            precision=PREC_FP32_RECHECK, out=None, stream=None):
+        """Per-colour results under several threshold sets in one pass.
+
+        thresholds: sequence of (v_th, r_novib) or (v_th, r_novib, pattern_mask).
+        Returns (max_r, count, pmask) device tensors of shape (n, n_sets)."""
+        import torch
+        n = rgb_dev.numel() // 3
+        sets = [tuple(x) for x in thresholds]
+        arr = (cvs_thresholds * max(len(sets), 1))()
+        for i, x in enumerate(sets):
+            arr[i] = make_thresholds(x[0], x[1], x[2] if len(x) > 2 else 0x7F, gamut_mode)
+        dev = rgb_dev.device
+        shape = (n, len(sets))
+        if out is None:
+            out = (torch.empty(shape, dtype=torch.float32, device=dev),
+                   torch.empty(shape, dtype=torch.int32, device=dev),
+                   torch.empty(shape, dtype=torch.uint8, device=dev))
+        g, keep = make_grid(radii, angles_deg)
+        m = cvs_capacity_map(out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
+        check(lib().cvs_search_colors_multi(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g), arr,
+                                            len(sets), int(precision), ctypes.byref(m),
+                                            _stream_ptr(stream)), "cvs_search_colors_multi")
         return out
 
     def search_colors_host(self, rgb, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,

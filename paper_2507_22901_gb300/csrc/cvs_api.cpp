@@ -102,6 +102,9 @@ struct cvs_ctx {
     std::map<std::array<int64_t, 7>, LaunchShape> tuned;
     Acc* acc_tune = nullptr;
     int64_t cap_acc_tune = 0;
+    // multi-threshold search: n x n_thr accumulators
+    Acc* acc_multi = nullptr;
+    int64_t cap_acc_multi = 0;
     unsigned long long* tune_counters = nullptr;
     // CUDA graphs: one captured setup+search+finalize sequence per input signature
     int use_graphs = 0;
@@ -526,6 +529,7 @@ void cvs_destroy(cvs_ctx* c) {
         if (p) cudaFree(p);
     drop_graphs(c);
     if (c->acc_tune) cudaFree(c->acc_tune);
+    if (c->acc_multi) cudaFree(c->acc_multi);
     if (c->tune_counters) cudaFree(c->tune_counters);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->h_counters) cudaFreeHost(c->h_counters);
@@ -705,6 +709,73 @@ cvs_status cvs_search_colors(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, cons
     st0 = graph_launch(c, key, st, enqueue);
     if (st0 == CVS_OK) c->last_pending = true;
     return st0;
+}
+
+cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n,
+                                   const cvs_grid* grid, const cvs_thresholds* thr,
+                                   int32_t n_thr, cvs_precision prec,
+                                   const cvs_capacity_map* out, void* stream) {
+    if (!c || !out || !thr) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (n < 0 || n > (int64_t)1 << 36) return fail(CVS_ERR_INVALID_ARG, "n out of range");
+    if (n_thr < 1 || n_thr > kMaxThresholdSets)
+        return fail(CVS_ERR_INVALID_ARG, "n_thr = %d, must be in [1, %d]", (int)n_thr,
+                    kMaxThresholdSets);
+    if (n > 0 && (!rgb_dev || !out->max_r || !out->count || !out->pmask))
+        return fail(CVS_ERR_INVALID_ARG, "NULL device buffer");
+    if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
+        return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    cvs_status st0 = check_grid(grid);
+    for (int s = 0; s < n_thr && st0 == CVS_OK; ++s) {
+        st0 = check_thresholds(thr + s);
+        if (st0 == CVS_OK && thr[s].gamut_mode != thr[0].gamut_mode)
+            st0 = fail(CVS_ERR_INVALID_ARG, "threshold set %d: gamut_mode differs from set 0", s);
+    }
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = ensure_targets(c, n);
+    if (st0 != CVS_OK) return st0;
+    if (n == 0) return CVS_OK;
+    CVS_CUDA(grow(&c->acc_multi, &c->cap_acc_multi, n * n_thr));
+    MultiArgs a{};
+    a.tf = c->tf;
+    a.td = c->td;
+    a.acc = c->acc_multi;
+    a.n_targets = n;
+    a.grid = c->grid;
+    a.qkey = c->qkey;
+    a.n_thr = n_thr;
+    for (int s = 0; s < n_thr; ++s) {
+        thresholds_to_int(thr + s, &a.hi_min[s], &a.lo_max[s]);
+        a.mask2[s] = thr[s].pattern_mask << 1;
+    }
+    a.clip = thr[0].gamut_mode;
+    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
+    a.half_w = (float)(0.5 - c->window);
+    a.prec = (int32_t)prec;
+    a.kchunk = choose_kchunk(c, n, c->grid.K, c->grid.H);
+    a.work_counter = c->counters;
+    a.stats = c->counters + 1;
+    a.num_sms = c->num_sms;
+    cudaStream_t st = (cudaStream_t)stream;
+    CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
+    CVS_CUDA(launch_init_acc(c->acc_multi, n * n_thr, st));
+    CVS_CUDA(cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), st));
+    CVS_CUDA(cudaEventRecord(c->ev0, st));
+    CVS_CUDA(launch_search_multi(a, st));
+    CVS_CUDA(cudaEventRecord(c->ev1, st));
+    CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, 4 * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, st));
+    CVS_CUDA(launch_finalize_colors(c->acc_multi, n * n_thr, out->max_r, out->count, out->pmask,
+                                    st));
+    cvs_stats& s = c->last;
+    s = cvs_stats{};
+    s.targets = n;
+    s.candidates = n * (int64_t)c->grid.K * c->grid.N;
+    s.colors_fp32 = prec == CVS_PREC_FP64 ? 0 : s.candidates;
+    s.symmetric = c->grid.sym;
+    s.precision = (int32_t)prec;
+    c->last_pending = true;
+    return CVS_OK;
 }
 
 cvs_status cvs_search_colors_host(cvs_ctx* c, const uint8_t* rgb_host, int64_t n,

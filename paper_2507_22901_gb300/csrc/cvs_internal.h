@@ -79,6 +79,27 @@ struct SearchArgs {
     int num_sms;
 };
 
+// The multi-threshold search: up to kMaxThresholdSets sets in one pass.
+constexpr int kMaxThresholdSets = 16;
+struct MultiArgs {
+    const TargetF32* tf;
+    const TargetF64* td;
+    Acc* acc;                  // n_targets * n_thr, index t * n_thr + s
+    int64_t n_targets;
+    GridDev grid;
+    const long long* qkey;
+    int32_t n_thr;
+    int32_t hi_min[kMaxThresholdSets], lo_max[kMaxThresholdSets];
+    uint32_t mask2[kMaxThresholdSets];
+    int32_t clip;              // shared by all sets
+    float half_w;
+    int32_t prec;
+    int32_t kchunk;
+    unsigned long long* work_counter;
+    unsigned long long* stats;
+    int num_sms;
+};
+
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_trig_table(const double* angles_dev, int n, double* s64, double* c64,
                               float2* sc32, int* status, cudaStream_t st);
@@ -89,6 +110,8 @@ cudaError_t launch_setup_images(const ImageDesc* imgs, int n_imgs, int64_t total
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t st);
 cudaError_t launch_finalize_colors(const Acc* acc, int64_t n, float* max_r, int32_t* count,
                                    uint8_t* pmask, cudaStream_t st);
+cudaError_t launch_search_multi(const MultiArgs& a, cudaStream_t st);
+cudaError_t launch_init_acc(Acc* acc, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t n,
                                    const ImageDesc* imgs, cudaStream_t st);
 cudaError_t launch_compact_pairs(const cvs_pair* dense, int64_t n_dense, cvs_pair* out,

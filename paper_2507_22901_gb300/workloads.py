@@ -38,6 +38,19 @@ TABLE1_RNOVIB = (0.5, 0.25, 0.125)
 DEFAULT_THRESHOLDS = dict(v_th=50.0, r_novib=0.5, pattern_mask=0x7F, gamut_mode=0)
 
 
+def table1_threshold_sets():
+    """The 12 (V_th, R_novib) combinations of Table 1, V_th-major."""
+    return [(float(v), float(r)) for v in TABLE1_VTH for r in TABLE1_RNOVIB]
+
+
+def presence_matrix(pmask) -> np.ndarray:
+    """Table 2's question from per-(colour, set) pattern masks: (7, n_colours)
+    bool, row p - 1 true where some set gives colour a pair for pattern p.
+    pmask: (n_colours, n_sets) uint8, bit p - 1 = pattern p has a pair."""
+    any_set = np.bitwise_or.reduce(np.asarray(pmask, np.uint8), axis=1)
+    return np.array([(any_set >> (p - 1)) & 1 for p in range(1, 8)], bool)
+
+
 def grid(config: int):
     """(radii, angles_deg) float64 arrays of a workload."""
     if config == 1:
