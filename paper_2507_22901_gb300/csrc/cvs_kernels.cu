@@ -188,8 +188,9 @@ __device__ __forceinline__ void delta_xz(const PairsT& P, float2 u2, float2 w2, 
 // colours run the same chain, so they travel as one float2 through the packed
 // FP32x2 instructions (component-wise IEEE round-to-nearest, as the scalar
 // ops).  Returns true if some code's unrounded value lies within W of a
-// rounding boundary.
-template <bool FAST>
+// rounding boundary.  LINSEG = false when every linear RGB value of the call
+// is known to lie above the sRGB linear segment (see pow_branch_only).
+template <bool FAST, bool LINSEG = true>
 __device__ __forceinline__ bool codes32(const PairsT& P, const PairsC& C, float2 u2, float2 w2,
                                         float half_w, int yp[3], int ym[3]) {
     float2 dX, dZ;
@@ -205,9 +206,11 @@ __device__ __forceinline__ bool codes32(const PairsT& P, const PairsC& C, float2
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pp) : "f"(e.x));
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pm) : "f"(e.y));
         const float2 vpow = __ffma2_rn(dup(269.025f), f2(pp, pm), dup(-14.025f));
-        const float2 vlin = __fmul2_rn(lin, dup(3294.6f));
-        const float2 v = f2(lin.x <= 0.0031308f ? vlin.x : vpow.x,
-                            lin.y <= 0.0031308f ? vlin.y : vpow.y);
+        float2 v = vpow;
+        if (LINSEG) {
+            const float2 vlin = __fmul2_rn(lin, dup(3294.6f));
+            v = f2(lin.x <= 0.0031308f ? vlin.x : vpow.x, lin.y <= 0.0031308f ? vlin.y : vpow.y);
+        }
         const float2 y = __fadd2_rn(v, dup(kMagic));
         const float2 rr = __fadd2_rn(y, dup(-kMagic));
         const float2 d = __ffma2_rn(rr, dup(-1.0f), v);  // v - rr, exact
@@ -217,6 +220,40 @@ __device__ __forceinline__ bool codes32(const PairsT& P, const PairsC& C, float2
         ym[c] = __float_as_int(y.y);
     }
     return flag;
+}
+
+// True when no candidate at radius r (any angle) of a fast-path target can
+// reach the linear segment of the sRGB encode (lin <= 0.0031308).  The f^-1
+// displacement u (c2 + u (c1 + u)) increases with u, so per channel the
+// smallest linear value over |u| <= r/500, |w| <= r/200 sits at an end of
+// each range.  The margin (2e-5) is far above the FP32 chain's error in
+// linear RGB (below 1e-6) and the rounding of this bound.
+__device__ __forceinline__ bool pow_branch_only(const TargetF32& T, const ChainF32& C, float r) {
+    const float U = r * 0.002f * 1.00001f, V = r * 0.005f * 1.00001f;
+    const float xlo = -U * (T.c2x - U * (T.c1x - U)), xhi = U * (T.c2x + U * (T.c1x + U));
+    const float zlo = -V * (T.c2z - V * (T.c1z - V)), zhi = V * (T.c2z + V * (T.c1z + V));
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float g = T.lin0[c] + fminf(C.Ax[c] * xlo, C.Ax[c] * xhi) +
+                        fminf(C.Bz[c] * zlo, C.Bz[c] * zhi);
+        ok = ok && g > 0.0031308f + 2e-5f;
+    }
+    return ok;
+}
+
+// First radius index in [k0, k1) whose candidates may reach the sRGB linear
+// segment (k1 if none); warp-uniform.
+__device__ __forceinline__ int first_linseg_radius(const TargetF32& T, const ChainF32& C,
+                                                   const float2* r2s, int k0, int k1) {
+    const unsigned lane = threadIdx.x & 31u;
+    for (int kb = k0; kb < k1; kb += 32) {
+        const int kk = kb + (int)lane;
+        const bool bad = kk < k1 && !pow_branch_only(T, C, r2s[kk].x);
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, bad);
+        if (b) return kb + __ffs(b) - 1;
+    }
+    return k1;
 }
 
 // Embedding-signal decision on biased codes y = kMagicBits + q (exact when no
@@ -498,14 +535,12 @@ struct Tally {
 
 // One 32-slot step of a work item: every lane evaluates slot (k, h).  With
 // CHECK, lanes past the item's last slot (active == false) contribute nothing.
-template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST>
-__device__ __forceinline__ void slot_step(const SearchArgs& A, const Smem& S, const TargetF32& T,
-                                          const PairsT& P, const PairsC& PC, const TargetF64& D,
-                                          const ChainF32& C, int64_t t, int k, int h, bool active,
-                                          Tally& acc, uint32_t* pq, int& pq_n, uint32_t* rq_t,
-                                          uint32_t* rq_kh, int& rq_n, unsigned long long& n_flag,
-                                          unsigned long long& n_re) {
-    const unsigned lane = lane_id();
+// Returns true for a flagged FP32 slot (decided later by drain_flagged); the
+// step itself never synchronises the warp.
+template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST, bool LINSEG>
+__device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, const PairsT& P,
+                                          const PairsC& PC, const TargetF64& D, int k, int h,
+                                          bool active, Tally& acc) {
     const int H = A.grid.H;
     const int inc = A.grid.sym ? 2 : 1;
     if (CHECK && !active) { k = 0; h = 0; }
@@ -516,7 +551,7 @@ __device__ __forceinline__ void slot_step(const SearchArgs& A, const Smem& S, co
         const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));  // (u, -u)
         const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));  // (w, -w)
         int yp[3], ym[3];
-        bool flag = codes32<FAST>(P, PC, u2, w2, A.half_w, yp, ym);
+        bool flag = codes32<FAST, LINSEG>(P, PC, u2, w2, A.half_w, yp, ym);
         if (CHECK) flag = flag && active;
         int pattern = decide32<CLIP>(yp, ym, S.lut, A.mask2);
         if (flag || (CHECK && !active)) pattern = 0;
@@ -538,25 +573,7 @@ __device__ __forceinline__ void slot_step(const SearchArgs& A, const Smem& S, co
                               A.target_id);
             }
         }
-        const unsigned fball = __ballot_sync(0xFFFFFFFFu, flag);
-        if (fball) {
-            if (flag) {
-                pq[pq_n + __popc(fball & ((1u << lane) - 1u))] = (uint32_t)k | ((uint32_t)h << 16);
-                ++n_flag;
-            }
-            pq_n += __popc(fball);
-            __syncwarp();
-            if (pq_n >= 32) {
-                drain_flagged<FAST>(A, S, T, C, t, pq, 32, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh,
-                                    rq_n, n_re);
-                const int rest = pq_n - 32;
-                const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
-                __syncwarp();
-                if ((int)lane < rest) pq[lane] = mv;
-                __syncwarp();
-                pq_n = rest;
-            }
-        }
+        return flag;
     } else {
         int qp[3], qm[3];
         const int pattern = (!CHECK || active) ? decide64_slot(A, D, k, h, qp, qm) : 0;
@@ -570,12 +587,94 @@ __device__ __forceinline__ void slot_step(const SearchArgs& A, const Smem& S, co
                 acc.pm |= 1u << pattern;
             }
         }
+        return false;
+    }
+}
+
+// Flag bitmap of the FP32 path: the main loop records which slots were
+// flagged, one bit per (iteration, lane), in kFlagWords words per lane of a
+// per-warp shared array (word w of lane l at [w * 32 + l]); bit j of word w is
+// iteration seg0 + 32 w + j.  The loop itself thus carries no warp vote and no
+// branch for flagged slots; collect_flagged compacts them after each segment.
+constexpr int kFlagWords = 8;
+constexpr int kSegIters = 32 * kFlagWords;
+
+// Iterations [it, end) of an item (within one segment starting at seg0), with
+// lanes at slot (k, h); flagged slots set their bits in fb.
+template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST, bool LINSEG>
+__device__ __forceinline__ void run_range(const SearchArgs& A, const Smem& S, const PairsT& P,
+                                          const PairsC& PC, const TargetF64& D, int& it, int end,
+                                          int seg0, int nslots, int q32, int r32, int& k, int& h,
+                                          Tally& acc, uint32_t* fb) {
+    const unsigned lane = lane_id();
+    const int H = A.grid.H;
+    while (it < end) {
+        const int w = (it - seg0) >> 5;
+        const int wend = min(end, seg0 + 32 * (w + 1));
+        uint32_t bits = 0, bit = 1u << ((it - seg0) & 31);
+        for (; it < wend; ++it) {
+            const bool active = !CHECK || it * 32 + (int)lane < nslots;
+            const bool flag = slot_step<PREC, FAST, CHECK, CLIP, LIST, LINSEG>(A, S, P, PC, D, k, h,
+                                                                             active, acc);
+            if (PREC == CVS_PREC_FP32_RECHECK && flag) bits |= bit;
+            bit <<= 1;
+            h += r32;
+            k += q32;
+            const bool wrap = h >= H;
+            h = wrap ? h - H : h;
+            k = wrap ? k + 1 : k;
+        }
+        if (PREC == CVS_PREC_FP32_RECHECK) fb[w * 32 + lane] |= bits;
+    }
+}
+
+// Queue the flagged slots of one segment (words [0, nwords) of fb) into pq,
+// 32 at a time, deciding each full batch with drain_flagged.
+template <bool FAST>
+__device__ __forceinline__ void collect_flagged(const SearchArgs& A, const Smem& S,
+                                                const TargetF32& T, const ChainF32& C, int64_t t,
+                                                int k0, int seg0, int nwords, uint32_t* fb,
+                                                uint32_t* pq, int& pq_n, Tally& acc,
+                                                uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
+                                                unsigned long long& n_flag,
+                                                unsigned long long& n_re) {
+    const unsigned lane = lane_id();
+    const int H = A.grid.H;
+    for (int w = 0; w < nwords; ++w) {
+        uint32_t bits = fb[w * 32 + lane];
+        fb[w * 32 + lane] = 0u;
+        while (true) {
+            const bool has = bits != 0u;
+            const unsigned ball = __ballot_sync(0xFFFFFFFFu, has);
+            if (!ball) break;
+            if (has) {
+                const int j = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int i = (seg0 + 32 * w + j) * 32 + (int)lane;  // slot index in the item
+                const int dk = i / H;
+                pq[pq_n + __popc(ball & ((1u << lane) - 1u))] =
+                    (uint32_t)(k0 + dk) | ((uint32_t)(i - dk * H) << 16);
+                ++n_flag;
+            }
+            pq_n += __popc(ball);
+            __syncwarp();
+            if (pq_n >= 32) {
+                drain_flagged<FAST>(A, S, T, C, t, pq, 32, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh,
+                                    rq_n, n_re);
+                const int rest = pq_n - 32;
+                const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
+                __syncwarp();
+                if ((int)lane < rest) pq[lane] = mv;
+                __syncwarp();
+                pq_n = rest;
+            }
+        }
     }
 }
 
 template <int PREC, bool FAST, bool CLIP, bool LIST>
 __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int64_t t, int k0,
-                                         int k1, const ChainF32& C, uint32_t* pq,
+                                         int k1, const ChainF32& C, uint32_t* pq, uint32_t* fb,
                                          uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
                                          unsigned long long& n_flag, unsigned long long& n_re) {
     const unsigned lane = lane_id();
@@ -593,19 +692,36 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
     // step by 32 = q32 H + r32, so one conditional wrap keeps h in [0, H)
     const int q32 = 32 / H, r32 = 32 - q32 * H;
     int k = k0 + (int)lane / H, h = (int)lane % H;
-    const int nfull = nslots >> 5;
-    for (int it = 0; it < nfull; ++it) {
-        slot_step<PREC, FAST, false, CLIP, LIST>(A, S, T, P, PC, D, C, t, k, h, true, acc, pq, pq_n, rq_t,
-                                     rq_kh, rq_n, n_flag, n_re);
-        h += r32;
-        k += q32;
-        const bool wrap = h >= H;
-        h = wrap ? h - H : h;
-        k = wrap ? k + 1 : k;
+    const int nfull = nslots >> 5, nit = (nslots + 31) >> 5;
+    // iterations below it_pow never reach the sRGB linear segment
+    int it_pow = 0;
+    if constexpr (PREC == CVS_PREC_FP32_RECHECK && FAST) {
+        const int k_split = first_linseg_radius(T, C, S.r2, k0, k1);
+        it_pow = k_split == k1 ? nit : ((k_split - k0) * H) >> 5;
     }
-    if (nslots & 31) {
-        slot_step<PREC, FAST, true, CLIP, LIST>(A, S, T, P, PC, D, C, t, k, h, (int)lane < (nslots & 31), acc,
-                                    pq, pq_n, rq_t, rq_kh, rq_n, n_flag, n_re);
+    int it = 0;
+    for (int seg0 = 0; seg0 < nit; seg0 += kSegIters) {
+        const int seg1 = min(seg0 + kSegIters, nit);
+        const int full_end = min(seg1, nfull);
+        if constexpr (PREC == CVS_PREC_FP32_RECHECK && FAST) {
+            run_range<PREC, FAST, false, CLIP, LIST, false>(A, S, P, PC, D, it, min(full_end, it_pow),
+                                                            seg0, nslots, q32, r32, k, h, acc, fb);
+        }
+        run_range<PREC, FAST, false, CLIP, LIST, true>(A, S, P, PC, D, it, full_end, seg0, nslots,
+                                                       q32, r32, k, h, acc, fb);
+        if (it < seg1) {  // the item's last, partial iteration
+            if (PREC == CVS_PREC_FP32_RECHECK && FAST && it < it_pow)
+                run_range<PREC, FAST, true, CLIP, LIST, false>(A, S, P, PC, D, it, seg1, seg0,
+                                                               nslots, q32, r32, k, h, acc, fb);
+            else
+                run_range<PREC, FAST, true, CLIP, LIST, true>(A, S, P, PC, D, it, seg1, seg0,
+                                                              nslots, q32, r32, k, h, acc, fb);
+        }
+        if (PREC == CVS_PREC_FP32_RECHECK) {
+            __syncwarp();
+            collect_flagged<FAST>(A, S, T, C, t, k0, seg0, (seg1 - seg0 + 31) >> 5, fb, pq, pq_n,
+                                  acc, rq_t, rq_kh, rq_n, n_flag, n_re);
+        }
     }
     if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0)
         drain_flagged<FAST>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh, rq_n,
@@ -652,6 +768,8 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
     S.rq_t = reinterpret_cast<uint32_t*>(q);
     S.rq_kh = S.rq_t + nwarps * kRqCap;
     uint32_t* pq = S.rq_kh + nwarps * kRqCap + warp * kRqCap;
+    uint32_t* fb = S.rq_kh + 2 * nwarps * kRqCap + warp * (kFlagWords * 32);
+    for (int w = 0; w < kFlagWords; ++w) fb[w * 32 + lane_id()] = 0u;
     build_decide_lut(S.lut, A.hi_min, A.lo_max);
     for (int i = threadIdx.x; i < K; i += blockDim.x) S.r2[i] = dup(A.grid.r32[i]);
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
@@ -684,13 +802,13 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
         if (PREC == CVS_PREC_FP32_RECHECK) {
             const uint32_t fl = A.tf[t].flags;
             if (fl & 1u)
-                run_item<PREC, true, CLIP, LIST>(A, S, t, k0, k1, C, pq, rq_t, rq_kh, rq_n, n_flag,
+                run_item<PREC, true, CLIP, LIST>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
                                                  n_re);
             else
-                run_item<PREC, false, CLIP, LIST>(A, S, t, k0, k1, C, pq, rq_t, rq_kh, rq_n, n_flag,
+                run_item<PREC, false, CLIP, LIST>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
                                                   n_re);
         } else {
-            run_item<PREC, true, CLIP, LIST>(A, S, t, k0, k1, C, pq, rq_t, rq_kh, rq_n, n_flag,
+            run_item<PREC, true, CLIP, LIST>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
                                              n_re);
         }
     }
@@ -802,6 +920,11 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
     const int q32 = 32 / H, r32 = 32 - q32 * H;
     int k = k0 + (int)lane / H, h = (int)lane % H;
     const int nit = (nslots + 31) >> 5;
+    int it_pow = 0;  // iterations whose radii never reach the sRGB linear segment
+    if (PREC == CVS_PREC_FP32_RECHECK && FAST) {
+        const int k_split = first_linseg_radius(T, C, r2s, k0, k1);
+        it_pow = k_split == k1 ? nit : ((k_split - k0) * H) >> 5;
+    }
     for (int it = 0; it < nit; ++it) {
         const bool active = it * 32 + (int)lane < nslots;
         const int kk = active ? k : k0, hh = active ? h : 0;
@@ -810,8 +933,10 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
         bool flag = false;
         if (PREC == CVS_PREC_FP32_RECHECK) {
             const float4 sc = sc4s[hh];
-            flag = codes32<FAST>(P, PC, __fmul2_rn(r2, f2(sc.x, sc.y)), __fmul2_rn(r2, f2(sc.z, sc.w)),
-                                 A.half_w, yp, ym) && active;
+            const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y)), w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
+            if (it < it_pow) flag = codes32<FAST, false>(P, PC, u2, w2, A.half_w, yp, ym);
+            else flag = codes32<FAST, true>(P, PC, u2, w2, A.half_w, yp, ym);
+            flag = flag && active;
         } else if (active) {
             pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + kk), __ldg(A.grid.s64 + hh),
                          __ldg(A.grid.c64 + hh), A.qkey, qp, qm);
@@ -1173,7 +1298,8 @@ cudaError_t launch_setup_images(const ImageDesc* imgs, int n_imgs, int64_t total
 int search_smem_bytes(const GridDev& g, int block) {
     // (r, r) pairs, angle quadruples, then per warp: FP64 queue (targets, slots)
     // and flagged queue
-    return ((g.K * 8 + 15) & ~15) + g.H * 16 + 3 * 512 + (block / 32) * kRqCap * 12;
+    return ((g.K * 8 + 15) & ~15) + g.H * 16 + 3 * 512 +
+           (block / 32) * (kRqCap * 12 + kFlagWords * 32 * 4);
 }
 
 template <int PREC, bool CLIP, bool LIST>
