@@ -46,7 +46,8 @@ def kernel_source_hash() -> str:
     import hashlib
     from pathlib import Path
     csrc = Path(__file__).resolve().parent / "paper_2507_22901_gb300" / "csrc"
-    data = (csrc / "cvs_kernels.cu").read_bytes() + (csrc / "cvs_device.cuh").read_bytes()
+    data = b"".join((csrc / f).read_bytes()
+                    for f in ("cvs_kernels.cu", "cvs_slot32.cuh", "cvs_device.cuh"))
     return hashlib.sha256(data).hexdigest()[:16]
 REASON_BITS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",

@@ -102,7 +102,7 @@ __device__ __forceinline__ int mid_cube_sign(double z, double t) {
 }
 
 // Cube root of a positive normal double, correctly rounded to nearest.
-__device__ __noinline__ double cbrt_rn(double t) {
+static __device__ __noinline__ double cbrt_rn(double t) {
     double y = cbrt(t);  // within a few ulps
 #pragma unroll 1
     for (int it = 0; it < 8; ++it) {
@@ -285,7 +285,7 @@ __device__ __forceinline__ dd_t dd_mul(dd_t x, dd_t y) {
 }
 
 // sin and cos of x degrees for x in [0, 45], as double-double.
-__device__ void sincos_dd_deg(double x, dd_t& s, dd_t& c) {
+static __device__ void sincos_dd_deg(double x, dd_t& s, dd_t& c) {
     // t = x * pi/180 (double-double)
     const double p = __dmul_rn(x, CVS_PI180_HI);
     double e = __fma_rn(x, CVS_PI180_HI, -p);
@@ -319,7 +319,7 @@ __device__ __forceinline__ double dd_round(dd_t v, int* uncertain) {
 // Correctly rounded sin / cos of an angle in degrees (any finite double).
 // The reduction to [0, 45] degrees is exact (fmod, then subtractions that
 // Sterbenz's lemma makes exact), so sin(j + 180) = -sin(j) bit for bit.
-__device__ void sincos_deg_rn(double deg, double* s_out, double* c_out, int* uncertain) {
+static __device__ void sincos_deg_rn(double deg, double* s_out, double* c_out, int* uncertain) {
     const bool neg = deg < 0.0;
     double t = fmod(fabs(deg), 360.0);  // exact, in [0, 360)
     double ssign = 1.0, csign = 1.0;

@@ -9,9 +9,12 @@
 //             L*, converts both colours to 8-bit sRGB in FP32 (FMA + MUFU),
 //             tests gamut and the V_th / R_novib embedding-signal condition,
 //             and reduces count / max radius / pattern mask per warp.  Slots
-//             whose FP32 codes sit within W of a rounding boundary, and whose
-//             decision could change, are queued in shared memory and
-//             re-decided 32 at a time in FP64 (one slot per lane).
+//             whose FP32 codes sit within W of a rounding boundary are marked
+//             in a per-lane bitmap, decided after each segment by exact
+//             interval analysis (32 at a time), and, where that cannot decide,
+//             re-decided in FP64 (one slot per lane).
+// The FP32 slot itself (chain, decision, interval analysis) is in
+// cvs_slot32.cuh; the multi-threshold search is in cvs_multi.cu.
 //   finalize: per-target accumulators -> caller's capacity maps.
 // When the angle list is closed under +180 degrees, slot h covers angles h and
 // h + N/2: the "minus" colour of one is the "plus" colour of the other.
@@ -19,14 +22,11 @@
 
 #include "cvs_device.cuh"
 #include "cvs_internal.h"
+#include "cvs_slot32.cuh"
 
 namespace cvs {
 
 namespace {
-
-constexpr int kRqCap = 64;  // re-decision queue entries per warp
-
-__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
 // ------------------------------------------------------------ trig table
 __global__ void k_trig_table(const double* __restrict__ ang, int n, double* s64, double* c64,
@@ -116,275 +116,6 @@ __global__ void k_setup_images(const ImageDesc* __restrict__ imgs, int n_imgs, i
     const int64_t y = local / im.width, x = local - y * im.width;
     const uint8_t* px = im.rgb + y * im.pitch + 3 * x;
     setup_one(px[0], px[1], px[2], rmax, ((uint64_t)i << 40) | (uint64_t)local, tf, td, acc, p);
-}
-
-// ------------------------------------------------------------ FP32 slot
-// Codes of the pair at displacement (u, w) = (r sin j / 500, -r cos j / 200) in
-// f-space, as biased integers y = kMagicBits + q.  The plus and minus colours
-// run the same chain, so they travel as one float2 through the packed FP32x2
-// instructions (component-wise IEEE round-to-nearest, as the scalar ops).
-// Returns true if some code's unrounded value lies within W of a rounding
-// boundary.
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-
-// Per-target constants duplicated into (plus, minus) pairs, built once per
-// work item so that the packed instructions find their operands paired.
-struct PairsT {
-    float2 c1x, c2x, c1z, c2z;
-    float2 fx0, fz0, X30, Z30;
-    float2 lin0[3];
-};
-struct PairsC {
-    float2 Ax[3], Bz[3];
-};
-
-__device__ __forceinline__ PairsT make_pairs(const TargetF32& T) {
-    PairsT P;
-    P.c1x = dup(T.c1x);
-    P.c2x = dup(T.c2x);
-    P.c1z = dup(T.c1z);
-    P.c2z = dup(T.c2z);
-    P.fx0 = dup(T.fx0);
-    P.fz0 = dup(T.fz0);
-    P.X30 = dup(T.X30);
-    P.Z30 = dup(T.Z30);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) P.lin0[c] = dup(T.lin0[c]);
-    return P;
-}
-
-__device__ __forceinline__ PairsC make_pairs(const ChainF32& C) {
-    PairsC P;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        P.Ax[c] = dup(C.Ax[c]);
-        P.Bz[c] = dup(C.Bz[c]);
-    }
-    return P;
-}
-
-// f^-1 displacement of X and Z for the pair: u2 = (u, -u), w2 = (w, -w).
-template <bool FAST>
-__device__ __forceinline__ void delta_xz(const PairsT& P, float2 u2, float2 w2, float2& dX,
-                                         float2& dZ) {
-    if (FAST) {
-        // (f0 + u)^3 - f0^3 = u (3 f0^2 + u (3 f0 + u)), for +u and -u at once
-        dX = __fmul2_rn(u2, __ffma2_rn(u2, __fadd2_rn(P.c1x, u2), P.c2x));
-        dZ = __fmul2_rn(w2, __ffma2_rn(w2, __fadd2_rn(P.c1z, w2), P.c2z));
-    } else {
-        const float brk = (float)kFinvBreak, add = (float)kFLinAdd, mul = (float)kFinvLinMul;
-        const float2 fx = __fadd2_rn(P.fx0, u2), fz = __fadd2_rn(P.fz0, w2);
-        const float2 cx = __fmul2_rn(__fmul2_rn(fx, fx), fx), cz = __fmul2_rn(__fmul2_rn(fz, fz), fz);
-        const float2 lx = __fmul2_rn(__fadd2_rn(fx, dup(-add)), dup(mul));
-        const float2 lz = __fmul2_rn(__fadd2_rn(fz, dup(-add)), dup(mul));
-        dX = __fadd2_rn(f2(fx.x > brk ? cx.x : lx.x, fx.y > brk ? cx.y : lx.y), neg2(P.X30));
-        dZ = __fadd2_rn(f2(fz.x > brk ? cz.x : lz.x, fz.y > brk ? cz.y : lz.y), neg2(P.Z30));
-    }
-}
-
-// Codes of the pair as biased integers y = kMagicBits + q.  The plus and minus
-// colours run the same chain, so they travel as one float2 through the packed
-// FP32x2 instructions (component-wise IEEE round-to-nearest, as the scalar
-// ops).  Returns true if some code's unrounded value lies within W of a
-// rounding boundary.  LINSEG = false when every linear RGB value of the call
-// is known to lie above the sRGB linear segment (see pow_branch_only).
-template <bool FAST, bool LINSEG = true>
-__device__ __forceinline__ bool codes32(const PairsT& P, const PairsC& C, float2 u2, float2 w2,
-                                        float half_w, int yp[3], int ym[3]) {
-    float2 dX, dZ;
-    delta_xz<FAST>(P, u2, w2, dX, dZ);
-    bool flag = false;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float2 lin = __ffma2_rn(C.Bz[c], dZ, __ffma2_rn(C.Ax[c], dX, P.lin0[c]));
-        float lgp, lgm, pp, pm;
-        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lgp) : "f"(lin.x));
-        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lgm) : "f"(lin.y));
-        const float2 e = __fmul2_rn(f2(lgp, lgm), dup(5.0f / 12.0f));
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pp) : "f"(e.x));
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pm) : "f"(e.y));
-        const float2 vpow = __ffma2_rn(dup(269.025f), f2(pp, pm), dup(-14.025f));
-        float2 v = vpow;
-        if (LINSEG) {
-            const float2 vlin = __fmul2_rn(lin, dup(3294.6f));
-            v = f2(lin.x <= 0.0031308f ? vlin.x : vpow.x, lin.y <= 0.0031308f ? vlin.y : vpow.y);
-        }
-        const float2 y = __fadd2_rn(v, dup(kMagic));
-        const float2 rr = __fadd2_rn(y, dup(-kMagic));
-        const float2 d = __ffma2_rn(rr, dup(-1.0f), v);  // v - rr, exact
-        flag |= fabsf(d.x) >= half_w;
-        flag |= fabsf(d.y) >= half_w;
-        yp[c] = __float_as_int(y.x);
-        ym[c] = __float_as_int(y.y);
-    }
-    return flag;
-}
-
-// True when no candidate at radius r (any angle) of a fast-path target can
-// reach the linear segment of the sRGB encode (lin <= 0.0031308).  The f^-1
-// displacement u (c2 + u (c1 + u)) increases with u, so per channel the
-// smallest linear value over |u| <= r/500, |w| <= r/200 sits at an end of
-// each range.  The margin (2e-5) is far above the FP32 chain's error in
-// linear RGB (below 1e-6) and the rounding of this bound.
-__device__ __forceinline__ bool pow_branch_only(const TargetF32& T, const ChainF32& C, float r) {
-    const float U = r * 0.002f * 1.00001f, V = r * 0.005f * 1.00001f;
-    const float xlo = -U * (T.c2x - U * (T.c1x - U)), xhi = U * (T.c2x + U * (T.c1x + U));
-    const float zlo = -V * (T.c2z - V * (T.c1z - V)), zhi = V * (T.c2z + V * (T.c1z + V));
-    bool ok = true;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float g = T.lin0[c] + fminf(C.Ax[c] * xlo, C.Ax[c] * xhi) +
-                        fminf(C.Bz[c] * zlo, C.Bz[c] * zhi);
-        ok = ok && g > 0.0031308f + 2e-5f;
-    }
-    return ok;
-}
-
-// First radius index in [k0, k1) whose candidates may reach the sRGB linear
-// segment (k1 if none); warp-uniform.
-__device__ __forceinline__ int first_linseg_radius(const TargetF32& T, const ChainF32& C,
-                                                   const float2* r2s, int k0, int k1) {
-    const unsigned lane = threadIdx.x & 31u;
-    for (int kb = k0; kb < k1; kb += 32) {
-        const int kk = kb + (int)lane;
-        const bool bad = kk < k1 && !pow_branch_only(T, C, r2s[kk].x);
-        const unsigned b = __ballot_sync(0xFFFFFFFFu, bad);
-        if (b) return kb + __ffs(b) - 1;
-    }
-    return k1;
-}
-
-// Embedding-signal decision on biased codes y = kMagicBits + q (exact when no
-// code is flagged).  Per channel the difference d = q+ - q- indexes a 512-entry
-// table in shared memory (index d & 511): bit 3 = neither high nor low, bit
-// (2 - c) = high.  OR-ing the three channels gives the pattern in bits 0..2 and
-// "invalid" in bit 3; okmask has bit p set for each enabled pattern p.
-// Gamut (reject): all six codes lie in [0, 255] exactly when the OR of the
-// six y, XOR kMagicBits, is at most 255 (every |q| here is far below 2^22).
-template <bool CLIP>
-__device__ __forceinline__ int decide32(const int yp_in[3], const int ym_in[3],
-                                        const uint8_t* __restrict__ lut, uint32_t okmask) {
-    int yp[3], ym[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        yp[c] = yp_in[c];
-        ym[c] = ym_in[c];
-        if (CLIP) {
-            yp[c] = min(max(yp[c], kMagicBits), kMagicBits + 255);
-            ym[c] = min(max(ym[c], kMagicBits), kMagicBits + 255);
-        }
-    }
-    bool in_gamut = true;
-    if (!CLIP) {
-        const uint32_t o = ((uint32_t)yp[0] | (uint32_t)ym[0] | (uint32_t)yp[1]) |
-                           ((uint32_t)ym[1] | (uint32_t)yp[2] | (uint32_t)ym[2]);
-        in_gamut = (o ^ (uint32_t)kMagicBits) <= 255u;
-    }
-    uint32_t comb = 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) comb |= lut[c * 512 + ((yp[c] - ym[c]) & 511)];
-    const bool ok = in_gamut && ((okmask >> comb) & 1u);
-    return ok ? (int)(comb & 7u) : 0;
-}
-
-// Build the three 512-entry channel tables of decide32 in shared memory.
-__device__ __forceinline__ void build_decide_lut(uint8_t* lut, int32_t hi_min, int32_t lo_max) {
-    for (int i = threadIdx.x; i < 3 * 512; i += blockDim.x) {
-        const int c = i >> 9, idx = i & 511;
-        const int d = idx < 256 ? idx : idx - 512;  // idx = d & 511 for d in [-256, 255]
-        const int ad = d < 0 ? -d : d;
-        uint8_t e;
-        if (ad > 255) e = 8;  // cannot happen for codes in [0, 255]
-        else {
-            const bool hi = ad >= hi_min, lo = ad <= lo_max;
-            e = (uint8_t)((hi ? (1u << (2 - c)) : 0u) | ((hi || lo) ? 0u : 8u));
-        }
-        lut[i] = e;
-    }
-}
-
-// Exact analysis of a slot with flagged codes: each flagged code may be one
-// off towards its nearby boundary.  intervals32 recomputes the slot (operation
-// for operation as codes32) and bounds every code; certain_from decides a
-// threshold set from the bounds: -1 = re-decide in FP64, else the exact
-// pattern (0 = fail).
-struct Intervals {
-    int lo[6], hi[6];  // values 0..2 plus colour, 3..5 minus colour
-    bool any_flag;
-};
-
-template <bool FAST>
-__device__ __noinline__ Intervals intervals32(const TargetF32 T, const ChainF32 C, float u,
-                                              float w, float half_w, int32_t clip) {
-    const PairsT P = make_pairs(T);
-    const PairsC PC = make_pairs(C);
-    float2 dX2, dZ2;
-    delta_xz<FAST>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
-    Intervals I;
-    I.any_flag = false;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float2 lin2 = __ffma2_rn(PC.Bz[c], dZ2, __ffma2_rn(PC.Ax[c], dX2, P.lin0[c]));
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const float lin = s ? lin2.y : lin2.x;
-            const float v = encode_v32(lin);
-            const float rr = __fsub_rn(__fadd_rn(v, kMagic), kMagic);
-            const int q = (int)rr;
-            const float d = __fsub_rn(v, rr);
-            const bool f = fabsf(d) >= half_w;
-            I.any_flag |= f;
-            const int j = 3 * s + c;
-            I.lo[j] = q - ((f && d < 0.0f) ? 1 : 0);
-            I.hi[j] = q + ((f && d >= 0.0f) ? 1 : 0);
-            if (clip) {
-                I.lo[j] = min(max(I.lo[j], 0), 255);
-                I.hi[j] = min(max(I.hi[j], 0), 255);
-            }
-        }
-    }
-    return I;
-}
-
-__device__ __forceinline__ int certain_from(const Intervals& I, int32_t hi_min, int32_t lo_max,
-                                            uint32_t mask2, int32_t clip, int list_mode) {
-    bool certain_out = false, maybe_out = false;
-    if (!clip) {
-#pragma unroll
-        for (int j = 0; j < 6; ++j) {
-            certain_out |= I.hi[j] < 0 || I.lo[j] > 255;
-            maybe_out |= I.lo[j] < 0 || I.hi[j] > 255;
-        }
-    }
-    if (certain_out) return 0;
-    bool certain_invalid = false, unstable = maybe_out;
-    int pattern = 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const int dmax = max(I.hi[c] - I.lo[3 + c], I.hi[3 + c] - I.lo[c]);
-        const int dmin = max(0, max(I.lo[c] - I.hi[3 + c], I.lo[3 + c] - I.hi[c]));
-        const int cls_lo = dmin >= hi_min ? 2 : (dmin <= lo_max ? 0 : 1);
-        const int cls_hi = dmax >= hi_min ? 2 : (dmax <= lo_max ? 0 : 1);
-        if (cls_lo == 1 && cls_hi == 1) certain_invalid = true;
-        if (cls_lo != cls_hi) unstable = true;
-        pattern |= (cls_lo == 2 ? 1 : 0) << (2 - c);
-    }
-    if (certain_invalid) return 0;
-    if (unstable) return -1;
-    const bool ok = (mask2 >> pattern) & 1u;
-    // a list needs the exact codes of a passing pair
-    if (ok && list_mode && I.any_flag) return -1;
-    return ok ? pattern : 0;
-}
-
-template <bool FAST>
-__device__ __noinline__ int certain32(const TargetF32 T, const ChainF32 C, float u, float w,
-                                      float half_w, int32_t hi_min, int32_t lo_max,
-                                      uint32_t mask2, int32_t clip, int list_mode) {
-    const Intervals I = intervals32<FAST>(T, C, u, w, half_w, clip);
-    return certain_from(I, hi_min, lo_max, mask2, clip, list_mode);
 }
 
 // ------------------------------------------------------------ search kernel
@@ -512,10 +243,10 @@ __device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S
         const uint32_t kh = pq[lane];
         k = (int)(kh & 0xFFFFu);
         h = (int)(kh >> 16);
-        const float r = S.r2[k].x;
-        const float4 sc = S.sc4[h];
-        pc = certain32<FAST>(T, C, r * sc.x, r * sc.z, A.half_w, A.hi_min, A.lo_max, A.mask2,
-                             A.clip, A.list_mode);
+        const float2 r2 = S.r2[k];
+        const float r = r2.x;
+        pc = certain32<FAST>(T, C, r2, S.sc4[h], A.half_w, A.hi_min, A.lo_max, A.mask2, A.clip,
+                             A.list_mode);
         if (pc > 0) {
             cnt += inc;
             rmax = fmaxf(rmax, r);
@@ -751,7 +482,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
 #define CVS_SEARCH_MAX_THREADS kSearchBlock
 #endif
 #ifndef CVS_SEARCH_MIN_BLOCKS
-#define CVS_SEARCH_MIN_BLOCKS 5
+#define CVS_SEARCH_MIN_BLOCKS 6
 #endif
 
 template <int PREC, bool CLIP, bool LIST>
@@ -823,243 +554,6 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
         if (n_flag) atomicAdd(A.stats + 0, n_flag);
         if (n_re) atomicAdd(A.stats + 1, n_re);
     }
-}
-
-// ------------------------------------------------------------ multi-threshold search
-// The paper's experiment (§3 Experiments, Table 1): every candidate decided
-// against n_thr threshold sets in one pass.  The pair chain runs once per slot;
-// each set has its own classification table; per set the warp's passes are
-// reduced with ballot / REDUX and lane s keeps set s's running totals.
-template <int PREC, bool FAST, bool CLIP>
-__device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s, const float4* sc4s,
-                                           const uint8_t* luts, int64_t t, int k0, int k1,
-                                           const ChainF32& C, uint32_t* pq, uint32_t* rq_kh,
-                                           unsigned long long& n_flag, unsigned long long& n_re) {
-    const unsigned lane = lane_id();
-    const int H = A.grid.H, NT = A.n_thr;
-    const int inc = A.grid.sym ? 2 : 1;
-    const int nslots = (k1 - k0) * H;
-    TargetF32 T;
-    TargetF64 D;
-    if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
-    else D = A.td[t];
-    const PairsT P = make_pairs(T);
-    const PairsC PC = make_pairs(C);
-    int cnt = 0;
-    uint32_t rbits = 0, pm = 0;  // set `lane`'s totals (lanes < NT)
-    int pq_n = 0;
-    // one warp-wide merge of per-lane patterns of set s into lane s's totals
-    auto merge = [&](int s, int pattern, float r) {
-        const bool pass = pattern > 0;
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, pass);
-        if (ball) {
-            const uint32_t pmw = __reduce_or_sync(0xFFFFFFFFu, pass ? (1u << pattern) : 0u);
-            const uint32_t rmw = __reduce_max_sync(0xFFFFFFFFu, pass ? __float_as_uint(r) : 0u);
-            if ((int)lane == s) {
-                cnt += __popc(ball) * inc;
-                pm |= pmw;
-                rbits = max(rbits, rmw);
-            }
-        }
-    };
-    // flagged slots: bounds once, then every set; FP64 when some set is undecided
-    auto drain = [&](int n) {
-        int k = 0, h = 0;
-        Intervals I{};
-        float r = 0.0f;
-        const bool mine = (int)lane < n;
-        if (mine) {
-            const uint32_t kh = pq[lane];
-            k = (int)(kh & 0xFFFFu);
-            h = (int)(kh >> 16);
-            r = r2s[k].x;
-            const float4 sc = sc4s[h];
-            I = intervals32<FAST>(T, C, r * sc.x, r * sc.z, A.half_w, CLIP ? 1 : 0);
-        }
-        bool need64 = false;
-        for (int s = 0; s < NT; ++s) {
-            const int pc = mine ? certain_from(I, A.hi_min[s], A.lo_max[s], A.mask2[s], CLIP ? 1 : 0, 0)
-                                : 0;
-            need64 |= pc < 0;
-            merge(s, pc < 0 ? 0 : pc, r);
-        }
-        // slots with an undecided set: exact FP64 codes, every set decided from them
-        // (the sets decided above are decided again identically, so count only here)
-        const unsigned b64 = __ballot_sync(0xFFFFFFFFu, need64);
-        if (b64) {
-            int qp[3] = {0, 0, 0}, qm[3] = {0, 0, 0};
-            if (need64) {
-                const double rr = __ldg(A.grid.r64 + k), ss = __ldg(A.grid.s64 + h),
-                             cc = __ldg(A.grid.c64 + h);
-                const TargetF64 DD = A.td[t];
-                pair_codes64(DD.L, DD.a, DD.b, rr, ss, cc, A.qkey, qp, qm);
-                if (CLIP) {
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        qp[i] = min(max(qp[i], 0), 255);
-                        qm[i] = min(max(qm[i], 0), 255);
-                    }
-                }
-                ++n_re;
-            }
-            for (int s = 0; s < NT; ++s) {
-                int pat = 0;
-                if (need64) {
-                    const int pc = certain_from(I, A.hi_min[s], A.lo_max[s], A.mask2[s],
-                                                CLIP ? 1 : 0, 0);
-                    if (pc < 0) {  // undecided in FP32: the FP64 decision counts now
-                        Decide dc{A.hi_min[s], A.lo_max[s], A.mask2[s], CLIP ? 1 : 0};
-                        pat = decide_codes(qp, qm, dc);
-                    }
-                }
-                merge(s, pat, r);
-            }
-        }
-        __syncwarp();
-    };
-    const int q32 = 32 / H, r32 = 32 - q32 * H;
-    int k = k0 + (int)lane / H, h = (int)lane % H;
-    const int nit = (nslots + 31) >> 5;
-    int it_pow = 0;  // iterations whose radii never reach the sRGB linear segment
-    if (PREC == CVS_PREC_FP32_RECHECK && FAST) {
-        const int k_split = first_linseg_radius(T, C, r2s, k0, k1);
-        it_pow = k_split == k1 ? nit : ((k_split - k0) * H) >> 5;
-    }
-    for (int it = 0; it < nit; ++it) {
-        const bool active = it * 32 + (int)lane < nslots;
-        const int kk = active ? k : k0, hh = active ? h : 0;
-        const float2 r2 = r2s[kk];
-        int yp[3], ym[3], qp[3], qm[3];
-        bool flag = false;
-        if (PREC == CVS_PREC_FP32_RECHECK) {
-            const float4 sc = sc4s[hh];
-            const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y)), w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
-            if (it < it_pow) flag = codes32<FAST, false>(P, PC, u2, w2, A.half_w, yp, ym);
-            else flag = codes32<FAST, true>(P, PC, u2, w2, A.half_w, yp, ym);
-            flag = flag && active;
-        } else if (active) {
-            pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + kk), __ldg(A.grid.s64 + hh),
-                         __ldg(A.grid.c64 + hh), A.qkey, qp, qm);
-            if (CLIP) {
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    qp[i] = min(max(qp[i], 0), 255);
-                    qm[i] = min(max(qm[i], 0), 255);
-                }
-            }
-        }
-        for (int s = 0; s < NT; ++s) {
-            int pattern = 0;
-            if (PREC == CVS_PREC_FP32_RECHECK) {
-                pattern = decide32<CLIP>(yp, ym, luts + s * 3 * 512, A.mask2[s]);
-                if (flag || !active) pattern = 0;
-            } else if (active) {
-                Decide dc{A.hi_min[s], A.lo_max[s], A.mask2[s], CLIP ? 1 : 0};
-                pattern = decide_codes(qp, qm, dc);
-            }
-            merge(s, pattern, r2.x);
-        }
-        if (PREC == CVS_PREC_FP32_RECHECK) {
-            const unsigned fball = __ballot_sync(0xFFFFFFFFu, flag);
-            if (fball) {
-                if (flag) {
-                    pq[pq_n + __popc(fball & ((1u << lane) - 1u))] = (uint32_t)kk | ((uint32_t)hh << 16);
-                    ++n_flag;
-                }
-                pq_n += __popc(fball);
-                __syncwarp();
-                if (pq_n >= 32) {
-                    drain(32);
-                    const int rest = pq_n - 32;
-                    const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
-                    __syncwarp();
-                    if ((int)lane < rest) pq[lane] = mv;
-                    __syncwarp();
-                    pq_n = rest;
-                }
-            }
-        }
-        h += r32;
-        k += q32;
-        const bool wrap = h >= H;
-        h = wrap ? h - H : h;
-        k = wrap ? k + 1 : k;
-    }
-    if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0) drain(pq_n);
-    if ((int)lane < NT && cnt) {
-        Acc* ac = A.acc + t * NT + lane;
-        atomicAdd(&ac->count, cnt);
-        atomicMax(&ac->rmax_bits, (int)rbits);
-        atomicOr(&ac->pmask, pm >> 1);
-    }
-    (void)rq_kh;
-}
-
-template <int PREC, bool CLIP>
-__global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS) k_search_multi(const MultiArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int K = A.grid.K, H = A.grid.H, NT = A.n_thr;
-    float2* r2s = reinterpret_cast<float2*>(smem);
-    float4* sc4s = reinterpret_cast<float4*>(smem + ((K * 8 + 15) & ~15));
-    uint8_t* luts = smem + ((K * 8 + 15) & ~15) + H * 16;
-    uint32_t* pq_all = reinterpret_cast<uint32_t*>(luts + ((NT * 3 * 512 + 15) & ~15));
-    const int warp = threadIdx.x >> 5;
-    uint32_t* pq = pq_all + warp * kRqCap;
-    for (int s2 = 0; s2 < NT; ++s2) build_decide_lut(luts + s2 * 3 * 512, A.hi_min[s2], A.lo_max[s2]);
-    for (int i = threadIdx.x; i < K; i += blockDim.x) r2s[i] = dup(A.grid.r32[i]);
-    for (int i = threadIdx.x; i < H; i += blockDim.x) {
-        const float2 sc = A.grid.sc32[i];
-        sc4s[i] = make_float4(sc.x, -sc.x, sc.y, -sc.y);
-    }
-    __syncthreads();
-    ChainF32 C;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        C.Ax[c] = __double2float_rn(__dmul_rn(c_MI[3 * c], c_W[0]));
-        C.Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
-    }
-    unsigned long long n_flag = 0, n_re = 0;
-    const int kchunk = A.kchunk;
-    const int n_kc = (K + kchunk - 1) / kchunk;
-    const unsigned long long n_items = (unsigned long long)A.n_targets * n_kc;
-    const unsigned lane = lane_id();
-    while (true) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(A.work_counter, 1ull);
-        item = __shfl_sync(0xFFFFFFFFu, item, 0);
-        if (item >= n_items) break;
-        const int64_t t = (int64_t)(item / (unsigned long long)n_kc);
-        const int kc = (int)(item - (unsigned long long)t * n_kc);
-        const int k0 = kc * kchunk, k1 = min(k0 + kchunk, K);
-        if (PREC == CVS_PREC_FP32_RECHECK) {
-            if (A.tf[t].flags & 1u)
-                multi_item<PREC, true, CLIP>(A, r2s, sc4s, luts, t, k0, k1, C, pq, nullptr, n_flag, n_re);
-            else
-                multi_item<PREC, false, CLIP>(A, r2s, sc4s, luts, t, k0, k1, C, pq, nullptr, n_flag, n_re);
-        } else {
-            multi_item<PREC, true, CLIP>(A, r2s, sc4s, luts, t, k0, k1, C, pq, nullptr, n_flag, n_re);
-        }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        n_flag += __shfl_xor_sync(0xFFFFFFFFu, n_flag, off);
-        n_re += __shfl_xor_sync(0xFFFFFFFFu, n_re, off);
-    }
-    if (lane == 0) {
-        if (n_flag) atomicAdd(A.stats + 0, n_flag);
-        if (n_re) atomicAdd(A.stats + 1, n_re);
-    }
-}
-
-__global__ void k_init_acc(Acc* __restrict__ acc, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    Acc z;
-    z.count = 0;
-    z.rmax_bits = __float_as_int(-1.0f);
-    z.pmask = 0;
-    z.pad = 0;
-    acc[i] = z;
 }
 
 // ------------------------------------------------------------ finalize
@@ -1329,40 +823,6 @@ cudaError_t launch_search_p(const SearchArgs& a, cudaStream_t st) {
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t st) {
     return a.prec == CVS_PREC_FP64 ? launch_search_p<CVS_PREC_FP64>(a, st)
                                    : launch_search_p<CVS_PREC_FP32_RECHECK>(a, st);
-}
-
-int multi_smem_bytes(const GridDev& g, int n_thr, int block) {
-    return ((g.K * 8 + 15) & ~15) + g.H * 16 + ((n_thr * 3 * 512 + 15) & ~15) +
-           (block / 32) * kRqCap * 4;
-}
-
-template <int PREC, bool CLIP>
-cudaError_t launch_multi_t(const MultiArgs& a, int block, cudaStream_t st) {
-    const int smem = multi_smem_bytes(a.grid, a.n_thr, block);
-    const void* fn = (const void*)k_search_multi<PREC, CLIP>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    k_search_multi<PREC, CLIP><<<a.num_sms * per_sm, block, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_search_multi(const MultiArgs& a, cudaStream_t st) {
-    const int block = kSearchBlock;
-    if (a.prec == CVS_PREC_FP64)
-        return a.clip ? launch_multi_t<CVS_PREC_FP64, true>(a, block, st)
-                      : launch_multi_t<CVS_PREC_FP64, false>(a, block, st);
-    return a.clip ? launch_multi_t<CVS_PREC_FP32_RECHECK, true>(a, block, st)
-                  : launch_multi_t<CVS_PREC_FP32_RECHECK, false>(a, block, st);
-}
-
-cudaError_t launch_init_acc(Acc* acc, int64_t n, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_init_acc<<<blocks_for(n, 256), 256, 0, st>>>(acc, n);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_finalize_colors(const Acc* acc, int64_t n, float* max_r, int32_t* count,

@@ -1,0 +1,294 @@
+// cvs_slot32.cuh - the FP32 slot of the colour-pair search (sm_103a), shared
+// by the single-threshold and the multi-threshold search kernels.
+//
+// A slot is one (radius k, angle h) of a target: the point-symmetric pair
+// (L*, a* +- r sin j, b* +- r cos j) of §2 Methods, converted back to 8-bit
+// sRGB.  This header holds the packed FP32x2 chain (codes32), the
+// table-driven embedding-signal decision (decide32), and the exact interval
+// analysis of slots whose codes sit near a rounding boundary (intervals32,
+// certain_from).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "cvs_device.cuh"
+#include "cvs_internal.h"
+
+namespace cvs {
+namespace {
+
+constexpr int kRqCap = 64;  // re-decision queue entries per warp
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// ------------------------------------------------------------ FP32 slot
+// Codes of the pair at displacement (u, w) = (r sin j / 500, -r cos j / 200) in
+// f-space, as biased integers y = kMagicBits + q.  The plus and minus colours
+// run the same chain, so they travel as one float2 through the packed FP32x2
+// instructions (component-wise IEEE round-to-nearest, as the scalar ops).
+// Returns true if some code's unrounded value lies within W of a rounding
+// boundary.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// Per-target constants duplicated into (plus, minus) pairs, built once per
+// work item so that the packed instructions find their operands paired.
+struct PairsT {
+    float2 c1x, c2x, c1z, c2z;
+    float2 fx0, fz0, X30, Z30;
+    float2 lin0[3];
+};
+struct PairsC {
+    float2 Ax[3], Bz[3];
+};
+
+__device__ __forceinline__ PairsT make_pairs(const TargetF32& T) {
+    PairsT P;
+    P.c1x = dup(T.c1x);
+    P.c2x = dup(T.c2x);
+    P.c1z = dup(T.c1z);
+    P.c2z = dup(T.c2z);
+    P.fx0 = dup(T.fx0);
+    P.fz0 = dup(T.fz0);
+    P.X30 = dup(T.X30);
+    P.Z30 = dup(T.Z30);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) P.lin0[c] = dup(T.lin0[c]);
+    return P;
+}
+
+__device__ __forceinline__ PairsC make_pairs(const ChainF32& C) {
+    PairsC P;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        P.Ax[c] = dup(C.Ax[c]);
+        P.Bz[c] = dup(C.Bz[c]);
+    }
+    return P;
+}
+
+// f^-1 displacement of X and Z for the pair: u2 = (u, -u), w2 = (w, -w).
+template <bool FAST>
+__device__ __forceinline__ void delta_xz(const PairsT& P, float2 u2, float2 w2, float2& dX,
+                                         float2& dZ) {
+    if (FAST) {
+        // (f0 + u)^3 - f0^3 = u (3 f0^2 + u (3 f0 + u)), for +u and -u at once
+        dX = __fmul2_rn(u2, __ffma2_rn(u2, __fadd2_rn(P.c1x, u2), P.c2x));
+        dZ = __fmul2_rn(w2, __ffma2_rn(w2, __fadd2_rn(P.c1z, w2), P.c2z));
+    } else {
+        const float brk = (float)kFinvBreak, add = (float)kFLinAdd, mul = (float)kFinvLinMul;
+        const float2 fx = __fadd2_rn(P.fx0, u2), fz = __fadd2_rn(P.fz0, w2);
+        const float2 cx = __fmul2_rn(__fmul2_rn(fx, fx), fx), cz = __fmul2_rn(__fmul2_rn(fz, fz), fz);
+        const float2 lx = __fmul2_rn(__fadd2_rn(fx, dup(-add)), dup(mul));
+        const float2 lz = __fmul2_rn(__fadd2_rn(fz, dup(-add)), dup(mul));
+        dX = __fadd2_rn(f2(fx.x > brk ? cx.x : lx.x, fx.y > brk ? cx.y : lx.y), neg2(P.X30));
+        dZ = __fadd2_rn(f2(fz.x > brk ? cz.x : lz.x, fz.y > brk ? cz.y : lz.y), neg2(P.Z30));
+    }
+}
+
+// Codes of the pair as biased integers y = kMagicBits + q.  The plus and minus
+// colours run the same chain, so they travel as one float2 through the packed
+// FP32x2 instructions (component-wise IEEE round-to-nearest, as the scalar
+// ops).  Returns true if some code's unrounded value lies within W of a
+// rounding boundary.  LINSEG = false when every linear RGB value of the call
+// is known to lie above the sRGB linear segment (see pow_branch_only).
+template <bool FAST, bool LINSEG = true>
+__device__ __forceinline__ bool codes32(const PairsT& P, const PairsC& C, float2 u2, float2 w2,
+                                        float half_w, int yp[3], int ym[3],
+                                        float2* resid = nullptr) {
+    float2 dX, dZ;
+    delta_xz<FAST>(P, u2, w2, dX, dZ);
+    bool flag = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 lin = __ffma2_rn(C.Bz[c], dZ, __ffma2_rn(C.Ax[c], dX, P.lin0[c]));
+        float lgp, lgm, pp, pm;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lgp) : "f"(lin.x));
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lgm) : "f"(lin.y));
+        const float2 e = __fmul2_rn(f2(lgp, lgm), dup(5.0f / 12.0f));
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pp) : "f"(e.x));
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(pm) : "f"(e.y));
+        const float2 vpow = __ffma2_rn(dup(269.025f), f2(pp, pm), dup(-14.025f));
+        float2 v = vpow;
+        if (LINSEG) {
+            const float2 vlin = __fmul2_rn(lin, dup(3294.6f));
+            v = f2(lin.x <= 0.0031308f ? vlin.x : vpow.x, lin.y <= 0.0031308f ? vlin.y : vpow.y);
+        }
+        const float2 y = __fadd2_rn(v, dup(kMagic));
+        const float2 rr = __fadd2_rn(y, dup(-kMagic));
+        const float2 d = __ffma2_rn(rr, dup(-1.0f), v);  // v - rr, exact
+        flag |= fabsf(d.x) >= half_w;
+        flag |= fabsf(d.y) >= half_w;
+        if (resid) resid[c] = d;  // v - round(v) of (plus, minus)
+        yp[c] = __float_as_int(y.x);
+        ym[c] = __float_as_int(y.y);
+    }
+    return flag;
+}
+
+// True when no candidate at radius r (any angle) of a fast-path target can
+// reach the linear segment of the sRGB encode (lin <= 0.0031308).  The f^-1
+// displacement u (c2 + u (c1 + u)) increases with u, so per channel the
+// smallest linear value over |u| <= r/500, |w| <= r/200 sits at an end of
+// each range.  The margin (2e-5) is far above the FP32 chain's error in
+// linear RGB (below 1e-6) and the rounding of this bound.
+__device__ __forceinline__ bool pow_branch_only(const TargetF32& T, const ChainF32& C, float r) {
+    const float U = r * 0.002f * 1.00001f, V = r * 0.005f * 1.00001f;
+    const float xlo = -U * (T.c2x - U * (T.c1x - U)), xhi = U * (T.c2x + U * (T.c1x + U));
+    const float zlo = -V * (T.c2z - V * (T.c1z - V)), zhi = V * (T.c2z + V * (T.c1z + V));
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float g = T.lin0[c] + fminf(C.Ax[c] * xlo, C.Ax[c] * xhi) +
+                        fminf(C.Bz[c] * zlo, C.Bz[c] * zhi);
+        ok = ok && g > 0.0031308f + 2e-5f;
+    }
+    return ok;
+}
+
+// First radius index in [k0, k1) whose candidates may reach the sRGB linear
+// segment (k1 if none); warp-uniform.
+__device__ __forceinline__ int first_linseg_radius(const TargetF32& T, const ChainF32& C,
+                                                   const float2* r2s, int k0, int k1) {
+    const unsigned lane = threadIdx.x & 31u;
+    for (int kb = k0; kb < k1; kb += 32) {
+        const int kk = kb + (int)lane;
+        const bool bad = kk < k1 && !pow_branch_only(T, C, r2s[kk].x);
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, bad);
+        if (b) return kb + __ffs(b) - 1;
+    }
+    return k1;
+}
+
+// Embedding-signal decision on biased codes y = kMagicBits + q (exact when no
+// code is flagged).  Per channel the difference d = q+ - q- indexes a 512-entry
+// table in shared memory (index d & 511): bit 3 = neither high nor low, bit
+// (2 - c) = high.  OR-ing the three channels gives the pattern in bits 0..2 and
+// "invalid" in bit 3; okmask has bit p set for each enabled pattern p.
+// Gamut (reject): all six codes lie in [0, 255] exactly when the OR of the
+// six y, XOR kMagicBits, is at most 255 (every |q| here is far below 2^22).
+template <bool CLIP>
+__device__ __forceinline__ int decide32(const int yp_in[3], const int ym_in[3],
+                                        const uint8_t* __restrict__ lut, uint32_t okmask) {
+    int yp[3], ym[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        yp[c] = yp_in[c];
+        ym[c] = ym_in[c];
+        if (CLIP) {
+            yp[c] = min(max(yp[c], kMagicBits), kMagicBits + 255);
+            ym[c] = min(max(ym[c], kMagicBits), kMagicBits + 255);
+        }
+    }
+    bool in_gamut = true;
+    if (!CLIP) {
+        const uint32_t o = ((uint32_t)yp[0] | (uint32_t)ym[0] | (uint32_t)yp[1]) |
+                           ((uint32_t)ym[1] | (uint32_t)yp[2] | (uint32_t)ym[2]);
+        in_gamut = (o ^ (uint32_t)kMagicBits) <= 255u;
+    }
+    uint32_t comb = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) comb |= lut[c * 512 + ((yp[c] - ym[c]) & 511)];
+    const bool ok = in_gamut && ((okmask >> comb) & 1u);
+    return ok ? (int)(comb & 7u) : 0;
+}
+
+// Build the three 512-entry channel tables of decide32 in shared memory.
+__device__ __forceinline__ void build_decide_lut(uint8_t* lut, int32_t hi_min, int32_t lo_max) {
+    for (int i = threadIdx.x; i < 3 * 512; i += blockDim.x) {
+        const int c = i >> 9, idx = i & 511;
+        const int d = idx < 256 ? idx : idx - 512;  // idx = d & 511 for d in [-256, 255]
+        const int ad = d < 0 ? -d : d;
+        uint8_t e;
+        if (ad > 255) e = 8;  // cannot happen for codes in [0, 255]
+        else {
+            const bool hi = ad >= hi_min, lo = ad <= lo_max;
+            e = (uint8_t)((hi ? (1u << (2 - c)) : 0u) | ((hi || lo) ? 0u : 8u));
+        }
+        lut[i] = e;
+    }
+}
+
+// Exact analysis of a slot with flagged codes: each flagged code may be one
+// off towards its nearby boundary.  intervals32 recomputes the slot (operation
+// for operation as codes32) and bounds every code; certain_from decides a
+// threshold set from the bounds: -1 = re-decide in FP64, else the exact
+// pattern (0 = fail).
+struct Intervals {
+    int lo[6], hi[6];  // values 0..2 plus colour, 3..5 minus colour
+    bool any_flag;
+};
+
+template <bool FAST>
+__device__ __forceinline__ Intervals intervals32(const TargetF32 T, const ChainF32 C, float2 r2,
+                                              float4 sc, float half_w, int32_t clip) {
+    const PairsT P = make_pairs(T);
+    const PairsC PC = make_pairs(C);
+    int yp[3], ym[3];
+    float2 d[3];
+    codes32<FAST, true>(P, PC, __fmul2_rn(r2, f2(sc.x, sc.y)), __fmul2_rn(r2, f2(sc.z, sc.w)),
+                        half_w, yp, ym, d);
+    Intervals I;
+    I.any_flag = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int q = (s ? ym[c] : yp[c]) - kMagicBits;
+            const float dd = s ? d[c].y : d[c].x;
+            const bool f = fabsf(dd) >= half_w;
+            I.any_flag |= f;
+            const int j = 3 * s + c;
+            I.lo[j] = q - ((f && dd < 0.0f) ? 1 : 0);
+            I.hi[j] = q + ((f && dd >= 0.0f) ? 1 : 0);
+            if (clip) {
+                I.lo[j] = min(max(I.lo[j], 0), 255);
+                I.hi[j] = min(max(I.hi[j], 0), 255);
+            }
+        }
+    }
+    return I;
+}
+
+__device__ __forceinline__ int certain_from(const Intervals& I, int32_t hi_min, int32_t lo_max,
+                                            uint32_t mask2, int32_t clip, int list_mode) {
+    bool certain_out = false, maybe_out = false;
+    if (!clip) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            certain_out |= I.hi[j] < 0 || I.lo[j] > 255;
+            maybe_out |= I.lo[j] < 0 || I.hi[j] > 255;
+        }
+    }
+    if (certain_out) return 0;
+    bool certain_invalid = false, unstable = maybe_out;
+    int pattern = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int dmax = max(I.hi[c] - I.lo[3 + c], I.hi[3 + c] - I.lo[c]);
+        const int dmin = max(0, max(I.lo[c] - I.hi[3 + c], I.lo[3 + c] - I.hi[c]));
+        const int cls_lo = dmin >= hi_min ? 2 : (dmin <= lo_max ? 0 : 1);
+        const int cls_hi = dmax >= hi_min ? 2 : (dmax <= lo_max ? 0 : 1);
+        if (cls_lo == 1 && cls_hi == 1) certain_invalid = true;
+        if (cls_lo != cls_hi) unstable = true;
+        pattern |= (cls_lo == 2 ? 1 : 0) << (2 - c);
+    }
+    if (certain_invalid) return 0;
+    if (unstable) return -1;
+    const bool ok = (mask2 >> pattern) & 1u;
+    // a list needs the exact codes of a passing pair
+    if (ok && list_mode && I.any_flag) return -1;
+    return ok ? pattern : 0;
+}
+
+template <bool FAST>
+__device__ __forceinline__ int certain32(const TargetF32& T, const ChainF32& C, float2 r2,
+                                         float4 sc, float half_w, int32_t hi_min, int32_t lo_max,
+                                         uint32_t mask2, int32_t clip, int list_mode) {
+    const Intervals I = intervals32<FAST>(T, C, r2, sc, half_w, clip);
+    return certain_from(I, hi_min, lo_max, mask2, clip, list_mode);
+}
+
+}  // namespace
+}  // namespace cvs
