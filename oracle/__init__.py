@@ -115,6 +115,9 @@ def lib() -> ctypes.CDLL:
             L.orc_search_colors.restype = None
             L.orc_decide_pair.argtypes = [vp, vp, d, d, u32, ctypes.c_int, vp, vp]
             L.orc_decide_pair.restype = ctypes.c_int
+            L.orc_embed.argtypes = [P(_Consts), vp, vp, i64, vp, i32, vp, vp, i32, d, d, u32,
+                                    ctypes.c_int, vp, vp, vp, ctypes.c_int]
+            L.orc_embed.restype = None
             L.orc_roundtrip_all.argtypes = [P(_Consts), P(d), ctypes.c_int]
             L.orc_roundtrip_all.restype = i64
             L.orc_openmp_max_threads.argtypes = []
@@ -272,3 +275,25 @@ def search_colors(rgbs, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gam
 
 def max_threads() -> int:
     return lib().orc_openmp_max_threads()
+
+
+def embed(rgbs, patterns, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0,
+          threads=1, trig_tab=None):
+    """Embedding of requested patterns (Fig. 1a): per pixel (frame_a (n,3) uint8,
+    frame_b (n,3) uint8, choice uint32 = k | m << 16 or 0xFFFFFFFF)."""
+    rgbs = np.ascontiguousarray(np.asarray(rgbs, np.uint8).reshape(-1, 3))
+    pats = np.ascontiguousarray(np.asarray(patterns, np.uint8).reshape(-1))
+    n = rgbs.shape[0]
+    if pats.shape[0] != n:
+        raise ValueError("one pattern per pixel")
+    radii = np.ascontiguousarray(radii, np.float64)
+    s, c = trig_tab if trig_tab is not None else trig_table(angles_deg)
+    s = np.ascontiguousarray(s, np.float64)
+    c = np.ascontiguousarray(c, np.float64)
+    fa = np.zeros((n, 3), np.uint8)
+    fb = np.zeros((n, 3), np.uint8)
+    choice = np.zeros(n, np.uint32)
+    lib().orc_embed(ctypes.byref(consts()), _ptr(rgbs), _ptr(pats), n, _ptr(radii), len(radii),
+                    _ptr(s), _ptr(c), len(s), float(v_th), float(r_novib), int(pattern_mask),
+                    int(gamut_mode), _ptr(fa), _ptr(fb), _ptr(choice), int(threads))
+    return fa, fb, choice

@@ -320,6 +320,60 @@ void orc_search_colors(const orc_consts* C, const uint8_t* rgb, int64_t n_target
     (void)n_threads;
 }
 
+/* Embedding (Fig. 1a: devices see an area that looks uniform to people switch
+ * between two colours).  Per pixel i with requested pattern p = pattern[i] in
+ * 1..7: among the candidates (k, m) whose pair passes with exactly pattern p,
+ * take the first in (radius value, k, m) order - the smallest colour shift,
+ * then the caller's radius and angle order.  Frame A gets the pair's "plus"
+ * colour (a* + D_a, b* + D_b), frame B its "minus" colour.  Pixels with p
+ * outside 1..7, or with no such candidate, keep their own colour in both
+ * frames.  choice[i] = k | m << 16, or 0xFFFFFFFF when nothing was embedded.
+ * rgb, frame_a, frame_b: 3 bytes per pixel, dense. */
+void orc_embed(const orc_consts* C, const uint8_t* rgb, const uint8_t* pattern,
+               int64_t n_pixels, const double* radii, int32_t n_radii, const double* sin_t,
+               const double* cos_t, int32_t n_angles, double v_th, double r_novib,
+               uint32_t pattern_mask, int gamut_mode, uint8_t* frame_a, uint8_t* frame_b,
+               uint32_t* choice, int n_threads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+    for (int64_t i = 0; i < n_pixels; ++i) {
+        const uint8_t* src = rgb + 3 * i;
+        int p = pattern[i];
+        int found = 0;
+        double best_r = 0.0;
+        uint32_t best = 0xFFFFFFFFu;
+        uint8_t best_plus[3] = {src[0], src[1], src[2]};
+        uint8_t best_minus[3] = {src[0], src[1], src[2]};
+        if (p >= 1 && p <= 7) {
+            double lab[3];
+            orc_target_lab(C, src, lab);
+            for (int32_t k = 0; k < n_radii; ++k) {
+                /* (k, m) run in increasing order, so only a strictly smaller
+                 * radius value can replace an earlier candidate */
+                if (found && !(radii[k] < best_r)) continue;
+                for (int32_t m = 0; m < n_angles; ++m) {
+                    int qp[3], qm[3];
+                    uint8_t op[3], om[3];
+                    orc_pair_codes(C, lab, radii[k], sin_t[m], cos_t[m], qp, qm);
+                    if (decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, op, om) != p)
+                        continue;
+                    found = 1;
+                    best_r = radii[k];
+                    best = (uint32_t)k | ((uint32_t)m << 16);
+                    memcpy(best_plus, op, 3);
+                    memcpy(best_minus, om, 3);
+                    break;  /* the smallest m of this radius */
+                }
+            }
+        }
+        memcpy(frame_a + 3 * i, best_plus, 3);
+        memcpy(frame_b + 3 * i, best_minus, 3);
+        choice[i] = best;
+    }
+    (void)n_threads;
+}
+
 /* Self-check over all 2^24 8-bit colours: RGB -> Lab -> linear RGB must give
  * back the decode table within max_err, and the same 8-bit codes.  Returns the
  * number of colours whose codes differ; *max_err receives the largest
