@@ -302,6 +302,32 @@ def run_extras(ctx, torch, device, W, cvs):
         "lookup_gb_s": px * 21 / look_s / 1e9,
         "maps_identical_to_search": same}
     del imgs, maps, maps2
+    # the embedding step: a 2D-code-like pattern map (16-pixel modules, 60% of
+    # them carrying a pattern 1..7) over a 1920x1080 and a 3840x2160 frame
+    emb = {}
+    for (w, h) in ((1920, 1080), (3840, 2160)):
+        terms = W.image_params(1, seed=21, sizes=[(w, h)])[0][2]
+        img = W.render_image_torch(w, h, terms, 21, device=device)
+        pat = torch.from_numpy(W.code_pattern(h, w, module=16, seed=21)).to(device)
+        fa, fb, ch = ctx.embed_image(img, pat, r3, a3, 50.0, 0.5)
+        ctx.synchronize()
+        reps = 3
+        t0.record()
+        for _ in range(reps):
+            ctx.embed_image(img, pat, r3, a3, 50.0, 0.5, frames=(fa, fb))
+        t1.record()
+        ctx.synchronize()
+        torch.cuda.synchronize(device)
+        sec = t0.elapsed_time(t1) / 1e3 / reps
+        req = int((pat > 0).sum().item())
+        got = int((ch >= 0).sum().item())
+        emb[f"{w}x{h}"] = {"seconds": sec, "frames_per_s": 1.0 / sec,
+                           "mpixels_per_s": w * h / sec / 1e6,
+                           "pixels_requested": req, "pixels_embedded": got,
+                           "embedded_fraction_of_requested": got / max(req, 1)}
+        del img, pat, fa, fb, ch
+    out["embedding"] = {"workload": "synthetic frame, 16-px modules, 60% carry a pattern; "
+                                    "64 radii x 180 angles, V_th 50, R_novib 0.5", **emb}
     # the experiment of §3: every cube colour under all 12 (V_th, R_novib) sets,
     # one multi-set pass against 12 single-set passes
     cube = torch.from_numpy(W.color_cube()).to(device)

@@ -231,6 +231,33 @@ cvs_status cvs_search_images(cvs_ctx* ctx, const cvs_image* batch, int32_t n,
                              cvs_precision prec, const cvs_capacity_map* maps,
                              void* stream);
 
+/* ---------------------------------------------------------------- embedding
+ * The embedding step of Fig. 1a: two frames shown in alternation look like
+ * the image to a person, while a camera sees the pixels with information
+ * switch between two colours.  Per pixel with requested pattern p (1..7, the
+ * Table 1 bit word R,G,B), the pair is the first passing candidate of pattern
+ * exactly p in (radius value, radius index k, angle index m) order, i.e. the
+ * smallest shift in L*a*b*; frame A gets its "plus" colour (a* + r sin j,
+ * b* + r cos j), frame B its "minus" colour.  Pixels whose pattern byte is 0
+ * or above 7, and pixels without such a pair, get their own colour in both
+ * frames.
+ *   img:         device image (HWC bytes, row pitch).
+ *   pattern_dev: device bytes, pattern of pixel (x, y) at y * pattern_pitch + x.
+ *   frame_a_dev, frame_b_dev: device outputs, HWC bytes, row pitch frame_pitch
+ *                (distinct buffers; each may alias img only if frame_pitch
+ *                equals its pitch - not recommended).
+ *   choice_dev:  optional device output (NULL to skip), width * height dense
+ *                uint32: k | m << 16, or 0xFFFFFFFF where nothing was embedded.
+ * The thresholds' pattern_mask still applies (a masked pattern never embeds).
+ * Asynchronous on `stream`.  cvs_get_stats reports the kernel time; its
+ * flagged / rechecked counters count the flagged slots that had to be decided
+ * exactly and those re-decided in FP64 (x2 on folded grids). */
+cvs_status cvs_embed_image(cvs_ctx* ctx, const cvs_image* img, const uint8_t* pattern_dev,
+                           int64_t pattern_pitch, const cvs_grid* grid,
+                           const cvs_thresholds* thr, cvs_precision prec,
+                           uint8_t* frame_a_dev, uint8_t* frame_b_dev, int64_t frame_pitch,
+                           uint32_t* choice_dev, void* stream);
+
 /* ------------------------------------------------ colour-keyed memoisation
  * A pixel's result is a pure function of its colour (and of the grid and
  * thresholds).  A capacity table holds the per-colour results of all 2^24

@@ -136,6 +136,8 @@ def lib() -> ctypes.CDLL:
                                    st),
         "cvs_search_colors_multi": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), i32, st,
                                      P(cvs_capacity_map), vp], st),
+        "cvs_embed_image": ([vp, P(cvs_image), vp, i64, P(cvs_grid), P(cvs_thresholds), st, vp,
+                             vp, i64, vp, vp], st),
         "cvs_search_images": ([vp, P(cvs_image), i32, P(cvs_grid), P(cvs_thresholds), st,
                                P(cvs_capacity_map), vp], st),
         "cvs_synchronize": ([vp, vp], st),
@@ -339,6 +341,35 @@ class Context:
                                            out[1].ctypes.data, out[2].ctypes.data),
               "cvs_search_colors_host")
         return out
+
+    def embed_image(self, image, pattern, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
+                    gamut_mode=0, precision=PREC_FP32_RECHECK, frames=None, choice=True,
+                    stream=None):
+        """The two alternating frames of an (H, W, 3) uint8 CUDA image carrying a
+        per-pixel pattern ((H, W) uint8 CUDA tensor, 1..7, 0 = none).
+        Returns (frame_a, frame_b, choice) CUDA tensors; choice (H, W) int32 view
+        of k | m << 16 (-1 where nothing was embedded) or None."""
+        import torch
+        if image.dim() != 3 or image.shape[2] != 3 or image.dtype != torch.uint8:
+            raise ValueError("image must be an (H, W, 3) uint8 tensor")
+        h, w = image.shape[0], image.shape[1]
+        if tuple(pattern.shape) != (h, w) or pattern.dtype != torch.uint8:
+            raise ValueError("pattern must be an (H, W) uint8 tensor")
+        if image.stride(2) != 1 or image.stride(1) != 3 or pattern.stride(1) != 1:
+            raise ValueError("rows must be dense (HWC image, row-major pattern)")
+        if frames is None:
+            frames = (torch.empty((h, w, 3), dtype=torch.uint8, device=image.device),
+                      torch.empty((h, w, 3), dtype=torch.uint8, device=image.device))
+        ch = torch.empty((h, w), dtype=torch.int32, device=image.device) if choice else None
+        im = cvs_image(image.data_ptr(), w, h, image.stride(0))
+        g, keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        check(lib().cvs_embed_image(self._h, ctypes.byref(im), pattern.data_ptr(), pattern.stride(0),
+                                    ctypes.byref(g), ctypes.byref(t), int(precision),
+                                    frames[0].data_ptr(), frames[1].data_ptr(),
+                                    frames[0].stride(0), ch.data_ptr() if ch is not None else None,
+                                    _stream_ptr(stream)), "cvs_embed_image")
+        return frames[0], frames[1], ch
 
     def search_images(self, images, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
                       gamut_mode=0, precision=PREC_FP32_RECHECK, maps=None, stream=None):

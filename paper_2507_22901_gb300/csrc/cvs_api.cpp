@@ -1,6 +1,7 @@
 // cvs_api.cpp - host side of libcvsearch: the C ABI declared in
 // include/cvsearch.h.  Validates arguments, owns the context's scratch memory
 // and grid tables, and launches the kernels of cvs_kernels.cu.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstdarg>
@@ -102,6 +103,8 @@ struct cvs_ctx {
     std::map<std::array<int64_t, 7>, LaunchShape> tuned;
     Acc* acc_tune = nullptr;
     int64_t cap_acc_tune = 0;
+    // embedding: radius indices sorted by (radius value, index), K entries
+    int32_t* d_order = nullptr;
     // multi-threshold search: n x n_thr accumulators
     Acc* acc_multi = nullptr;
     int64_t cap_acc_multi = 0;
@@ -178,6 +181,7 @@ cvs_status ensure_grid(cvs_ctx* c, const cvs_grid* g) {
         CVS_CUDA(cudaMalloc(&d.s64, sizeof(double) * kMaxGrid));
         CVS_CUDA(cudaMalloc(&d.c64, sizeof(double) * kMaxGrid));
         CVS_CUDA(cudaMalloc(&c->d_angles, sizeof(double) * kMaxGrid));
+        CVS_CUDA(cudaMalloc(&c->d_order, sizeof(int32_t) * kMaxGrid));
         c->cap_grid = kMaxGrid;
     }
     std::vector<float> r32(K);
@@ -186,7 +190,13 @@ cvs_status ensure_grid(cvs_ctx* c, const cvs_grid* g) {
         r32[i] = (float)g->radii[i];
         if (g->radii[i] > rmax) rmax = g->radii[i];
     }
+    std::vector<int32_t> order(K);
+    for (int i = 0; i < K; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [g](int32_t x, int32_t y) { return g->radii[x] < g->radii[y]; });
     cudaStream_t st = c->own;
+    CVS_CUDA(cudaMemcpyAsync(c->d_order, order.data(), sizeof(int32_t) * K,
+                             cudaMemcpyHostToDevice, st));
     CVS_CUDA(cudaMemcpyAsync(d.r64, g->radii, sizeof(double) * K, cudaMemcpyHostToDevice, st));
     CVS_CUDA(cudaMemcpyAsync(d.r32, r32.data(), sizeof(float) * K, cudaMemcpyHostToDevice, st));
     CVS_CUDA(cudaMemcpyAsync(c->d_angles, g->angles_deg, sizeof(double) * N,
@@ -524,7 +534,7 @@ void cvs_destroy(cvs_ctx* c) {
     void* ptrs[] = {c->grid.r32, c->grid.sc32, c->grid.r64, c->grid.s64, c->grid.c64,
                     c->d_angles, c->d_status, c->tf, c->td, c->acc, c->qkey, c->counters,
                     c->dense, c->compact, c->d_imgs, c->d_in, c->d_maxr, c->d_count, c->d_pmask,
-                    c->d_rgb1, c->d_probe};
+                    c->d_rgb1, c->d_probe, c->d_order};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     drop_graphs(c);
@@ -860,6 +870,74 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
     st0 = graph_launch(c, key, st, enqueue, &h);
     if (st0 == CVS_OK) c->last_pending = true;
     return st0;
+}
+
+cvs_status cvs_embed_image(cvs_ctx* c, const cvs_image* img, const uint8_t* pattern_dev,
+                           int64_t pattern_pitch, const cvs_grid* grid, const cvs_thresholds* thr,
+                           cvs_precision prec, uint8_t* frame_a_dev, uint8_t* frame_b_dev,
+                           int64_t frame_pitch, uint32_t* choice_dev, void* stream) {
+    if (!c || !img || !pattern_dev || !frame_a_dev || !frame_b_dev)
+        return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (!img->rgb || img->width <= 0 || img->height <= 0 || img->pitch_bytes < 3LL * img->width)
+        return fail(CVS_ERR_INVALID_ARG, "bad image pointer, size or pitch");
+    if (pattern_pitch < img->width) return fail(CVS_ERR_INVALID_ARG, "pattern pitch < width");
+    if (frame_pitch < 3LL * img->width) return fail(CVS_ERR_INVALID_ARG, "frame pitch < 3 * width");
+    if (frame_a_dev == frame_b_dev) return fail(CVS_ERR_INVALID_ARG, "the two frames must differ");
+    if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
+        return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    const int64_t px = (int64_t)img->width * img->height;
+    if (px >= ((int64_t)1 << 40)) return fail(CVS_ERR_INVALID_ARG, "image too large");
+    cvs_status st0 = check_grid(grid);
+    if (st0 == CVS_OK) st0 = check_thresholds(thr);
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = ensure_targets(c, px);
+    if (st0 != CVS_OK) return st0;
+    cudaStream_t st = (cudaStream_t)stream;
+    const ImageDesc h{img->rgb, img->pitch_bytes, img->width, img->height, 0, nullptr, nullptr,
+                      nullptr};
+    CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, 1));
+    CVS_CUDA(cudaMemcpyAsync(c->d_imgs, &h, sizeof(ImageDesc), cudaMemcpyHostToDevice, st));
+    CVS_CUDA(launch_setup_images(c->d_imgs, 1, px, c->grid.rmax, c->tf, c->td, c->acc, st));
+    EmbedArgs a{};
+    a.tf = c->tf;
+    a.td = c->td;
+    a.n = px;
+    a.rgb = img->rgb;
+    a.pitch = img->pitch_bytes;
+    a.width = img->width;
+    a.height = img->height;
+    a.pattern = pattern_dev;
+    a.pattern_pitch = pattern_pitch;
+    a.frame_a = frame_a_dev;
+    a.frame_b = frame_b_dev;
+    a.frame_pitch = frame_pitch;
+    a.choice = choice_dev;
+    a.grid = c->grid;
+    a.order = c->d_order;
+    a.qkey = c->qkey;
+    thresholds_to_int(thr, &a.hi_min, &a.lo_max);
+    a.mask2 = thr->pattern_mask << 1;
+    a.clip = thr->gamut_mode;
+    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
+    a.half_w = (float)(0.5 - c->window);
+    a.prec = (int32_t)prec;
+    a.work_counter = c->counters;
+    a.stats = c->counters + 1;
+    a.num_sms = c->num_sms;
+    CVS_CUDA(cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), st));
+    CVS_CUDA(cudaEventRecord(c->ev0, st));
+    CVS_CUDA(launch_embed(a, st));
+    CVS_CUDA(cudaEventRecord(c->ev1, st));
+    CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, 4 * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, st));
+    cvs_stats& s = c->last;
+    s = cvs_stats{};
+    s.targets = px;
+    s.symmetric = c->grid.sym;
+    s.precision = (int32_t)prec;
+    c->last_pending = true;
+    return CVS_OK;
 }
 
 cvs_status cvs_autotune(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, const cvs_grid* grid,

@@ -100,6 +100,34 @@ struct MultiArgs {
     int num_sms;
 };
 
+// The embedding step: per pixel the first passing pair of the requested
+// pattern in (radius value, radius index, angle index) order.
+struct EmbedArgs {
+    const TargetF32* tf;
+    const TargetF64* td;
+    int64_t n;                  // pixels (width * height)
+    const uint8_t* rgb;         // the image (HWC bytes, row pitch)
+    int64_t pitch;
+    int32_t width, height;
+    const uint8_t* pattern;     // requested pattern per pixel (row pitch), 1..7; else none
+    int64_t pattern_pitch;
+    uint8_t* frame_a;           // plus colours (HWC bytes, row pitch frame_pitch)
+    uint8_t* frame_b;           // minus colours
+    int64_t frame_pitch;
+    uint32_t* choice;           // dense width*height: k | m << 16, or 0xFFFFFFFF; may be NULL
+    GridDev grid;
+    const int32_t* order;       // K radius indices sorted by (radius value, index)
+    const long long* qkey;
+    int32_t hi_min, lo_max;
+    uint32_t mask2;
+    int32_t clip;
+    float half_w;
+    int32_t prec;
+    unsigned long long* work_counter;
+    unsigned long long* stats;  // [0] flagged slots decided exactly, [1] slots re-decided in FP64
+    int num_sms;
+};
+
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_trig_table(const double* angles_dev, int n, double* s64, double* c64,
                               float2* sc32, int* status, cudaStream_t st);
@@ -111,6 +139,7 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t st);
 cudaError_t launch_finalize_colors(const Acc* acc, int64_t n, float* max_r, int32_t* count,
                                    uint8_t* pmask, cudaStream_t st);
 cudaError_t launch_search_multi(const MultiArgs& a, cudaStream_t st);
+cudaError_t launch_embed(const EmbedArgs& a, cudaStream_t st);
 cudaError_t launch_init_acc(Acc* acc, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t n,
                                    const ImageDesc* imgs, cudaStream_t st);

@@ -140,6 +140,17 @@ def render_image_torch(w: int, h: int, terms, noise_seed: int, device="cuda"):
     return torch.clamp(torch.round(img).to(torch.int16) + noise, 0, 255).to(torch.uint8)
 
 
+def code_pattern(h: int, w: int, module: int = 8, seed: int = 0, fill: float = 0.6) -> np.ndarray:
+    """(h, w) uint8 requested-pattern map of a 2D-code-like embedding: square
+    modules of `module` pixels, each carrying one 3-bit pattern 1..7 with
+    probability `fill`, else 0 (nothing embedded)."""
+    rng = np.random.default_rng(seed)
+    mh, mw = -(-h // module), -(-w // module)
+    cells = rng.integers(1, 8, (mh, mw)).astype(np.uint8)
+    cells[rng.random((mh, mw)) >= fill] = 0
+    return np.ascontiguousarray(np.repeat(np.repeat(cells, module, 0), module, 1)[:h, :w])
+
+
 def serving_requests(n: int = 600, seed: int = 2, rate: float = 120.0):
     """Poisson arrivals: list of (arrival_time_s, width, height, image_param_index)."""
     rng = np.random.default_rng(seed)
