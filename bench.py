@@ -328,6 +328,34 @@ def run_extras(ctx, torch, device, W, cvs):
         del img, pat, fa, fb, ch
     out["embedding"] = {"workload": "synthetic frame, 16-px modules, 60% carry a pattern; "
                                     "64 radii x 180 angles, V_th 50, R_novib 0.5", **emb}
+    # the same frames through the embedding table (all 2^24 colours x 7 patterns)
+    t0.record()
+    etab = ctx.build_embed_table(r3, a3, 50.0, 0.5)
+    t1.record()
+    torch.cuda.synchronize(device)
+    etab_build_s = t0.elapsed_time(t1) / 1e3
+    via = {"table_build_s": etab_build_s}
+    for (w, h) in ((1920, 1080), (3840, 2160)):
+        terms = W.image_params(1, seed=21, sizes=[(w, h)])[0][2]
+        img = W.render_image_torch(w, h, terms, 21, device=device)
+        pat = torch.from_numpy(W.code_pattern(h, w, module=16, seed=21)).to(device)
+        d = ctx.embed_image(img, pat, r3, a3, 50.0, 0.5)
+        g = etab.embed_image(img, pat)
+        torch.cuda.synchronize(device)
+        same = all(torch.equal(x, y) for x, y in zip(d, g))
+        reps = 50
+        t0.record()
+        for _ in range(reps):
+            etab.embed_image(img, pat, frames=(g[0], g[1]))
+        t1.record()
+        torch.cuda.synchronize(device)
+        sec = t0.elapsed_time(t1) / 1e3 / reps
+        via[f"{w}x{h}"] = {"seconds": sec, "frames_per_s": 1.0 / sec,
+                           "identical_to_direct": same,
+                           "gb_s": w * h * 22 / sec / 1e9}
+        del img, pat, d, g
+    etab.close()
+    out["embedding_via_table"] = via
     # the experiment of §3: every cube colour under all 12 (V_th, R_novib) sets,
     # one multi-set pass against 12 single-set passes
     cube = torch.from_numpy(W.color_cube()).to(device)

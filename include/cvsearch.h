@@ -258,6 +258,26 @@ cvs_status cvs_embed_image(cvs_ctx* ctx, const cvs_image* img, const uint8_t* pa
                            uint8_t* frame_a_dev, uint8_t* frame_b_dev, int64_t frame_pitch,
                            uint32_t* choice_dev, void* stream);
 
+/* An embedding table: the pairs of cvs_embed_image for all 2^24 8-bit
+ * colours x 7 patterns, from one search of every colour (radii in sorted
+ * order, first hit per pattern).  Afterwards the frames of any image are a
+ * gather from the table, identical to cvs_embed_image's on the same grid,
+ * thresholds and precision.  The table lives on the context's device
+ * (2^24 x 7 x 12 bytes = 1.41 GB); the build is synchronous. */
+typedef struct cvs_etab cvs_etab;
+
+cvs_status cvs_etab_build(cvs_ctx* ctx, const cvs_grid* grid, const cvs_thresholds* thr,
+                          cvs_precision prec, cvs_etab** out, void* stream);
+
+/* Frames (and optionally choices) of one image from the table; arguments and
+ * layout as cvs_embed_image.  Asynchronous on `stream`. */
+cvs_status cvs_etab_embed_image(cvs_etab* table, const cvs_image* img, const uint8_t* pattern_dev,
+                                int64_t pattern_pitch, uint8_t* frame_a_dev, uint8_t* frame_b_dev,
+                                int64_t frame_pitch, uint32_t* choice_dev, void* stream);
+
+/* Release a table (waits for the device). */
+void cvs_etab_destroy(cvs_etab* table);
+
 /* ------------------------------------------------ colour-keyed memoisation
  * A pixel's result is a pure function of its colour (and of the grid and
  * thresholds).  A capacity table holds the per-colour results of all 2^24

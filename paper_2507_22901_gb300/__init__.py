@@ -8,7 +8,7 @@ entry point raises.
 """
 from ._build import build  # noqa: F401
 from .binding import (  # noqa: F401
-    PAIR_DTYPE, PREC_FP32_RECHECK, PREC_FP64, CapacityTable, Context, CvsError, Server,
+    PAIR_DTYPE, PREC_FP32_RECHECK, PREC_FP64, CapacityTable, Context, CvsError, EmbedTable, Server,
     header_functions, lib,
     signal_bounds,
 )

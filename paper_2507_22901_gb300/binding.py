@@ -149,6 +149,9 @@ def lib() -> ctypes.CDLL:
         "cvs_lut_lookup_images": ([vp, P(cvs_image), i32, P(cvs_capacity_map), vp], st),
         "cvs_lut_lookup_colors": ([vp, vp, i64, P(cvs_capacity_map), vp], st),
         "cvs_lut_destroy": ([vp], None),
+        "cvs_etab_build": ([vp, P(cvs_grid), P(cvs_thresholds), st, P(vp), vp], st),
+        "cvs_etab_embed_image": ([vp, P(cvs_image), vp, i64, vp, vp, i64, vp, vp], st),
+        "cvs_etab_destroy": ([vp], None),
         "cvs_reserve": ([vp, P(cvs_grid), i64, i32], st),
         "cvs_server_create": ([P(vp), P(cvs_server_config), P(cvs_grid), P(cvs_thresholds), st], st),
         "cvs_server_destroy": ([vp], None),
@@ -349,19 +352,7 @@ class Context:
         per-pixel pattern ((H, W) uint8 CUDA tensor, 1..7, 0 = none).
         Returns (frame_a, frame_b, choice) CUDA tensors; choice (H, W) int32 view
         of k | m << 16 (-1 where nothing was embedded) or None."""
-        import torch
-        if image.dim() != 3 or image.shape[2] != 3 or image.dtype != torch.uint8:
-            raise ValueError("image must be an (H, W, 3) uint8 tensor")
-        h, w = image.shape[0], image.shape[1]
-        if tuple(pattern.shape) != (h, w) or pattern.dtype != torch.uint8:
-            raise ValueError("pattern must be an (H, W) uint8 tensor")
-        if image.stride(2) != 1 or image.stride(1) != 3 or pattern.stride(1) != 1:
-            raise ValueError("rows must be dense (HWC image, row-major pattern)")
-        if frames is None:
-            frames = (torch.empty((h, w, 3), dtype=torch.uint8, device=image.device),
-                      torch.empty((h, w, 3), dtype=torch.uint8, device=image.device))
-        ch = torch.empty((h, w), dtype=torch.int32, device=image.device) if choice else None
-        im = cvs_image(image.data_ptr(), w, h, image.stride(0))
+        im, frames, ch = _embed_buffers(image, pattern, frames, choice)
         g, keep = make_grid(radii, angles_deg)
         t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
         check(lib().cvs_embed_image(self._h, ctypes.byref(im), pattern.data_ptr(), pattern.stride(0),
@@ -428,6 +419,17 @@ class Context:
                                   ctypes.byref(h), _stream_ptr(stream)), "cvs_lut_build")
         return CapacityTable(h)
 
+    def build_embed_table(self, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
+                          gamut_mode=0, precision=PREC_FP32_RECHECK,
+                          stream=None) -> "EmbedTable":
+        """Embedding table of all 2^24 colours x 7 patterns for this grid and thresholds."""
+        g, keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        h = ctypes.c_void_p()
+        check(lib().cvs_etab_build(self._h, ctypes.byref(g), ctypes.byref(t), int(precision),
+                                   ctypes.byref(h), _stream_ptr(stream)), "cvs_etab_build")
+        return EmbedTable(h)
+
     def precision_probe(self, rgb_dev, radii, angles_deg) -> dict:
         """FP32-vs-FP64 error report of every plus colour (see cvs_precision_probe)."""
         g, keep = make_grid(radii, angles_deg)
@@ -488,6 +490,50 @@ class CapacityTable:
         check(lib().cvs_lut_lookup_images(self._h, descs, n, cmaps, _stream_ptr(stream)),
               "cvs_lut_lookup_images")
         return maps
+
+
+def _embed_buffers(image, pattern, frames, choice):
+    import torch
+    if image.dim() != 3 or image.shape[2] != 3 or image.dtype != torch.uint8:
+        raise ValueError("image must be an (H, W, 3) uint8 tensor")
+    h, w = image.shape[0], image.shape[1]
+    if tuple(pattern.shape) != (h, w) or pattern.dtype != torch.uint8:
+        raise ValueError("pattern must be an (H, W) uint8 tensor")
+    if image.stride(2) != 1 or image.stride(1) != 3 or pattern.stride(1) != 1:
+        raise ValueError("rows must be dense (HWC image, row-major pattern)")
+    if frames is None:
+        frames = (torch.empty((h, w, 3), dtype=torch.uint8, device=image.device),
+                  torch.empty((h, w, 3), dtype=torch.uint8, device=image.device))
+    ch = torch.empty((h, w), dtype=torch.int32, device=image.device) if choice else None
+    return cvs_image(image.data_ptr(), w, h, image.stride(0)), frames, ch
+
+
+class EmbedTable:
+    """The embedding's pair for every colour and pattern (cvs_etab); frames
+    become gathers identical to Context.embed_image."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def close(self):
+        if self._h:
+            lib().cvs_etab_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def embed_image(self, image, pattern, frames=None, choice=True, stream=None):
+        im, frames, ch = _embed_buffers(image, pattern, frames, choice)
+        check(lib().cvs_etab_embed_image(self._h, ctypes.byref(im), pattern.data_ptr(),
+                                         pattern.stride(0), frames[0].data_ptr(),
+                                         frames[1].data_ptr(), frames[0].stride(0),
+                                         ch.data_ptr() if ch is not None else None,
+                                         _stream_ptr(stream)), "cvs_etab_embed_image")
+        return frames[0], frames[1], ch
 
 
 class Server:

@@ -1100,6 +1100,124 @@ cvs_status cvs_lut_lookup_images(cvs_lut* L, const cvs_image* batch, int32_t n,
     return CVS_OK;
 }
 
+}  // extern "C"
+
+struct cvs_etab {
+    int device = 0;
+    uint32_t* choice = nullptr;  // 2^24 x 7: k | m << 16, or 0xFFFFFFFF
+    uint64_t* codes = nullptr;   // 2^24 x 7: plus R,G,B and minus R,G,B in bytes 0..5
+};
+
+extern "C" {
+
+cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds* thr,
+                          cvs_precision prec, cvs_etab** out, void* stream) {
+    if (!c || !out) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
+        return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    cvs_status st0 = check_grid(grid);
+    if (st0 == CVS_OK) st0 = check_thresholds(thr);
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    constexpr int64_t kColours = int64_t(1) << 24, kChunk = int64_t(1) << 22;
+    if (st0 == CVS_OK) st0 = ensure_targets(c, kChunk);
+    if (st0 != CVS_OK) return st0;
+    cvs_etab* E = new cvs_etab();
+    E->device = c->device;
+    uint8_t* rgb = nullptr;
+    cudaError_t e = cudaMalloc(&E->choice, sizeof(uint32_t) * 7 * kColours);
+    if (e == cudaSuccess) e = cudaMalloc(&E->codes, sizeof(uint64_t) * 7 * kColours);
+    if (e == cudaSuccess) e = cudaMalloc(&rgb, 3 * kChunk);
+    if (e != cudaSuccess) {
+        if (rgb) cudaFree(rgb);
+        cvs_etab_destroy(E);
+        return fail(e == cudaErrorMemoryAllocation ? CVS_ERR_NO_MEMORY : CVS_ERR_CUDA,
+                    "cvs_etab_build: %s", cudaGetErrorString(e));
+    }
+    FirstHitArgs a{};
+    a.tf = c->tf;
+    a.td = c->td;
+    a.n_targets = kChunk;
+    a.grid = c->grid;
+    a.order = c->d_order;
+    a.qkey = c->qkey;
+    thresholds_to_int(thr, &a.hi_min, &a.lo_max);
+    a.mask2 = thr->pattern_mask << 1;
+    a.clip = thr->gamut_mode;
+    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
+    a.half_w = (float)(0.5 - c->window);
+    a.prec = (int32_t)prec;
+    a.kchunk = choose_kchunk(c, kChunk, c->grid.K, c->grid.H);
+    a.work_counter = c->counters;
+    a.stats = c->counters + 1;
+    a.num_sms = c->num_sms;
+    cudaStream_t st = (cudaStream_t)stream;
+    e = cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev0, st);
+    for (int64_t first = 0; first < kColours && e == cudaSuccess; first += kChunk) {
+        a.key = E->choice + 7 * first;
+        e = launch_rgb_iota(rgb, first, kChunk, st);
+        if (e == cudaSuccess)
+            e = launch_setup_colors(rgb, kChunk, c->grid.rmax, c->tf, c->td, c->acc, st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(a.key, 0xFF, sizeof(uint32_t) * 7 * kChunk, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = launch_first_hits(a, st);
+        if (e == cudaSuccess) e = launch_first_finalize(a, a.key, E->codes + 7 * first, st);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev1, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->h_counters, c->counters, 4 * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, st);
+    // the colour buffer is released once the stream has consumed it
+    cudaError_t se = cudaStreamSynchronize(st);
+    cudaFree(rgb);
+    if (e == cudaSuccess) e = se;
+    if (e != cudaSuccess) {
+        cvs_etab_destroy(E);
+        return fail(e == cudaErrorMemoryAllocation ? CVS_ERR_NO_MEMORY : CVS_ERR_CUDA,
+                    "cvs_etab_build: %s", cudaGetErrorString(e));
+    }
+    c->last = cvs_stats{};
+    c->last.candidates = kColours * (int64_t)c->grid.K * c->grid.N;
+    c->last.targets = kColours;
+    c->last.symmetric = c->grid.sym;
+    c->last.precision = (int32_t)prec;
+    c->last_pending = true;
+    collect_stats(c);
+    *out = E;
+    return CVS_OK;
+}
+
+void cvs_etab_destroy(cvs_etab* E) {
+    if (!E) return;
+    cudaSetDevice(E->device);
+    cudaDeviceSynchronize();
+    if (E->choice) cudaFree(E->choice);
+    if (E->codes) cudaFree(E->codes);
+    delete E;
+}
+
+cvs_status cvs_etab_embed_image(cvs_etab* E, const cvs_image* img, const uint8_t* pattern_dev,
+                                int64_t pattern_pitch, uint8_t* frame_a_dev, uint8_t* frame_b_dev,
+                                int64_t frame_pitch, uint32_t* choice_dev, void* stream) {
+    if (!E || !img || !pattern_dev || !frame_a_dev || !frame_b_dev)
+        return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    if (!img->rgb || img->width <= 0 || img->height <= 0 || img->pitch_bytes < 3LL * img->width)
+        return fail(CVS_ERR_INVALID_ARG, "bad image pointer, size or pitch");
+    if (pattern_pitch < img->width) return fail(CVS_ERR_INVALID_ARG, "pattern pitch < width");
+    if (frame_pitch < 3LL * img->width) return fail(CVS_ERR_INVALID_ARG, "frame pitch < 3 * width");
+    if (frame_a_dev == frame_b_dev) return fail(CVS_ERR_INVALID_ARG, "the two frames must differ");
+    if ((int64_t)img->width * img->height >= ((int64_t)1 << 40))
+        return fail(CVS_ERR_INVALID_ARG, "image too large");
+    CVS_CUDA(cudaSetDevice(E->device));
+    CVS_CUDA(launch_etab_gather(E->choice, E->codes, img->rgb, img->pitch_bytes, img->width,
+                                img->height, pattern_dev, pattern_pitch, frame_a_dev, frame_b_dev,
+                                frame_pitch, choice_dev, (cudaStream_t)stream));
+    return CVS_OK;
+}
+
 cvs_status cvs_reserve(cvs_ctx* c, const cvs_grid* grid, int64_t max_targets, int32_t max_images) {
     if (!c) return fail(CVS_ERR_INVALID_ARG, "NULL context");
     if (max_targets < 0 || max_images < 0) return fail(CVS_ERR_INVALID_ARG, "negative size");

@@ -263,7 +263,334 @@ __global__ void __launch_bounds__(kSearchBlock) k_embed(const EmbedArgs A) {
     }
 }
 
+// ------------------------------------------------------------ embedding table
+// A pixel's pair depends only on its colour and requested pattern, so a table
+// over all 2^24 colours x 7 patterns turns the embedding of any frame into a
+// gather.  The build is one search of every colour that keeps, per pattern,
+// the first hit in (rank of the radius in sorted order, angle slot) order:
+// key = rank << 16 | h.  Unflagged passes enter through a warp-wide OR of the
+// patterns seen (new patterns take the lowest lane, i.e. the smallest key of
+// the iteration); flagged slots are marked in a per-lane bitmap and decided
+// after each segment, entering through atomicMin on the key.
+constexpr int kHitWords = 8;
+constexpr int kHitSegIters = 32 * kHitWords;
+
+// Flagged slots of one segment: exact decision, atomicMin of passing keys.
+template <int PREC, bool FAST, bool CLIP>
+__device__ __forceinline__ void first_flagged(const FirstHitArgs& A, const float2* r2s,
+                                              const float4* sc4s, const TargetF32& T,
+                                              const ChainF32& C, const TargetF64& D, int64_t t,
+                                              int kk0, int seg0, int nwords, uint32_t* fb,
+                                              unsigned long long& n_exact,
+                                              unsigned long long& n_re) {
+    const unsigned lane = lane_id();
+    const int H = A.grid.H;
+    for (int w = 0; w < nwords; ++w) {
+        uint32_t bits = fb[w * 32 + lane];
+        fb[w * 32 + lane] = 0u;
+        while (__any_sync(0xFFFFFFFFu, bits != 0u)) {
+            if (bits) {
+                const int j = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int i = (seg0 + 32 * w + j) * 32 + (int)lane;
+                const int dk = i / H;
+                const int kq = kk0 + dk, hq = i - dk * H;
+                const Intervals I = intervals32<FAST>(T, C, r2s[kq], sc4s[hq], A.half_w, CLIP ? 1 : 0);
+                int pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, CLIP ? 1 : 0, 0);
+                ++n_exact;
+                if (pc < 0) {
+                    const int k = __ldg(A.order + kq);
+                    int qp[3], qm[3];
+                    pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + k), __ldg(A.grid.s64 + hq),
+                                 __ldg(A.grid.c64 + hq), A.qkey, qp, qm);
+                    if (CLIP) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            qp[c] = min(max(qp[c], 0), 255);
+                            qm[c] = min(max(qm[c], 0), 255);
+                        }
+                    }
+                    Decide dc{A.hi_min, A.lo_max, A.mask2, CLIP ? 1 : 0};
+                    pc = decide_codes(qp, qm, dc);
+                    ++n_re;
+                }
+                if (pc > 0)
+                    atomicMin(A.key + t * 7 + (pc - 1), ((uint32_t)kq << 16) | (uint32_t)hq);
+            }
+        }
+    }
+}
+
+// One work item: target t, ranks [kk0, kk1) of the sorted radii.
+template <int PREC, bool FAST, bool CLIP>
+__device__ __forceinline__ void first_item(const FirstHitArgs& A, const float2* r2s,
+                                           const float4* sc4s, const uint8_t* lut,
+                                           const TargetF32& T, const ChainF32& C,
+                                           const PairsC& PC, int64_t t, int kk0, int kk1,
+                                           uint32_t* fb, unsigned long long& n_exact,
+                                           unsigned long long& n_re) {
+    const unsigned lane = lane_id();
+    const int H = A.grid.H;
+    const int nslots = (kk1 - kk0) * H;
+    const TargetF64 D = A.td[t];
+    const PairsT P = make_pairs(T);
+    uint32_t best[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) best[q] = kNoChoice;
+    uint32_t found = 0;  // bit q: pattern q has an unflagged hit in this item
+    const int q32 = 32 / H, r32 = 32 - q32 * H;
+    int kk = kk0 + (int)lane / H, h = (int)lane % H;
+    const int nit = (nslots + 31) >> 5;
+    int it_pow = 0;  // iterations whose radii never reach the sRGB linear segment
+    if (PREC == CVS_PREC_FP32_RECHECK && FAST) {
+        const int ks = first_linseg_radius(T, C, r2s, kk0, kk1);
+        it_pow = ks == kk1 ? nit : ((ks - kk0) * H) >> 5;
+    }
+    for (int seg0 = 0; seg0 < nit; seg0 += kHitSegIters) {
+        const int seg1 = min(seg0 + kHitSegIters, nit);
+        for (int w = 0, it = seg0; it < seg1; ++w) {
+            uint32_t bits = 0;
+            const int wend = min(seg1, it + 32);
+            for (uint32_t bit = 1u; it < wend; ++it, bit <<= 1) {
+                const bool active = it * 32 + (int)lane < nslots;
+                const int kq = active ? kk : kk0, hq = active ? h : 0;
+                int pattern = 0;
+                if (PREC == CVS_PREC_FP32_RECHECK) {
+                    const float2 r2 = r2s[kq];
+                    const float4 sc = sc4s[hq];
+                    const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));
+                    const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
+                    int yp[3], ym[3];
+                    bool flag;
+                    if (it < it_pow) flag = codes32<FAST, false>(P, PC, u2, w2, A.half_w, yp, ym);
+                    else flag = codes32<FAST, true>(P, PC, u2, w2, A.half_w, yp, ym);
+                    pattern = decide32<CLIP>(yp, ym, lut, A.mask2);
+                    flag = flag && active;
+                    if (flag || !active) pattern = 0;
+                    if (flag) bits |= bit;
+                } else if (active) {
+                    const int k = __ldg(A.order + kq);
+                    int qp[3], qm[3];
+                    pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + k), __ldg(A.grid.s64 + hq),
+                                 __ldg(A.grid.c64 + hq), A.qkey, qp, qm);
+                    if (CLIP) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            qp[c] = min(max(qp[c], 0), 255);
+                            qm[c] = min(max(qm[c], 0), 255);
+                        }
+                    }
+                    Decide dc{A.hi_min, A.lo_max, A.mask2, CLIP ? 1 : 0};
+                    pattern = decide_codes(qp, qm, dc);
+                }
+                const uint32_t newp =
+                    __reduce_or_sync(0xFFFFFFFFu, pattern ? (1u << pattern) : 0u) & ~found;
+                if (newp) {  // the lowest lane holds the iteration's smallest key
+                    const uint32_t mykey = ((uint32_t)kq << 16) | (uint32_t)hq;
+#pragma unroll
+                    for (int q = 1; q <= 7; ++q) {
+                        if ((newp >> q) & 1u) {
+                            const unsigned b = __ballot_sync(0xFFFFFFFFu, pattern == q);
+                            best[q] = __shfl_sync(0xFFFFFFFFu, mykey, __ffs(b) - 1);
+                        }
+                    }
+                    found |= newp;
+                }
+                h += r32;
+                kk += q32;
+                const bool wrap = h >= H;
+                h = wrap ? h - H : h;
+                kk = wrap ? kk + 1 : kk;
+            }
+            if (PREC == CVS_PREC_FP32_RECHECK) fb[w * 32 + lane] = bits;
+        }
+        if (PREC == CVS_PREC_FP32_RECHECK) {
+            __syncwarp();
+            first_flagged<PREC, FAST, CLIP>(A, r2s, sc4s, T, C, D, t, kk0, seg0,
+                                            (seg1 - seg0 + 31) >> 5, fb, n_exact, n_re);
+        }
+    }
+    uint32_t mine = kNoChoice;  // lane q - 1 publishes pattern q
+#pragma unroll
+    for (int q = 1; q <= 7; ++q)
+        if ((int)lane == q - 1) mine = best[q];
+    if ((int)lane < 7 && ((found >> (lane + 1)) & 1u)) atomicMin(A.key + t * 7 + lane, mine);
+}
+
+template <int PREC, bool CLIP>
+__global__ void __launch_bounds__(kSearchBlock) k_first_hits(const FirstHitArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int K = A.grid.K, H = A.grid.H;
+    float2* r2s = reinterpret_cast<float2*>(smem);  // radii in rank order
+    float4* sc4s = reinterpret_cast<float4*>(smem + ((K * 8 + 15) & ~15));
+    uint8_t* lut = smem + ((K * 8 + 15) & ~15) + H * 16;
+    uint32_t* fb = reinterpret_cast<uint32_t*>(lut + 3 * 512) + (threadIdx.x >> 5) * (kHitWords * 32);
+    build_decide_lut(lut, A.hi_min, A.lo_max);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) r2s[i] = dup(A.grid.r32[A.order[i]]);
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        const float2 sc = A.grid.sc32[i];
+        sc4s[i] = make_float4(sc.x, -sc.x, sc.y, -sc.y);
+    }
+    const unsigned lane = lane_id();
+    for (int w = 0; w < kHitWords; ++w) fb[w * 32 + lane] = 0u;
+    __syncthreads();
+    ChainF32 C;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        C.Ax[c] = __double2float_rn(__dmul_rn(c_MI[3 * c], c_W[0]));
+        C.Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
+    }
+    const PairsC PC = make_pairs(C);
+    unsigned long long n_exact = 0, n_re = 0;
+    const int kchunk = A.kchunk;
+    const int n_kc = (K + kchunk - 1) / kchunk;
+    const unsigned long long n_items = (unsigned long long)A.n_targets * n_kc;
+    while (true) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(A.work_counter, 1ull);
+        item = __shfl_sync(0xFFFFFFFFu, item, 0);
+        if (item >= n_items) break;
+        const int64_t t = (int64_t)(item / (unsigned long long)n_kc);
+        const int kc = (int)(item - (unsigned long long)t * n_kc);
+        const int kk0 = kc * kchunk, kk1 = min(kk0 + kchunk, K);
+        TargetF32 T{};
+        if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
+        if (PREC == CVS_PREC_FP32_RECHECK && (T.flags & 1u))
+            first_item<PREC, true, CLIP>(A, r2s, sc4s, lut, T, C, PC, t, kk0, kk1, fb, n_exact,
+                                         n_re);
+        else
+            first_item<PREC, false, CLIP>(A, r2s, sc4s, lut, T, C, PC, t, kk0, kk1, fb, n_exact,
+                                          n_re);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        n_exact += __shfl_xor_sync(0xFFFFFFFFu, n_exact, off);
+        n_re += __shfl_xor_sync(0xFFFFFFFFu, n_re, off);
+    }
+    if (lane == 0) {
+        if (n_exact) atomicAdd(A.stats + 0, n_exact);
+        if (n_re) atomicAdd(A.stats + 1, n_re);
+    }
+}
+
+// Keys -> choices (in place) and the exact codes of each first hit, packed as
+// plus R, G, B in bytes 0..2 and minus R, G, B in bytes 3..5.
+template <int PREC, bool CLIP>
+__global__ void k_first_finalize(const FirstHitArgs A, uint32_t* __restrict__ choice,
+                                 uint64_t* __restrict__ codes) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= A.n_targets * 7) return;
+    const uint32_t key = choice[e];
+    if (key == kNoChoice) {
+        codes[e] = 0;
+        return;
+    }
+    const int64_t t = e / 7;
+    const int kk = (int)(key >> 16), h = (int)(key & 0xFFFFu);
+    const int k = __ldg(A.order + kk);
+    int qp[3], qm[3];
+    bool exact = false;
+    if (PREC == CVS_PREC_FP32_RECHECK) {
+        const TargetF32 T = A.tf[t];
+        ChainF32 C;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            C.Ax[c] = __double2float_rn(__dmul_rn(c_MI[3 * c], c_W[0]));
+            C.Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
+        }
+        const PairsT P = make_pairs(T);
+        const PairsC PC = make_pairs(C);
+        const float2 r2 = dup(A.grid.r32[k]);
+        const float2 sc = A.grid.sc32[h];
+        int yp[3], ym[3];
+        bool flag;
+        if (T.flags & 1u)
+            flag = codes32<true, true>(P, PC, __fmul2_rn(r2, f2(sc.x, -sc.x)),
+                                       __fmul2_rn(r2, f2(sc.y, -sc.y)), A.half_w, yp, ym);
+        else
+            flag = codes32<false, true>(P, PC, __fmul2_rn(r2, f2(sc.x, -sc.x)),
+                                        __fmul2_rn(r2, f2(sc.y, -sc.y)), A.half_w, yp, ym);
+        if (!flag) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                qp[c] = yp[c] - kMagicBits;
+                qm[c] = ym[c] - kMagicBits;
+            }
+            exact = true;
+        }
+    }
+    if (!exact) {
+        const TargetF64 D = A.td[t];
+        pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + k), __ldg(A.grid.s64 + h),
+                     __ldg(A.grid.c64 + h), A.qkey, qp, qm);
+    }
+    uint64_t v = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int a = CLIP ? min(max(qp[c], 0), 255) : qp[c];
+        const int b = CLIP ? min(max(qm[c], 0), 255) : qm[c];
+        v |= (uint64_t)(uint8_t)a << (8 * c);
+        v |= (uint64_t)(uint8_t)b << (8 * (3 + c));
+    }
+    codes[e] = v;
+    choice[e] = (uint32_t)k | ((uint32_t)h << 16);
+}
+
+// Frames of one image from the table: one thread per pixel (grid-stride).
+__global__ void k_etab_gather(const uint32_t* __restrict__ choice,
+                              const uint64_t* __restrict__ codes, const uint8_t* __restrict__ rgb,
+                              int64_t pitch, int32_t width, int64_t n,
+                              const uint8_t* __restrict__ pattern, int64_t pattern_pitch,
+                              uint8_t* __restrict__ frame_a, uint8_t* __restrict__ frame_b,
+                              int64_t frame_pitch, uint32_t* __restrict__ choice_out) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t y = t / width, x = t - y * width;
+        const uint8_t* src = rgb + y * pitch + 3 * x;
+        const uint8_t r = src[0], g = src[1], b = src[2];
+        const int p = pattern[y * pattern_pitch + x];
+        uint8_t a0 = r, a1 = g, a2 = b, b0 = r, b1 = g, b2 = b;
+        uint32_t ch = kNoChoice;
+        if (p >= 1 && p <= 7) {
+            const int64_t e = (((int64_t)r << 16) | ((int64_t)g << 8) | b) * 7 + (p - 1);
+            ch = __ldg(choice + e);
+            if (ch != kNoChoice) {
+                const uint64_t v = __ldg(reinterpret_cast<const unsigned long long*>(codes) + e);
+                a0 = (uint8_t)v;
+                a1 = (uint8_t)(v >> 8);
+                a2 = (uint8_t)(v >> 16);
+                b0 = (uint8_t)(v >> 24);
+                b1 = (uint8_t)(v >> 32);
+                b2 = (uint8_t)(v >> 40);
+            }
+        }
+        uint8_t* fa = frame_a + y * frame_pitch + 3 * x;
+        uint8_t* fb = frame_b + y * frame_pitch + 3 * x;
+        fa[0] = a0; fa[1] = a1; fa[2] = a2;
+        fb[0] = b0; fb[1] = b1; fb[2] = b2;
+        if (choice_out) choice_out[t] = ch;
+    }
+}
+
 int embed_smem_bytes(const GridDev& g) { return ((g.K * 8 + 15) & ~15) + g.H * 16 + 3 * 512; }
+
+int first_smem_bytes(const GridDev& g) {
+    return embed_smem_bytes(g) + (kSearchBlock / 32) * kHitWords * 32 * 4;
+}
+
+template <int PREC, bool CLIP>
+cudaError_t launch_first_t(const FirstHitArgs& a, cudaStream_t st) {
+    const int smem = first_smem_bytes(a.grid);
+    const void* fn = (const void*)k_first_hits<PREC, CLIP>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSearchBlock, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    k_first_hits<PREC, CLIP><<<a.num_sms * per_sm, kSearchBlock, smem, st>>>(a);
+    return cudaGetLastError();
+}
 
 template <int PREC, bool CLIP>
 cudaError_t launch_embed_t(const EmbedArgs& a, cudaStream_t st) {
@@ -280,6 +607,49 @@ cudaError_t launch_embed_t(const EmbedArgs& a, cudaStream_t st) {
 }
 
 }  // namespace
+
+cudaError_t launch_first_hits(const FirstHitArgs& a, cudaStream_t st) {
+    if (a.n_targets <= 0) return cudaSuccess;
+    if (a.prec == CVS_PREC_FP64)
+        return a.clip ? launch_first_t<CVS_PREC_FP64, true>(a, st)
+                      : launch_first_t<CVS_PREC_FP64, false>(a, st);
+    return a.clip ? launch_first_t<CVS_PREC_FP32_RECHECK, true>(a, st)
+                  : launch_first_t<CVS_PREC_FP32_RECHECK, false>(a, st);
+}
+
+cudaError_t launch_first_finalize(const FirstHitArgs& a, uint32_t* choice, uint64_t* codes,
+                                  cudaStream_t st) {
+    const int64_t n = a.n_targets * 7;
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)((n + 255) / 256);
+    if (a.prec == CVS_PREC_FP64) {
+        if (a.clip) k_first_finalize<CVS_PREC_FP64, true><<<blocks, 256, 0, st>>>(a, choice, codes);
+        else k_first_finalize<CVS_PREC_FP64, false><<<blocks, 256, 0, st>>>(a, choice, codes);
+    } else {
+        if (a.clip)
+            k_first_finalize<CVS_PREC_FP32_RECHECK, true><<<blocks, 256, 0, st>>>(a, choice, codes);
+        else
+            k_first_finalize<CVS_PREC_FP32_RECHECK, false><<<blocks, 256, 0, st>>>(a, choice, codes);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_etab_gather(const uint32_t* choice, const uint64_t* codes, const uint8_t* rgb,
+                               int64_t pitch, int32_t width, int32_t height,
+                               const uint8_t* pattern, int64_t pattern_pitch, uint8_t* frame_a,
+                               uint8_t* frame_b, int64_t frame_pitch, uint32_t* choice_out,
+                               cudaStream_t st) {
+    const int64_t n = (int64_t)width * height;
+    if (n <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n + 255) / 256, cap = (int64_t)(sms > 0 ? sms : 1) * 16;
+    k_etab_gather<<<(int)(want < cap ? want : cap), 256, 0, st>>>(
+        choice, codes, rgb, pitch, width, n, pattern, pattern_pitch, frame_a, frame_b, frame_pitch,
+        choice_out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_embed(const EmbedArgs& a, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;

@@ -128,6 +128,27 @@ struct EmbedArgs {
     int num_sms;
 };
 
+// The embedding table: per colour and pattern the first hit's key
+// (rank << 16 | h; rank = position of the radius in the sorted order).
+struct FirstHitArgs {
+    const TargetF32* tf;
+    const TargetF64* td;
+    int64_t n_targets;
+    GridDev grid;
+    const int32_t* order;       // K radius indices sorted by (radius value, index)
+    const long long* qkey;
+    int32_t hi_min, lo_max;
+    uint32_t mask2;
+    int32_t clip;
+    float half_w;
+    int32_t prec;
+    int32_t kchunk;             // ranks per work item
+    uint32_t* key;              // n_targets * 7, pattern p at t * 7 + p - 1; 0xFFFFFFFF = none
+    unsigned long long* work_counter;
+    unsigned long long* stats;
+    int num_sms;
+};
+
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_trig_table(const double* angles_dev, int n, double* s64, double* c64,
                               float2* sc32, int* status, cudaStream_t st);
@@ -140,6 +161,15 @@ cudaError_t launch_finalize_colors(const Acc* acc, int64_t n, float* max_r, int3
                                    uint8_t* pmask, cudaStream_t st);
 cudaError_t launch_search_multi(const MultiArgs& a, cudaStream_t st);
 cudaError_t launch_embed(const EmbedArgs& a, cudaStream_t st);
+cudaError_t launch_first_hits(const FirstHitArgs& a, cudaStream_t st);
+// keys (in place) -> choices k | m << 16, and the exact codes of each hit
+cudaError_t launch_first_finalize(const FirstHitArgs& a, uint32_t* choice, uint64_t* codes,
+                                  cudaStream_t st);
+cudaError_t launch_etab_gather(const uint32_t* choice, const uint64_t* codes, const uint8_t* rgb,
+                               int64_t pitch, int32_t width, int32_t height,
+                               const uint8_t* pattern, int64_t pattern_pitch, uint8_t* frame_a,
+                               uint8_t* frame_b, int64_t frame_pitch, uint32_t* choice_out,
+                               cudaStream_t st);
 cudaError_t launch_init_acc(Acc* acc, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t n,
                                    const ImageDesc* imgs, cudaStream_t st);

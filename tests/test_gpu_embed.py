@@ -143,3 +143,52 @@ def test_invalid_arguments(ctx, torch_cuda):
     with pytest.raises(cvs.CvsError) as ei:
         ctx.embed_image(img, pat, radii, ang, 50.0, 0.5, frames=(f, f))
     assert ei.value.status == binding.CVS_ERR_INVALID_ARG
+
+
+# ------------------------------------------------------------ embedding table
+@pytest.fixture(scope="module")
+def etab3(ctx):
+    radii, ang = W.grid(3)
+    t = ctx.build_embed_table(radii, ang, 50.0, 0.5)
+    yield t
+    t.close()
+
+
+def table_embed(torch, table, img, pat):
+    fa, fb, ch = table.embed_image(torch.from_numpy(img).cuda(), torch.from_numpy(pat).cuda())
+    torch.cuda.synchronize()
+    return fa.cpu().numpy(), fb.cpu().numpy(), ch.cpu().numpy()
+
+
+def test_table_matches_oracle_on_sampled_colours(etab3, torch_cuda):
+    rng = np.random.default_rng(13)
+    cols = rng.integers(0, 256, (300, 3)).astype(np.uint8)
+    img = np.repeat(cols, 7, axis=0).reshape(1, -1, 3)
+    pat = np.tile(np.arange(1, 8, dtype=np.uint8), 300).reshape(1, -1)
+    got = table_embed(torch_cuda, etab3, img, pat)
+    radii, ang = W.grid(3)
+    exp = oracle_embed(img, pat, radii, ang)
+    assert_same(got, exp, "table vs oracle")
+    assert (got[2] != NONE).sum() > 100
+
+
+def test_table_equals_direct_embedding(ctx, etab3, torch_cuda):
+    radii, ang = W.grid(3)
+    w, h = 1920, 1080
+    terms = W.image_params(1, seed=9, sizes=[(w, h)])[0][2]
+    img = W.render_image_numpy(w, h, terms, 9)
+    pat = W.code_pattern(h, w, module=16, seed=9, fill=0.5)
+    direct = gpu_embed(ctx, torch_cuda, img, pat, radii, ang)
+    assert_same(table_embed(torch_cuda, etab3, img, pat), direct, "table vs direct")
+
+
+def test_clip_mode_table_equals_direct(ctx, torch_cuda):
+    radii, ang = W.grid(3)
+    img = small_image(64, 40, 17)
+    pat = W.code_pattern(40, 64, module=2, seed=17, fill=1.0)
+    t = ctx.build_embed_table(radii, ang, 50.0, 0.5, gamut_mode=1)
+    try:
+        got = table_embed(torch_cuda, t, img, pat)
+    finally:
+        t.close()
+    assert_same(got, gpu_embed(ctx, torch_cuda, img, pat, radii, ang, gamut_mode=1), "clip table")
