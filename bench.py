@@ -39,7 +39,7 @@ LANES_PER_SM_CLK = 128
 # summarised in profiles/k_search_fp32_colour_cube_full.md (32,768-colour case
 # scaled by 8, traffic being proportional to the colours).  Valid only for the
 # kernel source it was taken from; otherwise the roofline reports null.
-TRAFFIC_CAPTURE = {"source_sha256_16": "3b7175f5f5b11923", "bytes_per_launch": 8 * 3.15904e6}
+TRAFFIC_CAPTURE = {"source_sha256_16": "f2dedd38a89bd1a6", "bytes_per_launch": 8 * 3.230208e6}
 
 
 def kernel_source_hash() -> str:
