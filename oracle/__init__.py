@@ -108,13 +108,15 @@ def lib() -> ctypes.CDLL:
             L.orc_pair_codes.argtypes = [P(_Consts), vp, d, d, d, vp, vp]
             L.orc_pair_codes.restype = None
             L.orc_search_color.argtypes = [P(_Consts), vp, u32, vp, i32, vp, vp, i32, d, d,
-                                           u32, ctypes.c_int, vp, i64]
+                                           u32, ctypes.c_int, d, vp, i64]
             L.orc_search_color.restype = i64
             L.orc_search_colors.argtypes = [P(_Consts), vp, i64, vp, i32, vp, vp, i32, d, d,
-                                            u32, ctypes.c_int, vp, vp, vp, ctypes.c_int]
+                                            u32, ctypes.c_int, d, vp, vp, vp, ctypes.c_int]
             L.orc_search_colors.restype = None
             L.orc_decide_pair.argtypes = [vp, vp, d, d, u32, ctypes.c_int, vp, vp]
             L.orc_decide_pair.restype = ctypes.c_int
+            L.orc_passes_dl.argtypes = [P(_Consts), vp, vp, d]
+            L.orc_passes_dl.restype = ctypes.c_int
             L.orc_embed.argtypes = [P(_Consts), vp, vp, i64, vp, i32, vp, vp, i32, d, d, u32,
                                     ctypes.c_int, vp, vp, vp, ctypes.c_int]
             L.orc_embed.restype = None
@@ -222,6 +224,13 @@ def decide_pair(q_plus, q_minus, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0)
     return pat, op, om
 
 
+def passes_dl(plus, minus, max_dl) -> bool:
+    """True if the two 8-bit colours differ in L* by at most max_dl (< 0: no limit)."""
+    a = np.ascontiguousarray(np.asarray(plus, np.uint8).reshape(3))
+    b = np.ascontiguousarray(np.asarray(minus, np.uint8).reshape(3))
+    return bool(lib().orc_passes_dl(ctypes.byref(consts()), _ptr(a), _ptr(b), float(max_dl)))
+
+
 def roundtrip_all(threads: int = 0):
     """(number of 8-bit colours whose RGB->Lab->RGB codes differ, max |lin - LUT|)."""
     err = ctypes.c_double(0.0)
@@ -237,7 +246,7 @@ def trig_table(angles_deg):
 
 # ---------------------------------------------------------------- searches
 def search_color(rgb, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0,
-                 target=0, cap=None, trig_tab=None):
+                 target=0, cap=None, trig_tab=None, max_dl=-1.0):
     """All passing pairs of one target, sorted by (k, m), as a PAIR_DTYPE array."""
     radii = np.ascontiguousarray(radii, np.float64)
     s, c = trig_tab if trig_tab is not None else trig_table(angles_deg)
@@ -249,13 +258,13 @@ def search_color(rgb, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut
     out = np.zeros(max(cap, 1), PAIR_DTYPE)
     n = lib().orc_search_color(ctypes.byref(consts()), _ptr(src), int(target), _ptr(radii),
                                len(radii), _ptr(s), _ptr(c), len(s), float(v_th),
-                               float(r_novib), int(pattern_mask), int(gamut_mode), _ptr(out),
-                               int(cap))
+                               float(r_novib), int(pattern_mask), int(gamut_mode), float(max_dl),
+                               _ptr(out), int(cap))
     return out[:min(n, cap)], int(n)
 
 
 def search_colors(rgbs, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0,
-                  threads=1, trig_tab=None):
+                  threads=1, trig_tab=None, max_dl=-1.0):
     """Per-target (max_r float32, count int32, pmask uint8) for an (n,3) uint8 array."""
     rgbs = np.ascontiguousarray(np.asarray(rgbs, np.uint8).reshape(-1, 3))
     radii = np.ascontiguousarray(radii, np.float64)
@@ -268,8 +277,8 @@ def search_colors(rgbs, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gam
     pmask = np.zeros(n, np.uint8)
     lib().orc_search_colors(ctypes.byref(consts()), _ptr(rgbs), n, _ptr(radii), len(radii),
                             _ptr(s), _ptr(c), len(s), float(v_th), float(r_novib),
-                            int(pattern_mask), int(gamut_mode), _ptr(max_r), _ptr(count),
-                            _ptr(pmask), int(threads))
+                            int(pattern_mask), int(gamut_mode), float(max_dl), _ptr(max_r),
+                            _ptr(count), _ptr(pmask), int(threads))
     return max_r, count, pmask
 
 

@@ -235,6 +235,24 @@ static int decide_pair(const int q_plus[3], const int q_minus[3], double v_th, d
     return pattern;
 }
 
+/* Perceptual refinement of the vibration condition (a reading: the paper fixes
+ * L* before quantisation, §2 Methods, and gives no tolerance after it): the
+ * two emitted 8-bit colours must differ in L* by at most max_dl, with each L*
+ * from step 1 applied to the emitted codes.  max_dl < 0 or NaN: no limit. */
+static int passes_dl(const orc_consts* C, const uint8_t op[3], const uint8_t om[3],
+                     double max_dl) {
+    if (!(max_dl >= 0.0)) return 1;
+    double lp[3], lm[3];
+    orc_target_lab(C, op, lp);
+    orc_target_lab(C, om, lm);
+    return fabs(lp[0] - lm[0]) <= max_dl;
+}
+
+/* Exported form of passes_dl for the oracle's own pins. */
+int orc_passes_dl(const orc_consts* C, const uint8_t op[3], const uint8_t om[3], double max_dl) {
+    return passes_dl(C, op, om, max_dl);
+}
+
 /* Exported form of decide_pair for the oracle's own pins. */
 int orc_decide_pair(const int q_plus[3], const int q_minus[3], double v_th, double r_novib,
                     uint32_t pattern_mask, int gamut_mode, uint8_t out_plus[3],
@@ -259,7 +277,8 @@ void orc_pair_codes(const orc_consts* C, const double lab[3], double r, double s
 int64_t orc_search_color(const orc_consts* C, const uint8_t rgb[3], uint32_t target,
                          const double* radii, int32_t n_radii, const double* sin_t,
                          const double* cos_t, int32_t n_angles, double v_th, double r_novib,
-                         uint32_t pattern_mask, int gamut_mode, orc_pair* out, int64_t cap) {
+                         uint32_t pattern_mask, int gamut_mode, double max_dl, orc_pair* out,
+                         int64_t cap) {
     double lab[3];
     orc_target_lab(C, rgb, lab);
     int64_t n = 0;
@@ -271,7 +290,7 @@ int64_t orc_search_color(const orc_consts* C, const uint8_t rgb[3], uint32_t tar
             memset(&rec, 0, sizeof rec);
             int pat = decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, rec.plus,
                                   rec.minus);
-            if (!pat) continue;
+            if (!pat || !passes_dl(C, rec.plus, rec.minus, max_dl)) continue;
             if (n < cap) {
                 rec.k = (uint16_t)k;
                 rec.m = (uint16_t)m;
@@ -290,8 +309,8 @@ int64_t orc_search_color(const orc_consts* C, const uint8_t rgb[3], uint32_t tar
 void orc_search_colors(const orc_consts* C, const uint8_t* rgb, int64_t n_targets,
                        const double* radii, int32_t n_radii, const double* sin_t,
                        const double* cos_t, int32_t n_angles, double v_th, double r_novib,
-                       uint32_t pattern_mask, int gamut_mode, float* max_r, int32_t* count,
-                       uint8_t* pmask, int n_threads) {
+                       uint32_t pattern_mask, int gamut_mode, double max_dl, float* max_r,
+                       int32_t* count, uint8_t* pmask, int n_threads) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
 #endif
@@ -307,7 +326,7 @@ void orc_search_colors(const orc_consts* C, const uint8_t* rgb, int64_t n_target
                 uint8_t op[3], om[3];
                 orc_pair_codes(C, lab, radii[k], sin_t[m], cos_t[m], qp, qm);
                 int pat = decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, op, om);
-                if (!pat) continue;
+                if (!pat || !passes_dl(C, op, om, max_dl)) continue;
                 ++cnt;
                 if (radii[k] > best) best = radii[k];
                 mask |= (uint8_t)(1u << (pat - 1));
