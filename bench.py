@@ -356,6 +356,24 @@ def run_extras(ctx, torch, device, W, cvs):
         del img, pat, d, g
     etab.close()
     out["embedding_via_table"] = via
+    # the luminance limit on emitted pairs (max_dl 0.1) over the bench workload
+    cube = torch.from_numpy(W.color_cube()).to(device)
+    r2, a2 = W.grid(2)
+    base = ctx.search_colors(cube, r2, a2, 50.0, 0.5)
+    ctx.synchronize()
+    ctx.set_option("max_dl", 0.1)
+    lim = ctx.search_colors(cube, r2, a2, 50.0, 0.5)
+    lim = ctx.search_colors(cube, r2, a2, 50.0, 0.5, out=lim)
+    ctx.synchronize()
+    st_l = ctx.stats()
+    ctx.set_option("max_dl", -1)
+    cand = cube.shape[0] * len(r2) * len(a2)
+    out["luminance_limit"] = {
+        "workload": "262,144 cube colours x 128 radii x 360 angles, max_dl 0.1",
+        "gcand_s": cand / (st_l["search_ms"] / 1e3) / 1e9,
+        "pairs_without_limit": int(base[1].sum().item()),
+        "pairs_with_limit": int(lim[1].sum().item())}
+    del cube, base, lim
     # the experiment of §3: every cube colour under all 12 (V_th, R_novib) sets,
     # one multi-set pass against 12 single-set passes
     cube = torch.from_numpy(W.color_cube()).to(device)

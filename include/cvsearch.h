@@ -457,6 +457,18 @@ cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const c
  *                   thresholds, precision, shape) is seen, and replay the graph
  *                   on later calls with the same signature (up to 8 graphs are
  *                   kept per context).  Default 0.
+ *   "max_dl"        a perceptual refinement of the vibration condition: a
+ *                   passing pair is kept only if its two emitted 8-bit colours
+ *                   differ in L* (step 1 of §2 Methods applied to each
+ *                   colour's codes) by at most this many units.  The paper
+ *                   fixes L* before quantisation and gives no tolerance after
+ *                   it, so the value is the caller's.  A negative value turns
+ *                   the limit off (the default).  The first non-negative value
+ *                   builds a table of the L* of all 2^24 colours (128 MiB,
+ *                   synchronous).  Applies to cvs_search_color(s),
+ *                   cvs_search_colors_host, cvs_search_images and
+ *                   cvs_lut_build; cvs_search_colors_multi, cvs_embed_image
+ *                   and cvs_etab_build return CVS_ERR_INVALID_ARG while it is on.
  * Read-only values for cvs_get_option: "graph_launches" (graph replays so
  * far), "graphs_cached".
  * Unknown names or out-of-range values return CVS_ERR_INVALID_ARG. */

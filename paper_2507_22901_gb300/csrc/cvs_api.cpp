@@ -103,6 +103,9 @@ struct cvs_ctx {
     std::map<std::array<int64_t, 7>, LaunchShape> tuned;
     Acc* acc_tune = nullptr;
     int64_t cap_acc_tune = 0;
+    // luminance limit on emitted pairs (off while max_dl < 0); L* of all 2^24 colours
+    double max_dl = -1.0;
+    double* ltab = nullptr;
     // embedding: radius indices sorted by (radius value, index), K entries
     int32_t* d_order = nullptr;
     // multi-threshold search: n x n_thr accumulators
@@ -371,6 +374,8 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
     a.list_mode = list_mode;
     a.dense = c->dense;
     a.target_id = target_id;
+    a.ltab = c->max_dl >= 0.0 ? c->ltab : nullptr;
+    a.max_dl = c->max_dl;
     a.work_counter = c->counters;
     a.stats = c->counters + 1;
     a.shape = c->shape;
@@ -534,7 +539,7 @@ void cvs_destroy(cvs_ctx* c) {
     void* ptrs[] = {c->grid.r32, c->grid.sc32, c->grid.r64, c->grid.s64, c->grid.c64,
                     c->d_angles, c->d_status, c->tf, c->td, c->acc, c->qkey, c->counters,
                     c->dense, c->compact, c->d_imgs, c->d_in, c->d_maxr, c->d_count, c->d_pmask,
-                    c->d_rgb1, c->d_probe, c->d_order};
+                    c->d_rgb1, c->d_probe, c->d_order, c->ltab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     drop_graphs(c);
@@ -573,6 +578,15 @@ cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
         if (value != 0 && value != 1) return fail(CVS_ERR_INVALID_ARG, "graphs is 0 or 1");
         c->use_graphs = (int)value;
         if (!c->use_graphs) drop_graphs(c);
+    } else if (!std::strcmp(name, "max_dl")) {
+        if (std::isnan(value)) return fail(CVS_ERR_INVALID_ARG, "max_dl is NaN");
+        if (value >= 0.0 && !c->ltab) {  // built once, before any capture can need it
+            CVS_CUDA(cudaSetDevice(c->device));
+            CVS_CUDA(cudaMalloc(&c->ltab, sizeof(double) << 24));
+            CVS_CUDA(launch_l_table(c->ltab, c->own));
+            CVS_CUDA(cudaStreamSynchronize(c->own));
+        }
+        c->max_dl = value < 0.0 ? -1.0 : value;
     } else {
         return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);
     }
@@ -587,6 +601,7 @@ cvs_status cvs_get_option(cvs_ctx* c, const char* name, double* value) {
     else if (!std::strcmp(name, "kchunk")) *value = c->shape.kchunk;
     else if (!std::strcmp(name, "autotune")) *value = c->autotune;
     else if (!std::strcmp(name, "graphs")) *value = c->use_graphs;
+    else if (!std::strcmp(name, "max_dl")) *value = c->max_dl;
     else if (!std::strcmp(name, "graph_launches")) *value = (double)c->graph_launches;
     else if (!std::strcmp(name, "graphs_cached")) *value = (double)c->graphs.size();
     else return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);
@@ -715,7 +730,8 @@ cvs_status cvs_search_colors(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, cons
                                  dbits(thr->r_novib), thr->pattern_mask,
                                  (uint64_t)thr->gamut_mode, (uint64_t)prec,
                                  (uint64_t)c->shape.block, (uint64_t)c->shape.blocks_per_sm,
-                                 (uint64_t)c->shape.kchunk, dbits(c->window)};
+                                 (uint64_t)c->shape.kchunk, dbits(c->window),
+                                 dbits(c->max_dl)};
     st0 = graph_launch(c, key, st, enqueue);
     if (st0 == CVS_OK) c->last_pending = true;
     return st0;
@@ -725,6 +741,8 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
                                    const cvs_grid* grid, const cvs_thresholds* thr,
                                    int32_t n_thr, cvs_precision prec,
                                    const cvs_capacity_map* out, void* stream) {
+    if (c && c->max_dl >= 0.0)
+        return fail(CVS_ERR_INVALID_ARG, "cvs_search_colors_multi does not support the max_dl option");
     if (!c || !out || !thr) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
     if (n < 0 || n > (int64_t)1 << 36) return fail(CVS_ERR_INVALID_ARG, "n out of range");
     if (n_thr < 1 || n_thr > kMaxThresholdSets)
@@ -861,7 +879,8 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
     std::vector<uint64_t> key = {2, (uint64_t)n, dbits(thr->v_th), dbits(thr->r_novib),
                                  thr->pattern_mask, (uint64_t)thr->gamut_mode, (uint64_t)prec,
                                  (uint64_t)c->shape.block, (uint64_t)c->shape.blocks_per_sm,
-                                 (uint64_t)c->shape.kchunk, dbits(c->window)};
+                                 (uint64_t)c->shape.kchunk, dbits(c->window),
+                                 dbits(c->max_dl)};
     for (const ImageDesc& d : h) {
         key.insert(key.end(), {(uint64_t)d.rgb, (uint64_t)d.pitch, (uint64_t)d.width,
                                (uint64_t)d.height, (uint64_t)d.max_r, (uint64_t)d.count,
@@ -876,6 +895,8 @@ cvs_status cvs_embed_image(cvs_ctx* c, const cvs_image* img, const uint8_t* patt
                            int64_t pattern_pitch, const cvs_grid* grid, const cvs_thresholds* thr,
                            cvs_precision prec, uint8_t* frame_a_dev, uint8_t* frame_b_dev,
                            int64_t frame_pitch, uint32_t* choice_dev, void* stream) {
+    if (c && c->max_dl >= 0.0)
+        return fail(CVS_ERR_INVALID_ARG, "cvs_embed_image does not support the max_dl option");
     if (!c || !img || !pattern_dev || !frame_a_dev || !frame_b_dev)
         return fail(CVS_ERR_INVALID_ARG, "NULL argument");
     if (!img->rgb || img->width <= 0 || img->height <= 0 || img->pitch_bytes < 3LL * img->width)
@@ -1112,6 +1133,8 @@ extern "C" {
 
 cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds* thr,
                           cvs_precision prec, cvs_etab** out, void* stream) {
+    if (c && c->max_dl >= 0.0)
+        return fail(CVS_ERR_INVALID_ARG, "cvs_etab_build does not support the max_dl option");
     if (!c || !out) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)

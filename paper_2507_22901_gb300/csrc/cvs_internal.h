@@ -73,6 +73,8 @@ struct SearchArgs {
     int32_t list_mode;         // 1: write records into `dense`
     cvs_pair* dense;           // K*N records (list mode)
     uint32_t target_id;        // list mode: copied into records
+    const double* ltab;        // L* of all 2^24 colours when the luminance limit is on, else NULL
+    double max_dl;             // the limit on |L*(plus) - L*(minus)| of an emitted pair
     unsigned long long* work_counter;
     unsigned long long* stats; // [0] flagged, [1] rechecked
     LaunchShape shape;
@@ -175,6 +177,8 @@ cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t 
                                    const ImageDesc* imgs, cudaStream_t st);
 cudaError_t launch_compact_pairs(const cvs_pair* dense, int64_t n_dense, cvs_pair* out,
                                  unsigned long long* n_out, cudaStream_t st);
+// L* of all 2^24 8-bit colours (index R << 16 | G << 8 | B), as step 1 forms it.
+cudaError_t launch_l_table(double* ltab, cudaStream_t st);
 cudaError_t launch_target_lab(const uint8_t* rgb, int64_t n, double* lab, cudaStream_t st);
 cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int64_t n,
                                    const GridDev& g, const long long* qkey,

@@ -153,6 +153,15 @@ __device__ __forceinline__ void write_records(cvs_pair* dense, int N, int H, int
     }
 }
 
+// The luminance limit on an emitted pair (codes in [0, 255]): the two colours'
+// L* (step 1 applied to the codes, from the table) differ by at most max_dl.
+__device__ __forceinline__ bool dl_ok(const double* __restrict__ ltab, double max_dl,
+                                      const int qp[3], const int qm[3]) {
+    const int ip = (qp[0] << 16) | (qp[1] << 8) | qp[2];
+    const int im = (qm[0] << 16) | (qm[1] << 8) | qm[2];
+    return fabs(__dsub_rn(__ldg(ltab + ip), __ldg(ltab + im))) <= max_dl;
+}
+
 // Exact FP64 decision of one slot; returns the pattern (0 = fail) and the
 // emitted codes (clamped in clip mode).
 __device__ __forceinline__ int decide64_slot(const SearchArgs& A, const TargetF64& D, int k, int h,
@@ -171,7 +180,8 @@ __device__ __forceinline__ int decide64_slot(const SearchArgs& A, const TargetF6
             qm[i] = min(max(qm[i], 0), 255);
         }
     }
-    return decide_codes(qp, qm, dc);
+    const int pattern = decide_codes(qp, qm, dc);
+    return (pattern && A.ltab && !dl_ok(A.ltab, A.max_dl, qp, qm)) ? 0 : pattern;
 }
 
 // Re-decide up to 32 queued slots in FP64, one per lane, and merge them.
@@ -245,8 +255,11 @@ __device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S
         h = (int)(kh >> 16);
         const float2 r2 = S.r2[k];
         const float r = r2.x;
-        pc = certain32<FAST>(T, C, r2, S.sc4[h], A.half_w, A.hi_min, A.lo_max, A.mask2, A.clip,
-                             A.list_mode);
+        // a list and the luminance limit need the exact codes of a passing pair
+        const Intervals I = intervals32<FAST>(T, C, r2, S.sc4[h], A.half_w, A.clip);
+        pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, A.clip,
+                          A.list_mode || A.ltab != nullptr);
+        if (pc > 0 && A.ltab && !dl_ok(A.ltab, A.max_dl, I.lo, I.lo + 3)) pc = 0;
         if (pc > 0) {
             cnt += inc;
             rmax = fmaxf(rmax, r);
@@ -268,7 +281,7 @@ struct Tally {
 // CHECK, lanes past the item's last slot (active == false) contribute nothing.
 // Returns true for a flagged FP32 slot (decided later by drain_flagged); the
 // step itself never synchronises the warp.
-template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST, bool LINSEG>
+template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST, bool LINSEG, bool DL>
 __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, const PairsT& P,
                                           const PairsC& PC, const TargetF64& D, int k, int h,
                                           bool active, Tally& acc) {
@@ -286,6 +299,19 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
         if (CHECK) flag = flag && active;
         int pattern = decide32<CLIP>(yp, ym, S.lut, A.mask2);
         if (flag || (CHECK && !active)) pattern = 0;
+        if (DL && pattern) {
+            int qp[3], qm[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                qp[c] = yp[c] - kMagicBits;
+                qm[c] = ym[c] - kMagicBits;
+                if (CLIP) {
+                    qp[c] = min(max(qp[c], 0), 255);
+                    qm[c] = min(max(qm[c], 0), 255);
+                }
+            }
+            if (!dl_ok(A.ltab, A.max_dl, qp, qm)) pattern = 0;
+        }
         if (pattern) {
             if (!LIST) {
                 acc.cnt += inc;
@@ -332,7 +358,7 @@ constexpr int kSegIters = 32 * kFlagWords;
 
 // Iterations [it, end) of an item (within one segment starting at seg0), with
 // lanes at slot (k, h); flagged slots set their bits in fb.
-template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST, bool LINSEG>
+template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST, bool LINSEG, bool DL>
 __device__ __forceinline__ void run_range(const SearchArgs& A, const Smem& S, const PairsT& P,
                                           const PairsC& PC, const TargetF64& D, int& it, int end,
                                           int seg0, int nslots, int q32, int r32, int& k, int& h,
@@ -345,8 +371,8 @@ __device__ __forceinline__ void run_range(const SearchArgs& A, const Smem& S, co
         uint32_t bits = 0, bit = 1u << ((it - seg0) & 31);
         for (; it < wend; ++it) {
             const bool active = !CHECK || it * 32 + (int)lane < nslots;
-            const bool flag = slot_step<PREC, FAST, CHECK, CLIP, LIST, LINSEG>(A, S, P, PC, D, k, h,
-                                                                             active, acc);
+            const bool flag = slot_step<PREC, FAST, CHECK, CLIP, LIST, LINSEG, DL>(A, S, P, PC, D, k,
+                                                                                 h, active, acc);
             if (PREC == CVS_PREC_FP32_RECHECK && flag) bits |= bit;
             bit <<= 1;
             h += r32;
@@ -403,7 +429,7 @@ __device__ __forceinline__ void collect_flagged(const SearchArgs& A, const Smem&
     }
 }
 
-template <int PREC, bool FAST, bool CLIP, bool LIST>
+template <int PREC, bool FAST, bool CLIP, bool LIST, bool DL>
 __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int64_t t, int k0,
                                          int k1, const ChainF32& C, uint32_t* pq, uint32_t* fb,
                                          uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
@@ -435,17 +461,17 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
         const int seg1 = min(seg0 + kSegIters, nit);
         const int full_end = min(seg1, nfull);
         if constexpr (PREC == CVS_PREC_FP32_RECHECK && FAST) {
-            run_range<PREC, FAST, false, CLIP, LIST, false>(A, S, P, PC, D, it, min(full_end, it_pow),
+            run_range<PREC, FAST, false, CLIP, LIST, false, DL>(A, S, P, PC, D, it, min(full_end, it_pow),
                                                             seg0, nslots, q32, r32, k, h, acc, fb);
         }
-        run_range<PREC, FAST, false, CLIP, LIST, true>(A, S, P, PC, D, it, full_end, seg0, nslots,
+        run_range<PREC, FAST, false, CLIP, LIST, true, DL>(A, S, P, PC, D, it, full_end, seg0, nslots,
                                                        q32, r32, k, h, acc, fb);
         if (it < seg1) {  // the item's last, partial iteration
             if (PREC == CVS_PREC_FP32_RECHECK && FAST && it < it_pow)
-                run_range<PREC, FAST, true, CLIP, LIST, false>(A, S, P, PC, D, it, seg1, seg0,
+                run_range<PREC, FAST, true, CLIP, LIST, false, DL>(A, S, P, PC, D, it, seg1, seg0,
                                                                nslots, q32, r32, k, h, acc, fb);
             else
-                run_range<PREC, FAST, true, CLIP, LIST, true>(A, S, P, PC, D, it, seg1, seg0,
+                run_range<PREC, FAST, true, CLIP, LIST, true, DL>(A, S, P, PC, D, it, seg1, seg0,
                                                               nslots, q32, r32, k, h, acc, fb);
         }
         if (PREC == CVS_PREC_FP32_RECHECK) {
@@ -485,7 +511,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
 #define CVS_SEARCH_MIN_BLOCKS 6
 #endif
 
-template <int PREC, bool CLIP, bool LIST>
+template <int PREC, bool CLIP, bool LIST, bool DL>
 __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
     k_search(const SearchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -533,13 +559,13 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
         if (PREC == CVS_PREC_FP32_RECHECK) {
             const uint32_t fl = A.tf[t].flags;
             if (fl & 1u)
-                run_item<PREC, true, CLIP, LIST>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
+                run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
                                                  n_re);
             else
-                run_item<PREC, false, CLIP, LIST>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
+                run_item<PREC, false, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
                                                   n_re);
         } else {
-            run_item<PREC, true, CLIP, LIST>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
+            run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
                                              n_re);
         }
     }
@@ -609,6 +635,15 @@ __global__ void __launch_bounds__(1024) k_compact_pairs(const cvs_pair* __restri
         __syncthreads();
     }
     if (threadIdx.x == 0) *n_out = (unsigned long long)base;
+}
+
+// ------------------------------------------------------------ L* of all colours
+__global__ void k_l_table(double* __restrict__ ltab) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ((int64_t)1 << 24)) return;
+    double L, a, b;
+    target_lab64((uint32_t)(i >> 16), (uint32_t)(i >> 8) & 255u, (uint32_t)i & 255u, L, a, b);
+    ltab[i] = L;
 }
 
 // ------------------------------------------------------------ L*a*b* only
@@ -796,10 +831,10 @@ int search_smem_bytes(const GridDev& g, int block) {
            (block / 32) * (kRqCap * 12 + kFlagWords * 32 * 4);
 }
 
-template <int PREC, bool CLIP, bool LIST>
+template <int PREC, bool CLIP, bool LIST, bool DL>
 cudaError_t launch_search_t(const SearchArgs& a, cudaStream_t st) {
     const int smem = search_smem_bytes(a.grid, a.shape.block);
-    const void* fn = (const void*)k_search<PREC, CLIP, LIST>;
+    const void* fn = (const void*)k_search<PREC, CLIP, LIST, DL>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = a.shape.blocks_per_sm;
@@ -808,16 +843,21 @@ cudaError_t launch_search_t(const SearchArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    k_search<PREC, CLIP, LIST><<<a.num_sms * per_sm, a.shape.block, smem, st>>>(a);
+    k_search<PREC, CLIP, LIST, DL><<<a.num_sms * per_sm, a.shape.block, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int PREC, bool DL>
+cudaError_t launch_search_d(const SearchArgs& a, cudaStream_t st) {
+    if (a.clip) return a.list_mode ? launch_search_t<PREC, true, true, DL>(a, st)
+                                   : launch_search_t<PREC, true, false, DL>(a, st);
+    return a.list_mode ? launch_search_t<PREC, false, true, DL>(a, st)
+                       : launch_search_t<PREC, false, false, DL>(a, st);
 }
 
 template <int PREC>
 cudaError_t launch_search_p(const SearchArgs& a, cudaStream_t st) {
-    if (a.clip) return a.list_mode ? launch_search_t<PREC, true, true>(a, st)
-                                   : launch_search_t<PREC, true, false>(a, st);
-    return a.list_mode ? launch_search_t<PREC, false, true>(a, st)
-                       : launch_search_t<PREC, false, false>(a, st);
+    return a.ltab ? launch_search_d<PREC, true>(a, st) : launch_search_d<PREC, false>(a, st);
 }
 
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t st) {
@@ -842,6 +882,11 @@ cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t 
 cudaError_t launch_compact_pairs(const cvs_pair* dense, int64_t n_dense, cvs_pair* out,
                                  unsigned long long* n_out, cudaStream_t st) {
     k_compact_pairs<<<1, 1024, 0, st>>>(dense, n_dense, out, n_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l_table(double* ltab, cudaStream_t st) {
+    k_l_table<<<(1 << 24) / 256, 256, 0, st>>>(ltab);
     return cudaGetLastError();
 }
 
