@@ -34,6 +34,10 @@ CAND_PER_4K_FRAME = 3840 * 2160 * 64 * 180
 # conversion and half a pair decision per candidate; see the roofline section
 # of the design notes): 53.5 FP32/INT lane operations + 6 MUFU operations.
 ALG_ISSUES_PER_CAND = 59.5
+# a candidate rejected before the encode (gamut reject, the warp's 32 slots all
+# certainly out of range): displacement 1 + cube expansion 6 + linear RGB 6 +
+# range test 6 issues
+ALG_ISSUES_PER_SKIPPED = 19.0
 LANES_PER_SM_CLK = 128
 # DRAM bytes of one FP32 search launch on this workload, from the ncu capture
 # summarised in profiles/k_search_fp32_colour_cube_full.md (32,768-colour case
@@ -506,7 +510,7 @@ def run_ours(args, world, rank, local):
     # ---- timed region: device-resident inputs, L2 flushed between steps
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
-    step_ms, kern_ms, flagged, rechecked = [], [], 0, 0
+    step_ms, kern_ms, flagged, rechecked, skipped = [], [], 0, 0, 0
     barrier(world)
     torch.cuda.synchronize(device)
     with ClockSampler(local) as clk:
@@ -521,6 +525,7 @@ def run_ours(args, world, rank, local):
             kern_ms.append(st["search_ms"])
             flagged += st["flagged"]
             rechecked += st["rechecked"]
+            skipped += st["skipped"]
     torch.cuda.synchronize(device)
     barrier(world)
     total_s = max_over_ranks(sum(step_ms) / 1e3, world, device)
@@ -568,7 +573,9 @@ def run_ours(args, world, rank, local):
     c = clk.summary()
     f_mhz = c["sm_mhz"] or 2070.0
     kern_avg_s = sum(kern_ms) / len(kern_ms) / 1e3
-    achieved = ALG_ISSUES_PER_CAND * cand / kern_avg_s / 1e12
+    skip_c = skipped / args.steps  # per launch
+    alg_ops = ALG_ISSUES_PER_CAND * (cand - skip_c) + ALG_ISSUES_PER_SKIPPED * skip_c
+    achieved = alg_ops / kern_avg_s / 1e12
     num_sms = torch.cuda.get_device_properties(device).multi_processor_count
     peak = num_sms * LANES_PER_SM_CLK * f_mhz * 1e6 / 1e12
 
@@ -600,6 +607,8 @@ def run_ours(args, world, rank, local):
                      "peak_basis": f"{num_sms} SMs x {LANES_PER_SM_CLK} lanes x "
                                    f"{f_mhz:.0f} MHz median SM clock under load",
                      "ops_per_candidate": ALG_ISSUES_PER_CAND,
+                     "ops_per_skipped_candidate": ALG_ISSUES_PER_SKIPPED,
+                     "skipped_fraction": skip_c / cand,
                      "kernel_ms": kern_avg_s * 1e3},
         "clocks": {"sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"],
                    "reasons": c["reasons"], "samples": c["samples"]},

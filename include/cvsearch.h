@@ -141,6 +141,9 @@ typedef struct {
     int32_t precision;       /* cvs_precision of the call */
     double search_ms;        /* device time of the search kernel (CUDA events on the
                                 call's stream) */
+    int64_t skipped;         /* candidates rejected without encoding: in gamut-reject
+                                mode, a warp's 32 slots whose linear RGB all lie
+                                certainly outside the range of codes 0..255 */
 } cvs_stats;
 
 /* ---------------------------------------------------------------- context */

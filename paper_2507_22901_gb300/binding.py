@@ -63,7 +63,8 @@ class cvs_stats(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int64), ("colors_fp32", ctypes.c_int64),
                 ("flagged", ctypes.c_int64), ("rechecked", ctypes.c_int64),
                 ("targets", ctypes.c_int64), ("symmetric", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("search_ms", ctypes.c_double)]
+                ("precision", ctypes.c_int32), ("search_ms", ctypes.c_double),
+                ("skipped", ctypes.c_int64)]
 
 
 class cvs_precision_report(ctypes.Structure):

@@ -73,7 +73,7 @@ struct cvs_ctx {
     Acc* acc = nullptr;
     int64_t cap_tf = 0, cap_td = 0, cap_acc = 0;
     long long* qkey = nullptr;
-    unsigned long long* counters = nullptr;  // [0] work, [1] flagged, [2] rechecked, [3] n_out
+    unsigned long long* counters = nullptr;  // kNumCounters: work, flagged, rechecked, n_out, skipped
     unsigned long long* h_counters = nullptr;  // pinned copy
     // list mode
     cvs_pair* dense = nullptr;
@@ -296,7 +296,7 @@ cvs_status tune_shape(cvs_ctx* c, const SearchArgs& base, cudaStream_t st, Launc
     const int64_t cap = (int64_t)3e10 / (per_target > 0 ? per_target : 1);
     if (n > cap) n = cap < 1 ? 1 : cap;
     CVS_CUDA(grow(&c->acc_tune, &c->cap_acc_tune, n));
-    if (!c->tune_counters) CVS_CUDA(cudaMalloc(&c->tune_counters, 4 * sizeof(unsigned long long)));
+    if (!c->tune_counters) CVS_CUDA(cudaMalloc(&c->tune_counters, kNumCounters * sizeof(unsigned long long)));
     std::vector<LaunchShape> cand;
     const int auto_k = choose_kchunk(c, n, K, H);
     const int min_k = (64 + H - 1) / H;
@@ -334,7 +334,7 @@ cvs_status tune_shape(cvs_ctx* c, const SearchArgs& base, cudaStream_t st, Launc
         a.shape = sh;
         double ms_min = 1e300;
         for (int rep = 0; rep < 3 && status == CVS_OK; ++rep) {
-            cudaError_t e = cudaMemsetAsync(c->tune_counters, 0, 3 * sizeof(unsigned long long), st);
+            cudaError_t e = cudaMemsetAsync(c->tune_counters, 0, kNumCounters * sizeof(unsigned long long), st);
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
             if (e == cudaSuccess) e = launch_search(a, st);
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
@@ -395,11 +395,11 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
         if (it != c->tuned.end()) a.shape = it->second;
     }
     const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    CVS_CUDA(cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), st));
+    CVS_CUDA(cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st));
     CVS_CUDA(cudaEventRecordWithFlags(c->ev0, st, ev_flags));
     CVS_CUDA(launch_search(a, st));
     CVS_CUDA(cudaEventRecordWithFlags(c->ev1, st, ev_flags));
-    CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, 4 * sizeof(unsigned long long),
+    CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, kNumCounters * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, st));
     cvs_stats& s = c->last;
     s = cvs_stats{};
@@ -487,6 +487,7 @@ void collect_stats(cvs_ctx* c) {
     const int f = c->grid.sym ? 2 : 1;
     c->last.flagged = (int64_t)c->h_counters[1] * f;
     c->last.rechecked = (int64_t)c->h_counters[2] * f;
+    c->last.skipped = (int64_t)c->h_counters[4] * f;
     c->last_pending = false;
 }
 
@@ -514,8 +515,8 @@ cvs_status cvs_create(cvs_ctx** out, int device) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&c->qkey, 257 * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc(&c->counters, 4 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->counters, kNumCounters * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, kNumCounters * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_rgb1, 16);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_probe, 32);
@@ -787,11 +788,11 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     cudaStream_t st = (cudaStream_t)stream;
     CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
     CVS_CUDA(launch_init_acc(c->acc_multi, n * n_thr, st));
-    CVS_CUDA(cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), st));
+    CVS_CUDA(cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st));
     CVS_CUDA(cudaEventRecord(c->ev0, st));
     CVS_CUDA(launch_search_multi(a, st));
     CVS_CUDA(cudaEventRecord(c->ev1, st));
-    CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, 4 * sizeof(unsigned long long),
+    CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, kNumCounters * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, st));
     CVS_CUDA(launch_finalize_colors(c->acc_multi, n * n_thr, out->max_r, out->count, out->pmask,
                                     st));
@@ -946,11 +947,11 @@ cvs_status cvs_embed_image(cvs_ctx* c, const cvs_image* img, const uint8_t* patt
     a.work_counter = c->counters;
     a.stats = c->counters + 1;
     a.num_sms = c->num_sms;
-    CVS_CUDA(cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), st));
+    CVS_CUDA(cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st));
     CVS_CUDA(cudaEventRecord(c->ev0, st));
     CVS_CUDA(launch_embed(a, st));
     CVS_CUDA(cudaEventRecord(c->ev1, st));
-    CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, 4 * sizeof(unsigned long long),
+    CVS_CUDA(cudaMemcpyAsync(c->h_counters, c->counters, kNumCounters * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, st));
     cvs_stats& s = c->last;
     s = cvs_stats{};
@@ -1176,7 +1177,7 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
     a.stats = c->counters + 1;
     a.num_sms = c->num_sms;
     cudaStream_t st = (cudaStream_t)stream;
-    e = cudaMemsetAsync(c->counters, 0, 3 * sizeof(unsigned long long), st);
+    e = cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev0, st);
     for (int64_t first = 0; first < kColours && e == cudaSuccess; first += kChunk) {
         a.key = E->choice + 7 * first;
@@ -1191,7 +1192,7 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
     }
     if (e == cudaSuccess) e = cudaEventRecord(c->ev1, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->h_counters, c->counters, 4 * sizeof(unsigned long long),
+        e = cudaMemcpyAsync(c->h_counters, c->counters, kNumCounters * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, st);
     // the colour buffer is released once the stream has consumed it
     cudaError_t se = cudaStreamSynchronize(st);

@@ -275,6 +275,7 @@ struct Tally {
     int cnt;
     float rmax;
     uint32_t pm;
+    uint32_t skip;  // slots of this lane skipped as certainly out of gamut
 };
 
 // One 32-slot step of a work item: every lane evaluates slot (k, h).  With
@@ -294,8 +295,17 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
         const float4 sc = S.sc4[h];
         const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));  // (u, -u)
         const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));  // (w, -w)
+        float2 lin[3];
+        lin32<FAST>(P, PC, u2, w2, lin);
+        if (!CLIP) {  // gamut reject: a warp whose pairs all leave the gamut is done
+            const bool out = surely_out32(lin) || (CHECK && !active);
+            if (__all_sync(0xFFFFFFFFu, out)) {
+                acc.skip += (!CHECK || active) ? 1u : 0u;
+                return false;
+            }
+        }
         int yp[3], ym[3];
-        bool flag = codes32<FAST, LINSEG>(P, PC, u2, w2, A.half_w, yp, ym);
+        bool flag = encode32<LINSEG>(lin, A.half_w, yp, ym, nullptr);
         if (CHECK) flag = flag && active;
         int pattern = decide32<CLIP>(yp, ym, S.lut, A.mask2);
         if (flag || (CHECK && !active)) pattern = 0;
@@ -433,7 +443,8 @@ template <int PREC, bool FAST, bool CLIP, bool LIST, bool DL>
 __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int64_t t, int k0,
                                          int k1, const ChainF32& C, uint32_t* pq, uint32_t* fb,
                                          uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
-                                         unsigned long long& n_flag, unsigned long long& n_re) {
+                                         unsigned long long& n_flag, unsigned long long& n_re,
+                                         unsigned long long& n_skip) {
     const unsigned lane = lane_id();
     const int H = A.grid.H;
     const int nslots = (k1 - k0) * H;
@@ -443,7 +454,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
     else D = A.td[t];
     const PairsT P = make_pairs(T);
     const PairsC PC = make_pairs(C);
-    Tally acc{0, -1.0f, 0u};
+    Tally acc{0, -1.0f, 0u, 0u};
     int pq_n = 0;  // flagged slots waiting for drain_flagged (warp-uniform)
     // slot i of the item is (k0 + i / H, i % H); lanes start at i = lane and
     // step by 32 = q32 H + r32, so one conditional wrap keeps h in [0, H)
@@ -483,6 +494,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
     if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0)
         drain_flagged<FAST>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh, rq_n,
                             n_re);
+    n_skip += acc.skip;
     if (!LIST) {
         int cnt = acc.cnt;
         float rmax = acc.rmax;
@@ -543,7 +555,7 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
     uint32_t* rq_t = S.rq_t + warp * kRqCap;
     uint32_t* rq_kh = S.rq_kh + warp * kRqCap;
     int rq_n = 0;
-    unsigned long long n_flag = 0, n_re = 0;
+    unsigned long long n_flag = 0, n_re = 0, n_skip = 0;
     const int kchunk = A.shape.kchunk;
     const int n_kc = (K + kchunk - 1) / kchunk;
     const unsigned long long n_items = (unsigned long long)A.n_targets * n_kc;
@@ -560,13 +572,13 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
             const uint32_t fl = A.tf[t].flags;
             if (fl & 1u)
                 run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
-                                                 n_re);
+                                                 n_re, n_skip);
             else
                 run_item<PREC, false, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
-                                                  n_re);
+                                                  n_re, n_skip);
         } else {
             run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
-                                             n_re);
+                                             n_re, n_skip);
         }
     }
     if (PREC == CVS_PREC_FP32_RECHECK && rq_n > 0) flush_queue(A, rq_t, rq_kh, rq_n, &n_re);
@@ -575,10 +587,12 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
     for (int off = 16; off > 0; off >>= 1) {
         n_flag += __shfl_xor_sync(0xFFFFFFFFu, n_flag, off);
         n_re += __shfl_xor_sync(0xFFFFFFFFu, n_re, off);
+        n_skip += __shfl_xor_sync(0xFFFFFFFFu, n_skip, off);
     }
     if (lane == 0) {
         if (n_flag) atomicAdd(A.stats + 0, n_flag);
         if (n_re) atomicAdd(A.stats + 1, n_re);
+        if (n_skip) atomicAdd(A.stats + 3, n_skip);
     }
 }
 

@@ -32,7 +32,7 @@ constexpr size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 // Byte offsets of the buffers inside the scratch array.
 constexpr size_t kOffQkey = 0;
 constexpr size_t kOffCounters = kOffQkey + up256(257 * sizeof(long long));
-constexpr size_t kOffStatus = kOffCounters + up256(4 * sizeof(unsigned long long));
+constexpr size_t kOffStatus = kOffCounters + up256(cvs::kNumCounters * sizeof(unsigned long long));
 constexpr size_t kOffR32 = kOffStatus + up256(sizeof(int));
 constexpr size_t kOffSc32 = kOffR32 + up256(kMaxRadii * sizeof(float));
 constexpr size_t kOffR64 = kOffSc32 + up256(kMaxAngles * sizeof(float2));
@@ -179,7 +179,7 @@ cvs_status run(int device, const uint8_t* rgb_dev, int64_t n, const cvs_grid* g,
     a.shape.kchunk = kchunk;
     a.num_sms = num_sms;
     NA_CUDA(cvs::launch_setup_colors(rgb_dev, n, rmax, tf, td, acc, st));
-    NA_CUDA(cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), st));
+    NA_CUDA(cudaMemsetAsync(counters, 0, cvs::kNumCounters * sizeof(unsigned long long), st));
     NA_CUDA(cvs::launch_search(a, st));
     NA_CUDA(cvs::launch_finalize_colors(acc, n, out->max_r, out->count, out->pmask, st));
     return CVS_OK;

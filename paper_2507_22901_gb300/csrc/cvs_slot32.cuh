@@ -93,16 +93,24 @@ __device__ __forceinline__ void delta_xz(const PairsT& P, float2 u2, float2 w2, 
 // ops).  Returns true if some code's unrounded value lies within W of a
 // rounding boundary.  LINSEG = false when every linear RGB value of the call
 // is known to lie above the sRGB linear segment (see pow_branch_only).
-template <bool FAST, bool LINSEG = true>
-__device__ __forceinline__ bool codes32(const PairsT& P, const PairsC& C, float2 u2, float2 w2,
-                                        float half_w, int yp[3], int ym[3],
-                                        float2* resid = nullptr) {
+// Linear RGB of the pair (plus in .x, minus in .y), per channel.
+template <bool FAST>
+__device__ __forceinline__ void lin32(const PairsT& P, const PairsC& C, float2 u2, float2 w2,
+                                      float2 lin[3]) {
     float2 dX, dZ;
     delta_xz<FAST>(P, u2, w2, dX, dZ);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lin[c] = __ffma2_rn(C.Bz[c], dZ, __ffma2_rn(C.Ax[c], dX, P.lin0[c]));
+}
+
+// Encode and round the pair's linear values (see codes32).
+template <bool LINSEG>
+__device__ __forceinline__ bool encode32(const float2 lin_in[3], float half_w, int yp[3],
+                                         int ym[3], float2* resid) {
     bool flag = false;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float2 lin = __ffma2_rn(C.Bz[c], dZ, __ffma2_rn(C.Ax[c], dX, P.lin0[c]));
+        const float2 lin = lin_in[c];
         float lgp, lgm, pp, pm;
         asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lgp) : "f"(lin.x));
         asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lgm) : "f"(lin.y));
@@ -125,6 +133,34 @@ __device__ __forceinline__ bool codes32(const PairsT& P, const PairsC& C, float2
         ym[c] = __float_as_int(y.y);
     }
     return flag;
+}
+
+template <bool FAST, bool LINSEG = true>
+__device__ __forceinline__ bool codes32(const PairsT& P, const PairsC& C, float2 u2, float2 w2,
+                                        float half_w, int yp[3], int ym[3],
+                                        float2* resid = nullptr) {
+    float2 lin[3];
+    lin32<FAST>(P, C, u2, w2, lin);
+    return encode32<LINSEG>(lin, half_w, yp, ym, resid);
+}
+
+// True when some linear value of the pair lies certainly outside the range of
+// codes 0..255 (below the threshold of code 0 or at or above that of code 256,
+// by a margin of 1e-5, far above the FP32 chain's error in linear RGB of about
+// 1e-6): in gamut-reject mode such a pair fails whatever its codes.
+constexpr double kQthrHost[257] = CVS_QTHR_INIT;
+constexpr float kLinOutLo = (float)kQthrHost[0] - 1e-5f;
+constexpr float kLinOutHi = (float)kQthrHost[256] + 1e-5f;
+__device__ __forceinline__ bool surely_out32(const float2 lin[3]) {
+    constexpr float mid = 0.5f * (kLinOutLo + kLinOutHi), half = 0.5f * (kLinOutHi - kLinOutLo);
+    bool out = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 dv = __fadd2_rn(lin[c], dup(-mid));
+        out |= fabsf(dv.x) > half;
+        out |= fabsf(dv.y) > half;
+    }
+    return out;
 }
 
 // True when no candidate at radius r (any angle) of a fast-path target can
