@@ -510,7 +510,7 @@ def run_ours(args, world, rank, local):
     # ---- timed region: device-resident inputs, L2 flushed between steps
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
-    step_ms, kern_ms, flagged, rechecked, skipped = [], [], 0, 0, 0
+    step_ms, kern_ms, flagged, rechecked, skipped, pruned = [], [], 0, 0, 0, 0
     barrier(world)
     torch.cuda.synchronize(device)
     with ClockSampler(local) as clk:
@@ -526,6 +526,7 @@ def run_ours(args, world, rank, local):
             flagged += st["flagged"]
             rechecked += st["rechecked"]
             skipped += st["skipped"]
+            pruned += st["pruned"]
     torch.cuda.synchronize(device)
     barrier(world)
     total_s = max_over_ranks(sum(step_ms) / 1e3, world, device)
@@ -574,7 +575,8 @@ def run_ours(args, world, rank, local):
     f_mhz = c["sm_mhz"] or 2070.0
     kern_avg_s = sum(kern_ms) / len(kern_ms) / 1e3
     skip_c = skipped / args.steps  # per launch
-    alg_ops = ALG_ISSUES_PER_CAND * (cand - skip_c) + ALG_ISSUES_PER_SKIPPED * skip_c
+    prune_c = pruned / args.steps  # rejected by the per-radius bound: no per-candidate work
+    alg_ops = ALG_ISSUES_PER_CAND * (cand - skip_c - prune_c) + ALG_ISSUES_PER_SKIPPED * skip_c
     achieved = alg_ops / kern_avg_s / 1e12
     num_sms = torch.cuda.get_device_properties(device).multi_processor_count
     peak = num_sms * LANES_PER_SM_CLK * f_mhz * 1e6 / 1e12
@@ -609,6 +611,7 @@ def run_ours(args, world, rank, local):
                      "ops_per_candidate": ALG_ISSUES_PER_CAND,
                      "ops_per_skipped_candidate": ALG_ISSUES_PER_SKIPPED,
                      "skipped_fraction": skip_c / cand,
+                     "pruned_fraction": prune_c / cand,
                      "kernel_ms": kern_avg_s * 1e3},
         "clocks": {"sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"],
                    "reasons": c["reasons"], "samples": c["samples"]},

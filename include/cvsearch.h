@@ -144,6 +144,9 @@ typedef struct {
     int64_t skipped;         /* candidates rejected without encoding: in gamut-reject
                                 mode, a warp's 32 slots whose linear RGB all lie
                                 certainly outside the range of codes 0..255 */
+    int64_t pruned;          /* candidates rejected without any work: radii below the
+                                first one where, by a bound on the pair's code
+                                difference, some channel could be high */
 } cvs_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -488,6 +488,7 @@ void collect_stats(cvs_ctx* c) {
     c->last.flagged = (int64_t)c->h_counters[1] * f;
     c->last.rechecked = (int64_t)c->h_counters[2] * f;
     c->last.skipped = (int64_t)c->h_counters[4] * f;
+    c->last.pruned = (int64_t)c->h_counters[5] * f;
     c->last_pending = false;
 }
 

@@ -60,8 +60,9 @@ struct LaunchShape {
 
 // Device counters of a search: [0] work items taken, [1] flagged slots,
 // [2] slots re-decided in FP64, [3] pairs written by the list compaction,
-// [4] slots skipped as certainly out of gamut.  The kernels get counters + 1.
-constexpr int kNumCounters = 5;
+// [4] slots skipped as certainly out of gamut, [5] slots below the first
+// radius where a pair may pass.  The kernels get counters + 1.
+constexpr int kNumCounters = 6;
 
 struct SearchArgs {
     const TargetF32* tf;
@@ -81,7 +82,7 @@ struct SearchArgs {
     const double* ltab;        // L* of all 2^24 colours when the luminance limit is on, else NULL
     double max_dl;             // the limit on |L*(plus) - L*(minus)| of an emitted pair
     unsigned long long* work_counter;
-    unsigned long long* stats; // [0] flagged, [1] rechecked, [3] skipped (see kNumCounters)
+    unsigned long long* stats; // [0] flagged, [1] rechecked, [3] skipped, [4] pruned
     LaunchShape shape;
     int num_sms;
 };

@@ -275,7 +275,8 @@ struct Tally {
     int cnt;
     float rmax;
     uint32_t pm;
-    uint32_t skip;  // slots of this lane skipped as certainly out of gamut
+    uint32_t skip;   // slots of this lane skipped as certainly out of gamut
+    uint32_t prune;  // slots of the item below the first radius where a pair may pass
 };
 
 // One 32-slot step of a work item: every lane evaluates slot (k, h).  With
@@ -444,7 +445,8 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
                                          int k1, const ChainF32& C, uint32_t* pq, uint32_t* fb,
                                          uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
                                          unsigned long long& n_flag, unsigned long long& n_re,
-                                         unsigned long long& n_skip) {
+                                         unsigned long long& n_skip,
+                                         unsigned long long& n_prune) {
     const unsigned lane = lane_id();
     const int H = A.grid.H;
     const int nslots = (k1 - k0) * H;
@@ -454,7 +456,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
     else D = A.td[t];
     const PairsT P = make_pairs(T);
     const PairsC PC = make_pairs(C);
-    Tally acc{0, -1.0f, 0u, 0u};
+    Tally acc{0, -1.0f, 0u, 0u, 0u};
     int pq_n = 0;  // flagged slots waiting for drain_flagged (warp-uniform)
     // slot i of the item is (k0 + i / H, i % H); lanes start at i = lane and
     // step by 32 = q32 H + r32, so one conditional wrap keeps h in [0, H)
@@ -468,7 +470,19 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
         it_pow = k_split == k1 ? nit : ((k_split - k0) * H) >> 5;
     }
     int it = 0;
-    for (int seg0 = 0; seg0 < nit; seg0 += kSegIters) {
+    if constexpr (PREC == CVS_PREC_FP32_RECHECK && FAST) {
+        // iterations wholly below the first radius where a pair may pass are skipped
+        const int k_pass = first_possible_radius(T, C, S.r2, k0, k1, A.hi_min);
+        if (k_pass > k0) {
+            it = k_pass == k1 ? nit : ((k_pass - k0) * H) >> 5;
+            const int i = it * 32 + (int)lane;
+            const int dk = i / H;
+            k = k0 + dk;
+            h = i - dk * H;
+            if (lane == 0) acc.prune += k_pass == k1 ? (uint32_t)nslots : (uint32_t)(it * 32);
+        }
+    }
+    for (int seg0 = it; seg0 < nit; seg0 += kSegIters) {
         const int seg1 = min(seg0 + kSegIters, nit);
         const int full_end = min(seg1, nfull);
         if constexpr (PREC == CVS_PREC_FP32_RECHECK && FAST) {
@@ -495,6 +509,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
         drain_flagged<FAST>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh, rq_n,
                             n_re);
     n_skip += acc.skip;
+    n_prune += acc.prune;
     if (!LIST) {
         int cnt = acc.cnt;
         float rmax = acc.rmax;
@@ -555,7 +570,7 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
     uint32_t* rq_t = S.rq_t + warp * kRqCap;
     uint32_t* rq_kh = S.rq_kh + warp * kRqCap;
     int rq_n = 0;
-    unsigned long long n_flag = 0, n_re = 0, n_skip = 0;
+    unsigned long long n_flag = 0, n_re = 0, n_skip = 0, n_prune = 0;
     const int kchunk = A.shape.kchunk;
     const int n_kc = (K + kchunk - 1) / kchunk;
     const unsigned long long n_items = (unsigned long long)A.n_targets * n_kc;
@@ -572,13 +587,13 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
             const uint32_t fl = A.tf[t].flags;
             if (fl & 1u)
                 run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
-                                                 n_re, n_skip);
+                                                 n_re, n_skip, n_prune);
             else
                 run_item<PREC, false, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
-                                                  n_re, n_skip);
+                                                  n_re, n_skip, n_prune);
         } else {
             run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
-                                             n_re, n_skip);
+                                             n_re, n_skip, n_prune);
         }
     }
     if (PREC == CVS_PREC_FP32_RECHECK && rq_n > 0) flush_queue(A, rq_t, rq_kh, rq_n, &n_re);
@@ -588,11 +603,13 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
         n_flag += __shfl_xor_sync(0xFFFFFFFFu, n_flag, off);
         n_re += __shfl_xor_sync(0xFFFFFFFFu, n_re, off);
         n_skip += __shfl_xor_sync(0xFFFFFFFFu, n_skip, off);
+        n_prune += __shfl_xor_sync(0xFFFFFFFFu, n_prune, off);
     }
     if (lane == 0) {
         if (n_flag) atomicAdd(A.stats + 0, n_flag);
         if (n_re) atomicAdd(A.stats + 1, n_re);
         if (n_skip) atomicAdd(A.stats + 3, n_skip);
+        if (n_prune) atomicAdd(A.stats + 4, n_prune);
     }
 }
 

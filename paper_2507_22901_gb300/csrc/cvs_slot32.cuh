@@ -183,6 +183,52 @@ __device__ __forceinline__ bool pow_branch_only(const TargetF32& T, const ChainF
     return ok;
 }
 
+// True when no pair of a fast-path target at radius r (any angle) can have a
+// high channel, so every candidate there fails (pattern 000 never passes):
+//   the pair's difference in linear RGB is, with u = r sin j / 500 and
+//   w = -r cos j / 200,  Ax (2 c2x u + 2 u^3) + Bz (2 c2z w + 2 w^3),  whose
+//   size over all angles is at most 2 sqrt((Ax c2x U)^2 + (Bz c2z V)^2)
+//   + 2 |Ax| U^3 + 2 |Bz| V^3 (U = r/500, V = r/200);
+//   the encode's slope in code units is at most 3294.6 up to lin = 0.0031308
+//   and 112.09375 lin^(-7/12) above it (decreasing), so over values no lower
+//   than the pair's lower bound lo the codes differ by at most slope(lo) times
+//   that difference, plus one for the two roundings.
+// A channel is high only if its codes differ by at least hi_min.  The bound is
+// evaluated in FP32 with a relative margin of 1e-4 and an absolute one of 1e-3.
+__device__ __forceinline__ bool certain_fail_radius(const TargetF32& T, const ChainF32& C,
+                                                    float r, int32_t hi_min) {
+    const float U = r * 0.002f * 1.00001f, V = r * 0.005f * 1.00001f;
+    const float xlo = -U * (T.c2x - U * (T.c1x - U)), xhi = U * (T.c2x + U * (T.c1x + U));
+    const float zlo = -V * (T.c2z - V * (T.c1z - V)), zhi = V * (T.c2z + V * (T.c1z + V));
+    bool fail = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float ax = fabsf(C.Ax[c]), bz = fabsf(C.Bz[c]);
+        const float p = ax * T.c2x * U, q = bz * T.c2z * V;
+        const float dlin = 2.0f * sqrtf(p * p + q * q) + 2.0f * (ax * U * U * U + bz * V * V * V);
+        const float lo = T.lin0[c] + fminf(C.Ax[c] * xlo, C.Ax[c] * xhi) +
+                         fminf(C.Bz[c] * zlo, C.Bz[c] * zhi);
+        const float slope = lo <= 0.0031308f ? 3294.6f : 112.09375f * exp2f(-7.0f / 12.0f * log2f(lo));
+        fail = fail && slope * dlin * 1.0001f + 1.001f < (float)hi_min;
+    }
+    return fail;
+}
+
+// First radius index in [k0, k1) whose candidates may pass (k1 if none);
+// warp-uniform.
+__device__ __forceinline__ int first_possible_radius(const TargetF32& T, const ChainF32& C,
+                                                     const float2* r2s, int k0, int k1,
+                                                     int32_t hi_min) {
+    const unsigned lane = threadIdx.x & 31u;
+    for (int kb = k0; kb < k1; kb += 32) {
+        const int kk = kb + (int)lane;
+        const bool maybe = kk < k1 && !certain_fail_radius(T, C, r2s[kk].x, hi_min);
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, maybe);
+        if (b) return kb + __ffs(b) - 1;
+    }
+    return k1;
+}
+
 // First radius index in [k0, k1) whose candidates may reach the sRGB linear
 // segment (k1 if none); warp-uniform.
 __device__ __forceinline__ int first_linseg_radius(const TargetF32& T, const ChainF32& C,
