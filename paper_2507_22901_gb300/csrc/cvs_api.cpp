@@ -774,9 +774,11 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     a.grid = c->grid;
     a.qkey = c->qkey;
     a.n_thr = n_thr;
+    a.hi_min_all = 256;
     for (int s = 0; s < n_thr; ++s) {
         thresholds_to_int(thr + s, &a.hi_min[s], &a.lo_max[s]);
         a.mask2[s] = thr[s].pattern_mask << 1;
+        a.hi_min_all = a.hi_min[s] < a.hi_min_all ? a.hi_min[s] : a.hi_min_all;
     }
     a.clip = thr[0].gamut_mode;
     if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;

@@ -111,10 +111,14 @@ __device__ __forceinline__ int embed_radius(const EmbedArgs& A, const float2* r2
             const bool active = h < H && w.h == kNone;
             const float4 sc = sc4s[h < H ? h : 0];
             const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y)), w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
+            float2 lin[3];
+            lin32<FAST>(P, PC, u2, w2, lin);
+            // gamut reject: 32 slots that all leave the gamut hold no hit
+            if (!CLIP && __all_sync(0xFFFFFFFFu, !active || surely_out32(lin))) continue;
             int yp[3], ym[3];
             bool flag;
-            if (pow_only) flag = codes32<FAST, false>(P, PC, u2, w2, A.half_w, yp, ym);
-            else flag = codes32<FAST, true>(P, PC, u2, w2, A.half_w, yp, ym);
+            if (pow_only) flag = encode32<false>(lin, A.half_w, yp, ym, nullptr);
+            else flag = encode32<true>(lin, A.half_w, yp, ym, nullptr);
             const int pat = decide32<CLIP>(yp, ym, lut, A.mask2);
             if (active) {
                 if (!flag) {
@@ -183,6 +187,10 @@ __device__ __forceinline__ bool embed_pixel(const EmbedArgs& A, const float2* r2
     const PairsT P = make_pairs(T);
     for (int kk = 0; kk < A.grid.K; ++kk) {
         const int k = __ldg(A.order + kk);
+        // no pair at this radius can have a high channel
+        if (PREC == CVS_PREC_FP32_RECHECK && FAST &&
+            certain_fail_radius(T, C, r2s[k].x, A.hi_min))
+            continue;
         Hit w;
         const int best = embed_radius<PREC, FAST, CLIP>(A, r2s, sc4s, lut, T, P, PC, C, D, k, p, w,
                                                         n_exact, n_re);
@@ -342,11 +350,20 @@ __device__ __forceinline__ void first_item(const FirstHitArgs& A, const float2* 
     int kk = kk0 + (int)lane / H, h = (int)lane % H;
     const int nit = (nslots + 31) >> 5;
     int it_pow = 0;  // iterations whose radii never reach the sRGB linear segment
+    int it0 = 0;     // iterations wholly below the first radius where a pair may pass
     if (PREC == CVS_PREC_FP32_RECHECK && FAST) {
         const int ks = first_linseg_radius(T, C, r2s, kk0, kk1);
         it_pow = ks == kk1 ? nit : ((ks - kk0) * H) >> 5;
+        const int kp = first_possible_radius(T, C, r2s, kk0, kk1, A.hi_min);
+        if (kp > kk0) {
+            it0 = kp == kk1 ? nit : ((kp - kk0) * H) >> 5;
+            const int i = it0 * 32 + (int)lane;
+            const int dk = i / H;
+            kk = kk0 + dk;
+            h = i - dk * H;
+        }
     }
-    for (int seg0 = 0; seg0 < nit; seg0 += kHitSegIters) {
+    for (int seg0 = it0; seg0 < nit; seg0 += kHitSegIters) {
         const int seg1 = min(seg0 + kHitSegIters, nit);
         for (int w = 0, it = seg0; it < seg1; ++w) {
             uint32_t bits = 0;
@@ -360,14 +377,20 @@ __device__ __forceinline__ void first_item(const FirstHitArgs& A, const float2* 
                     const float4 sc = sc4s[hq];
                     const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));
                     const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
-                    int yp[3], ym[3];
-                    bool flag;
-                    if (it < it_pow) flag = codes32<FAST, false>(P, PC, u2, w2, A.half_w, yp, ym);
-                    else flag = codes32<FAST, true>(P, PC, u2, w2, A.half_w, yp, ym);
-                    pattern = decide32<CLIP>(yp, ym, lut, A.mask2);
-                    flag = flag && active;
-                    if (flag || !active) pattern = 0;
-                    if (flag) bits |= bit;
+                    float2 lin[3];
+                    lin32<FAST>(P, PC, u2, w2, lin);
+                    // gamut reject: a warp whose pairs all leave the gamut has no hit
+                    const bool skip = !CLIP && __all_sync(0xFFFFFFFFu, !active || surely_out32(lin));
+                    if (!skip) {
+                        int yp[3], ym[3];
+                        bool flag;
+                        if (it < it_pow) flag = encode32<false>(lin, A.half_w, yp, ym, nullptr);
+                        else flag = encode32<true>(lin, A.half_w, yp, ym, nullptr);
+                        pattern = decide32<CLIP>(yp, ym, lut, A.mask2);
+                        flag = flag && active;
+                        if (flag || !active) pattern = 0;
+                        if (flag) bits |= bit;
+                    }
                 } else if (active) {
                     const int k = __ldg(A.order + kq);
                     int qp[3], qm[3];

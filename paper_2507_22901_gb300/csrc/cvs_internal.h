@@ -99,6 +99,7 @@ struct MultiArgs {
     int32_t n_thr;
     int32_t hi_min[kMaxThresholdSets], lo_max[kMaxThresholdSets];
     uint32_t mask2[kMaxThresholdSets];
+    int32_t hi_min_all;        // the smallest hi_min of the sets
     int32_t clip;              // shared by all sets
     float half_w;
     int32_t prec;

@@ -107,11 +107,20 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
     int k = k0 + (int)lane / H, h = (int)lane % H;
     const int nit = (nslots + 31) >> 5;
     int it_pow = 0;  // iterations whose radii never reach the sRGB linear segment
+    int it0 = 0;     // iterations wholly below the first radius where some set may pass
     if (PREC == CVS_PREC_FP32_RECHECK && FAST) {
         const int k_split = first_linseg_radius(T, C, r2s, k0, k1);
         it_pow = k_split == k1 ? nit : ((k_split - k0) * H) >> 5;
+        const int kp = first_possible_radius(T, C, r2s, k0, k1, A.hi_min_all);
+        if (kp > k0) {
+            it0 = kp == k1 ? nit : ((kp - k0) * H) >> 5;
+            const int i = it0 * 32 + (int)lane;
+            const int dk = i / H;
+            k = k0 + dk;
+            h = i - dk * H;
+        }
     }
-    for (int it = 0; it < nit; ++it) {
+    for (int it = it0; it < nit; ++it) {
         const bool active = it * 32 + (int)lane < nslots;
         const int kk = active ? k : k0, hh = active ? h : 0;
         const float2 r2 = r2s[kk];
@@ -120,8 +129,19 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
         if (PREC == CVS_PREC_FP32_RECHECK) {
             const float4 sc = sc4s[hh];
             const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y)), w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
-            if (it < it_pow) flag = codes32<FAST, false>(P, PC, u2, w2, A.half_w, yp, ym);
-            else flag = codes32<FAST, true>(P, PC, u2, w2, A.half_w, yp, ym);
+            float2 lin[3];
+            lin32<FAST>(P, PC, u2, w2, lin);
+            // gamut reject: a warp whose pairs all leave the gamut passes no set
+            if (!CLIP && __all_sync(0xFFFFFFFFu, !active || surely_out32(lin))) {
+                h += r32;
+                k += q32;
+                const bool wrap = h >= H;
+                h = wrap ? h - H : h;
+                k = wrap ? k + 1 : k;
+                continue;
+            }
+            if (it < it_pow) flag = encode32<false>(lin, A.half_w, yp, ym, nullptr);
+            else flag = encode32<true>(lin, A.half_w, yp, ym, nullptr);
             flag = flag && active;
         } else if (active) {
             pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + kk), __ldg(A.grid.s64 + hh),
