@@ -185,11 +185,16 @@ __device__ __forceinline__ bool embed_pixel(const EmbedArgs& A, const float2* r2
     if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
     const TargetF64 D = A.td[t];
     const PairsT P = make_pairs(T);
+    const uint32_t need = (uint32_t)p;  // channels pattern p needs high (bit 2 - c)
+    // a channel p needs high that cannot be high at the largest radius: no pair
+    if (PREC == CVS_PREC_FP32_RECHECK && FAST &&
+        (high_possible(T, C, r2s[__ldg(A.order + A.grid.K - 1)].x, A.hi_min) & need) != need)
+        return false;
     for (int kk = 0; kk < A.grid.K; ++kk) {
         const int k = __ldg(A.order + kk);
-        // no pair at this radius can have a high channel
+        // at this radius a channel p needs high cannot be high
         if (PREC == CVS_PREC_FP32_RECHECK && FAST &&
-            certain_fail_radius(T, C, r2s[k].x, A.hi_min))
+            (high_possible(T, C, r2s[k].x, A.hi_min) & need) != need)
             continue;
         Hit w;
         const int best = embed_radius<PREC, FAST, CLIP>(A, r2s, sc4s, lut, T, P, PC, C, D, k, p, w,

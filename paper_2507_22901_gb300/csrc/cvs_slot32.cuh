@@ -195,12 +195,14 @@ __device__ __forceinline__ bool pow_branch_only(const TargetF32& T, const ChainF
 //   that difference, plus one for the two roundings.
 // A channel is high only if its codes differ by at least hi_min.  The bound is
 // evaluated in FP32 with a relative margin of 1e-4 and an absolute one of 1e-3.
-__device__ __forceinline__ bool certain_fail_radius(const TargetF32& T, const ChainF32& C,
-                                                    float r, int32_t hi_min) {
+// The channels (bit 2 - c, as in a pattern) that could be high at radius r;
+// the bound grows with r.
+__device__ __forceinline__ uint32_t high_possible(const TargetF32& T, const ChainF32& C, float r,
+                                                  int32_t hi_min) {
     const float U = r * 0.002f * 1.00001f, V = r * 0.005f * 1.00001f;
     const float xlo = -U * (T.c2x - U * (T.c1x - U)), xhi = U * (T.c2x + U * (T.c1x + U));
     const float zlo = -V * (T.c2z - V * (T.c1z - V)), zhi = V * (T.c2z + V * (T.c1z + V));
-    bool fail = true;
+    uint32_t mask = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float ax = fabsf(C.Ax[c]), bz = fabsf(C.Bz[c]);
@@ -209,9 +211,14 @@ __device__ __forceinline__ bool certain_fail_radius(const TargetF32& T, const Ch
         const float lo = T.lin0[c] + fminf(C.Ax[c] * xlo, C.Ax[c] * xhi) +
                          fminf(C.Bz[c] * zlo, C.Bz[c] * zhi);
         const float slope = lo <= 0.0031308f ? 3294.6f : 112.09375f * exp2f(-7.0f / 12.0f * log2f(lo));
-        fail = fail && slope * dlin * 1.0001f + 1.001f < (float)hi_min;
+        if (!(slope * dlin * 1.0001f + 1.001f < (float)hi_min)) mask |= 1u << (2 - c);
     }
-    return fail;
+    return mask;
+}
+
+__device__ __forceinline__ bool certain_fail_radius(const TargetF32& T, const ChainF32& C,
+                                                    float r, int32_t hi_min) {
+    return high_possible(T, C, r, hi_min) == 0u;
 }
 
 // First radius index in [k0, k1) whose candidates may pass (k1 if none);
