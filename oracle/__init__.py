@@ -115,7 +115,7 @@ def lib() -> ctypes.CDLL:
             L.orc_search_colors.restype = None
             L.orc_decide_pair.argtypes = [vp, vp, d, d, u32, ctypes.c_int, vp, vp]
             L.orc_decide_pair.restype = ctypes.c_int
-            L.orc_passes_dl.argtypes = [P(_Consts), vp, vp, d]
+            L.orc_passes_dl.argtypes = [P(_Consts), d, vp, vp, d]
             L.orc_passes_dl.restype = ctypes.c_int
             L.orc_embed.argtypes = [P(_Consts), vp, vp, i64, vp, i32, vp, vp, i32, d, d, u32,
                                     ctypes.c_int, vp, vp, vp, ctypes.c_int]
@@ -224,11 +224,12 @@ def decide_pair(q_plus, q_minus, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0)
     return pat, op, om
 
 
-def passes_dl(plus, minus, max_dl) -> bool:
-    """True if the two 8-bit colours differ in L* by at most max_dl (< 0: no limit)."""
+def passes_dl(target_l, plus, minus, max_dl) -> bool:
+    """True if both 8-bit colours' L* lie within max_dl of target_l (< 0: no limit)."""
     a = np.ascontiguousarray(np.asarray(plus, np.uint8).reshape(3))
     b = np.ascontiguousarray(np.asarray(minus, np.uint8).reshape(3))
-    return bool(lib().orc_passes_dl(ctypes.byref(consts()), _ptr(a), _ptr(b), float(max_dl)))
+    return bool(lib().orc_passes_dl(ctypes.byref(consts()), float(target_l), _ptr(a), _ptr(b),
+                                    float(max_dl)))
 
 
 def roundtrip_all(threads: int = 0):

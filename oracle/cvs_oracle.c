@@ -236,21 +236,22 @@ static int decide_pair(const int q_plus[3], const int q_minus[3], double v_th, d
 }
 
 /* Perceptual refinement of the vibration condition (a reading: the paper fixes
- * L* before quantisation, §2 Methods, and gives no tolerance after it): the
- * two emitted 8-bit colours must differ in L* by at most max_dl, with each L*
- * from step 1 applied to the emitted codes.  max_dl < 0 or NaN: no limit. */
-static int passes_dl(const orc_consts* C, const uint8_t op[3], const uint8_t om[3],
-                     double max_dl) {
+ * L* before quantisation, §2 Methods, and gives no tolerance after it): each
+ * emitted 8-bit colour's L* (step 1 applied to its codes) must lie within
+ * max_dl of the target's L*.  max_dl < 0 or NaN: no limit. */
+static int passes_dl(const orc_consts* C, double L_target, const uint8_t op[3],
+                     const uint8_t om[3], double max_dl) {
     if (!(max_dl >= 0.0)) return 1;
     double lp[3], lm[3];
     orc_target_lab(C, op, lp);
     orc_target_lab(C, om, lm);
-    return fabs(lp[0] - lm[0]) <= max_dl;
+    return fabs(lp[0] - L_target) <= max_dl && fabs(lm[0] - L_target) <= max_dl;
 }
 
 /* Exported form of passes_dl for the oracle's own pins. */
-int orc_passes_dl(const orc_consts* C, const uint8_t op[3], const uint8_t om[3], double max_dl) {
-    return passes_dl(C, op, om, max_dl);
+int orc_passes_dl(const orc_consts* C, double L_target, const uint8_t op[3], const uint8_t om[3],
+                  double max_dl) {
+    return passes_dl(C, L_target, op, om, max_dl);
 }
 
 /* Exported form of decide_pair for the oracle's own pins. */
@@ -290,7 +291,7 @@ int64_t orc_search_color(const orc_consts* C, const uint8_t rgb[3], uint32_t tar
             memset(&rec, 0, sizeof rec);
             int pat = decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, rec.plus,
                                   rec.minus);
-            if (!pat || !passes_dl(C, rec.plus, rec.minus, max_dl)) continue;
+            if (!pat || !passes_dl(C, lab[0], rec.plus, rec.minus, max_dl)) continue;
             if (n < cap) {
                 rec.k = (uint16_t)k;
                 rec.m = (uint16_t)m;
@@ -326,7 +327,7 @@ void orc_search_colors(const orc_consts* C, const uint8_t* rgb, int64_t n_target
                 uint8_t op[3], om[3];
                 orc_pair_codes(C, lab, radii[k], sin_t[m], cos_t[m], qp, qm);
                 int pat = decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, op, om);
-                if (!pat || !passes_dl(C, op, om, max_dl)) continue;
+                if (!pat || !passes_dl(C, lab[0], op, om, max_dl)) continue;
                 ++cnt;
                 if (radii[k] > best) best = radii[k];
                 mask |= (uint8_t)(1u << (pat - 1));

@@ -15,11 +15,15 @@ import oracle
 
 
 def test_passes_dl_fixed_points():
-    assert oracle.passes_dl((10, 200, 30), (10, 200, 30), 0.0)
-    assert not oracle.passes_dl((0, 0, 0), (255, 255, 255), 99.999)
-    assert oracle.passes_dl((0, 0, 0), (255, 255, 255), 100.0)  # L* = 0 and 100 exactly
-    assert oracle.passes_dl((0, 0, 0), (255, 255, 255), -1.0)  # negative: no limit
-    assert oracle.passes_dl((0, 0, 0), (255, 255, 255), float("nan"))
+    l_mid = oracle.target_lab((10, 200, 30))[0]
+    assert oracle.passes_dl(l_mid, (10, 200, 30), (10, 200, 30), 0.0)
+    # black and white have L* = 0 and 100 exactly
+    assert not oracle.passes_dl(50.0, (0, 0, 0), (255, 255, 255), 49.999)
+    assert oracle.passes_dl(50.0, (0, 0, 0), (255, 255, 255), 50.0)
+    assert not oracle.passes_dl(0.0, (0, 0, 0), (255, 255, 255), 99.999)
+    assert oracle.passes_dl(0.0, (0, 0, 0), (255, 255, 255), 100.0)
+    assert oracle.passes_dl(0.0, (0, 0, 0), (255, 255, 255), -1.0)  # negative: no limit
+    assert oracle.passes_dl(0.0, (0, 0, 0), (255, 255, 255), float("nan"))
 
 
 def _pairs(rgb, radii, angles, gamut):
@@ -31,7 +35,8 @@ def _pairs(rgb, radii, angles, gamut):
             qp, qm = oracle.pair_codes(lab, r, s[m], c[m])
             pat, op, om = oracle.decide_pair(qp, qm, 50, 0.5, 0x7F, gamut)
             if pat:
-                dl = abs(oracle.target_lab(op)[0] - oracle.target_lab(om)[0])
+                dl = max(abs(oracle.target_lab(op)[0] - lab[0]),
+                         abs(oracle.target_lab(om)[0] - lab[0]))
                 out.append((k, m, pat, dl))
     return out
 
