@@ -66,7 +66,7 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison arm")
-    p.add_argument("--cpu-sample", type=int, default=2048,
+    p.add_argument("--cpu-sample", type=int, default=32768,
                    help="colours of the cube timed on the CPU oracle")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the precision study and the one-pass image measurement")
@@ -191,7 +191,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     from paper_2507_22901_gb300 import workloads as W  # noqa: F401
-    n = max(16, args.cpu_sample // 4)
+    n = max(16, args.cpu_sample // 16)  # about 0.7 s of oracle work per step on 16 cores
     for _ in range(args.warmup):
         time_oracle(max(8, n // 8))
     vals, cand_total, dt_total, threads = [], 0, 0.0, 1

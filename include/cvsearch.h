@@ -464,9 +464,9 @@ cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const c
  *                   on later calls with the same signature (up to 8 graphs are
  *                   kept per context).  Default 0.
  *   "max_dl"        a perceptual refinement of the vibration condition: a
- *                   passing pair is kept only if its two emitted 8-bit colours
- *                   differ in L* (step 1 of §2 Methods applied to each
- *                   colour's codes) by at most this many units.  The paper
+ *                   passing pair is kept only if each of its two emitted 8-bit
+ *                   colours has an L* (step 1 of §2 Methods applied to its
+ *                   codes) within this many units of the target's L*.  The paper
  *                   fixes L* before quantisation and gives no tolerance after
  *                   it, so the value is the caller's.  A negative value turns
  *                   the limit off (the default).  The first non-negative value

@@ -153,13 +153,15 @@ __device__ __forceinline__ void write_records(cvs_pair* dense, int N, int H, int
     }
 }
 
-// The luminance limit on an emitted pair (codes in [0, 255]): the two colours'
-// L* (step 1 applied to the codes, from the table) differ by at most max_dl.
+// The luminance limit on an emitted pair (codes in [0, 255]): each colour's
+// L* (step 1 applied to its codes, from the table) lies within max_dl of the
+// target's L*.
 __device__ __forceinline__ bool dl_ok(const double* __restrict__ ltab, double max_dl,
-                                      const int qp[3], const int qm[3]) {
+                                      double l_target, const int qp[3], const int qm[3]) {
     const int ip = (qp[0] << 16) | (qp[1] << 8) | qp[2];
     const int im = (qm[0] << 16) | (qm[1] << 8) | qm[2];
-    return fabs(__dsub_rn(__ldg(ltab + ip), __ldg(ltab + im))) <= max_dl;
+    return fabs(__dsub_rn(__ldg(ltab + ip), l_target)) <= max_dl &&
+           fabs(__dsub_rn(__ldg(ltab + im), l_target)) <= max_dl;
 }
 
 // Exact FP64 decision of one slot; returns the pattern (0 = fail) and the
@@ -181,7 +183,7 @@ __device__ __forceinline__ int decide64_slot(const SearchArgs& A, const TargetF6
         }
     }
     const int pattern = decide_codes(qp, qm, dc);
-    return (pattern && A.ltab && !dl_ok(A.ltab, A.max_dl, qp, qm)) ? 0 : pattern;
+    return (pattern && A.ltab && !dl_ok(A.ltab, A.max_dl, D.L, qp, qm)) ? 0 : pattern;
 }
 
 // Re-decide up to 32 queued slots in FP64, one per lane, and merge them.
@@ -259,7 +261,7 @@ __device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S
         const Intervals I = intervals32<FAST>(T, C, r2, S.sc4[h], A.half_w, A.clip);
         pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, A.clip,
                           A.list_mode || A.ltab != nullptr);
-        if (pc > 0 && A.ltab && !dl_ok(A.ltab, A.max_dl, I.lo, I.lo + 3)) pc = 0;
+        if (pc > 0 && A.ltab && !dl_ok(A.ltab, A.max_dl, A.td[t].L, I.lo, I.lo + 3)) pc = 0;
         if (pc > 0) {
             cnt += inc;
             rmax = fmaxf(rmax, r);
@@ -321,7 +323,7 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
                     qm[c] = min(max(qm[c], 0), 255);
                 }
             }
-            if (!dl_ok(A.ltab, A.max_dl, qp, qm)) pattern = 0;
+            if (!dl_ok(A.ltab, A.max_dl, D.L, qp, qm)) pattern = 0;
         }
         if (pattern) {
             if (!LIST) {
@@ -453,7 +455,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
     TargetF32 T;
     TargetF64 D;
     if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
-    else D = A.td[t];
+    if (PREC != CVS_PREC_FP32_RECHECK || DL) D = A.td[t];  // the limit needs the target's L*
     const PairsT P = make_pairs(T);
     const PairsC PC = make_pairs(C);
     Tally acc{0, -1.0f, 0u, 0u, 0u};
