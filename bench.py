@@ -378,6 +378,32 @@ def run_extras(ctx, torch, device, W, cvs):
         "pairs_without_limit": int(base[1].sum().item()),
         "pairs_with_limit": int(lim[1].sum().item())}
     del cube, base, lim
+    # the paper's own timed experiment (§3, Table 1): its 9 colours under all 12
+    # (V_th, R_novib) combinations and all 7 patterns, as one multi-set pass on
+    # the 61-radius x 360-angle grid (the paper does not state its grid)
+    t1rgb = torch.tensor(list(W.TABLE1_COLORS.values()), dtype=torch.uint8, device=device)
+    r1, a1 = W.grid(1)
+    sets1 = W.table1_threshold_sets()
+    res1 = ctx.search_colors_multi(t1rgb, r1, a1, sets1)
+    ctx.synchronize()
+    reps = 50
+    t0.record()
+    for _ in range(reps):
+        ctx.search_colors_multi(t1rgb, r1, a1, sets1, out=res1)
+    t1.record()
+    torch.cuda.synchronize(device)
+    sec1 = t0.elapsed_time(t1) / 1e3 / reps
+    h2 = time.perf_counter()
+    for _ in range(reps):
+        ctx.search_colors_multi(t1rgb, r1, a1, sets1, out=res1)
+        ctx.synchronize()
+    host_s = (time.perf_counter() - h2) / reps
+    out["table1_experiment"] = {
+        "workload": "9 Table 1 colours x 12 (V_th, R_novib) x 7 patterns; 61 radii x 360 angles",
+        "device_s": sec1, "call_to_result_s": host_s,
+        "paper_array_method_s": 62.62, "paper_hardware": "MacBook Pro 13-inch 2019 (CPU), grid unstated",
+        "presence": W.presence_matrix(res1[2].cpu().numpy()).astype(int).tolist()}
+    del t1rgb, res1
     # the experiment of §3: every cube colour under all 12 (V_th, R_novib) sets,
     # one multi-set pass against 12 single-set passes
     cube = torch.from_numpy(W.color_cube()).to(device)

@@ -775,9 +775,12 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     a.qkey = c->qkey;
     a.n_thr = n_thr;
     a.hi_min_all = 256;
+    a.all_patterns = 1;
     for (int s = 0; s < n_thr; ++s) {
         thresholds_to_int(thr + s, &a.hi_min[s], &a.lo_max[s]);
-        a.mask2[s] = thr[s].pattern_mask << 1;
+        for (int p = 1; p <= 7; ++p)
+            if ((thr[s].pattern_mask >> (p - 1)) & 1u) a.pmask_sets[p] |= 1u << s;
+        if ((thr[s].pattern_mask & 0x7Fu) != 0x7Fu) a.all_patterns = 0;
         a.hi_min_all = a.hi_min[s] < a.hi_min_all ? a.hi_min[s] : a.hi_min_all;
     }
     a.clip = thr[0].gamut_mode;
@@ -785,6 +788,7 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     a.half_w = (float)(0.5 - c->window);
     a.prec = (int32_t)prec;
     a.kchunk = choose_kchunk(c, n, c->grid.K, c->grid.H);
+    if (a.kchunk > multi_max_chunk()) a.kchunk = multi_max_chunk();
     a.work_counter = c->counters;
     a.stats = c->counters + 1;
     a.num_sms = c->num_sms;

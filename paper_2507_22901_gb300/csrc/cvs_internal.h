@@ -98,7 +98,8 @@ struct MultiArgs {
     const long long* qkey;
     int32_t n_thr;
     int32_t hi_min[kMaxThresholdSets], lo_max[kMaxThresholdSets];
-    uint32_t mask2[kMaxThresholdSets];
+    uint32_t pmask_sets[8];    // [p]: bit s set if set s enables pattern p (1..7)
+    int32_t all_patterns;      // 1 if every set enables all seven patterns
     int32_t hi_min_all;        // the smallest hi_min of the sets
     int32_t clip;              // shared by all sets
     float half_w;
@@ -169,6 +170,7 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t st);
 cudaError_t launch_finalize_colors(const Acc* acc, int64_t n, float* max_r, int32_t* count,
                                    uint8_t* pmask, cudaStream_t st);
 cudaError_t launch_search_multi(const MultiArgs& a, cudaStream_t st);
+int multi_max_chunk();  // largest radii per work item of the multi-threshold search
 cudaError_t launch_embed(const EmbedArgs& a, cudaStream_t st);
 cudaError_t launch_first_hits(const FirstHitArgs& a, cudaStream_t st);
 // keys (in place) -> choices k | m << 16, and the exact codes of each hit

@@ -1,6 +1,18 @@
 // cvs_multi.cu - the multi-threshold colour-pair search (sm_103a): every
 // candidate decided against up to kMaxThresholdSets (V_th, R_novib, mask) sets
 // in one pass (§3 Experiments, Table 1).
+//
+// The pair codes are formed once per slot (cvs_slot32.cuh).  The decision is
+// bit-sliced over the sets: a shared table maps a channel's code difference
+// |d| (0..255, 256 = out of range) to two 16-bit masks, the sets that call the
+// channel high and those that call it low, so a slot costs three table reads
+// whatever the number of sets.  Per lane, passes are counted in bytes (four
+// sets per word), patterns are OR-ed into one set mask per pattern, and the
+// sets passing at each radius are OR-ed per warp into a shared per-radius mask
+// from which the largest passing radius is read at the end of the item.
+// Flagged slots are marked in a per-lane bitmap and decided after each
+// segment: bounds once, every set from them, FP64 codes when some set stays
+// open.
 #include <cuda_runtime.h>
 
 #include "cvs_device.cuh"
@@ -11,98 +23,176 @@ namespace cvs {
 
 namespace {
 
-// ------------------------------------------------------------ multi-threshold search
-// The paper's experiment (§3 Experiments, Table 1): every candidate decided
-// against n_thr threshold sets in one pass.  The pair chain runs once per slot;
-// each set has its own classification table; per set the warp's passes are
-// reduced with ballot / REDUX and lane s keeps set s's running totals.
-template <int PREC, bool FAST, bool CLIP>
-__device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s, const float4* sc4s,
-                                           const uint8_t* luts, int64_t t, int k0, int k1,
-                                           const ChainF32& C, uint32_t* pq, uint32_t* rq_kh,
-                                           unsigned long long& n_flag, unsigned long long& n_re) {
+constexpr int kMultiWords = 7;                  // flag words per lane per segment
+constexpr int kMultiSegIters = 32 * kMultiWords;  // < 256: byte counters cannot overflow
+constexpr int kMultiMaxChunk = 256;             // radii per work item (per-radius masks)
+
+// Table entry of |d| = i: bit s set if set s calls the channel high (i >= hi_min[s]),
+// bit 16 + s if it calls it low (i <= lo_max[s]); i = 256 stands for out of range.
+__device__ __forceinline__ void build_set_table(uint32_t* ts, const MultiArgs& A) {
+    for (int i = threadIdx.x; i < 257; i += blockDim.x) {
+        uint32_t e = 0;
+        for (int s = 0; s < A.n_thr; ++s) {
+            if (i <= 255 && i >= A.hi_min[s]) e |= 1u << s;
+            if (i <= A.lo_max[s]) e |= 1u << (16 + s);
+        }
+        ts[i] = e;
+    }
+}
+
+__device__ __forceinline__ uint32_t fold16(uint32_t x) { return (x | (x >> 16)) & 0xFFFFu; }
+
+// Sets passing with channel table entries e[3] (high planes in the low half);
+// hR/hG/hB receive the passing sets' high planes.  in_range: all codes in 0..255.
+template <bool ALLMASK>
+__device__ __forceinline__ uint32_t pass_sets(const uint32_t e[3], bool in_range, uint32_t setmask,
+                                              const uint32_t* pmask_sets, uint32_t& hR,
+                                              uint32_t& hG, uint32_t& hB) {
+    const uint32_t valid = fold16(e[0]) & fold16(e[1]) & fold16(e[2]);
+    uint32_t ok = valid & (e[0] | e[1] | e[2]) & setmask & (in_range ? 0xFFFFu : 0u);
+    hR = e[0] & ok;
+    hG = e[1] & ok;
+    hB = e[2] & ok;
+    if (!ALLMASK) {  // sets whose mask disallows the slot's pattern fail
+        // with the planes masked by ok, a pattern's minterm is empty outside ok
+        // (every pattern 1..7 has a high channel)
+        uint32_t allowed = 0;
+        allowed |= (~hR & ~hG & hB) & pmask_sets[1];
+        allowed |= (~hR & hG & ~hB) & pmask_sets[2];
+        allowed |= (~hR & hG & hB) & pmask_sets[3];
+        allowed |= (hR & ~hG & ~hB) & pmask_sets[4];
+        allowed |= (hR & ~hG & hB) & pmask_sets[5];
+        allowed |= (hR & hG & ~hB) & pmask_sets[6];
+        allowed |= (hR & hG & hB) & pmask_sets[7];
+        ok = allowed;
+        hR &= ok;
+        hG &= ok;
+        hB &= ok;
+    }
+    return ok;
+}
+
+// Per-lane tallies of one work item.
+struct MultiTally {
+    uint32_t c4[4];  // pass counts, byte b of word j = set 4 j + b
+    uint32_t pm[8];  // pm[p]: sets with a pass of pattern p
+    uint32_t cnt;    // lane s: set s's count so far (flushed bytes)
+};
+
+__device__ __forceinline__ void tally_patterns(MultiTally& m, uint32_t hR, uint32_t hG,
+                                               uint32_t hB) {
+    m.pm[1] |= ~hR & ~hG & hB;
+    m.pm[2] |= ~hR & hG & ~hB;
+    m.pm[3] |= ~hR & hG & hB;
+    m.pm[4] |= hR & ~hG & ~hB;
+    m.pm[5] |= hR & ~hG & hB;
+    m.pm[6] |= hR & hG & ~hB;
+    m.pm[7] |= hR & hG & hB;
+}
+
+__device__ __forceinline__ void tally_counts(MultiTally& m, uint32_t ok, int nw) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (j < nw) m.c4[j] += (((ok >> (4 * j)) & 15u) * 0x00204081u) & 0x01010101u;
+}
+
+// Byte counters -> lane s's 32-bit count of set s.
+__device__ __forceinline__ void flush_counts(MultiTally& m, int NT) {
+    const unsigned lane = lane_id();
+    for (int s = 0; s < NT; ++s) {
+        const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, (m.c4[s >> 2] >> (8 * (s & 3))) & 255u);
+        if ((int)lane == s) m.cnt += v;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) m.c4[j] = 0;
+}
+
+// Exact decision of one flagged slot against every set; passes go straight to
+// the accumulators (rare).
+template <int PREC, bool FAST, bool CLIP, bool ALLMASK>
+__device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* r2s,
+                                              const float4* sc4s, const uint32_t* ts,
+                                              const TargetF32& T, const ChainF32& C,
+                                              const TargetF64& D, int64_t t, int k, int h,
+                                              uint32_t setmask, unsigned long long& n_re) {
+    const int NT = A.n_thr;
+    const Intervals I = intervals32<FAST>(T, C, r2s[k], sc4s[h], A.half_w, CLIP ? 1 : 0);
+    bool certain_out = false, maybe_out = false;
+    if (!CLIP) {
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            certain_out |= I.hi[j] < 0 || I.lo[j] > 255;
+            maybe_out |= I.lo[j] < 0 || I.hi[j] > 255;
+        }
+    }
+    if (certain_out) return;
+    uint32_t e[3], unstable = 0, cinv = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int dmax = max(I.hi[c] - I.lo[3 + c], I.hi[3 + c] - I.lo[c]);
+        const int dmin = max(0, max(I.lo[c] - I.hi[3 + c], I.lo[3 + c] - I.hi[c]));
+        const uint32_t eL = ts[min(dmin, 256)], eH = ts[min(dmax, 256)];
+        const uint32_t stable = ~fold16(eL ^ eH) & 0xFFFFu;
+        cinv |= stable & ~fold16(eL);  // certainly neither high nor low: the set fails
+        unstable |= ~stable;
+        e[c] = eL;
+    }
+    uint32_t open = (maybe_out ? 0xFFFFu : unstable) & ~cinv & setmask;
+    uint32_t hR, hG, hB, ok;
+    if (open) {  // some set's decision depends on a code the bounds leave open: FP64
+        int qp[3], qm[3];
+        pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + k), __ldg(A.grid.s64 + h),
+                     __ldg(A.grid.c64 + h), A.qkey, qp, qm);
+        bool in_range = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (CLIP) {
+                qp[c] = min(max(qp[c], 0), 255);
+                qm[c] = min(max(qm[c], 0), 255);
+            }
+            in_range = in_range && qp[c] >= 0 && qp[c] <= 255 && qm[c] >= 0 && qm[c] <= 255;
+            e[c] = ts[min(abs(qp[c] - qm[c]), 256)];
+        }
+        ok = pass_sets<ALLMASK>(e, in_range, setmask, A.pmask_sets, hR, hG, hB);
+        ++n_re;
+    } else {
+        ok = pass_sets<ALLMASK>(e, true, setmask & ~cinv, A.pmask_sets, hR, hG, hB);
+    }
+    if (!ok) return;
+    const int inc = A.grid.sym ? 2 : 1;
+    const int r_bits = __float_as_int(r2s[k].x);
+    for (int s = 0; s < NT; ++s) {
+        if (!((ok >> s) & 1u)) continue;
+        const int p = (int)((((hR >> s) & 1u) << 2) | (((hG >> s) & 1u) << 1) | ((hB >> s) & 1u));
+        Acc* ac = A.acc + t * NT + s;
+        atomicAdd(&ac->count, inc);
+        atomicMax(&ac->rmax_bits, r_bits);
+        atomicOr(&ac->pmask, 1u << (p - 1));
+    }
+}
+
+// One work item: target t, radii [k0, k1) (k1 - k0 <= kMultiMaxChunk).
+template <int PREC, bool FAST, bool CLIP, bool ALLMASK>
+__device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s,
+                                           const float4* sc4s, const uint32_t* ts, uint32_t* fb,
+                                           uint32_t* okr, const TargetF32& T, const ChainF32& C,
+                                           const PairsC& PC, int64_t t, int k0, int k1,
+                                           unsigned long long& n_flag,
+                                           unsigned long long& n_re) {
     const unsigned lane = lane_id();
     const int H = A.grid.H, NT = A.n_thr;
     const int inc = A.grid.sym ? 2 : 1;
     const int nslots = (k1 - k0) * H;
-    TargetF32 T;
-    TargetF64 D;
-    if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
-    else D = A.td[t];
+    const uint32_t setmask = (1u << NT) - 1u;
+    const int nw = (NT + 3) >> 2;
+    const TargetF64 D = A.td[t];
     const PairsT P = make_pairs(T);
-    const PairsC PC = make_pairs(C);
-    int cnt = 0;
-    uint32_t rbits = 0, pm = 0;  // set `lane`'s totals (lanes < NT)
-    int pq_n = 0;
-    // one warp-wide merge of per-lane patterns of set s into lane s's totals
-    auto merge = [&](int s, int pattern, float r) {
-        const bool pass = pattern > 0;
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, pass);
-        if (ball) {
-            const uint32_t pmw = __reduce_or_sync(0xFFFFFFFFu, pass ? (1u << pattern) : 0u);
-            const uint32_t rmw = __reduce_max_sync(0xFFFFFFFFu, pass ? __float_as_uint(r) : 0u);
-            if ((int)lane == s) {
-                cnt += __popc(ball) * inc;
-                pm |= pmw;
-                rbits = max(rbits, rmw);
-            }
-        }
-    };
-    // flagged slots: bounds once, then every set; FP64 when some set is undecided
-    auto drain = [&](int n) {
-        int k = 0, h = 0;
-        Intervals I{};
-        float r = 0.0f;
-        const bool mine = (int)lane < n;
-        if (mine) {
-            const uint32_t kh = pq[lane];
-            k = (int)(kh & 0xFFFFu);
-            h = (int)(kh >> 16);
-            r = r2s[k].x;
-            const float4 sc = sc4s[h];
-            I = intervals32<FAST>(T, C, r2s[k], sc, A.half_w, CLIP ? 1 : 0);
-        }
-        bool need64 = false;
-        for (int s = 0; s < NT; ++s) {
-            const int pc = mine ? certain_from(I, A.hi_min[s], A.lo_max[s], A.mask2[s], CLIP ? 1 : 0, 0)
-                                : 0;
-            need64 |= pc < 0;
-            merge(s, pc < 0 ? 0 : pc, r);
-        }
-        // slots with an undecided set: exact FP64 codes, every set decided from them
-        // (the sets decided above are decided again identically, so count only here)
-        const unsigned b64 = __ballot_sync(0xFFFFFFFFu, need64);
-        if (b64) {
-            int qp[3] = {0, 0, 0}, qm[3] = {0, 0, 0};
-            if (need64) {
-                const double rr = __ldg(A.grid.r64 + k), ss = __ldg(A.grid.s64 + h),
-                             cc = __ldg(A.grid.c64 + h);
-                const TargetF64 DD = A.td[t];
-                pair_codes64(DD.L, DD.a, DD.b, rr, ss, cc, A.qkey, qp, qm);
-                if (CLIP) {
+    MultiTally m;
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        qp[i] = min(max(qp[i], 0), 255);
-                        qm[i] = min(max(qm[i], 0), 255);
-                    }
-                }
-                ++n_re;
-            }
-            for (int s = 0; s < NT; ++s) {
-                int pat = 0;
-                if (need64) {
-                    const int pc = certain_from(I, A.hi_min[s], A.lo_max[s], A.mask2[s],
-                                                CLIP ? 1 : 0, 0);
-                    if (pc < 0) {  // undecided in FP32: the FP64 decision counts now
-                        Decide dc{A.hi_min[s], A.lo_max[s], A.mask2[s], CLIP ? 1 : 0};
-                        pat = decide_codes(qp, qm, dc);
-                    }
-                }
-                merge(s, pat, r);
-            }
-        }
-        __syncwarp();
-    };
+    for (int j = 0; j < 4; ++j) m.c4[j] = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) m.pm[p] = 0;
+    m.cnt = 0;
     const int q32 = 32 / H, r32 = 32 - q32 * H;
     int k = k0 + (int)lane / H, h = (int)lane % H;
     const int nit = (nslots + 31) >> 5;
@@ -120,103 +210,152 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
             h = i - dk * H;
         }
     }
-    for (int it = it0; it < nit; ++it) {
-        const bool active = it * 32 + (int)lane < nslots;
-        const int kk = active ? k : k0, hh = active ? h : 0;
-        const float2 r2 = r2s[kk];
-        int yp[3], ym[3], qp[3], qm[3];
-        bool flag = false;
-        if (PREC == CVS_PREC_FP32_RECHECK) {
-            const float4 sc = sc4s[hh];
-            const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y)), w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
-            float2 lin[3];
-            lin32<FAST>(P, PC, u2, w2, lin);
-            // gamut reject: a warp whose pairs all leave the gamut passes no set
-            if (!CLIP && __all_sync(0xFFFFFFFFu, !active || surely_out32(lin))) {
+    for (int seg0 = it0; seg0 < nit; seg0 += kMultiSegIters) {
+        const int seg1 = min(seg0 + kMultiSegIters, nit);
+        for (int w = 0, it = seg0; it < seg1; ++w) {
+            uint32_t bits = 0;
+            const int wend = min(seg1, it + 32);
+            for (uint32_t bit = 1u; it < wend; ++it, bit <<= 1) {
+                const bool active = it * 32 + (int)lane < nslots;
+                const int kq = active ? k : k0, hq = active ? h : 0;
+                uint32_t ok = 0, hR = 0, hG = 0, hB = 0;
+                bool skip = false;
+                if (PREC == CVS_PREC_FP32_RECHECK) {
+                    const float2 r2 = r2s[kq];
+                    const float4 sc = sc4s[hq];
+                    const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));
+                    const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
+                    float2 lin[3];
+                    lin32<FAST>(P, PC, u2, w2, lin);
+                    // gamut reject: a warp whose pairs all leave the gamut passes no set
+                    skip = !CLIP && __all_sync(0xFFFFFFFFu, !active || surely_out32(lin));
+                    if (!skip) {
+                        int yp[3], ym[3];
+                        bool flag;
+                        if (it < it_pow) flag = encode32<false>(lin, A.half_w, yp, ym, nullptr);
+                        else flag = encode32<true>(lin, A.half_w, yp, ym, nullptr);
+                        flag = flag && active;
+                        if (flag) bits |= bit;
+                        uint32_t e[3];
+                        uint32_t o = 0;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            int a = yp[c] - kMagicBits, b = ym[c] - kMagicBits;
+                            if (CLIP) {
+                                a = min(max(a, 0), 255);
+                                b = min(max(b, 0), 255);
+                            }
+                            o |= (uint32_t)a | (uint32_t)b;
+                            e[c] = ts[min(abs(a - b), 256)];
+                        }
+                        if (active && !flag)
+                            ok = pass_sets<ALLMASK>(e, o <= 255u, setmask, A.pmask_sets, hR, hG, hB);
+                    }
+                } else if (active) {
+                    int qp[3], qm[3];
+                    pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + kq), __ldg(A.grid.s64 + hq),
+                                 __ldg(A.grid.c64 + hq), A.qkey, qp, qm);
+                    uint32_t e[3];
+                    bool in_range = true;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        if (CLIP) {
+                            qp[c] = min(max(qp[c], 0), 255);
+                            qm[c] = min(max(qm[c], 0), 255);
+                        }
+                        in_range = in_range && qp[c] >= 0 && qp[c] <= 255 && qm[c] >= 0 &&
+                                   qm[c] <= 255;
+                        e[c] = ts[min(abs(qp[c] - qm[c]), 256)];
+                    }
+                    ok = pass_sets<ALLMASK>(e, in_range, setmask, A.pmask_sets, hR, hG, hB);
+                }
+                if (!skip) {
+                    tally_counts(m, ok, nw);
+                    tally_patterns(m, hR, hG, hB);
+                    // sets passing at each radius of the iteration, OR-ed per warp
+                    const int ka = __shfl_sync(0xFFFFFFFFu, kq, 0);
+                    const int kb = __reduce_max_sync(0xFFFFFFFFu, (unsigned)kq);
+                    for (int kr = ka; kr <= kb; ++kr) {
+                        const uint32_t mk = __reduce_or_sync(0xFFFFFFFFu, kq == kr ? ok : 0u);
+                        if (lane == 0 && mk) okr[kr - k0] |= mk;
+                    }
+                }
                 h += r32;
                 k += q32;
                 const bool wrap = h >= H;
                 h = wrap ? h - H : h;
                 k = wrap ? k + 1 : k;
-                continue;
             }
-            if (it < it_pow) flag = encode32<false>(lin, A.half_w, yp, ym, nullptr);
-            else flag = encode32<true>(lin, A.half_w, yp, ym, nullptr);
-            flag = flag && active;
-        } else if (active) {
-            pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + kk), __ldg(A.grid.s64 + hh),
-                         __ldg(A.grid.c64 + hh), A.qkey, qp, qm);
-            if (CLIP) {
+            if (PREC == CVS_PREC_FP32_RECHECK) fb[w * 32 + lane] = bits;
+        }
+        flush_counts(m, NT);
+        if (PREC == CVS_PREC_FP32_RECHECK) {  // the segment's flagged slots
+            __syncwarp();
+            const int nwords = (seg1 - seg0 + 31) >> 5;
+            for (int w = 0; w < nwords; ++w) {
+                uint32_t bits = fb[w * 32 + lane];
+                while (__any_sync(0xFFFFFFFFu, bits != 0u)) {
+                    if (bits) {
+                        const int j = __ffs(bits) - 1;
+                        bits &= bits - 1u;
+                        const int i = (seg0 + 32 * w + j) * 32 + (int)lane;
+                        const int dk = i / H;
+                        ++n_flag;
+                        multi_flagged<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t,
+                                                                 k0 + dk, i - dk * H, setmask,
+                                                                 n_re);
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // item totals: lane s publishes set s
+    uint32_t pmask = 0;
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    qp[i] = min(max(qp[i], 0), 255);
-                    qm[i] = min(max(qm[i], 0), 255);
-                }
-            }
-        }
-        for (int s = 0; s < NT; ++s) {
-            int pattern = 0;
-            if (PREC == CVS_PREC_FP32_RECHECK) {
-                pattern = decide32<CLIP>(yp, ym, luts + s * 3 * 512, A.mask2[s]);
-                if (flag || !active) pattern = 0;
-            } else if (active) {
-                Decide dc{A.hi_min[s], A.lo_max[s], A.mask2[s], CLIP ? 1 : 0};
-                pattern = decide_codes(qp, qm, dc);
-            }
-            merge(s, pattern, r2.x);
-        }
-        if (PREC == CVS_PREC_FP32_RECHECK) {
-            const unsigned fball = __ballot_sync(0xFFFFFFFFu, flag);
-            if (fball) {
-                if (flag) {
-                    pq[pq_n + __popc(fball & ((1u << lane) - 1u))] = (uint32_t)kk | ((uint32_t)hh << 16);
-                    ++n_flag;
-                }
-                pq_n += __popc(fball);
-                __syncwarp();
-                if (pq_n >= 32) {
-                    drain(32);
-                    const int rest = pq_n - 32;
-                    const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
-                    __syncwarp();
-                    if ((int)lane < rest) pq[lane] = mv;
-                    __syncwarp();
-                    pq_n = rest;
-                }
-            }
-        }
-        h += r32;
-        k += q32;
-        const bool wrap = h >= H;
-        h = wrap ? h - H : h;
-        k = wrap ? k + 1 : k;
+    for (int p = 1; p <= 7; ++p) {
+        const uint32_t wp = __reduce_or_sync(0xFFFFFFFFu, m.pm[p]);
+        if ((wp >> lane) & 1u) pmask |= 1u << (p - 1);
     }
-    if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0) drain(pq_n);
-    if ((int)lane < NT && cnt) {
+    // largest passing radius per set from the per-radius masks
+    int rbits_mine = __float_as_int(-1.0f);
+    for (int s = 0; s < NT; ++s) {
+        float rm = -1.0f;
+        for (int kr = k0 + (int)lane; kr < k1; kr += 32)
+            if ((okr[kr - k0] >> s) & 1u) rm = fmaxf(rm, r2s[kr].x);
+        const int b = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)__float_as_int(fmaxf(rm, 0.0f)));
+        const bool any = __any_sync(0xFFFFFFFFu, rm >= 0.0f);
+        if ((int)lane == s && any) rbits_mine = b;
+    }
+    for (int kr = k0 + (int)lane; kr < k1; kr += 32) okr[kr - k0] = 0u;
+    __syncwarp();
+    if ((int)lane < NT && m.cnt) {
         Acc* ac = A.acc + t * NT + lane;
-        atomicAdd(&ac->count, cnt);
-        atomicMax(&ac->rmax_bits, (int)rbits);
-        atomicOr(&ac->pmask, pm >> 1);
+        atomicAdd(&ac->count, (int)m.cnt * inc);
+        atomicMax(&ac->rmax_bits, rbits_mine);
+        atomicOr(&ac->pmask, pmask);
     }
-    (void)rq_kh;
 }
 
-template <int PREC, bool CLIP>
+template <int PREC, bool CLIP, bool ALLMASK>
 __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int K = A.grid.K, H = A.grid.H, NT = A.n_thr;
+    const int K = A.grid.K, H = A.grid.H;
     float2* r2s = reinterpret_cast<float2*>(smem);
     float4* sc4s = reinterpret_cast<float4*>(smem + ((K * 8 + 15) & ~15));
-    uint8_t* luts = smem + ((K * 8 + 15) & ~15) + H * 16;
-    uint32_t* pq_all = reinterpret_cast<uint32_t*>(luts + ((NT * 3 * 512 + 15) & ~15));
+    uint32_t* ts = reinterpret_cast<uint32_t*>(smem + ((K * 8 + 15) & ~15) + H * 16);
+    uint32_t* per_warp = ts + 260;  // 257 table entries, padded to 16 bytes
     const int warp = threadIdx.x >> 5;
-    uint32_t* pq = pq_all + warp * kRqCap;
-    for (int s2 = 0; s2 < NT; ++s2) build_decide_lut(luts + s2 * 3 * 512, A.hi_min[s2], A.lo_max[s2]);
+    uint32_t* fb = per_warp + warp * (kMultiWords * 32 + kMultiMaxChunk);
+    uint32_t* okr = fb + kMultiWords * 32;
+    build_set_table(ts, A);
     for (int i = threadIdx.x; i < K; i += blockDim.x) r2s[i] = dup(A.grid.r32[i]);
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
         const float2 sc = A.grid.sc32[i];
         sc4s[i] = make_float4(sc.x, -sc.x, sc.y, -sc.y);
     }
+    const unsigned lane = lane_id();
+    for (int i = (int)lane; i < kMultiWords * 32 + kMultiMaxChunk; i += 32) fb[i] = 0u;
     __syncthreads();
     ChainF32 C;
 #pragma unroll
@@ -224,11 +363,11 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
         C.Ax[c] = __double2float_rn(__dmul_rn(c_MI[3 * c], c_W[0]));
         C.Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
     }
+    const PairsC PC = make_pairs(C);
     unsigned long long n_flag = 0, n_re = 0;
     const int kchunk = A.kchunk;
     const int n_kc = (K + kchunk - 1) / kchunk;
     const unsigned long long n_items = (unsigned long long)A.n_targets * n_kc;
-    const unsigned lane = lane_id();
     while (true) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(A.work_counter, 1ull);
@@ -237,14 +376,14 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
         const int64_t t = (int64_t)(item / (unsigned long long)n_kc);
         const int kc = (int)(item - (unsigned long long)t * n_kc);
         const int k0 = kc * kchunk, k1 = min(k0 + kchunk, K);
-        if (PREC == CVS_PREC_FP32_RECHECK) {
-            if (A.tf[t].flags & 1u)
-                multi_item<PREC, true, CLIP>(A, r2s, sc4s, luts, t, k0, k1, C, pq, nullptr, n_flag, n_re);
-            else
-                multi_item<PREC, false, CLIP>(A, r2s, sc4s, luts, t, k0, k1, C, pq, nullptr, n_flag, n_re);
-        } else {
-            multi_item<PREC, true, CLIP>(A, r2s, sc4s, luts, t, k0, k1, C, pq, nullptr, n_flag, n_re);
-        }
+        TargetF32 T{};
+        if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
+        if (PREC == CVS_PREC_FP32_RECHECK && (T.flags & 1u))
+            multi_item<PREC, true, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, okr, T, C, PC, t, k0, k1,
+                                                  n_flag, n_re);
+        else
+            multi_item<PREC, false, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, okr, T, C, PC, t, k0, k1,
+                                                   n_flag, n_re);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -268,34 +407,44 @@ __global__ void k_init_acc(Acc* __restrict__ acc, int64_t n) {
     acc[i] = z;
 }
 
-}  // namespace
-
-int multi_smem_bytes(const GridDev& g, int n_thr, int block) {
-    return ((g.K * 8 + 15) & ~15) + g.H * 16 + ((n_thr * 3 * 512 + 15) & ~15) +
-           (block / 32) * kRqCap * 4;
+int multi_smem_bytes(const GridDev& g, int block) {
+    return ((g.K * 8 + 15) & ~15) + g.H * 16 + 260 * 4 +
+           (block / 32) * (kMultiWords * 32 + kMultiMaxChunk) * 4;
 }
 
-template <int PREC, bool CLIP>
-cudaError_t launch_multi_t(const MultiArgs& a, int block, cudaStream_t st) {
-    const int smem = multi_smem_bytes(a.grid, a.n_thr, block);
-    const void* fn = (const void*)k_search_multi<PREC, CLIP>;
+template <int PREC, bool CLIP, bool ALLMASK>
+cudaError_t launch_multi_t(const MultiArgs& a, cudaStream_t st) {
+    const int block = kSearchBlock;
+    const int smem = multi_smem_bytes(a.grid, block);
+    const void* fn = (const void*)k_search_multi<PREC, CLIP, ALLMASK>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    k_search_multi<PREC, CLIP><<<a.num_sms * per_sm, block, smem, st>>>(a);
+    k_search_multi<PREC, CLIP, ALLMASK><<<a.num_sms * per_sm, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+template <int PREC>
+cudaError_t launch_multi_p(const MultiArgs& a, cudaStream_t st) {
+    if (a.clip)
+        return a.all_patterns ? launch_multi_t<PREC, true, true>(a, st)
+                              : launch_multi_t<PREC, true, false>(a, st);
+    return a.all_patterns ? launch_multi_t<PREC, false, true>(a, st)
+                          : launch_multi_t<PREC, false, false>(a, st);
+}
+
+}  // namespace
+
+int multi_max_chunk() { return kMultiMaxChunk; }
+
 cudaError_t launch_search_multi(const MultiArgs& a, cudaStream_t st) {
-    const int block = kSearchBlock;
-    if (a.prec == CVS_PREC_FP64)
-        return a.clip ? launch_multi_t<CVS_PREC_FP64, true>(a, block, st)
-                      : launch_multi_t<CVS_PREC_FP64, false>(a, block, st);
-    return a.clip ? launch_multi_t<CVS_PREC_FP32_RECHECK, true>(a, block, st)
-                  : launch_multi_t<CVS_PREC_FP32_RECHECK, false>(a, block, st);
+    if (a.kchunk < 1 || a.kchunk > kMultiMaxChunk || a.n_thr < 1 || a.n_thr > kMaxThresholdSets)
+        return cudaErrorInvalidValue;
+    return a.prec == CVS_PREC_FP64 ? launch_multi_p<CVS_PREC_FP64>(a, st)
+                                   : launch_multi_p<CVS_PREC_FP32_RECHECK>(a, st);
 }
 
 cudaError_t launch_init_acc(Acc* acc, int64_t n, cudaStream_t st) {
