@@ -70,6 +70,9 @@ def parse_args():
                    help="colours of the cube timed on the CPU oracle")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the precision study and the one-pass image measurement")
+    p.add_argument("--gather-profile", action="store_true",
+                   help="only the table gathers (one 3840x2160 frame through the embedding "
+                        "table, four images through the capacity table), for profiling")
     p.add_argument("--cube-step", type=int, default=4, choices=[4, 8, 16],
                    help="channel step of the colour cube (4 = the 262,144-colour workload; "
                         "larger steps give the small cases used for profiling)")
@@ -354,9 +357,12 @@ def run_extras(ctx, torch, device, W, cvs):
         t1.record()
         torch.cuda.synchronize(device)
         sec = t0.elapsed_time(t1) / 1e3 / reps
+        # per pixel: colour 3 + pattern 1 + frames 6 + choice 4 bytes, plus the
+        # table entry's 10 bytes (codes 6, choice 4) where a pattern is requested
+        alg_bytes = w * h * 14 + int((pat > 0).sum().item()) * 10
         via[f"{w}x{h}"] = {"seconds": sec, "frames_per_s": 1.0 / sec,
                            "identical_to_direct": same,
-                           "gb_s": w * h * 22 / sec / 1e9}
+                           "algorithmic_bytes": alg_bytes, "gb_s": alg_bytes / sec / 1e9}
         del img, pat, d, g
     etab.close()
     out["embedding_via_table"] = via
@@ -654,8 +660,56 @@ def run_ours(args, world, rank, local):
     ctx.close()
 
 
+def run_gather_profile(args):
+    """The HBM-bound table gathers on their own: build the embedding table and
+    the capacity table (64 radii x 180 angles), then gather one 3840x2160 frame
+    and four 1920x1080 images `args.steps` times each.  Prints one JSON line
+    with the achieved bandwidth per gather (algorithmic bytes / time)."""
+    import torch
+    import paper_2507_22901_gb300 as cvs
+    from paper_2507_22901_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    ctx = cvs.Context(0)
+    r3, a3 = W.grid(3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    terms = W.image_params(1, seed=21, sizes=[(3840, 2160)])[0][2]
+    img = W.render_image_torch(3840, 2160, terms, 21, device=dev)
+    pat = torch.from_numpy(W.code_pattern(2160, 3840, module=16, seed=21)).to(dev)
+    etab = ctx.build_embed_table(r3, a3, 50.0, 0.5)
+    fa, fb, ch = etab.embed_image(img, pat)
+    torch.cuda.synchronize(dev)
+    ev0.record()
+    for _ in range(args.steps):
+        etab.embed_image(img, pat, frames=(fa, fb))
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    t_emb = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    etab.close()
+    lut = ctx.build_lut(r3, a3, 50.0, 0.5)
+    imgs = [W.render_image_torch(1920, 1080, W.image_params(1, seed=30 + i, sizes=[(1920, 1080)])[0][2],
+                                 30 + i, device=dev) for i in range(4)]
+    maps = lut.lookup_images(imgs)
+    torch.cuda.synchronize(dev)
+    ev0.record()
+    for _ in range(args.steps):
+        lut.lookup_images(imgs, maps=maps)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    t_lut = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    lut.close()
+    px4k, pxl = 3840 * 2160, 4 * 1920 * 1080
+    emb_bytes = px4k * 14 + int((pat > 0).sum().item()) * 10  # see embedding_via_table
+    print(json.dumps({
+        "k_etab_gather": {"pixels": px4k, "seconds": t_emb, "algorithmic_bytes": emb_bytes,
+                          "gb_s": emb_bytes / t_emb / 1e9},
+        "k_lut_gather_images": {"pixels": pxl, "seconds": t_lut, "bytes_per_pixel": 21,
+                                "gb_s": pxl * 21 / t_lut / 1e9}}))
+
+
 def main():
     args = parse_args()
+    if args.gather_profile:
+        return run_gather_profile(args)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

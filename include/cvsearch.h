@@ -269,7 +269,7 @@ cvs_status cvs_embed_image(cvs_ctx* ctx, const cvs_image* img, const uint8_t* pa
  * order, first hit per pattern).  Afterwards the frames of any image are a
  * gather from the table, identical to cvs_embed_image's on the same grid,
  * thresholds and precision.  The table lives on the context's device
- * (2^24 x 7 x 12 bytes = 1.41 GB); the build is synchronous. */
+ * (2^24 x 7 entries of 16 bytes = 1.88 GB); the build is synchronous. */
 typedef struct cvs_etab cvs_etab;
 
 cvs_status cvs_etab_build(cvs_ctx* ctx, const cvs_grid* grid, const cvs_thresholds* thr,

@@ -1133,8 +1133,7 @@ cvs_status cvs_lut_lookup_images(cvs_lut* L, const cvs_image* batch, int32_t n,
 
 struct cvs_etab {
     int device = 0;
-    uint32_t* choice = nullptr;  // 2^24 x 7: k | m << 16, or 0xFFFFFFFF
-    uint64_t* codes = nullptr;   // 2^24 x 7: plus R,G,B and minus R,G,B in bytes 0..5
+    uint4* entry = nullptr;  // 2^24 x 7 entries of 16 bytes (codes and choice)
 };
 
 extern "C" {
@@ -1157,11 +1156,13 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
     cvs_etab* E = new cvs_etab();
     E->device = c->device;
     uint8_t* rgb = nullptr;
-    cudaError_t e = cudaMalloc(&E->choice, sizeof(uint32_t) * 7 * kColours);
-    if (e == cudaSuccess) e = cudaMalloc(&E->codes, sizeof(uint64_t) * 7 * kColours);
+    uint32_t* keys = nullptr;  // one chunk's first-hit keys
+    cudaError_t e = cudaMalloc(&E->entry, sizeof(uint4) * 7 * kColours);
+    if (e == cudaSuccess) e = cudaMalloc(&keys, sizeof(uint32_t) * 7 * kChunk);
     if (e == cudaSuccess) e = cudaMalloc(&rgb, 3 * kChunk);
     if (e != cudaSuccess) {
         if (rgb) cudaFree(rgb);
+        if (keys) cudaFree(keys);
         cvs_etab_destroy(E);
         return fail(e == cudaErrorMemoryAllocation ? CVS_ERR_NO_MEMORY : CVS_ERR_CUDA,
                     "cvs_etab_build: %s", cudaGetErrorString(e));
@@ -1187,7 +1188,7 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
     e = cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev0, st);
     for (int64_t first = 0; first < kColours && e == cudaSuccess; first += kChunk) {
-        a.key = E->choice + 7 * first;
+        a.key = keys;
         e = launch_rgb_iota(rgb, first, kChunk, st);
         if (e == cudaSuccess)
             e = launch_setup_colors(rgb, kChunk, c->grid.rmax, c->tf, c->td, c->acc, st);
@@ -1195,15 +1196,16 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
             e = cudaMemsetAsync(a.key, 0xFF, sizeof(uint32_t) * 7 * kChunk, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long), st);
         if (e == cudaSuccess) e = launch_first_hits(a, st);
-        if (e == cudaSuccess) e = launch_first_finalize(a, a.key, E->codes + 7 * first, st);
+        if (e == cudaSuccess) e = launch_first_finalize(a, keys, E->entry + 7 * first, st);
     }
     if (e == cudaSuccess) e = cudaEventRecord(c->ev1, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->h_counters, c->counters, kNumCounters * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, st);
-    // the colour buffer is released once the stream has consumed it
+    // the scratch buffers are released once the stream has consumed them
     cudaError_t se = cudaStreamSynchronize(st);
     cudaFree(rgb);
+    cudaFree(keys);
     if (e == cudaSuccess) e = se;
     if (e != cudaSuccess) {
         cvs_etab_destroy(E);
@@ -1225,8 +1227,7 @@ void cvs_etab_destroy(cvs_etab* E) {
     if (!E) return;
     cudaSetDevice(E->device);
     cudaDeviceSynchronize();
-    if (E->choice) cudaFree(E->choice);
-    if (E->codes) cudaFree(E->codes);
+    if (E->entry) cudaFree(E->entry);
     delete E;
 }
 
@@ -1243,9 +1244,9 @@ cvs_status cvs_etab_embed_image(cvs_etab* E, const cvs_image* img, const uint8_t
     if ((int64_t)img->width * img->height >= ((int64_t)1 << 40))
         return fail(CVS_ERR_INVALID_ARG, "image too large");
     CVS_CUDA(cudaSetDevice(E->device));
-    CVS_CUDA(launch_etab_gather(E->choice, E->codes, img->rgb, img->pitch_bytes, img->width,
-                                img->height, pattern_dev, pattern_pitch, frame_a_dev, frame_b_dev,
-                                frame_pitch, choice_dev, (cudaStream_t)stream));
+    CVS_CUDA(launch_etab_gather(E->entry, img->rgb, img->pitch_bytes, img->width, img->height,
+                                pattern_dev, pattern_pitch, frame_a_dev, frame_b_dev, frame_pitch,
+                                choice_dev, (cudaStream_t)stream));
     return CVS_OK;
 }
 

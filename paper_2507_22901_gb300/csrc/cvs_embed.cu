@@ -501,16 +501,17 @@ __global__ void __launch_bounds__(kSearchBlock) k_first_hits(const FirstHitArgs 
     }
 }
 
-// Keys -> choices (in place) and the exact codes of each first hit, packed as
-// plus R, G, B in bytes 0..2 and minus R, G, B in bytes 3..5.
+// Keys -> table entries of 16 bytes (one sector read per lookup):
+//   x = plus R | plus G << 8 | plus B << 16 | minus R << 24,
+//   y = minus G | minus B << 8,  z = choice k | m << 16 (0xFFFFFFFF: none),  w = 0.
 template <int PREC, bool CLIP>
-__global__ void k_first_finalize(const FirstHitArgs A, uint32_t* __restrict__ choice,
-                                 uint64_t* __restrict__ codes) {
+__global__ void k_first_finalize(const FirstHitArgs A, const uint32_t* __restrict__ keys,
+                                 uint4* __restrict__ entry) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= A.n_targets * 7) return;
-    const uint32_t key = choice[e];
+    const uint32_t key = keys[e];
     if (key == kNoChoice) {
-        codes[e] = 0;
+        entry[e] = make_uint4(0u, 0u, kNoChoice, 0u);
         return;
     }
     const int64_t t = e / 7;
@@ -560,43 +561,51 @@ __global__ void k_first_finalize(const FirstHitArgs A, uint32_t* __restrict__ ch
         v |= (uint64_t)(uint8_t)a << (8 * c);
         v |= (uint64_t)(uint8_t)b << (8 * (3 + c));
     }
-    codes[e] = v;
-    choice[e] = (uint32_t)k | ((uint32_t)h << 16);
+    entry[e] = make_uint4((uint32_t)v, (uint32_t)(v >> 32), (uint32_t)k | ((uint32_t)h << 16), 0u);
 }
 
-// Frames of one image from the table: one thread per pixel (grid-stride).
-__global__ void k_etab_gather(const uint32_t* __restrict__ choice,
-                              const uint64_t* __restrict__ codes, const uint8_t* __restrict__ rgb,
+// Frames of one image from the table: grid-stride over pixels, four pixels per
+// thread per step so that four table reads are in flight at once.
+__global__ void k_etab_gather(const uint4* __restrict__ entry, const uint8_t* __restrict__ rgb,
                               int64_t pitch, int32_t width, int64_t n,
                               const uint8_t* __restrict__ pattern, int64_t pattern_pitch,
                               uint8_t* __restrict__ frame_a, uint8_t* __restrict__ frame_b,
                               int64_t frame_pitch, uint32_t* __restrict__ choice_out) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t y = t / width, x = t - y * width;
-        const uint8_t* src = rgb + y * pitch + 3 * x;
-        const uint8_t r = src[0], g = src[1], b = src[2];
-        const int p = pattern[y * pattern_pitch + x];
-        uint8_t a0 = r, a1 = g, a2 = b, b0 = r, b1 = g, b2 = b;
-        uint32_t ch = kNoChoice;
-        if (p >= 1 && p <= 7) {
-            const int64_t e = (((int64_t)r << 16) | ((int64_t)g << 8) | b) * 7 + (p - 1);
-            ch = __ldg(choice + e);
-            if (ch != kNoChoice) {
-                const uint64_t v = __ldg(reinterpret_cast<const unsigned long long*>(codes) + e);
-                a0 = (uint8_t)v;
-                a1 = (uint8_t)(v >> 8);
-                a2 = (uint8_t)(v >> 16);
-                b0 = (uint8_t)(v >> 24);
-                b1 = (uint8_t)(v >> 32);
-                b2 = (uint8_t)(v >> 40);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; base < n;
+         base += 4 * stride) {
+        uint32_t src[4];
+        uint4 e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = base + u * stride;
+            e[u] = make_uint4(0u, 0u, kNoChoice, 0u);
+            src[u] = 0;
+            if (t < n) {
+                const int64_t y = t / width, x = t - y * width;
+                const uint8_t* px = rgb + y * pitch + 3 * x;
+                src[u] = (uint32_t)px[0] | ((uint32_t)px[1] << 8) | ((uint32_t)px[2] << 16);
+                const int p = pattern[y * pattern_pitch + x];
+                if (p >= 1 && p <= 7) {
+                    const int64_t c = ((int64_t)px[0] << 16) | ((int64_t)px[1] << 8) | px[2];
+                    e[u] = __ldg(entry + c * 7 + (p - 1));
+                }
             }
         }
-        uint8_t* fa = frame_a + y * frame_pitch + 3 * x;
-        uint8_t* fb = frame_b + y * frame_pitch + 3 * x;
-        fa[0] = a0; fa[1] = a1; fa[2] = a2;
-        fb[0] = b0; fb[1] = b1; fb[2] = b2;
-        if (choice_out) choice_out[t] = ch;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = base + u * stride;
+            if (t >= n) continue;
+            const int64_t y = t / width, x = t - y * width;
+            uint8_t* fa = frame_a + y * frame_pitch + 3 * x;
+            uint8_t* fb = frame_b + y * frame_pitch + 3 * x;
+            const bool hit = e[u].z != kNoChoice;
+            const uint32_t a = hit ? e[u].x : src[u];
+            const uint32_t b = hit ? ((e[u].x >> 24) | (e[u].y << 8)) : src[u];
+            fa[0] = (uint8_t)a; fa[1] = (uint8_t)(a >> 8); fa[2] = (uint8_t)(a >> 16);
+            fb[0] = (uint8_t)b; fb[1] = (uint8_t)(b >> 8); fb[2] = (uint8_t)(b >> 16);
+            if (choice_out) choice_out[t] = e[u].z;
+        }
     }
 }
 
@@ -645,36 +654,35 @@ cudaError_t launch_first_hits(const FirstHitArgs& a, cudaStream_t st) {
                   : launch_first_t<CVS_PREC_FP32_RECHECK, false>(a, st);
 }
 
-cudaError_t launch_first_finalize(const FirstHitArgs& a, uint32_t* choice, uint64_t* codes,
+cudaError_t launch_first_finalize(const FirstHitArgs& a, const uint32_t* keys, uint4* entry,
                                   cudaStream_t st) {
     const int64_t n = a.n_targets * 7;
     if (n <= 0) return cudaSuccess;
     const int blocks = (int)((n + 255) / 256);
     if (a.prec == CVS_PREC_FP64) {
-        if (a.clip) k_first_finalize<CVS_PREC_FP64, true><<<blocks, 256, 0, st>>>(a, choice, codes);
-        else k_first_finalize<CVS_PREC_FP64, false><<<blocks, 256, 0, st>>>(a, choice, codes);
+        if (a.clip) k_first_finalize<CVS_PREC_FP64, true><<<blocks, 256, 0, st>>>(a, keys, entry);
+        else k_first_finalize<CVS_PREC_FP64, false><<<blocks, 256, 0, st>>>(a, keys, entry);
     } else {
         if (a.clip)
-            k_first_finalize<CVS_PREC_FP32_RECHECK, true><<<blocks, 256, 0, st>>>(a, choice, codes);
+            k_first_finalize<CVS_PREC_FP32_RECHECK, true><<<blocks, 256, 0, st>>>(a, keys, entry);
         else
-            k_first_finalize<CVS_PREC_FP32_RECHECK, false><<<blocks, 256, 0, st>>>(a, choice, codes);
+            k_first_finalize<CVS_PREC_FP32_RECHECK, false><<<blocks, 256, 0, st>>>(a, keys, entry);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_etab_gather(const uint32_t* choice, const uint64_t* codes, const uint8_t* rgb,
-                               int64_t pitch, int32_t width, int32_t height,
-                               const uint8_t* pattern, int64_t pattern_pitch, uint8_t* frame_a,
-                               uint8_t* frame_b, int64_t frame_pitch, uint32_t* choice_out,
-                               cudaStream_t st) {
+cudaError_t launch_etab_gather(const uint4* entry, const uint8_t* rgb, int64_t pitch,
+                               int32_t width, int32_t height, const uint8_t* pattern,
+                               int64_t pattern_pitch, uint8_t* frame_a, uint8_t* frame_b,
+                               int64_t frame_pitch, uint32_t* choice_out, cudaStream_t st) {
     const int64_t n = (int64_t)width * height;
     if (n <= 0) return cudaSuccess;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t want = (n + 255) / 256, cap = (int64_t)(sms > 0 ? sms : 1) * 16;
+    const int64_t want = (n + 1023) / 1024, cap = (int64_t)(sms > 0 ? sms : 1) * 16;
     k_etab_gather<<<(int)(want < cap ? want : cap), 256, 0, st>>>(
-        choice, codes, rgb, pitch, width, n, pattern, pattern_pitch, frame_a, frame_b, frame_pitch,
+        entry, rgb, pitch, width, n, pattern, pattern_pitch, frame_a, frame_b, frame_pitch,
         choice_out);
     return cudaGetLastError();
 }

@@ -173,14 +173,13 @@ cudaError_t launch_search_multi(const MultiArgs& a, cudaStream_t st);
 int multi_max_chunk();  // largest radii per work item of the multi-threshold search
 cudaError_t launch_embed(const EmbedArgs& a, cudaStream_t st);
 cudaError_t launch_first_hits(const FirstHitArgs& a, cudaStream_t st);
-// keys (in place) -> choices k | m << 16, and the exact codes of each hit
-cudaError_t launch_first_finalize(const FirstHitArgs& a, uint32_t* choice, uint64_t* codes,
+// keys -> 16-byte table entries: the exact codes of each hit and its choice
+cudaError_t launch_first_finalize(const FirstHitArgs& a, const uint32_t* keys, uint4* entry,
                                   cudaStream_t st);
-cudaError_t launch_etab_gather(const uint32_t* choice, const uint64_t* codes, const uint8_t* rgb,
-                               int64_t pitch, int32_t width, int32_t height,
-                               const uint8_t* pattern, int64_t pattern_pitch, uint8_t* frame_a,
-                               uint8_t* frame_b, int64_t frame_pitch, uint32_t* choice_out,
-                               cudaStream_t st);
+cudaError_t launch_etab_gather(const uint4* entry, const uint8_t* rgb, int64_t pitch,
+                               int32_t width, int32_t height, const uint8_t* pattern,
+                               int64_t pattern_pitch, uint8_t* frame_a, uint8_t* frame_b,
+                               int64_t frame_pitch, uint32_t* choice_out, cudaStream_t st);
 cudaError_t launch_init_acc(Acc* acc, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t n,
                                    const ImageDesc* imgs, cudaStream_t st);
