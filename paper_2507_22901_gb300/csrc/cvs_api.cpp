@@ -769,6 +769,7 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     MultiArgs a{};
     a.tf = c->tf;
     a.td = c->td;
+    a.order = c->d_order;
     a.acc = c->acc_multi;
     a.n_targets = n;
     a.grid = c->grid;

@@ -92,6 +92,7 @@ constexpr int kMaxThresholdSets = 16;
 struct MultiArgs {
     const TargetF32* tf;
     const TargetF64* td;
+    const int32_t* order;      // K radius indices sorted by (radius value, index)
     Acc* acc;                  // n_targets * n_thr, index t * n_thr + s
     int64_t n_targets;
     GridDev grid;

@@ -7,9 +7,10 @@
 // |d| (0..255, 256 = out of range) to two 16-bit masks, the sets that call the
 // channel high and those that call it low, so a slot costs three table reads
 // whatever the number of sets.  Per lane, passes are counted in bytes (four
-// sets per word), patterns are OR-ed into one set mask per pattern, and the
-// sets passing at each radius are OR-ed per warp into a shared per-radius mask
-// from which the largest passing radius is read at the end of the item.
+// sets per word) and patterns are OR-ed into one set mask per pattern.  A work
+// item takes its radii in decreasing order, so a lane's first pass of a set is
+// its largest passing radius for that set: it is recorded once, in shared
+// memory, and the warp's maximum is taken at the end of the item.
 // Flagged slots are marked in a per-lane bitmap and decided after each
 // segment: bounds once, every set from them, FP64 codes when some set stays
 // open.
@@ -25,7 +26,7 @@ namespace {
 
 constexpr int kMultiWords = 7;                  // flag words per lane per segment
 constexpr int kMultiSegIters = 32 * kMultiWords;  // < 256: byte counters cannot overflow
-constexpr int kMultiMaxChunk = 256;             // radii per work item (per-radius masks)
+constexpr int kMultiMaxChunk = 8192;            // radii per work item
 
 // Table entry of |d| = i: bit s set if set s calls the channel high (i >= hi_min[s]),
 // bit 16 + s if it calls it low (i <= lo_max[s]); i = 256 stands for out of range.
@@ -113,10 +114,10 @@ template <int PREC, bool FAST, bool CLIP, bool ALLMASK>
 __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* r2s,
                                               const float4* sc4s, const uint32_t* ts,
                                               const TargetF32& T, const ChainF32& C,
-                                              const TargetF64& D, int64_t t, int k, int h,
+                                              const TargetF64& D, int64_t t, int kk, int h,
                                               uint32_t setmask, unsigned long long& n_re) {
     const int NT = A.n_thr;
-    const Intervals I = intervals32<FAST>(T, C, r2s[k], sc4s[h], A.half_w, CLIP ? 1 : 0);
+    const Intervals I = intervals32<FAST>(T, C, r2s[kk], sc4s[h], A.half_w, CLIP ? 1 : 0);
     bool certain_out = false, maybe_out = false;
     if (!CLIP) {
 #pragma unroll
@@ -141,7 +142,7 @@ __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* 
     uint32_t hR, hG, hB, ok;
     if (open) {  // some set's decision depends on a code the bounds leave open: FP64
         int qp[3], qm[3];
-        pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + k), __ldg(A.grid.s64 + h),
+        pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + __ldg(A.order + kk)), __ldg(A.grid.s64 + h),
                      __ldg(A.grid.c64 + h), A.qkey, qp, qm);
         bool in_range = true;
 #pragma unroll
@@ -160,7 +161,7 @@ __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* 
     }
     if (!ok) return;
     const int inc = A.grid.sym ? 2 : 1;
-    const int r_bits = __float_as_int(r2s[k].x);
+    const int r_bits = __float_as_int(r2s[kk].x);
     for (int s = 0; s < NT; ++s) {
         if (!((ok >> s) & 1u)) continue;
         const int p = (int)((((hR >> s) & 1u) << 2) | (((hG >> s) & 1u) << 1) | ((hB >> s) & 1u));
@@ -171,18 +172,17 @@ __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* 
     }
 }
 
-// One work item: target t, radii [k0, k1) (k1 - k0 <= kMultiMaxChunk).
+// One work item: target t, radius ranks [kk0, kk1), taken in decreasing order.
 template <int PREC, bool FAST, bool CLIP, bool ALLMASK>
 __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s,
                                            const float4* sc4s, const uint32_t* ts, uint32_t* fb,
-                                           uint32_t* okr, const TargetF32& T, const ChainF32& C,
-                                           const PairsC& PC, int64_t t, int k0, int k1,
+                                           float* rmx, const TargetF32& T, const ChainF32& C,
+                                           const PairsC& PC, int64_t t, int kk0, int kk1,
                                            unsigned long long& n_flag,
                                            unsigned long long& n_re) {
     const unsigned lane = lane_id();
     const int H = A.grid.H, NT = A.n_thr;
     const int inc = A.grid.sym ? 2 : 1;
-    const int nslots = (k1 - k0) * H;
     const uint32_t setmask = (1u << NT) - 1u;
     const int nw = (NT + 3) >> 2;
     const TargetF64 D = A.td[t];
@@ -193,31 +193,28 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
 #pragma unroll
     for (int p = 0; p < 8; ++p) m.pm[p] = 0;
     m.cnt = 0;
+    uint32_t seen = 0;  // sets this lane has seen pass (its largest radius is recorded)
+    for (int s = 0; s < NT; ++s) rmx[s * 32 + lane] = 0.0f;  // radius 0 never passes
+    // slot i of the item is (rank kk1 - 1 - i / H, i % H); lanes step by 32
     const int q32 = 32 / H, r32 = 32 - q32 * H;
-    int k = k0 + (int)lane / H, h = (int)lane % H;
-    const int nit = (nslots + 31) >> 5;
-    int it_pow = 0;  // iterations whose radii never reach the sRGB linear segment
-    int it0 = 0;     // iterations wholly below the first radius where some set may pass
+    int kk = kk1 - 1 - (int)lane / H, h = (int)lane % H;
+    int klo = kk0;      // ranks below klo certainly fail for every set
+    int it_pow = 1 << 30;  // iterations from here on never reach the sRGB linear segment
     if (PREC == CVS_PREC_FP32_RECHECK && FAST) {
-        const int k_split = first_linseg_radius(T, C, r2s, k0, k1);
-        it_pow = k_split == k1 ? nit : ((k_split - k0) * H) >> 5;
-        const int kp = first_possible_radius(T, C, r2s, k0, k1, A.hi_min_all);
-        if (kp > k0) {
-            it0 = kp == k1 ? nit : ((kp - k0) * H) >> 5;
-            const int i = it0 * 32 + (int)lane;
-            const int dk = i / H;
-            k = k0 + dk;
-            h = i - dk * H;
-        }
+        klo = first_possible_radius(T, C, r2s, kk0, kk1, A.hi_min_all);
+        const int k_split = first_linseg_radius(T, C, r2s, kk0, kk1);  // ranks below: pow only
+        it_pow = ((kk1 - k_split) * H + 31) >> 5;
     }
-    for (int seg0 = it0; seg0 < nit; seg0 += kMultiSegIters) {
+    const int nslots = (kk1 - klo) * H;
+    const int nit = (nslots + 31) >> 5;
+    for (int seg0 = 0; seg0 < nit; seg0 += kMultiSegIters) {
         const int seg1 = min(seg0 + kMultiSegIters, nit);
         for (int w = 0, it = seg0; it < seg1; ++w) {
             uint32_t bits = 0;
             const int wend = min(seg1, it + 32);
             for (uint32_t bit = 1u; it < wend; ++it, bit <<= 1) {
                 const bool active = it * 32 + (int)lane < nslots;
-                const int kq = active ? k : k0, hq = active ? h : 0;
+                const int kq = active ? kk : kk1 - 1, hq = active ? h : 0;
                 uint32_t ok = 0, hR = 0, hG = 0, hB = 0;
                 bool skip = false;
                 if (PREC == CVS_PREC_FP32_RECHECK) {
@@ -232,7 +229,7 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
                     if (!skip) {
                         int yp[3], ym[3];
                         bool flag;
-                        if (it < it_pow) flag = encode32<false>(lin, A.half_w, yp, ym, nullptr);
+                        if (it >= it_pow) flag = encode32<false>(lin, A.half_w, yp, ym, nullptr);
                         else flag = encode32<true>(lin, A.half_w, yp, ym, nullptr);
                         flag = flag && active;
                         if (flag) bits |= bit;
@@ -253,8 +250,8 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
                     }
                 } else if (active) {
                     int qp[3], qm[3];
-                    pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + kq), __ldg(A.grid.s64 + hq),
-                                 __ldg(A.grid.c64 + hq), A.qkey, qp, qm);
+                    pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + __ldg(A.order + kq)),
+                                 __ldg(A.grid.s64 + hq), __ldg(A.grid.c64 + hq), A.qkey, qp, qm);
                     uint32_t e[3];
                     bool in_range = true;
 #pragma unroll
@@ -272,19 +269,22 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
                 if (!skip) {
                     tally_counts(m, ok, nw);
                     tally_patterns(m, hR, hG, hB);
-                    // sets passing at each radius of the iteration, OR-ed per warp
-                    const int ka = __shfl_sync(0xFFFFFFFFu, kq, 0);
-                    const int kb = __reduce_max_sync(0xFFFFFFFFu, (unsigned)kq);
-                    for (int kr = ka; kr <= kb; ++kr) {
-                        const uint32_t mk = __reduce_or_sync(0xFFFFFFFFu, kq == kr ? ok : 0u);
-                        if (lane == 0 && mk) okr[kr - k0] |= mk;
+                    uint32_t fresh = ok & ~seen;  // radii decrease: the first pass is the largest
+                    if (fresh) {
+                        seen |= fresh;
+                        const float r = r2s[kq].x;
+                        while (fresh) {
+                            const int s = __ffs(fresh) - 1;
+                            fresh &= fresh - 1u;
+                            rmx[s * 32 + lane] = r;
+                        }
                     }
                 }
                 h += r32;
-                k += q32;
+                kk -= q32;
                 const bool wrap = h >= H;
                 h = wrap ? h - H : h;
-                k = wrap ? k + 1 : k;
+                kk = wrap ? kk - 1 : kk;
             }
             if (PREC == CVS_PREC_FP32_RECHECK) fb[w * 32 + lane] = bits;
         }
@@ -302,7 +302,7 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
                         const int dk = i / H;
                         ++n_flag;
                         multi_flagged<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t,
-                                                                 k0 + dk, i - dk * H, setmask,
+                                                                 kk1 - 1 - dk, i - dk * H, setmask,
                                                                  n_re);
                     }
                 }
@@ -317,17 +317,11 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
         const uint32_t wp = __reduce_or_sync(0xFFFFFFFFu, m.pm[p]);
         if ((wp >> lane) & 1u) pmask |= 1u << (p - 1);
     }
-    // largest passing radius per set from the per-radius masks
     int rbits_mine = __float_as_int(-1.0f);
     for (int s = 0; s < NT; ++s) {
-        float rm = -1.0f;
-        for (int kr = k0 + (int)lane; kr < k1; kr += 32)
-            if ((okr[kr - k0] >> s) & 1u) rm = fmaxf(rm, r2s[kr].x);
-        const int b = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)__float_as_int(fmaxf(rm, 0.0f)));
-        const bool any = __any_sync(0xFFFFFFFFu, rm >= 0.0f);
-        if ((int)lane == s && any) rbits_mine = b;
+        const uint32_t b = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(rmx[s * 32 + lane]));
+        if ((int)lane == s && b != 0u) rbits_mine = (int)b;
     }
-    for (int kr = k0 + (int)lane; kr < k1; kr += 32) okr[kr - k0] = 0u;
     __syncwarp();
     if ((int)lane < NT && m.cnt) {
         Acc* ac = A.acc + t * NT + lane;
@@ -346,16 +340,16 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
     uint32_t* ts = reinterpret_cast<uint32_t*>(smem + ((K * 8 + 15) & ~15) + H * 16);
     uint32_t* per_warp = ts + 260;  // 257 table entries, padded to 16 bytes
     const int warp = threadIdx.x >> 5;
-    uint32_t* fb = per_warp + warp * (kMultiWords * 32 + kMultiMaxChunk);
-    uint32_t* okr = fb + kMultiWords * 32;
+    uint32_t* fb = per_warp + warp * (kMultiWords * 32 + kMaxThresholdSets * 32);
+    float* rmx = reinterpret_cast<float*>(fb + kMultiWords * 32);
     build_set_table(ts, A);
-    for (int i = threadIdx.x; i < K; i += blockDim.x) r2s[i] = dup(A.grid.r32[i]);
+    for (int i = threadIdx.x; i < K; i += blockDim.x) r2s[i] = dup(A.grid.r32[A.order[i]]);
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
         const float2 sc = A.grid.sc32[i];
         sc4s[i] = make_float4(sc.x, -sc.x, sc.y, -sc.y);
     }
     const unsigned lane = lane_id();
-    for (int i = (int)lane; i < kMultiWords * 32 + kMultiMaxChunk; i += 32) fb[i] = 0u;
+    for (int i = (int)lane; i < kMultiWords * 32; i += 32) fb[i] = 0u;
     __syncthreads();
     ChainF32 C;
 #pragma unroll
@@ -379,10 +373,10 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
         TargetF32 T{};
         if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
         if (PREC == CVS_PREC_FP32_RECHECK && (T.flags & 1u))
-            multi_item<PREC, true, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, okr, T, C, PC, t, k0, k1,
+            multi_item<PREC, true, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, rmx, T, C, PC, t, k0, k1,
                                                   n_flag, n_re);
         else
-            multi_item<PREC, false, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, okr, T, C, PC, t, k0, k1,
+            multi_item<PREC, false, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, rmx, T, C, PC, t, k0, k1,
                                                    n_flag, n_re);
     }
 #pragma unroll
@@ -409,7 +403,7 @@ __global__ void k_init_acc(Acc* __restrict__ acc, int64_t n) {
 
 int multi_smem_bytes(const GridDev& g, int block) {
     return ((g.K * 8 + 15) & ~15) + g.H * 16 + 260 * 4 +
-           (block / 32) * (kMultiWords * 32 + kMultiMaxChunk) * 4;
+           (block / 32) * (kMultiWords * 32 + kMaxThresholdSets * 32) * 4;
 }
 
 template <int PREC, bool CLIP, bool ALLMASK>
