@@ -242,7 +242,7 @@ __device__ __forceinline__ void push_fp64(const SearchArgs& A, bool need64, int6
 
 // Decide up to 32 flagged slots of target t, one per lane: exact interval
 // analysis in FP32, FP64 re-decision where the analysis cannot decide.
-template <bool FAST>
+template <bool FAST, bool DL>
 __device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S,
                                               const TargetF32& T, const ChainF32& C, int64_t t,
                                               uint32_t* pq, int n, int& cnt, float& rmax,
@@ -259,9 +259,8 @@ __device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S
         const float r = r2.x;
         // a list and the luminance limit need the exact codes of a passing pair
         const Intervals I = intervals32<FAST>(T, C, r2, S.sc4[h], A.half_w, A.clip);
-        pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, A.clip,
-                          A.list_mode || A.ltab != nullptr);
-        if (pc > 0 && A.ltab && !dl_ok(A.ltab, A.max_dl, A.td[t].L, I.lo, I.lo + 3)) pc = 0;
+        pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, A.clip, A.list_mode || DL);
+        if (DL && pc > 0 && !dl_ok(A.ltab, A.max_dl, A.td[t].L, I.lo, I.lo + 3)) pc = 0;
         if (pc > 0) {
             cnt += inc;
             rmax = fmaxf(rmax, r);
@@ -400,7 +399,7 @@ __device__ __forceinline__ void run_range(const SearchArgs& A, const Smem& S, co
 
 // Queue the flagged slots of one segment (words [0, nwords) of fb) into pq,
 // 32 at a time, deciding each full batch with drain_flagged.
-template <bool FAST>
+template <bool FAST, bool DL>
 __device__ __forceinline__ void collect_flagged(const SearchArgs& A, const Smem& S,
                                                 const TargetF32& T, const ChainF32& C, int64_t t,
                                                 int k0, int seg0, int nwords, uint32_t* fb,
@@ -429,7 +428,7 @@ __device__ __forceinline__ void collect_flagged(const SearchArgs& A, const Smem&
             pq_n += __popc(ball);
             __syncwarp();
             if (pq_n >= 32) {
-                drain_flagged<FAST>(A, S, T, C, t, pq, 32, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh,
+                drain_flagged<FAST, DL>(A, S, T, C, t, pq, 32, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh,
                                     rq_n, n_re);
                 const int rest = pq_n - 32;
                 const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
@@ -503,12 +502,12 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
         }
         if (PREC == CVS_PREC_FP32_RECHECK) {
             __syncwarp();
-            collect_flagged<FAST>(A, S, T, C, t, k0, seg0, (seg1 - seg0 + 31) >> 5, fb, pq, pq_n,
+            collect_flagged<FAST, DL>(A, S, T, C, t, k0, seg0, (seg1 - seg0 + 31) >> 5, fb, pq, pq_n,
                                   acc, rq_t, rq_kh, rq_n, n_flag, n_re);
         }
     }
     if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0)
-        drain_flagged<FAST>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh, rq_n,
+        drain_flagged<FAST, DL>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh, rq_n,
                             n_re);
     n_skip += acc.skip;
     n_prune += acc.prune;
