@@ -384,6 +384,20 @@ def run_extras(ctx, torch, device, W, cvs):
         "pairs_without_limit": int(base[1].sum().item()),
         "pairs_with_limit": int(lim[1].sum().item())}
     del cube, base, lim
+    # pair lists of many colours: every passing pair of the 4096-colour precision
+    # set on the 64-radius x 180-angle grid, grouped by colour in (k, m) order
+    pc = torch.from_numpy(W.precision_colors()).to(device)
+    recs, offs = ctx.search_colors_pairs(pc, r3, a3, 50.0, 0.5)
+    t0.record()
+    recs, offs = ctx.search_colors_pairs(pc, r3, a3, 50.0, 0.5, cap=int(offs[-1]))
+    t1.record()
+    torch.cuda.synchronize(device)
+    sec_p = t0.elapsed_time(t1) / 1e3
+    out["pair_lists"] = {"workload": "4096 precision-set colours x 64 radii x 180 angles",
+                         "pairs": int(offs[-1]), "seconds": sec_p,
+                         "gcand_s": 4096 * len(r3) * len(a3) / sec_p / 1e9,
+                         "mpairs_s": int(offs[-1]) / sec_p / 1e6}
+    del pc, recs
     # the paper's own timed experiment (§3, Table 1): its 9 colours under all 12
     # (V_th, R_novib) combinations and all 7 patterns, as one multi-set pass on
     # the 61-radius x 360-angle grid (the paper does not state its grid)

@@ -197,6 +197,20 @@ cvs_status cvs_search_color(cvs_ctx* ctx, const uint8_t rgb[3], uint32_t target,
                             cvs_precision prec, cvs_pair* out_host, size_t cap,
                             size_t* n_out);
 
+/* Every passing pair of n colours (the extraction of cvs_search_color for many
+ * targets; for an image, the colours of its pixels, each result being a pure
+ * function of the colour).  rgb_dev: device, 3n bytes.  out_dev: device array
+ * of cap records; the pairs of colour i occupy [offsets[i], offsets[i+1]) in
+ * (k, m) order, each record's target field = i.  offsets_host: optional host
+ * array of n + 1 entries.  *n_out receives the total number of pairs; when it
+ * exceeds cap, nothing is written to out_dev and CVS_ERR_TRUNCATED is
+ * returned (offsets_host and *n_out are still filled, so the call can be
+ * repeated with a larger buffer).  n <= 2^31.  Synchronous on `stream`. */
+cvs_status cvs_search_colors_pairs(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
+                                   const cvs_grid* grid, const cvs_thresholds* thr,
+                                   cvs_precision prec, cvs_pair* out_dev, int64_t cap,
+                                   int64_t* offsets_host, int64_t* n_out, void* stream);
+
 /* Per-target results for n colours.  rgb_dev: device, 3n bytes (R,G,B per
  * colour).  out_dev: device capacity map of n entries.  Asynchronous on
  * `stream`; the device buffers must stay valid until it completes. */

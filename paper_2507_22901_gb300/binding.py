@@ -133,6 +133,8 @@ def lib() -> ctypes.CDLL:
                               vp, ctypes.c_size_t, P(ctypes.c_size_t)], st),
         "cvs_search_colors": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), st,
                                P(cvs_capacity_map), vp], st),
+        "cvs_search_colors_pairs": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), st, vp, i64,
+                                     vp, P(i64), vp], st),
         "cvs_search_colors_host": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), st, vp, vp, vp],
                                    st),
         "cvs_search_colors_multi": ([vp, vp, i64, P(cvs_grid), P(cvs_thresholds), i32, st,
@@ -305,6 +307,32 @@ class Context:
                                       ctypes.byref(t), int(precision), ctypes.byref(m),
                                       _stream_ptr(stream)), "cvs_search_colors")
         return out
+
+    def search_colors_pairs(self, rgb_dev, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
+                            gamut_mode=0, precision=PREC_FP32_RECHECK, cap=None, stream=None):
+        """Every passing pair of n colours: (records (total, 16) uint8 CUDA tensor
+        viewable as PAIR_DTYPE, offsets int64 NumPy array of n + 1)."""
+        import torch
+        n = rgb_dev.numel() // 3
+        g, keep = make_grid(radii, angles_deg)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        offs = np.zeros(n + 1, np.int64)
+        total = ctypes.c_int64()
+        if cap is None:  # ask for the size first
+            st = lib().cvs_search_colors_pairs(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g),
+                                               ctypes.byref(t), int(precision), None, 0,
+                                               offs.ctypes.data, ctypes.byref(total),
+                                               _stream_ptr(stream))
+            if st not in (CVS_OK, CVS_ERR_TRUNCATED):
+                check(st, "cvs_search_colors_pairs")
+            cap = total.value
+        out = torch.empty((max(cap, 1), 16), dtype=torch.uint8, device=rgb_dev.device)
+        st = lib().cvs_search_colors_pairs(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g),
+                                           ctypes.byref(t), int(precision), out.data_ptr(), cap,
+                                           offs.ctypes.data, ctypes.byref(total),
+                                           _stream_ptr(stream))
+        check(st, "cvs_search_colors_pairs")
+        return out[:total.value], offs
 
     def search_colors_multi(self, rgb_dev, radii, angles_deg, thresholds, gamut_mode=0,
                             precision=PREC_FP32_RECHECK, out=None, stream=None):

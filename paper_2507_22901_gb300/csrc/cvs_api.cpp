@@ -103,6 +103,9 @@ struct cvs_ctx {
     std::map<std::array<int64_t, 7>, LaunchShape> tuned;
     Acc* acc_tune = nullptr;
     int64_t cap_acc_tune = 0;
+    // pair lists of many colours: per-colour offsets into the caller's output
+    int64_t* d_offs = nullptr;
+    int64_t cap_offs = 0;
     // luminance limit on emitted pairs (off while max_dl < 0); L* of all 2^24 colours
     double max_dl = -1.0;
     double* ltab = nullptr;
@@ -541,7 +544,7 @@ void cvs_destroy(cvs_ctx* c) {
     void* ptrs[] = {c->grid.r32, c->grid.sc32, c->grid.r64, c->grid.s64, c->grid.c64,
                     c->d_angles, c->d_status, c->tf, c->td, c->acc, c->qkey, c->counters,
                     c->dense, c->compact, c->d_imgs, c->d_in, c->d_maxr, c->d_count, c->d_pmask,
-                    c->d_rgb1, c->d_probe, c->d_order, c->ltab};
+                    c->d_rgb1, c->d_probe, c->d_order, c->ltab, c->d_offs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     drop_graphs(c);
@@ -690,6 +693,70 @@ cvs_status cvs_search_color(cvs_ctx* c, const uint8_t rgb[3], uint32_t target,
         CVS_CUDA(cudaMemcpy(out_host, c->compact, ncopy * sizeof(cvs_pair), cudaMemcpyDeviceToHost));
     if ((size_t)n > cap)
         return fail(CVS_ERR_TRUNCATED, "%llu passing pairs, capacity %zu", n, cap);
+    return CVS_OK;
+}
+
+cvs_status cvs_search_colors_pairs(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n,
+                                   const cvs_grid* grid, const cvs_thresholds* thr,
+                                   cvs_precision prec, cvs_pair* out_dev, int64_t cap,
+                                   int64_t* offsets_host, int64_t* n_out, void* stream) {
+    if (!c || !n_out || (cap > 0 && !out_dev)) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
+    *n_out = 0;
+    if (n < 0 || n > ((int64_t)1 << 31)) return fail(CVS_ERR_INVALID_ARG, "n out of range");
+    if (cap < 0) return fail(CVS_ERR_INVALID_ARG, "negative capacity");
+    if (n > 0 && !rgb_dev) return fail(CVS_ERR_INVALID_ARG, "NULL device buffer");
+    if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
+        return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    cvs_status st0 = check_grid(grid);
+    if (st0 == CVS_OK) st0 = check_thresholds(thr);
+    if (st0 == CVS_OK) st0 = set_device(c);
+    if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = ensure_targets(c, n > 0 ? n : 1);
+    if (st0 != CVS_OK) return st0;
+    if (offsets_host) offsets_host[0] = 0;
+    if (n == 0) return CVS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // pass 1: the number of passing pairs of each colour
+    CVS_CUDA(grow(&c->d_maxr, &c->cap_maxr, n));
+    CVS_CUDA(grow(&c->d_count, &c->cap_count, n));
+    CVS_CUDA(grow(&c->d_pmask, &c->cap_pmask, n));
+    CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
+    st0 = run_search(c, n, thr, prec, 0, 0, st);
+    if (st0 != CVS_OK) return st0;
+    CVS_CUDA(launch_finalize_colors(c->acc, n, c->d_maxr, c->d_count, c->d_pmask, st));
+    std::vector<int32_t> counts((size_t)n);
+    CVS_CUDA(cudaMemcpyAsync(counts.data(), c->d_count, sizeof(int32_t) * (size_t)n,
+                             cudaMemcpyDeviceToHost, st));
+    CVS_CUDA(cudaStreamSynchronize(st));
+    std::vector<int64_t> offs((size_t)n + 1);
+    offs[0] = 0;
+    for (int64_t i = 0; i < n; ++i) offs[i + 1] = offs[i] + counts[i];
+    if (offsets_host) std::memcpy(offsets_host, offs.data(), sizeof(int64_t) * ((size_t)n + 1));
+    const int64_t total = offs[n];
+    *n_out = total;
+    if (total > cap)
+        return fail(CVS_ERR_TRUNCATED, "%lld passing pairs, capacity %lld", (long long)total,
+                    (long long)cap);
+    if (total == 0) return CVS_OK;
+    // pass 2: dense records of a batch of colours, then one ordered compaction per colour
+    const int64_t kn = (int64_t)c->grid.K * c->grid.N;
+    const int64_t budget = (int64_t)512 << 20;  // bytes of dense records per batch
+    int64_t batch = budget / (kn * (int64_t)sizeof(cvs_pair));
+    batch = batch < 1 ? 1 : (batch > n ? n : batch);
+    CVS_CUDA(grow(&c->dense, &c->cap_dense, batch * kn));
+    CVS_CUDA(grow(&c->d_offs, &c->cap_offs, n + 1));
+    CVS_CUDA(cudaMemcpyAsync(c->d_offs, offs.data(), sizeof(int64_t) * ((size_t)n + 1),
+                             cudaMemcpyHostToDevice, st));
+    for (int64_t t0 = 0; t0 < n; t0 += batch) {
+        const int64_t b = n - t0 < batch ? n - t0 : batch;
+        CVS_CUDA(cudaMemsetAsync(c->dense, 0, sizeof(cvs_pair) * (size_t)(b * kn), st));
+        CVS_CUDA(launch_setup_colors(rgb_dev + 3 * t0, b, c->grid.rmax, c->tf, c->td, c->acc, st));
+        st0 = run_search(c, b, thr, prec, 1, (uint32_t)t0, st);
+        if (st0 != CVS_OK) return st0;
+        CVS_CUDA(launch_compact_pairs_batch(c->dense, kn, b, c->d_offs + t0, out_dev, st));
+    }
+    CVS_CUDA(cudaStreamSynchronize(st));
+    collect_stats(c);
     return CVS_OK;
 }
 

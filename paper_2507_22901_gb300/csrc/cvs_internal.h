@@ -186,6 +186,10 @@ cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t 
                                    const ImageDesc* imgs, cudaStream_t st);
 cudaError_t launch_compact_pairs(const cvs_pair* dense, int64_t n_dense, cvs_pair* out,
                                  unsigned long long* n_out, cudaStream_t st);
+// Block b compacts target b's kn dense records (pattern 0 = empty) into
+// out + offsets[b], keeping their order.
+cudaError_t launch_compact_pairs_batch(const cvs_pair* dense, int64_t kn, int64_t n_targets,
+                                      const int64_t* offsets, cvs_pair* out, cudaStream_t st);
 // L* of all 2^24 8-bit colours (index R << 16 | G << 8 | B), as step 1 forms it.
 cudaError_t launch_l_table(double* ltab, cudaStream_t st);
 cudaError_t launch_target_lab(const uint8_t* rgb, int64_t n, double* lab, cudaStream_t st);

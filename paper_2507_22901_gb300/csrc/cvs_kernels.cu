@@ -200,8 +200,8 @@ __device__ __noinline__ void flush_queue(const SearchArgs& A, uint32_t* rq_t, ui
         const int pat = decide64_slot(A, D, k, h, qp, qm);
         if (pat) {
             if (A.list_mode) {
-                write_records(A.dense, A.grid.N, A.grid.H, A.grid.sym, k, h, qp, qm, pat, 1u,
-                              A.target_id);
+                write_records(A.dense + (int64_t)t * A.grid.K * A.grid.N, A.grid.N, A.grid.H,
+                              A.grid.sym, k, h, qp, qm, pat, 1u, A.target_id + t);
             } else {
                 Acc* ac = A.acc + t;
                 atomicAdd(&ac->count, inc);
@@ -286,8 +286,8 @@ struct Tally {
 // step itself never synchronises the warp.
 template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST, bool LINSEG, bool DL>
 __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, const PairsT& P,
-                                          const PairsC& PC, const TargetF64& D, int k, int h,
-                                          bool active, Tally& acc) {
+                                          const PairsC& PC, const TargetF64& D, int64_t t, int k,
+                                          int h, bool active, Tally& acc) {
     const int H = A.grid.H;
     const int inc = A.grid.sym ? 2 : 1;
     if (CHECK && !active) { k = 0; h = 0; }
@@ -338,8 +338,8 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
                     qp[c] = a;
                     qm[c] = b;
                 }
-                write_records(A.dense, A.grid.N, H, A.grid.sym, k, h, qp, qm, pattern, 0u,
-                              A.target_id);
+                write_records(A.dense + t * A.grid.K * A.grid.N, A.grid.N, H, A.grid.sym, k, h, qp, qm,
+                              pattern, 0u, A.target_id + (uint32_t)t);
             }
         }
         return flag;
@@ -348,8 +348,8 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
         const int pattern = (!CHECK || active) ? decide64_slot(A, D, k, h, qp, qm) : 0;
         if (pattern) {
             if (LIST) {
-                write_records(A.dense, A.grid.N, H, A.grid.sym, k, h, qp, qm, pattern, 0u,
-                              A.target_id);
+                write_records(A.dense + t * A.grid.K * A.grid.N, A.grid.N, H, A.grid.sym, k, h, qp, qm,
+                              pattern, 0u, A.target_id + (uint32_t)t);
             } else {
                 acc.cnt += inc;
                 acc.rmax = fmaxf(acc.rmax, r);
@@ -372,7 +372,8 @@ constexpr int kSegIters = 32 * kFlagWords;
 // lanes at slot (k, h); flagged slots set their bits in fb.
 template <int PREC, bool FAST, bool CHECK, bool CLIP, bool LIST, bool LINSEG, bool DL>
 __device__ __forceinline__ void run_range(const SearchArgs& A, const Smem& S, const PairsT& P,
-                                          const PairsC& PC, const TargetF64& D, int& it, int end,
+                                          const PairsC& PC, const TargetF64& D, int64_t t, int& it,
+                                          int end,
                                           int seg0, int nslots, int q32, int r32, int& k, int& h,
                                           Tally& acc, uint32_t* fb) {
     const unsigned lane = lane_id();
@@ -383,8 +384,8 @@ __device__ __forceinline__ void run_range(const SearchArgs& A, const Smem& S, co
         uint32_t bits = 0, bit = 1u << ((it - seg0) & 31);
         for (; it < wend; ++it) {
             const bool active = !CHECK || it * 32 + (int)lane < nslots;
-            const bool flag = slot_step<PREC, FAST, CHECK, CLIP, LIST, LINSEG, DL>(A, S, P, PC, D, k,
-                                                                                 h, active, acc);
+            const bool flag = slot_step<PREC, FAST, CHECK, CLIP, LIST, LINSEG, DL>(A, S, P, PC, D, t,
+                                                                                 k, h, active, acc);
             if (PREC == CVS_PREC_FP32_RECHECK && flag) bits |= bit;
             bit <<= 1;
             h += r32;
@@ -487,17 +488,17 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
         const int seg1 = min(seg0 + kSegIters, nit);
         const int full_end = min(seg1, nfull);
         if constexpr (PREC == CVS_PREC_FP32_RECHECK && FAST) {
-            run_range<PREC, FAST, false, CLIP, LIST, false, DL>(A, S, P, PC, D, it, min(full_end, it_pow),
+            run_range<PREC, FAST, false, CLIP, LIST, false, DL>(A, S, P, PC, D, t, it, min(full_end, it_pow),
                                                             seg0, nslots, q32, r32, k, h, acc, fb);
         }
-        run_range<PREC, FAST, false, CLIP, LIST, true, DL>(A, S, P, PC, D, it, full_end, seg0, nslots,
+        run_range<PREC, FAST, false, CLIP, LIST, true, DL>(A, S, P, PC, D, t, it, full_end, seg0, nslots,
                                                        q32, r32, k, h, acc, fb);
         if (it < seg1) {  // the item's last, partial iteration
             if (PREC == CVS_PREC_FP32_RECHECK && FAST && it < it_pow)
-                run_range<PREC, FAST, true, CLIP, LIST, false, DL>(A, S, P, PC, D, it, seg1, seg0,
+                run_range<PREC, FAST, true, CLIP, LIST, false, DL>(A, S, P, PC, D, t, it, seg1, seg0,
                                                                nslots, q32, r32, k, h, acc, fb);
             else
-                run_range<PREC, FAST, true, CLIP, LIST, true, DL>(A, S, P, PC, D, it, seg1, seg0,
+                run_range<PREC, FAST, true, CLIP, LIST, true, DL>(A, S, P, PC, D, t, it, seg1, seg0,
                                                               nslots, q32, r32, k, h, acc, fb);
         }
         if (PREC == CVS_PREC_FP32_RECHECK) {
@@ -667,6 +668,38 @@ __global__ void __launch_bounds__(1024) k_compact_pairs(const cvs_pair* __restri
         __syncthreads();
     }
     if (threadIdx.x == 0) *n_out = (unsigned long long)base;
+}
+
+// Ordered compaction of a batch of targets' dense records: block b moves the
+// passing records of target b (kn entries, (k, m) order) to out + offsets[b].
+__global__ void __launch_bounds__(1024) k_compact_pairs_batch(const cvs_pair* __restrict__ dense,
+                                                              int64_t kn,
+                                                              const int64_t* __restrict__ offsets,
+                                                              cvs_pair* out) {
+    __shared__ int warp_sums[32];
+    __shared__ long long base;
+    const cvs_pair* src = dense + (int64_t)blockIdx.x * kn;
+    cvs_pair* dst = out + offsets[blockIdx.x];
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t start = 0; start < kn; start += blockDim.x) {
+        const int64_t i = start + threadIdx.x;
+        const bool valid = i < kn && src[i].pattern != 0;
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, valid);
+        if (lane == 0) warp_sums[warp] = __popc(ball);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < warp) before += warp_sums[w];
+            total += warp_sums[w];
+        }
+        if (valid) dst[base + before + __popc(ball & ((1u << lane) - 1u))] = src[i];
+        __syncthreads();
+        if (threadIdx.x == 0) base += total;
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------ L* of all colours
@@ -914,6 +947,13 @@ cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t 
 cudaError_t launch_compact_pairs(const cvs_pair* dense, int64_t n_dense, cvs_pair* out,
                                  unsigned long long* n_out, cudaStream_t st) {
     k_compact_pairs<<<1, 1024, 0, st>>>(dense, n_dense, out, n_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_pairs_batch(const cvs_pair* dense, int64_t kn, int64_t n_targets,
+                                      const int64_t* offsets, cvs_pair* out, cudaStream_t st) {
+    if (n_targets <= 0 || kn <= 0) return cudaSuccess;
+    k_compact_pairs_batch<<<(unsigned)n_targets, 1024, 0, st>>>(dense, kn, offsets, out);
     return cudaGetLastError();
 }
 
