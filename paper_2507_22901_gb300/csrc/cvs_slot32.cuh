@@ -183,18 +183,24 @@ __device__ __forceinline__ bool pow_branch_only(const TargetF32& T, const ChainF
     return ok;
 }
 
-// True when no pair of a fast-path target at radius r (any angle) can have a
-// high channel, so every candidate there fails (pattern 000 never passes):
+// Radius bound.  At radius r (any angle) no pair of a fast-path target can
+// have a high channel c when its codes cannot differ by hi_min:
 //   the pair's difference in linear RGB is, with u = r sin j / 500 and
 //   w = -r cos j / 200,  Ax (2 c2x u + 2 u^3) + Bz (2 c2z w + 2 w^3),  whose
-//   size over all angles is at most 2 sqrt((Ax c2x U)^2 + (Bz c2z V)^2)
+//   size over all angles is at most D = 2 sqrt((Ax c2x U)^2 + (Bz c2z V)^2)
 //   + 2 |Ax| U^3 + 2 |Bz| V^3 (U = r/500, V = r/200);
-//   the encode's slope in code units is at most 3294.6 up to lin = 0.0031308
-//   and 112.09375 lin^(-7/12) above it (decreasing), so over values no lower
-//   than the pair's lower bound lo the codes differ by at most slope(lo) times
-//   that difference, plus one for the two roundings.
-// A channel is high only if its codes differ by at least hi_min.  The bound is
-// evaluated in FP32 with a relative margin of 1e-4 and an absolute one of 1e-3.
+//   both linear values are at least lo (the bound of pow_branch_only);
+//   the encode in code units, v(x) = 3294.6 x up to x = 0.0031308 and
+//   269.025 x^(5/12) - 14.025 above, is increasing and concave (its slope only
+//   falls), so two values no lower than lo and at most D apart encode to
+//   values at most v(lo + D) - v(lo) apart, and their codes at most that plus
+//   one.
+// The bound is evaluated in FP32 with lo lowered by 1e-5, D raised by a
+// relative 1e-4, and 0.01 code units added, far above its rounding errors.
+__device__ __forceinline__ float v_enc_bound(float x) {
+    return x <= 0.0031308f ? 3294.6f * x : 269.025f * exp2f(5.0f / 12.0f * log2f(x)) - 14.025f;
+}
+
 // The channels (bit 2 - c, as in a pattern) that could be high at radius r;
 // the bound grows with r.
 __device__ __forceinline__ uint32_t high_possible(const TargetF32& T, const ChainF32& C, float r,
@@ -207,11 +213,12 @@ __device__ __forceinline__ uint32_t high_possible(const TargetF32& T, const Chai
     for (int c = 0; c < 3; ++c) {
         const float ax = fabsf(C.Ax[c]), bz = fabsf(C.Bz[c]);
         const float p = ax * T.c2x * U, q = bz * T.c2z * V;
-        const float dlin = 2.0f * sqrtf(p * p + q * q) + 2.0f * (ax * U * U * U + bz * V * V * V);
+        const float dlin = (2.0f * sqrtf(p * p + q * q) + 2.0f * (ax * U * U * U + bz * V * V * V)) *
+                           1.0001f;
         const float lo = T.lin0[c] + fminf(C.Ax[c] * xlo, C.Ax[c] * xhi) +
-                         fminf(C.Bz[c] * zlo, C.Bz[c] * zhi);
-        const float slope = lo <= 0.0031308f ? 3294.6f : 112.09375f * exp2f(-7.0f / 12.0f * log2f(lo));
-        if (!(slope * dlin * 1.0001f + 1.001f < (float)hi_min)) mask |= 1u << (2 - c);
+                         fminf(C.Bz[c] * zlo, C.Bz[c] * zhi) - 1e-5f;
+        const float dv = v_enc_bound(lo + dlin) - v_enc_bound(lo) + 0.01f;
+        if (!(dv + 1.001f < (float)hi_min)) mask |= 1u << (2 - c);
     }
     return mask;
 }
