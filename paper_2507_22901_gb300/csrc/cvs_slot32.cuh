@@ -163,23 +163,40 @@ __device__ __forceinline__ bool surely_out32(const float2 lin[3]) {
     return out;
 }
 
+// Lower bound of channel c's linear value over the pair's two colours at any
+// angle, for displacements up to U = r/500 and V = r/200 (with margins), of a
+// fast-path target: the larger of two bounds.  The f^-1 displacement
+// u (c2 + u (c1 + u)) increases with u, so the X and Z terms are each smallest
+// at an end of their range; and since u = U sin j and w = -V cos j move
+// together, their linear parts form a sinusoid of amplitude
+// sqrt((Ax c2x U)^2 + (Bz c2z V)^2), the quadratic parts are at least
+// min(0, Ax c1x) U^2 and min(0, Bz c1z) V^2 and the cubic parts at least
+// -|Ax| U^3 and -|Bz| V^3.
+__device__ __forceinline__ float lin_lower_bound(const TargetF32& T, const ChainF32& C, float U,
+                                                 float V, float xlo, float xhi, float zlo,
+                                                 float zhi, int c) {
+    const float ends = T.lin0[c] + fminf(C.Ax[c] * xlo, C.Ax[c] * xhi) +
+                       fminf(C.Bz[c] * zlo, C.Bz[c] * zhi);
+    const float p = C.Ax[c] * T.c2x * U, q = C.Bz[c] * T.c2z * V;
+    const float coupled = T.lin0[c] - sqrtf(p * p + q * q) +
+                          fminf(0.0f, C.Ax[c] * T.c1x) * U * U +
+                          fminf(0.0f, C.Bz[c] * T.c1z) * V * V -
+                          (fabsf(C.Ax[c]) * U * U * U + fabsf(C.Bz[c]) * V * V * V);
+    return fmaxf(ends, coupled);
+}
+
 // True when no candidate at radius r (any angle) of a fast-path target can
-// reach the linear segment of the sRGB encode (lin <= 0.0031308).  The f^-1
-// displacement u (c2 + u (c1 + u)) increases with u, so per channel the
-// smallest linear value over |u| <= r/500, |w| <= r/200 sits at an end of
-// each range.  The margin (2e-5) is far above the FP32 chain's error in
-// linear RGB (below 1e-6) and the rounding of this bound.
+// reach the linear segment of the sRGB encode (lin <= 0.0031308): every
+// channel's lower bound stays above it by a margin (2e-5) far above the FP32
+// chain's error in linear RGB (below 1e-6) and the rounding of the bound.
 __device__ __forceinline__ bool pow_branch_only(const TargetF32& T, const ChainF32& C, float r) {
     const float U = r * 0.002f * 1.00001f, V = r * 0.005f * 1.00001f;
     const float xlo = -U * (T.c2x - U * (T.c1x - U)), xhi = U * (T.c2x + U * (T.c1x + U));
     const float zlo = -V * (T.c2z - V * (T.c1z - V)), zhi = V * (T.c2z + V * (T.c1z + V));
     bool ok = true;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float g = T.lin0[c] + fminf(C.Ax[c] * xlo, C.Ax[c] * xhi) +
-                        fminf(C.Bz[c] * zlo, C.Bz[c] * zhi);
-        ok = ok && g > 0.0031308f + 2e-5f;
-    }
+    for (int c = 0; c < 3; ++c)
+        ok = ok && lin_lower_bound(T, C, U, V, xlo, xhi, zlo, zhi, c) > 0.0031308f + 2e-5f;
     return ok;
 }
 
@@ -189,7 +206,7 @@ __device__ __forceinline__ bool pow_branch_only(const TargetF32& T, const ChainF
 //   w = -r cos j / 200,  Ax (2 c2x u + 2 u^3) + Bz (2 c2z w + 2 w^3),  whose
 //   size over all angles is at most D = 2 sqrt((Ax c2x U)^2 + (Bz c2z V)^2)
 //   + 2 |Ax| U^3 + 2 |Bz| V^3 (U = r/500, V = r/200);
-//   both linear values are at least lo (the bound of pow_branch_only);
+//   both linear values are at least lo (lin_lower_bound);
 //   the encode in code units, v(x) = 3294.6 x up to x = 0.0031308 and
 //   269.025 x^(5/12) - 14.025 above, is increasing and concave (its slope only
 //   falls), so two values no lower than lo and at most D apart encode to
@@ -215,8 +232,7 @@ __device__ __forceinline__ uint32_t high_possible(const TargetF32& T, const Chai
         const float p = ax * T.c2x * U, q = bz * T.c2z * V;
         const float dlin = (2.0f * sqrtf(p * p + q * q) + 2.0f * (ax * U * U * U + bz * V * V * V)) *
                            1.0001f;
-        const float lo = T.lin0[c] + fminf(C.Ax[c] * xlo, C.Ax[c] * xhi) +
-                         fminf(C.Bz[c] * zlo, C.Bz[c] * zhi) - 1e-5f;
+        const float lo = lin_lower_bound(T, C, U, V, xlo, xhi, zlo, zhi, c) - 1e-5f;
         const float dv = v_enc_bound(lo + dlin) - v_enc_bound(lo) + 0.01f;
         if (!(dv + 1.001f < (float)hi_min)) mask |= 1u << (2 - c);
     }
