@@ -43,7 +43,7 @@ LANES_PER_SM_CLK = 128
 # summarised in profiles/k_search_fp32_colour_cube_full.md (32,768-colour case
 # scaled by 8, traffic being proportional to the colours).  Valid only for the
 # kernel source it was taken from; otherwise the roofline reports null.
-TRAFFIC_CAPTURE = {"source_sha256_16": "37152ee18c6913d4", "bytes_per_launch": 8 * 3.189248e6}
+TRAFFIC_CAPTURE = {"source_sha256_16": "f344b0e05f22c3b9", "bytes_per_launch": 8 * 3.205632e6}
 
 
 def kernel_source_hash() -> str:
