@@ -279,6 +279,25 @@ def run_extras(ctx, torch, device, W, cvs):
     torch.cuda.synchronize(device)
     sec = t0.elapsed_time(t1) / 1e3
     cand3 = px * len(r3) * len(a3)
+    # the same batch with one search per distinct colour (option "dedup")
+    ctx.set_option("dedup", 1)
+    maps_d = ctx.search_images(imgs, r3, a3, 50.0, 0.5)
+    ctx.synchronize()
+    torch.cuda.synchronize(device)
+    t0.record()
+    ctx.search_images(imgs, r3, a3, 50.0, 0.5, maps=maps_d)
+    t1.record()
+    ctx.synchronize()
+    torch.cuda.synchronize(device)
+    sec_d = t0.elapsed_time(t1) / 1e3
+    n_distinct = ctx.stats()["targets"]
+    ctx.set_option("dedup", 0)
+    same_d = all(torch.equal(a, b) for m, m2 in zip(maps, maps_d) for a, b in zip(m, m2))
+    del maps_d
+    out["images_dedup"] = {"seconds": sec_d, "distinct_colours": n_distinct,
+                           "images_per_s": len(imgs) / sec_d,
+                           "effective_gcand_s": px * len(r3) * len(a3) / sec_d / 1e9,
+                           "maps_identical_to_search": same_d}
     out["images"] = {"workload": "48 images 256..3840 x 256..2160 (seed 0), 64 radii x 180 angles",
                      "pixels": px, "seconds": sec, "gcand_s": cand3 / sec / 1e9,
                      "images_per_s": len(imgs) / sec,

@@ -489,6 +489,12 @@ cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const c
  *                   cvs_search_colors_host, cvs_search_images and
  *                   cvs_lut_build; cvs_search_colors_multi, cvs_embed_image
  *                   and cvs_etab_build return CVS_ERR_INVALID_ARG while it is on.
+ *   "dedup"         1: cvs_search_images searches each distinct colour of the
+ *                   batch once (a pixel's maps depend only on its colour) and
+ *                   gathers the maps per pixel; the maps are identical.  The
+ *                   call then synchronises `stream` once (to size the search)
+ *                   and is not captured in a CUDA graph; the context keeps
+ *                   about 130 MB of tables for it.  Default 0.
  * Read-only values for cvs_get_option: "graph_launches" (graph replays so
  * far), "graphs_cached".
  * Unknown names or out-of-range values return CVS_ERR_INVALID_ARG. */

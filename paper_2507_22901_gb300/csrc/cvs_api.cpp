@@ -103,6 +103,13 @@ struct cvs_ctx {
     std::map<std::array<int64_t, 7>, LaunchShape> tuned;
     Acc* acc_tune = nullptr;
     int64_t cap_acc_tune = 0;
+    // per-batch colour de-duplication of the image search (option "dedup")
+    int dedup = 0;
+    uint8_t* d_present = nullptr;   // 2^24 bytes
+    int32_t* d_index = nullptr;     // 2^24 colour -> distinct-colour index
+    uint8_t* d_unique = nullptr;    // 3 x 2^24 distinct colours
+    int* d_scan = nullptr;          // 1024 block sums + the distinct count
+    int* h_unique = nullptr;        // pinned copy of the distinct count
     // pair lists of many colours: per-colour offsets into the caller's output
     int64_t* d_offs = nullptr;
     int64_t cap_offs = 0;
@@ -544,7 +551,8 @@ void cvs_destroy(cvs_ctx* c) {
     void* ptrs[] = {c->grid.r32, c->grid.sc32, c->grid.r64, c->grid.s64, c->grid.c64,
                     c->d_angles, c->d_status, c->tf, c->td, c->acc, c->qkey, c->counters,
                     c->dense, c->compact, c->d_imgs, c->d_in, c->d_maxr, c->d_count, c->d_pmask,
-                    c->d_rgb1, c->d_probe, c->d_order, c->ltab, c->d_offs};
+                    c->d_rgb1, c->d_probe, c->d_order, c->ltab, c->d_offs,
+                    c->d_present, c->d_index, c->d_unique, c->d_scan};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     drop_graphs(c);
@@ -553,6 +561,7 @@ void cvs_destroy(cvs_ctx* c) {
     if (c->tune_counters) cudaFree(c->tune_counters);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->h_counters) cudaFreeHost(c->h_counters);
+    if (c->h_unique) cudaFreeHost(c->h_unique);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->own) cudaStreamDestroy(c->own);
@@ -583,6 +592,9 @@ cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
         if (value != 0 && value != 1) return fail(CVS_ERR_INVALID_ARG, "graphs is 0 or 1");
         c->use_graphs = (int)value;
         if (!c->use_graphs) drop_graphs(c);
+    } else if (!std::strcmp(name, "dedup")) {
+        if (value != 0 && value != 1) return fail(CVS_ERR_INVALID_ARG, "dedup is 0 or 1");
+        c->dedup = (int)value;
     } else if (!std::strcmp(name, "max_dl")) {
         if (std::isnan(value)) return fail(CVS_ERR_INVALID_ARG, "max_dl is NaN");
         if (value >= 0.0 && !c->ltab) {  // built once, before any capture can need it
@@ -607,6 +619,7 @@ cvs_status cvs_get_option(cvs_ctx* c, const char* name, double* value) {
     else if (!std::strcmp(name, "autotune")) *value = c->autotune;
     else if (!std::strcmp(name, "graphs")) *value = c->use_graphs;
     else if (!std::strcmp(name, "max_dl")) *value = c->max_dl;
+    else if (!std::strcmp(name, "dedup")) *value = c->dedup;
     else if (!std::strcmp(name, "graph_launches")) *value = (double)c->graph_launches;
     else if (!std::strcmp(name, "graphs_cached")) *value = (double)c->graphs.size();
     else return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);
@@ -936,6 +949,34 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
     if (st0 == CVS_OK) st0 = check_thresholds(thr);
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (c->dedup) {  // one search per distinct colour of the batch
+        constexpr int64_t kColours = int64_t(1) << 24;
+        if (st0 == CVS_OK) st0 = ensure_targets(c, total < kColours ? total : kColours);
+        if (st0 != CVS_OK) return st0;
+        if (!c->d_present) {
+            CVS_CUDA(cudaMalloc(&c->d_present, (size_t)kColours));
+            CVS_CUDA(cudaMalloc(&c->d_index, sizeof(int32_t) * (size_t)kColours));
+            CVS_CUDA(cudaMalloc(&c->d_unique, 3 * (size_t)kColours));
+            CVS_CUDA(cudaMalloc(&c->d_scan, sizeof(int) * 1025));
+            CVS_CUDA(cudaMallocHost(&c->h_unique, sizeof(int)));
+        }
+        cudaStream_t st = (cudaStream_t)stream;
+        CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, n));
+        CVS_CUDA(cudaMemcpyAsync(c->d_imgs, h.data(), sizeof(ImageDesc) * n,
+                                 cudaMemcpyHostToDevice, st));
+        CVS_CUDA(launch_dedup_mark(c->d_imgs, n, total, c->d_present, st));
+        CVS_CUDA(launch_dedup_scan(c->d_present, c->d_scan, c->d_scan + 1024, c->d_index,
+                                   c->d_unique, st));
+        CVS_CUDA(cudaMemcpyAsync(c->h_unique, c->d_scan + 1024, sizeof(int),
+                                 cudaMemcpyDeviceToHost, st));
+        CVS_CUDA(cudaStreamSynchronize(st));
+        const int64_t nu = *c->h_unique;
+        CVS_CUDA(launch_setup_colors(c->d_unique, nu, c->grid.rmax, c->tf, c->td, c->acc, st));
+        st0 = run_search(c, nu, thr, prec, 0, 0, st);
+        if (st0 != CVS_OK) return st0;
+        CVS_CUDA(launch_dedup_gather(c->d_imgs, n, total, c->d_index, c->acc, st));
+        return CVS_OK;
+    }
     if (st0 == CVS_OK) st0 = ensure_targets(c, total);
     if (st0 != CVS_OK) return st0;
     cudaStream_t st = (cudaStream_t)stream;

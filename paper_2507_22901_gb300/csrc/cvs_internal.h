@@ -190,6 +190,17 @@ cudaError_t launch_compact_pairs(const cvs_pair* dense, int64_t n_dense, cvs_pai
 // out + offsets[b], keeping their order.
 cudaError_t launch_compact_pairs_batch(const cvs_pair* dense, int64_t kn, int64_t n_targets,
                                       const int64_t* offsets, cvs_pair* out, cudaStream_t st);
+// Per-batch colour de-duplication of the image search (cvs_dedup.cu).
+// mark: present[c] = 1 for every pixel colour c (the map is cleared first).
+cudaError_t launch_dedup_mark(const ImageDesc* imgs, int n_imgs, int64_t total, uint8_t* present,
+                              cudaStream_t st);
+// scan: index[c] = rank of present colour c, unique_rgb = the present colours
+// in colour order, *n_unique = their number; block_sums: 1024 ints of scratch.
+cudaError_t launch_dedup_scan(const uint8_t* present, int* block_sums, int* n_unique,
+                              int32_t* index, uint8_t* unique_rgb, cudaStream_t st);
+// gather: every pixel's maps from acc[index[its colour]].
+cudaError_t launch_dedup_gather(const ImageDesc* imgs, int n_imgs, int64_t total,
+                                const int32_t* index, const Acc* acc, cudaStream_t st);
 // L* of all 2^24 8-bit colours (index R << 16 | G << 8 | B), as step 1 forms it.
 cudaError_t launch_l_table(double* ltab, cudaStream_t st);
 cudaError_t launch_target_lab(const uint8_t* rgb, int64_t n, double* lab, cudaStream_t st);
