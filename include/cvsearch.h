@@ -495,6 +495,17 @@ cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const c
  *                   call then synchronises `stream` once (to size the search)
  *                   and is not captured in a CUDA graph; the context keeps
  *                   about 130 MB of tables for it.  Default 0.
+ *   "angle_ranges"  the FP32 search in gamut-reject mode on a folded, evenly
+ *                   spaced angle grid can first turn, per target and radius,
+ *                   bounds on the pair's linear RGB (a sinusoid in the angle
+ *                   plus a bounded rest) into the angle slots where a pair can
+ *                   stay in gamut with a channel able to read high, and then
+ *                   search only those slots; results are identical.  0: never;
+ *                   1: always; 2 (default): decided per grid and thresholds by
+ *                   a probe of 4096 targets spread over the first call (which
+ *                   synchronises `stream` once), where the ranges list under
+ *                   0.6 of the slots the plain search would walk.  The context
+ *                   keeps up to 256 MiB of scratch for the ranges.
  * Read-only values for cvs_get_option: "graph_launches" (graph replays so
  * far), "graphs_cached".
  * Unknown names or out-of-range values return CVS_ERR_INVALID_ARG. */

@@ -103,6 +103,15 @@ struct cvs_ctx {
     std::map<std::array<int64_t, 7>, LaunchShape> tuned;
     Acc* acc_tune = nullptr;
     int64_t cap_acc_tune = 0;
+    // the FP32 search walks per-radius angle ranges where the grid allows:
+    // 0 never, 1 always, 2 where a probe of the first call per grid and
+    // thresholds finds they list well under the slots of the plain walk
+    int angle_ranges = 2;
+    uint2* arc_ranges = nullptr;  // scratch of the angle ranges
+    int64_t cap_arc = 0;
+    unsigned long long* d_arc_probe = nullptr;
+    unsigned long long* h_arc_probe = nullptr;
+    std::map<std::array<int64_t, 5>, bool> arc_choice;
     // per-batch colour de-duplication of the image search (option "dedup")
     int dedup = 0;
     uint8_t* d_present = nullptr;   // 2^24 bytes
@@ -229,6 +238,17 @@ cvs_status ensure_grid(cvs_ctx* c, const cvs_grid* g) {
         if (!(s[m + N / 2] == -s[m] && co[m + N / 2] == -co[m])) sym = 0;
     d.sym = sym;
     d.H = sym ? N / 2 : N;
+    // Angle ranges need slot h at angle angles[0] + h * 360 / N, h < N / 2.
+    int even = sym;
+    const double step = 360.0 / N;
+    for (int m = 0; even && m < N / 2; ++m) {
+        const double want = g->angles_deg[0] + m * step;
+        if (!(std::fabs(g->angles_deg[m] - want) <= 1e-9 * (1.0 + std::fabs(want)))) even = 0;
+    }
+    d.arcs_ok = even;
+    d.th0 = (float)(g->angles_deg[0] * (3.14159265358979323846 / 180.0));
+    d.inv_step = even ? (float)(N / (2.0 * 3.14159265358979323846)) : 0.0f;
+    d.arcs = d.arcs_ok && c->angle_ranges;
     d.N = N;
     d.rmax = rmax;
     c->radii.assign(g->radii, g->radii + K);
@@ -239,6 +259,8 @@ cvs_status ensure_grid(cvs_ctx* c, const cvs_grid* g) {
 }
 
 void drop_graphs(cvs_ctx* c);
+
+cvs_status ensure_arc_scratch(cvs_ctx* c, int64_t n);
 
 cvs_status ensure_targets(cvs_ctx* c, int64_t n) {
     if (c->cap_tf < n || c->cap_td < n || c->cap_acc < n) {
@@ -260,7 +282,7 @@ cvs_status ensure_targets(cvs_ctx* c, int64_t n) {
         c->cap_td = n;
     }
     CVS_CUDA(grow(&c->acc, &c->cap_acc, n));
-    return CVS_OK;
+    return ensure_arc_scratch(c, n);  // before any capture can need it
 }
 
 void thresholds_to_int(const cvs_thresholds* t, int32_t* hi_min, int32_t* lo_max) {
@@ -365,6 +387,52 @@ cvs_status tune_shape(cvs_ctx* c, const SearchArgs& base, cudaStream_t st, Launc
     return status;
 }
 
+// Entries of angle-range scratch a search of n targets uses (one chunk).
+int64_t arc_entries(const cvs_ctx* c, int64_t n) {
+    const int64_t K = c->grid.K > 0 ? c->grid.K : 1;
+    const int64_t per_chunk = kArcScratchEntries / K > 0 ? kArcScratchEntries / K : 1;
+    return (n < per_chunk ? (n > 0 ? n : 1) : per_chunk) * K;
+}
+
+cvs_status ensure_arc_scratch(cvs_ctx* c, int64_t n) {
+    if (!c->grid.arcs) return CVS_OK;
+    const int64_t need = arc_entries(c, n);
+    if (c->cap_arc >= need) return CVS_OK;
+    drop_graphs(c);  // captured graphs point at the buffer about to be replaced
+    if (c->arc_ranges) CVS_CUDA(cudaFree(c->arc_ranges));
+    c->arc_ranges = nullptr;
+    c->cap_arc = 0;
+    CVS_CUDA(cudaMalloc(&c->arc_ranges, sizeof(uint2) * (size_t)need));
+    c->cap_arc = need;
+    return CVS_OK;
+}
+
+// Angle ranges pay where they list well under the slots a plain walk searches
+// (the walk over a list costs about a fifth more per slot, plus the ranges
+// pass): measure both counts on targets spread evenly over the call,
+// synchronously.
+constexpr int64_t kArcProbeTargets = 4096;
+constexpr double kArcProbeRatio = 0.6;
+
+cvs_status arc_probe(cvs_ctx* c, const SearchArgs& a, int64_t n, cudaStream_t st,
+                     std::map<std::array<int64_t, 5>, bool>::iterator* it,
+                     const std::array<int64_t, 5>& key) {
+    if (!c->d_arc_probe) {
+        CVS_CUDA(cudaMalloc(&c->d_arc_probe, 2 * sizeof(unsigned long long)));
+        CVS_CUDA(cudaMallocHost(&c->h_arc_probe, 2 * sizeof(unsigned long long)));
+    }
+    int64_t nt = n < kArcProbeTargets ? n : kArcProbeTargets;
+    if (nt * c->grid.K > a.arc_cap) nt = a.arc_cap / c->grid.K;
+    const int64_t stride = nt > 0 ? n / nt : 1;  // evenly over the call's targets
+    CVS_CUDA(launch_arc_probe(a, nt, stride, c->d_arc_probe, st));
+    CVS_CUDA(cudaMemcpyAsync(c->h_arc_probe, c->d_arc_probe, 2 * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, st));
+    CVS_CUDA(cudaStreamSynchronize(st));
+    const double covered = (double)c->h_arc_probe[0], plain = (double)c->h_arc_probe[1];
+    *it = c->arc_choice.emplace(key, covered < kArcProbeRatio * plain).first;
+    return CVS_OK;
+}
+
 cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_precision prec,
                       int list_mode, uint32_t target_id, cudaStream_t st, bool capturing = false) {
     SearchArgs a{};
@@ -390,6 +458,27 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
     a.stats = c->counters + 1;
     a.shape = c->shape;
     a.shape.kchunk = choose_kchunk(c, n, c->grid.K, c->grid.H);
+    a.num_sms = c->num_sms;
+    if (a.grid.arcs && prec == CVS_PREC_FP32_RECHECK) {
+        const int64_t need = arc_entries(c, n);
+        if (c->cap_arc < need && !capturing) {
+            cvs_status as = ensure_arc_scratch(c, n);
+            if (as != CVS_OK) return as;
+        }
+        if (c->cap_arc < need) a.grid.arcs = 0;  // (inside a capture) the plain walk
+        a.arc_ranges = c->arc_ranges;
+        a.arc_cap = c->cap_arc;
+        if (a.grid.arcs && !a.clip && c->angle_ranges == 2) {
+            const std::array<int64_t, 5> key = {c->grid_gen, a.hi_min, a.lo_max, a.mask2,
+                                                (int64_t)list_mode};
+            auto it = c->arc_choice.find(key);
+            if (it == c->arc_choice.end() && !capturing) {
+                cvs_status ps = arc_probe(c, a, n, st, &it, key);
+                if (ps != CVS_OK) return ps;
+            }
+            if (it != c->arc_choice.end() && !it->second) a.grid.arcs = 0;
+        }
+    }
     a.num_sms = c->num_sms;
     // a tuned shape applies when the caller has not fixed the shape by hand
     if (c->shape.kchunk == 0 && c->shape.blocks_per_sm == 0 && c->shape.block == kSearchBlock) {
@@ -552,7 +641,8 @@ void cvs_destroy(cvs_ctx* c) {
                     c->d_angles, c->d_status, c->tf, c->td, c->acc, c->qkey, c->counters,
                     c->dense, c->compact, c->d_imgs, c->d_in, c->d_maxr, c->d_count, c->d_pmask,
                     c->d_rgb1, c->d_probe, c->d_order, c->ltab, c->d_offs,
-                    c->d_present, c->d_index, c->d_unique, c->d_scan};
+                    c->d_present, c->d_index, c->d_unique, c->d_scan, c->arc_ranges,
+                    c->d_arc_probe};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     drop_graphs(c);
@@ -562,6 +652,7 @@ void cvs_destroy(cvs_ctx* c) {
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->h_counters) cudaFreeHost(c->h_counters);
     if (c->h_unique) cudaFreeHost(c->h_unique);
+    if (c->h_arc_probe) cudaFreeHost(c->h_arc_probe);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->own) cudaStreamDestroy(c->own);
@@ -595,6 +686,16 @@ cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
     } else if (!std::strcmp(name, "dedup")) {
         if (value != 0 && value != 1) return fail(CVS_ERR_INVALID_ARG, "dedup is 0 or 1");
         c->dedup = (int)value;
+    } else if (!std::strcmp(name, "angle_ranges")) {
+        if (value != 0 && value != 1 && value != 2)
+            return fail(CVS_ERR_INVALID_ARG, "angle_ranges is 0, 1 or 2");
+        c->angle_ranges = (int)value;
+        const int arcs = c->grid.arcs_ok && c->angle_ranges;
+        if (arcs != c->grid.arcs) {
+            drop_graphs(c);
+            c->grid.arcs = arcs;
+            c->tuned.clear();
+        }
     } else if (!std::strcmp(name, "max_dl")) {
         if (std::isnan(value)) return fail(CVS_ERR_INVALID_ARG, "max_dl is NaN");
         if (value >= 0.0 && !c->ltab) {  // built once, before any capture can need it
@@ -620,6 +721,7 @@ cvs_status cvs_get_option(cvs_ctx* c, const char* name, double* value) {
     else if (!std::strcmp(name, "graphs")) *value = c->use_graphs;
     else if (!std::strcmp(name, "max_dl")) *value = c->max_dl;
     else if (!std::strcmp(name, "dedup")) *value = c->dedup;
+    else if (!std::strcmp(name, "angle_ranges")) *value = c->angle_ranges;
     else if (!std::strcmp(name, "graph_launches")) *value = (double)c->graph_launches;
     else if (!std::strcmp(name, "graphs_cached")) *value = (double)c->graphs.size();
     else return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);

@@ -26,6 +26,10 @@ struct GridDev {
     int32_t K = 0, N = 0;      // radii, angles
     int32_t H = 0;             // angle slots per radius (N/2 when folded, else N)
     int32_t sym = 0;           // 1 if angles fold by +180 degrees
+    int32_t arcs_ok = 0;       // folded and evenly spaced: slot h at angle th0 + h pi / H
+    int32_t arcs = 0;          // the search walks per-radius angle ranges (arcs_ok and enabled)
+    float th0 = 0.0f;          // angle of slot 0 (radians)
+    float inv_step = 0.0f;     // slots per radian (H / pi)
     double rmax = 0.0;
     float* r32 = nullptr;      // K
     float2* sc32 = nullptr;    // N: (sin/500, -cos/200) in FP32
@@ -85,7 +89,13 @@ struct SearchArgs {
     unsigned long long* stats; // [0] flagged, [1] rechecked, [3] skipped, [4] pruned
     LaunchShape shape;
     int num_sms;
+    uint2* arc_ranges;         // angle ranges per (target, radius) of a chunk (grid.arcs, FP32)
+    int64_t arc_cap;           // entries of arc_ranges
 };
+
+// Entries of the angle-range scratch: targets are searched in chunks of
+// kArcScratchEntries / K (8 bytes per (target, radius)).
+constexpr int64_t kArcScratchEntries = int64_t(1) << 25;
 
 // The multi-threshold search: up to kMaxThresholdSets sets in one pass.
 constexpr int kMaxThresholdSets = 16;
@@ -168,6 +178,11 @@ cudaError_t launch_setup_colors(const uint8_t* rgb, int64_t n, double rmax, Targ
 cudaError_t launch_setup_images(const ImageDesc* imgs, int n_imgs, int64_t total, double rmax,
                                 TargetF32* tf, TargetF64* td, Acc* acc, cudaStream_t st);
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t st);
+// Slot counts of the angle ranges of targets 0, stride, ..., (nt - 1) stride:
+// counts[0] = slots the ranges list, counts[1] = slots of the radii a plain
+// walk searches.
+cudaError_t launch_arc_probe(const SearchArgs& a, int64_t nt, int64_t stride,
+                             unsigned long long* counts, cudaStream_t st);
 cudaError_t launch_finalize_colors(const Acc* acc, int64_t n, float* max_r, int32_t* count,
                                    uint8_t* pmask, cudaStream_t st);
 cudaError_t launch_search_multi(const MultiArgs& a, cudaStream_t st);

@@ -531,6 +531,349 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
     }
 }
 
+// ------------------------------------------------------------ angle-range items
+// k_arc_ranges writes, per (target, radius) of a chunk, up to two slot ranges
+// (start | len << 16; a third or more merged into the second, a superset) with
+// bit 31 of the first word set where the radius may reach the sRGB linear
+// segment, or kSlowRadius for a radius on the slow path (searched whole).
+// run_item_arcs concatenates, per warp, the ranges of up to kArcRadii radii
+// into a list and evaluates only the listed slots, 32 at a time whatever
+// radius they belong to; the rest certainly fail.  List entry j: al[j] =
+// radius offset (bits 0..6) | linear-segment bit (bit 7) | (first slot - first
+// position + kArcBias) << 8, and its first position pos[j] = al[kArcEntries
+// + j].  Fast-path radii's entries start at index 0, slow-path radii's (whole
+// radii) at kSlowBase; each region ends with a sentinel position.
+constexpr int kArcRadii = 128;
+constexpr int kSlowBase = kArcRadii * 2 + 1;
+constexpr int kArcEntries = kSlowBase + kArcRadii + 3;
+constexpr int kArcWords = 2 * kArcEntries;
+constexpr int kArcBias = 1 << 23;
+constexpr uint32_t kSlowRadius = 0xFFFFFFFFu;
+
+__device__ __forceinline__ int warp_exclusive_sum(int v, int& total) {
+    const unsigned lane = lane_id();
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+        if ((int)lane >= off) x += y;
+    }
+    total = __shfl_sync(0xFFFFFFFFu, x, 31);
+    return x - v;
+}
+
+// The slot of position p of a list region (entries up to jend, whose
+// sentinel position is pos[jend]): j0 is the entry holding position b - 1
+// (jbeg - 1 before the region), so the entries starting in [b, b + 31] are
+// among j0 + 1 .. j0 + 32, one per lane; a lane's entry is j0 plus the starts
+// at or before it.  Returns the entry word and advances j0 to the entry
+// holding b + 31.
+__device__ __forceinline__ uint32_t list_step(const uint32_t* al, int jend, int b, int& j0) {
+    const unsigned lane = lane_id();
+    const uint32_t* pos = al + kArcEntries;
+    const int ji = j0 + 1 + (int)lane;
+    const int d = ji <= jend ? (int)pos[ji] - b : 64;
+    const uint32_t starts = __reduce_or_sync(0xFFFFFFFFu, d < 32 ? 1u << d : 0u);
+    const int jj = j0 + __popc(starts & ((2u << lane) - 1u));
+    j0 += __popc(starts);
+    return al[jj];
+}
+
+// Queue the flagged slots of one segment of a list region (words [0, nwords)
+// of fb; bit i of word w of lane l = position seg + 32 (32 w + i) + l) into
+// pq, deciding each full batch of 32 with drain_flagged.
+template <bool FAST, bool DL>
+__device__ __forceinline__ void collect_list(const SearchArgs& A, const Smem& S, const ChainF32& C,
+                                             int64_t t, int kg, const uint32_t* al, int jbeg,
+                                             int jend, int seg, int nwords, uint32_t* fb,
+                                             uint32_t* pq, int& pq_n, Tally& acc, uint32_t* rq_t,
+                                             uint32_t* rq_kh, int& rq_n,
+                                             unsigned long long& n_flag,
+                                             unsigned long long& n_re) {
+    const unsigned lane = lane_id();
+    const uint32_t* pos = al + kArcEntries;
+    for (int w = 0; w < nwords; ++w) {
+        uint32_t bits = fb[w * 32 + lane];
+        fb[w * 32 + lane] = 0u;
+        while (true) {
+            const bool has = bits != 0u;
+            const unsigned ball = __ballot_sync(0xFFFFFFFFu, has);
+            if (!ball) break;
+            if (has) {
+                const int i = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int p = seg + 32 * (32 * w + i) + (int)lane;
+                int lo = jbeg, hi = jend - 1;  // the last entry starting at or before p
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if ((int)pos[mid] <= p) lo = mid; else hi = mid - 1;
+                }
+                const uint32_t e = al[lo];
+                const uint32_t k = (uint32_t)kg + (e & 127u);
+                const uint32_t h = (uint32_t)(p + (int)(e >> 8) - kArcBias);
+                pq[pq_n + __popc(ball & ((1u << lane) - 1u))] = k | (h << 16);
+                ++n_flag;
+            }
+            pq_n += __popc(ball);
+            __syncwarp();
+            if (pq_n >= 32) {
+                const TargetF32 T = A.tf[t];
+                drain_flagged<FAST, DL>(A, S, T, C, t, pq, 32, acc.cnt, acc.rmax, acc.pm, rq_t,
+                                        rq_kh, rq_n, n_re);
+                const int rest = pq_n - 32;
+                const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
+                __syncwarp();
+                if ((int)lane < rest) pq[lane] = mv;
+                __syncwarp();
+                pq_n = rest;
+            }
+        }
+    }
+}
+
+// Positions [pbeg, pend) of a list region (entries jbeg .. jend - 1, entry
+// jbeg starting at pbeg), 32 per step, in one slot variant (LINSEG fixed by
+// the caller); the last, partial step is peeled.  Flagged slots set their
+// bits in fb and are collected after each segment of kSegIters steps.
+template <bool FAST, bool LINSEG, bool LIST, bool DL>
+__device__ __forceinline__ void run_list(const SearchArgs& A, const Smem& S, const PairsT& P,
+                                         const PairsC& PC, const TargetF64& D, const ChainF32& C,
+                                         int64_t t, int kg, const uint32_t* al, int jbeg, int jend,
+                                         int pbeg, int pend, Tally& acc, uint32_t* fb,
+                                         uint32_t* pq, int& pq_n, uint32_t* rq_t, uint32_t* rq_kh,
+                                         int& rq_n, unsigned long long& n_flag,
+                                         unsigned long long& n_re) {
+    constexpr int PREC = CVS_PREC_FP32_RECHECK;
+    const unsigned lane = lane_id();
+    const int pfull = pbeg + ((pend - pbeg) & ~31);  // start of the partial step
+    int j0 = jbeg - 1;
+    for (int seg = pbeg; seg < pend; seg += 32 * kSegIters) {
+        const int seg_end = min(pend, seg + 32 * kSegIters);
+        int b = seg;
+        while (b < seg_end) {
+            const int q = (b - seg) >> 5;  // step index within the segment
+            const int w = q >> 5;
+            const int wend = min(seg_end, seg + 1024 * (w + 1));
+            uint32_t bits = 0, bit = 1u << (q & 31);
+            for (; b < min(wend, pfull); b += 32) {
+                const int p = b + (int)lane;
+                const uint32_t e = list_step(al, jend, b, j0);
+                const int k = kg + (int)(e & 127u), h = p + (int)(e >> 8) - kArcBias;
+                if (slot_step<PREC, FAST, false, false, LIST, LINSEG, DL>(A, S, P, PC, D, t, k, h,
+                                                                          true, acc))
+                    bits |= bit;
+                bit <<= 1;
+            }
+            if (b < wend) {  // the partial step
+                const int p = b + (int)lane;
+                const bool active = p < pend;
+                const uint32_t e = list_step(al, jend, b, j0);
+                const int k = kg + (int)(e & 127u), h = p + (int)(e >> 8) - kArcBias;
+                if (slot_step<PREC, FAST, true, false, LIST, LINSEG, DL>(A, S, P, PC, D, t, k, h,
+                                                                         active, acc))
+                    bits |= bit;
+                b = wend;
+            }
+            fb[w * 32 + lane] |= bits;
+        }
+        __syncwarp();
+        const int nsteps = (seg_end - seg + 31) >> 5;
+        collect_list<FAST, DL>(A, S, C, t, kg, al, jbeg, jend, seg, (nsteps + 31) >> 5, fb, pq,
+                               pq_n, acc, rq_t, rq_kh, rq_n, n_flag, n_re);
+    }
+}
+
+// A work item of the FP32 path (gamut reject) on a grid with angle ranges;
+// see above.
+template <bool LIST, bool DL>
+__device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S, int64_t t,
+                                              int k0, int k1, const ChainF32& C, uint32_t* pq,
+                                              uint32_t* fb, uint32_t* al, uint32_t* rq_t,
+                                              uint32_t* rq_kh, int& rq_n,
+                                              unsigned long long& n_flag,
+                                              unsigned long long& n_re,
+                                              unsigned long long& n_skip,
+                                              unsigned long long& n_prune) {
+    const unsigned lane = lane_id();
+    const int H = A.grid.H, K = A.grid.K;
+    TargetF64 D;
+    if (DL) D = A.td[t];
+    const PairsT P = make_pairs(A.tf[t]);
+    const PairsC PC = make_pairs(C);
+    Tally acc{0, -1.0f, 0u, 0u, 0u};
+    int pq_n = 0;
+    uint32_t* pos = al + kArcEntries;
+    const uint2* ranges = A.arc_ranges + t * K;
+    for (int kb = k0; kb < k1; kb += kArcRadii) {
+        const int kb1 = min(k1, kb + kArcRadii);
+        int nf = 0, pf = 0, ns = 0, ps = 0, jlin = -1, plin = 0;
+        for (int kg = kb; kg < kb1; kg += 32) {
+            const int k = kg + (int)lane;
+            const uint2 o = k < kb1 ? ranges[k] : make_uint2(0u, 0u);
+            const int slow = o.x == kSlowRadius ? 1 : 0;
+            const uint32_t w0 = slow ? 0u : (o.x & 0x7FFFFFFFu), w1 = slow ? 0u : o.y;
+            const int l0 = (int)(w0 >> 16), l1 = (int)(w1 >> 16);
+            const int n = (l0 > 0 ? 1 : 0) + (l1 > 0 ? 1 : 0);
+            const int tot = l0 + l1;
+            const uint32_t linbit = (slow || (o.x >> 31)) ? (1u << 7) : 0u;
+            if (k < kb1 && !slow) acc.prune += (uint32_t)(H - tot);
+            int nr, pr, nsr, psr;
+            const int eoff = nf + warp_exclusive_sum(n, nr);
+            const int poff = pf + warp_exclusive_sum(tot, pr);
+            const int soff = ns + warp_exclusive_sum(slow, nsr);
+            const int spoff = ps + warp_exclusive_sum(slow ? H : 0, psr);
+            // entries before the first one that may reach the linear segment skip its select
+            const unsigned lin_lanes = __ballot_sync(0xFFFFFFFFu, n > 0 && linbit);
+            if (jlin < 0 && lin_lanes) {
+                const int ll = __ffs(lin_lanes) - 1;
+                jlin = __shfl_sync(0xFFFFFFFFu, eoff, ll);
+                plin = __shfl_sync(0xFFFFFFFFu, poff, ll);
+            }
+            const uint32_t koff = (uint32_t)(k - kb);
+            int e = eoff, q = poff;
+            if (l0 > 0) {
+                al[e] = koff | linbit | ((uint32_t)((int)(w0 & 0xFFFFu) - q + kArcBias) << 8);
+                pos[e] = (uint32_t)q;
+                ++e;
+                q += l0;
+            }
+            if (l1 > 0) {
+                al[e] = koff | linbit | ((uint32_t)((int)(w1 & 0xFFFFu) - q + kArcBias) << 8);
+                pos[e] = (uint32_t)q;
+            }
+            if (slow) {
+                al[kSlowBase + soff] = koff | (1u << 7) | ((uint32_t)(kArcBias - spoff) << 8);
+                pos[kSlowBase + soff] = (uint32_t)spoff;
+            }
+            nf += nr;
+            pf += pr;
+            ns += nsr;
+            ps += psr;
+        }
+        if (jlin < 0) {
+            jlin = nf;
+            plin = pf;
+        }
+        if (lane == 0) {
+            pos[nf] = (uint32_t)pf;
+            pos[kSlowBase + ns] = (uint32_t)ps;
+        }
+        __syncwarp();
+        run_list<true, false, LIST, DL>(A, S, P, PC, D, C, t, kb, al, 0, jlin, 0, plin, acc, fb,
+                                        pq, pq_n, rq_t, rq_kh, rq_n, n_flag, n_re);
+        run_list<true, true, LIST, DL>(A, S, P, PC, D, C, t, kb, al, jlin, nf, plin, pf, acc, fb,
+                                       pq, pq_n, rq_t, rq_kh, rq_n, n_flag, n_re);
+        if (ns) {  // the slow path decides its own flagged slots
+            if (pq_n > 0) {
+                const TargetF32 T = A.tf[t];
+                drain_flagged<true, DL>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t,
+                                        rq_kh, rq_n, n_re);
+                pq_n = 0;
+            }
+            run_list<false, true, LIST, DL>(A, S, P, PC, D, C, t, kb, al, kSlowBase,
+                                            kSlowBase + ns, 0, ps, acc, fb, pq, pq_n, rq_t, rq_kh,
+                                            rq_n, n_flag, n_re);
+            if (pq_n > 0) {
+                const TargetF32 T = A.tf[t];
+                drain_flagged<false, DL>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t,
+                                         rq_kh, rq_n, n_re);
+                pq_n = 0;
+            }
+        }
+        __syncwarp();  // the list is rebuilt for the next block of radii
+    }
+    if (pq_n > 0) {
+        const TargetF32 T = A.tf[t];
+        drain_flagged<true, DL>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh,
+                                rq_n, n_re);
+    }
+    n_skip += acc.skip;
+    n_prune += acc.prune;
+    if (!LIST) {
+        int cnt = acc.cnt;
+        float rmax = acc.rmax;
+        uint32_t pm = acc.pm;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
+            rmax = fmaxf(rmax, __shfl_xor_sync(0xFFFFFFFFu, rmax, off));
+            pm |= __shfl_xor_sync(0xFFFFFFFFu, pm, off);
+        }
+        if (lane == 0 && cnt) {
+            Acc* ac = A.acc + t;
+            atomicAdd(&ac->count, cnt);
+            atomicMax(&ac->rmax_bits, __float_as_int(rmax));
+            atomicOr(&ac->pmask, pm >> 1);  // bit p-1 for pattern p
+        }
+    }
+}
+
+// The slot ranges of a chunk of targets (see run_item_arcs): one warp per
+// target, lanes over its radii.
+template <bool CLIP>
+__global__ void k_arc_ranges(const SearchArgs A, int64_t nt, uint2* __restrict__ out,
+                             unsigned long long* __restrict__ probe, int64_t stride) {
+    ChainF32 C;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        C.Ax[c] = __double2float_rn(__dmul_rn(c_MI[3 * c], c_W[0]));
+        C.Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
+    }
+    uint32_t chm = 0;
+#pragma unroll
+    for (int p = 1; p < 8; ++p) chm |= ((A.mask2 >> p) & 1u) ? (uint32_t)p : 0u;
+    const int K = A.grid.K, H = A.grid.H;
+    const unsigned lane = lane_id();
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long covered = 0, plain = 0;  // probe: slots listed / walked without ranges
+    for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < nt;
+         t += nwarps) {
+        const TargetF32 T = A.tf[t * stride];
+        for (int k = (int)lane; k < K; k += 32) {
+            const float r = __ldg(A.grid.r32 + k);
+            uint2 o;
+            if (!((T.flags & 1u) || fast_radius(T, r))) {
+                o = make_uint2(kSlowRadius, 0u);
+                if (probe) {
+                    covered += H;
+                    plain += H;
+                }
+            } else {
+                uint32_t rr[kMaxArcRanges];
+                int tot = 0;
+                bool lin = true;
+                const int n = radius_ranges_body<CLIP>(T, C, r, A.hi_min, chm, A.grid.th0,
+                                                       A.grid.inv_step, H, rr, tot, lin);
+                o.x = n > 0 ? rr[0] : 0u;
+                o.y = 0u;
+                if (n == 2) o.y = rr[1];
+                if (n > 2) {  // cover the second to the last range with one
+                    const uint32_t s1 = rr[1] & 0xFFFFu, last = rr[n - 1];
+                    const uint32_t e = (last & 0xFFFFu) + (last >> 16);
+                    o.y = s1 | ((e - s1) << 16);
+                }
+                if (lin) o.x |= 1u << 31;
+                if (probe) {
+                    covered += tot;
+                    plain += certain_fail_radius(T, C, r, A.hi_min) ? 0 : H;
+                }
+            }
+            out[t * K + k] = o;
+        }
+    }
+    if (probe) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            covered += __shfl_xor_sync(0xFFFFFFFFu, covered, off);
+            plain += __shfl_xor_sync(0xFFFFFFFFu, plain, off);
+        }
+        if (lane == 0 && plain) {
+            atomicAdd(probe, covered);
+            atomicAdd(probe + 1, plain);
+        }
+    }
+}
+
 // Launch bounds of the search kernel: blocks of up to CVS_SEARCH_MAX_THREADS
 // threads, at least CVS_SEARCH_MIN_BLOCKS of them resident per SM.
 #ifndef CVS_SEARCH_MAX_THREADS
@@ -539,9 +882,16 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
 #ifndef CVS_SEARCH_MIN_BLOCKS
 #define CVS_SEARCH_MIN_BLOCKS 6
 #endif
+#ifndef CVS_ARCS_MIN_BLOCKS
+#define CVS_ARCS_MIN_BLOCKS 6
+#endif
 
-template <int PREC, bool CLIP, bool LIST, bool DL>
-__global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
+// ARCS: the angle-range walk (FP32, gamut reject, a grid with angle ranges),
+// a separate instantiation so that the plain walk's code and registers stay
+// as they are without it.  (ARCS = false compiles no range walk at all.)
+template <int PREC, bool CLIP, bool LIST, bool DL, bool ARCS>
+__global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS,
+                                  ARCS ? CVS_ARCS_MIN_BLOCKS : CVS_SEARCH_MIN_BLOCKS)
     k_search(const SearchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = A.grid.K, H = A.grid.H;
@@ -555,6 +905,7 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
     S.rq_kh = S.rq_t + nwarps * kRqCap;
     uint32_t* pq = S.rq_kh + nwarps * kRqCap + warp * kRqCap;
     uint32_t* fb = S.rq_kh + 2 * nwarps * kRqCap + warp * (kFlagWords * 32);
+    uint32_t* al = S.rq_kh + 2 * nwarps * kRqCap + nwarps * (kFlagWords * 32) + warp * kArcWords;
     for (int w = 0; w < kFlagWords; ++w) fb[w * 32 + lane_id()] = 0u;
     build_decide_lut(S.lut, A.hi_min, A.lo_max);
     for (int i = threadIdx.x; i < K; i += blockDim.x) S.r2[i] = dup(A.grid.r32[i]);
@@ -585,7 +936,12 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS, CVS_SEARCH_MIN_BLOCKS)
         const int64_t t = (int64_t)(item / (unsigned long long)n_kc);
         const int kc = (int)(item - (unsigned long long)t * n_kc);
         const int k0 = kc * kchunk, k1 = min(k0 + kchunk, K);
-        if (PREC == CVS_PREC_FP32_RECHECK) {
+        // (a run-time test: the plain walk stays compiled into the range
+        // kernel, which measured faster than without it)
+        if (ARCS && PREC == CVS_PREC_FP32_RECHECK && !CLIP && A.grid.arcs) {
+            run_item_arcs<LIST, DL>(A, S, t, k0, k1, C, pq, fb, al, rq_t, rq_kh, rq_n, n_flag,
+                                          n_re, n_skip, n_prune);
+        } else if (PREC == CVS_PREC_FP32_RECHECK) {
             const uint32_t fl = A.tf[t].flags;
             if (fl & 1u)
                 run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
@@ -891,15 +1247,22 @@ cudaError_t launch_setup_images(const ImageDesc* imgs, int n_imgs, int64_t total
 
 int search_smem_bytes(const GridDev& g, int block) {
     // (r, r) pairs, angle quadruples, then per warp: FP64 queue (targets, slots)
-    // and flagged queue
+    // and flagged queue, and on grids with angle ranges the range list
     return ((g.K * 8 + 15) & ~15) + g.H * 16 + 3 * 512 +
-           (block / 32) * (kRqCap * 12 + kFlagWords * 32 * 4);
+           (block / 32) * (kRqCap * 12 + kFlagWords * 32 * 4 + (g.arcs ? kArcWords * 4 : 0));
 }
 
 template <int PREC, bool CLIP, bool LIST, bool DL>
-cudaError_t launch_search_t(const SearchArgs& a, cudaStream_t st) {
+cudaError_t launch_search_t(const SearchArgs& a_in, cudaStream_t st) {
+    SearchArgs a = a_in;
+    // (in clip mode only the high arcs prune, too few slots to pay for the walk)
+    const bool arcs = PREC == CVS_PREC_FP32_RECHECK && !CLIP && a.grid.arcs && a.arc_ranges &&
+                      a.arc_cap >= a.grid.K;
+    a.grid.arcs = arcs ? 1 : 0;
     const int smem = search_smem_bytes(a.grid, a.shape.block);
-    const void* fn = (const void*)k_search<PREC, CLIP, LIST, DL>;
+    constexpr bool kArcsKernel = PREC == CVS_PREC_FP32_RECHECK && !CLIP;
+    const void* fn = arcs ? (const void*)k_search<PREC, CLIP, LIST, DL, kArcsKernel>
+                          : (const void*)k_search<PREC, CLIP, LIST, DL, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = a.shape.blocks_per_sm;
@@ -908,8 +1271,34 @@ cudaError_t launch_search_t(const SearchArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
     }
-    k_search<PREC, CLIP, LIST, DL><<<a.num_sms * per_sm, a.shape.block, smem, st>>>(a);
-    return cudaGetLastError();
+    if (!arcs) {
+        k_search<PREC, CLIP, LIST, DL, false><<<a.num_sms * per_sm, a.shape.block, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    // angle ranges: per chunk of targets, the ranges pass, then the search
+    const int64_t chunk = a.arc_cap / a.grid.K;
+    for (int64_t t0 = 0; t0 < a_in.n_targets; t0 += chunk) {
+        const int64_t nt = a_in.n_targets - t0 < chunk ? a_in.n_targets - t0 : chunk;
+        SearchArgs c = a;
+        c.tf += t0;
+        c.td += t0;
+        c.acc += t0;
+        c.n_targets = nt;
+        c.target_id = a.target_id + (uint32_t)t0;
+        if (c.dense) c.dense += t0 * (int64_t)a.grid.K * a.grid.N;
+        if (t0 > 0) {
+            e = cudaMemsetAsync(c.work_counter, 0, sizeof(unsigned long long), st);
+            if (e != cudaSuccess) return e;
+        }
+        const int64_t want = (nt + 7) / 8, cap = (int64_t)a.num_sms * 16;  // 8 warps a block
+        k_arc_ranges<false><<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(
+            c, nt, c.arc_ranges, nullptr, 1);
+        k_search<PREC, CLIP, LIST, DL, kArcsKernel><<<a.num_sms * per_sm, a.shape.block, smem, st>>>(
+            c);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <int PREC, bool DL>
@@ -923,6 +1312,16 @@ cudaError_t launch_search_d(const SearchArgs& a, cudaStream_t st) {
 template <int PREC>
 cudaError_t launch_search_p(const SearchArgs& a, cudaStream_t st) {
     return a.ltab ? launch_search_d<PREC, true>(a, st) : launch_search_d<PREC, false>(a, st);
+}
+
+cudaError_t launch_arc_probe(const SearchArgs& a, int64_t nt, int64_t stride,
+                             unsigned long long* counts, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess || nt <= 0) return e;
+    const int64_t want = (nt + 7) / 8, cap = (int64_t)a.num_sms * 16;
+    k_arc_ranges<false><<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(a, nt, a.arc_ranges,
+                                                                            counts, stride);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_search(const SearchArgs& a, cudaStream_t st) {

@@ -273,6 +273,258 @@ __device__ __forceinline__ int first_linseg_radius(const TargetF32& T, const Cha
     return k1;
 }
 
+// ------------------------------------------------------------ angle ranges
+// At radius r the pair's linear RGB, channel c, is lin0 + E(j) +- O(j) with
+// u = U sin j, w = -V cos j (U = r/500, V = r/200) and, from the cubic
+// expansion of f^-1 about the target,
+//   O(j) = Ax (c2x u + u^3) + Bz (c2z w + w^3)       (odd part)
+//   E(j) = Ax c1x u^2 + Bz c1z w^2                   (even part).
+// Since sin^3 = (3 sin - sin 3j)/4 and cos^3 = (3 cos + cos 3j)/4,
+//   O(j) = alpha sin j + beta cos j + rho(j),
+//   alpha = Ax U (c2x + 3U^2/4), beta = -Bz V (c2z + 3V^2/4),
+//   |rho| <= eps = sqrt((Ax U^3)^2 + (Bz V^3)^2) / 4,
+// and E(j) = P sin^2 j + Q cos^2 j lies between P = Ax c1x U^2 and
+// Q = Bz c1z V^2.  With R = |(alpha, beta)| and j0 the zero of the sinusoid,
+// |O(j)| is within eps of R |sin(j - j0)|, a function of period pi.  So:
+// - gamut (reject): both colours in range need |O| <= G = min(lin0 + max(P,Q)
+//   - lo_out, hi_out - lin0 - min(P,Q)), i.e. |sin(j - j0)| <= (G + eps)/R:
+//   an arc about j0;
+// - a high channel needs codes hi_min apart, which by the concavity bound of
+//   high_possible needs 2|O| >= tau = v^-1(v(lo) + hi_min - 1) - lo: outside
+//   the arc |sin(j - j0)| < (tau/2 - eps)/R about j0.
+// A slot can pass only inside every gamut arc and outside the "low" arc of at
+// least one channel that an enabled pattern needs high.  radius_ranges_body turns
+// these arcs into slot-index ranges of a folded, evenly spaced grid (slot h
+// at th0 + h pi/H) and intersects them by a sweep over their end points.
+// Every bound carries margins far above its FP32 rounding: arguments of asin
+// by a relative 1e-4, angles by 2e-4 rad, linear values by 1e-5.
+constexpr int kMaxArcRanges = 4;  // more ranges fall back to the whole radius
+constexpr float kArcAngleMargin = 2e-4f;
+
+// Arc tangent of y/x in [-pi, pi] for the angle ranges, branch-free: octant
+// reduction to t = min/max in [0, 1] and an odd polynomial of degree 11 in t
+// (coefficients fitted here by weighted least squares on [0, 1]; largest
+// error 1.8e-6 rad in FP32, two orders below kArcAngleMargin).
+__device__ __forceinline__ float atan2_arc(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(fmaxf(ax, ay), 1e-30f), mn = fminf(ax, ay);
+    const float t = __fdividef(mn, mx), s = t * t;
+    float p = -0.01171913929283619f;
+    p = fmaf(p, s, 0.052647363394498825f);
+    p = fmaf(p, s, -0.1164264902472496f);
+    p = fmaf(p, s, 0.19354037940502167f);
+    p = fmaf(p, s, -0.33262282609939575f);
+    p = fmaf(p, s, 0.9999772310256958f);
+    float a = p * t;
+    a = ay > ax ? 1.5707963267948966f - a : a;
+    a = x < 0.0f ? 3.141592653589793f - a : a;
+    return copysignf(a, y);
+}
+
+// Arc sine of x in [0, 0.9999] (callers treat larger arguments separately).
+__device__ __forceinline__ float asin_arc(float x) {
+    const float c2 = fmaxf(1.0f - x * x, 1e-30f);
+    return atan2_arc(x, c2 * rsqrtf(c2));
+}
+
+// The encode bound v(x) of high_possible and a lower bound of its inverse
+// (the x with v(x) >= y), on the approximate MUFU log and exp; callers keep
+// margins far above their errors (relative 2^-21).  v steps down by about
+// 0.007 code units at the segment boundary, so near it both inverse
+// branches are taken.
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float v_enc_fast(float x) {
+    const float pw = fmaf(269.025f, ex2_approx((5.0f / 12.0f) * lg2_approx(fmaxf(x, 1e-30f))), -14.025f);
+    return x <= 0.0031308f ? 3294.6f * x : pw;
+}
+__device__ __forceinline__ float v_inv_fast(float y) {
+    const float pw = ex2_approx(2.4f * lg2_approx(fmaxf((y + 14.025f) * (1.0f / 269.025f), 1e-30f)));
+    return y <= 10.32f ? fminf(y * (1.0f / 3294.6f), pw) : pw;
+}
+
+// True when every candidate at radius r of target T stays on the cubic branch
+// of f^-1 (f-values above 6/29 by a margin far above their FP32 rounding).
+__device__ __forceinline__ bool fast_radius(const TargetF32& T, float r) {
+    const float lim = (float)kFinvBreak * 1.00001f + 1e-6f;
+    return T.fx0 - r * 0.002f * 1.00001f > lim && T.fz0 - r * 0.005f * 1.00001f > lim;
+}
+
+// Slots within circular distance `half` (index units) of centre c in
+// (-H, 2H), as a circular range (start, len) over H slots; len 0 = none,
+// len H = all.  Branch-free.
+__device__ __forceinline__ void arc_range(float c, float half, int H, int& start, int& len) {
+    const float hh = fminf(half, 0.5f * (float)H);
+    const int a = (int)ceilf(c - hh), b = (int)floorf(c + hh);
+    int l = b - a + 1;
+    int s0 = a < 0 ? a + H : a;
+    s0 = s0 >= H ? s0 - H : s0;
+    const bool none = !(half >= 0.0f) || l <= 0;
+    const bool all = !none && (half >= 0.5f * (float)H || l >= H);
+    len = none ? 0 : (all ? H : l);
+    start = (none || all) ? 0 : s0;
+}
+
+// Gamut and low arcs of channel c at radius r as circular slot ranges:
+// (gamut start, gamut len, low start, low len); gamut len -1 = no pair of the
+// radius is in gamut.
+__device__ __forceinline__ int4 channel_ranges(const TargetF32 T, const ChainF32 C, float r, int c,
+                                              int32_t hi_min, int need_high, int clip, float th0,
+                                              float inv_step, int H, float& lo_out) {
+    const float U = r * 0.002f, V = r * 0.005f;
+    const float Ui = U * 1.00001f, Vi = V * 1.00001f;
+    const float ax = c == 0 ? C.Ax[0] : (c == 1 ? C.Ax[1] : C.Ax[2]);
+    const float bz = c == 0 ? C.Bz[0] : (c == 1 ? C.Bz[1] : C.Bz[2]);
+    const float l0 = c == 0 ? T.lin0[0] : (c == 1 ? T.lin0[1] : T.lin0[2]);
+    const float alpha = ax * U * (T.c2x + 0.75f * U * U);
+    const float beta = -bz * V * (T.c2z + 0.75f * V * V);
+    const float R2 = fmaxf(alpha * alpha + beta * beta, 1e-30f);
+    const float invR = rsqrtf(R2) * 1.00001f;  // 1/R, rounded up
+    const float au = ax * Ui * Ui * Ui, bv = bz * Vi * Vi * Vi;
+    const float e2 = fmaxf(au * au + bv * bv, 1e-36f);
+    const float eps = 0.25f * e2 * rsqrtf(e2) * 1.0001f + 1e-7f;
+    float cidx = (atan2_arc(-beta, alpha) - th0) * inv_step;
+    cidx -= (float)H * floorf(cidx * (1.0f / (float)H));
+    int4 o;
+    if (clip) {
+        o.x = 0;
+        o.y = H;
+    } else {
+        const float P = ax * T.c1x * U * U, Q = bz * T.c1z * V * V;
+        const float G = fminf(l0 + fmaxf(P, Q) - kLinOutLo, kLinOutHi - l0 - fminf(P, Q)) + eps +
+                        1e-5f;
+        const float x = G * invR * 1.0001f + 1e-6f;
+        const float half = (asin_arc(fminf(x, 0.9999f)) + kArcAngleMargin) * inv_step;
+        arc_range(cidx, x >= 0.9999f ? (float)H : half, H, o.x, o.y);
+        if (G < 0.0f) o.y = -1;
+    }
+    // the lower bound of lin_lower_bound, per channel
+    const float xlo = -Ui * (T.c2x - Ui * (T.c1x - Ui)), xhi = Ui * (T.c2x + Ui * (T.c1x + Ui));
+    const float zlo = -Vi * (T.c2z - Vi * (T.c1z - Vi)), zhi = Vi * (T.c2z + Vi * (T.c1z + Vi));
+    const float ends = l0 + fminf(ax * xlo, ax * xhi) + fminf(bz * zlo, bz * zhi);
+    const float p = ax * T.c2x * Ui, q = bz * T.c2z * Vi;
+    const float pq2 = fmaxf(p * p + q * q, 1e-36f);
+    const float coupled = l0 - pq2 * rsqrtf(pq2) * 1.00001f + fminf(0.0f, ax * T.c1x) * Ui * Ui +
+                          fminf(0.0f, bz * T.c1z) * Vi * Vi -
+                          (fabsf(ax) * Ui * Ui * Ui + fabsf(bz) * Vi * Vi * Vi);
+    float lo = fmaxf(ends, coupled) - 1e-5f;
+    lo_out = lo;
+    if (!clip) lo = fmaxf(lo, kLinOutLo);
+    const float y = v_enc_fast(lo) + (float)hi_min - 1.02f;
+    const float tau = (v_inv_fast(y) - lo) * 0.9999f - 3e-6f;
+    const float x = (0.5f * tau - eps) * invR * 0.9999f - 1e-6f;
+    const float half = (asin_arc(fminf(x, 0.9999f)) - kArcAngleMargin) * inv_step;
+    // no low arc where x <= 0; all slots where x >= 1 or the channel is not needed
+    const bool all_low = x >= 1.0f || !need_high;
+    arc_range(cidx, all_low ? (float)H : (x > 0.0f ? half : -1.0f), H, o.z, o.w);
+    return o;
+}
+
+// Feasible slot ranges of radius r for a fast-path target: writes up to
+// kMaxArcRanges entries (start | len << 16), disjoint and ascending, to out
+// and returns their number; total = slots covered; lin = some candidate may
+// reach the sRGB linear segment (its lower bound, as in pow_branch_only, is
+// not above the segment by 2e-5).  chm: channels an enabled pattern needs
+// high (bit 2 - c for channel c).
+template <bool CLIP>
+__device__ __forceinline__ int radius_ranges_body(const TargetF32& T, const ChainF32& C, float r,
+                                                  int32_t hi_min, uint32_t chm, float th0,
+                                                  float inv_step, int H, uint32_t* out,
+                                                  int& total, bool& lin) {
+    int rs[6], rl[6];  // ranges 0..2: gamut arcs, 3..5: low arcs
+    bool empty = false;
+    lin = false;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float lo;
+        const int4 o = channel_ranges(T, C, r, c, hi_min, (chm >> (2 - c)) & 1u, CLIP ? 1 : 0, th0,
+                                      inv_step, H, lo);
+        lin |= !(lo > 0.0031308f + 1e-5f);
+        empty |= o.y < 0;
+        rs[c] = o.x;
+        rl[c] = max(o.y, 0);
+        rs[3 + c] = o.z;
+        rl[3 + c] = o.w;
+    }
+    total = 0;
+    // no slot: a gamut arc is empty, or no channel can be high anywhere
+    if (empty || (rl[0] == 0 || rl[1] == 0 || rl[2] == 0) ||
+        (rl[3] == H && rl[4] == H && rl[5] == H))
+        return 0;
+    // every slot: all gamut arcs whole and some channel free of a low arc
+    if (rl[0] == H && rl[1] == H && rl[2] == H && (rl[3] == 0 || rl[4] == 0 || rl[5] == 0)) {
+        out[0] = (uint32_t)H << 16;
+        total = H;
+        return 1;
+    }
+    // membership of slot 0, and the positions (> 0) where a range is entered or left
+    constexpr int kSentinel = 0x7FFFFFFF;
+    uint32_t state = 0;
+    int ev[12];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const int s0 = rs[i], l = rl[i];
+        const bool partial = l > 0 && l < H;
+        if (l >= H || (partial && (s0 == 0 || s0 + l > H))) state |= 1u << i;
+        const int e1 = s0 + l >= H ? s0 + l - H : s0 + l;
+        ev[2 * i] = (partial && s0 > 0) ? (s0 << 3) | i : kSentinel;
+        ev[2 * i + 1] = (partial && e1 > 0) ? (e1 << 3) | i : kSentinel;
+    }
+    // sort the 12 keys (position, range): Batcher's odd-even merge network for
+    // 16 keys restricted to 12 (41 comparators; checked on all 0/1 inputs)
+    constexpr int kNet[41][2] = {
+        {0, 1}, {2, 3}, {0, 2}, {1, 3}, {1, 2}, {4, 5}, {6, 7}, {4, 6}, {5, 7}, {5, 6}, {0, 4},
+        {2, 6}, {2, 4}, {1, 5}, {3, 7}, {3, 5}, {1, 2}, {3, 4}, {5, 6}, {8, 9}, {10, 11}, {8, 10},
+        {9, 11}, {9, 10}, {0, 8}, {4, 8}, {2, 10}, {6, 10}, {2, 4}, {6, 8}, {1, 9}, {5, 9}, {3, 11},
+        {7, 11}, {3, 5}, {7, 9}, {1, 2}, {3, 4}, {5, 6}, {7, 8}, {9, 10}};
+#pragma unroll
+    for (int q = 0; q < 41; ++q) {
+        const int a = kNet[q][0], b = kNet[q][1];
+        const int lo2 = min(ev[a], ev[b]), hi2 = max(ev[a], ev[b]);
+        ev[a] = lo2;
+        ev[b] = hi2;
+    }
+    // F = inside all gamut arcs and outside the low arc of some channel
+    auto feasible = [](uint32_t st) { return (st & 7u) == 7u && ((~st >> 3) & 7u) != 0u; };
+    bool cur = feasible(state);
+    int start = 0, n = 0;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        const int key = ev[i];
+        const bool valid = key != kSentinel;
+        state ^= valid ? 1u << (key & 7) : 0u;
+        const int pos = key >> 3;
+        const bool last = i == 11 || (ev[i + 1 < 12 ? i + 1 : 11] >> 3) != pos;
+        const bool nf = feasible(state);
+        const bool change = valid && last && nf != cur;
+        const bool close = change && !nf;
+        if (close && n < kMaxArcRanges) out[n] = (uint32_t)start | ((uint32_t)(pos - start) << 16);
+        total += close ? pos - start : 0;
+        n += close ? 1 : 0;
+        start = (change && nf) ? pos : start;
+        cur = change ? nf : cur;
+    }
+    if (cur) {
+        if (n < kMaxArcRanges) out[n] = (uint32_t)start | ((uint32_t)(H - start) << 16);
+        ++n;
+        total += H - start;
+    }
+    if (n > kMaxArcRanges) {  // unusual: cover the whole radius instead
+        out[0] = (uint32_t)H << 16;
+        n = 1;
+        total = H;
+    }
+    return n;
+}
+
 // Embedding-signal decision on biased codes y = kMagicBits + q (exact when no
 // code is flagged).  Per channel the difference d = q+ - q- indexes a 512-entry
 // table in shared memory (index d & 511): bit 3 = neither high nor low, bit

@@ -129,16 +129,26 @@ def test_embedding_matches_oracle(ctx, torch_cuda, name):
     assert np.array_equal(ch.cpu().numpy().reshape(-1).view(np.uint32), ec)
 
 
-def test_both_prunes_run_on_the_cube_grid(ctx, torch_cuda):
-    """On the colour-cube grid both prunes must fire (else the tests above
-    would not exercise them) and the results still equal the oracle."""
+@pytest.mark.parametrize("angle_ranges", [0, 1])
+def test_prunes_run_on_the_cube_grid(ctx, torch_cuda, angle_ranges):
+    """On the colour-cube grid the prunes must fire (else the tests above would
+    not exercise them) and the results still equal the oracle: without angle
+    ranges the radius bound and the out-of-gamut warp skip, with them the
+    per-radius angle ranges."""
     cube = W.color_cube(16)
     radii, ang = W.grid(2)
-    out = ctx.search_colors(dev(torch_cuda, cube), radii, ang, 50.0, 0.5)
-    ctx.synchronize()
-    st = ctx.stats()
+    ctx.set_option("angle_ranges", angle_ranges)
+    try:
+        out = ctx.search_colors(dev(torch_cuda, cube), radii, ang, 50.0, 0.5)
+        ctx.synchronize()
+        st = ctx.stats()
+    finally:
+        ctx.set_option("angle_ranges", 2)
     cand = len(cube) * len(radii) * len(ang)
     assert st["candidates"] == cand
-    assert st["pruned"] > 0.05 * cand and st["skipped"] > 0.2 * cand
+    if angle_ranges:
+        assert st["pruned"] > 0.5 * cand
+    else:
+        assert st["pruned"] > 0.05 * cand and st["skipped"] > 0.2 * cand
     exp = oracle.search_colors(cube, radii, ang, 50.0, 0.5, threads=THREADS)
     same(tuple(x.cpu().numpy() for x in out), exp, "cube step 16")
