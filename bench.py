@@ -43,7 +43,7 @@ LANES_PER_SM_CLK = 128
 # summarised in profiles/k_search_fp32_colour_cube_full.md (32,768-colour case
 # scaled by 8, traffic being proportional to the colours).  Valid only for the
 # kernel source it was taken from; otherwise the roofline reports null.
-TRAFFIC_CAPTURE = {"source_sha256_16": "f344b0e05f22c3b9", "bytes_per_launch": 8 * 3.205632e6}
+TRAFFIC_CAPTURE = {"source_sha256_16": "e75bc554f621302e", "bytes_per_launch": 8 * 36.68864e6}
 
 
 def kernel_source_hash() -> str:
@@ -575,7 +575,7 @@ def run_ours(args, world, rank, local):
     # ---- timed region: device-resident inputs, L2 flushed between steps
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
-    step_ms, kern_ms, flagged, rechecked, skipped, pruned = [], [], 0, 0, 0, 0
+    step_ms, kern_ms, ranges_ms, flagged, rechecked, skipped, pruned = [], [], [], 0, 0, 0, 0
     barrier(world)
     torch.cuda.synchronize(device)
     with ClockSampler(local) as clk:
@@ -587,7 +587,8 @@ def run_ours(args, world, rank, local):
             ctx.synchronize(stream)
             step_ms.append(start.elapsed_time(end))
             st = ctx.stats()
-            kern_ms.append(st["search_ms"])
+            kern_ms.append(st["search_ms"] - st["ranges_ms"])
+            ranges_ms.append(st["ranges_ms"])
             flagged += st["flagged"]
             rechecked += st["rechecked"]
             skipped += st["skipped"]
@@ -639,6 +640,8 @@ def run_ours(args, world, rank, local):
     c = clk.summary()
     f_mhz = c["sm_mhz"] or 2070.0
     kern_avg_s = sum(kern_ms) / len(kern_ms) / 1e3
+    ranges_avg_ms = sum(ranges_ms) / len(ranges_ms)
+    chunks = -(-n * 128 // (1 << 25)) if ranges_avg_ms > 0 else 0  # angle-range passes per step
     skip_c = skipped / args.steps  # per launch
     prune_c = pruned / args.steps  # rejected by the per-radius bound: no per-candidate work
     alg_ops = ALG_ISSUES_PER_CAND * (cand - skip_c - prune_c) + ALG_ISSUES_PER_SKIPPED * skip_c
@@ -665,8 +668,9 @@ def run_ours(args, world, rank, local):
                     "window_code_units": ctx.get_option("fp32_window")},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(rgb_h.nbytes),
                 "d2h_bytes_per_step": int(n * 9), "matches_device_result": e2e_match},
-        "gpu_launches": 3 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "k_search<fp32>", "achieved": achieved,
+        "gpu_launches": (3 + chunks) * args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_search<fp32>" + (" (angle ranges)" if chunks else ""),
+                     "achieved": achieved,
                      "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                      "traffic": (TRAFFIC_CAPTURE["bytes_per_launch"]
                                  if kernel_source_hash() == TRAFFIC_CAPTURE["source_sha256_16"]
@@ -677,7 +681,9 @@ def run_ours(args, world, rank, local):
                      "ops_per_skipped_candidate": ALG_ISSUES_PER_SKIPPED,
                      "skipped_fraction": skip_c / cand,
                      "pruned_fraction": prune_c / cand,
-                     "kernel_ms": kern_avg_s * 1e3},
+                     "kernel_ms": kern_avg_s * 1e3,
+                     "ranges_pass_ms": ranges_avg_ms,
+                     "ranges_pass_share": ranges_avg_ms / (ranges_avg_ms + kern_avg_s * 1e3)},
         "clocks": {"sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"],
                    "reasons": c["reasons"], "samples": c["samples"]},
     }

@@ -146,7 +146,10 @@ typedef struct {
                                 certainly outside the range of codes 0..255 */
     int64_t pruned;          /* candidates rejected without any work: radii below the
                                 first one where, by a bound on the pair's code
-                                difference, some channel could be high */
+                                difference, some channel could be high, and (option
+                                "angle_ranges") slots outside a radius's ranges */
+    double ranges_ms;        /* of search_ms, the angle-ranges pass before the search
+                                kernel (first chunk of targets; 0 without it) */
 } cvs_stats;
 
 /* ---------------------------------------------------------------- context */

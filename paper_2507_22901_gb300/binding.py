@@ -64,7 +64,8 @@ class cvs_stats(ctypes.Structure):
                 ("flagged", ctypes.c_int64), ("rechecked", ctypes.c_int64),
                 ("targets", ctypes.c_int64), ("symmetric", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("search_ms", ctypes.c_double),
-                ("skipped", ctypes.c_int64), ("pruned", ctypes.c_int64)]
+                ("skipped", ctypes.c_int64), ("pruned", ctypes.c_int64),
+                ("ranges_ms", ctypes.c_double)]
 
 
 class cvs_precision_report(ctypes.Structure):

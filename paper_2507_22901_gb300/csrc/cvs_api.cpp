@@ -98,6 +98,8 @@ struct cvs_ctx {
     cvs_stats last{};
     bool last_pending = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the search kernel
+    cudaEvent_t ev_mid = nullptr;  // after the angle-ranges pass (first chunk)
+    bool last_arcs = false;        // the last search took the angle ranges
     // autotuning: best launch shape per (grid, precision, modes, size bucket)
     int autotune = 0;
     std::map<std::array<int64_t, 7>, LaunchShape> tuned;
@@ -495,6 +497,10 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
     }
     const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     CVS_CUDA(cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st));
+    a.ev_ranges = c->ev_mid;
+    a.ev_flags = ev_flags;
+    c->last_arcs = a.grid.arcs && !a.clip && prec == CVS_PREC_FP32_RECHECK && a.arc_ranges &&
+                   a.arc_cap >= a.grid.K;
     CVS_CUDA(cudaEventRecordWithFlags(c->ev0, st, ev_flags));
     CVS_CUDA(launch_search(a, st));
     CVS_CUDA(cudaEventRecordWithFlags(c->ev1, st, ev_flags));
@@ -583,6 +589,9 @@ void collect_stats(cvs_ctx* c) {
     if (!c->last_pending) return;
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) c->last.search_ms = ms;
+    c->last.ranges_ms = 0.0;
+    if (c->last_arcs && cudaEventElapsedTime(&ms, c->ev0, c->ev_mid) == cudaSuccess)
+        c->last.ranges_ms = ms;
     const int f = c->grid.sym ? 2 : 1;
     c->last.flagged = (int64_t)c->h_counters[1] * f;
     c->last.rechecked = (int64_t)c->h_counters[2] * f;
@@ -622,6 +631,7 @@ cvs_status cvs_create(cvs_ctx** out, int device) {
     if (e == cudaSuccess) e = cudaMalloc(&c->d_probe, 32);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev_mid);
     if (e == cudaSuccess) e = copy_qkeys_to(c->qkey, c->own);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->own);
     if (e != cudaSuccess) {
@@ -655,6 +665,7 @@ void cvs_destroy(cvs_ctx* c) {
     if (c->h_arc_probe) cudaFreeHost(c->h_arc_probe);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->ev_mid) cudaEventDestroy(c->ev_mid);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
 }
@@ -979,6 +990,7 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
     CVS_CUDA(launch_init_acc(c->acc_multi, n * n_thr, st));
     CVS_CUDA(cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st));
+    c->last_arcs = false;
     CVS_CUDA(cudaEventRecord(c->ev0, st));
     CVS_CUDA(launch_search_multi(a, st));
     CVS_CUDA(cudaEventRecord(c->ev1, st));
@@ -1166,6 +1178,7 @@ cvs_status cvs_embed_image(cvs_ctx* c, const cvs_image* img, const uint8_t* patt
     a.stats = c->counters + 1;
     a.num_sms = c->num_sms;
     CVS_CUDA(cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st));
+    c->last_arcs = false;
     CVS_CUDA(cudaEventRecord(c->ev0, st));
     CVS_CUDA(launch_embed(a, st));
     CVS_CUDA(cudaEventRecord(c->ev1, st));
@@ -1397,6 +1410,7 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
     a.num_sms = c->num_sms;
     cudaStream_t st = (cudaStream_t)stream;
     e = cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st);
+    c->last_arcs = false;
     if (e == cudaSuccess) e = cudaEventRecord(c->ev0, st);
     for (int64_t first = 0; first < kColours && e == cudaSuccess; first += kChunk) {
         a.key = keys;

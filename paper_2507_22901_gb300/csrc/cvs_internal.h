@@ -91,6 +91,8 @@ struct SearchArgs {
     int num_sms;
     uint2* arc_ranges;         // angle ranges per (target, radius) of a chunk (grid.arcs, FP32)
     int64_t arc_cap;           // entries of arc_ranges
+    void* ev_ranges;           // host: a cudaEvent_t recorded after the first ranges pass, or NULL
+    unsigned ev_flags;         // host: its record flags
 };
 
 // Entries of the angle-range scratch: targets are searched in chunks of

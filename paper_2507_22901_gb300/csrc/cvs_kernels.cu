@@ -1293,6 +1293,10 @@ cudaError_t launch_search_t(const SearchArgs& a_in, cudaStream_t st) {
         const int64_t want = (nt + 7) / 8, cap = (int64_t)a.num_sms * 16;  // 8 warps a block
         k_arc_ranges<false><<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(
             c, nt, c.arc_ranges, nullptr, 1);
+        if (t0 == 0 && a.ev_ranges) {
+            e = cudaEventRecordWithFlags((cudaEvent_t)a.ev_ranges, st, a.ev_flags);
+            if (e != cudaSuccess) return e;
+        }
         k_search<PREC, CLIP, LIST, DL, kArcsKernel><<<a.num_sms * per_sm, a.shape.block, smem, st>>>(
             c);
         e = cudaGetLastError();
