@@ -810,8 +810,12 @@ __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S
 
 // The slot ranges of a chunk of targets (see run_item_arcs): one warp per
 // target, lanes over its radii.
+#ifndef CVS_ARC_PASS_MIN_BLOCKS
+#define CVS_ARC_PASS_MIN_BLOCKS 3
+#endif
 template <bool CLIP>
-__global__ void k_arc_ranges(const SearchArgs A, int64_t nt, uint2* __restrict__ out,
+__global__ void __launch_bounds__(256, CVS_ARC_PASS_MIN_BLOCKS)
+    k_arc_ranges(const SearchArgs A, int64_t nt, uint2* __restrict__ out,
                              unsigned long long* __restrict__ probe, int64_t stride) {
     ChainF32 C;
 #pragma unroll

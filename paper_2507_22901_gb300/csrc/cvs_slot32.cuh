@@ -373,38 +373,38 @@ __device__ __forceinline__ void arc_range(float c, float half, int H, int& start
     start = (none || all) ? 0 : s0;
 }
 
-// Gamut and low arcs of channel c at radius r as circular slot ranges:
-// (gamut start, gamut len, low start, low len); gamut len -1 = no pair of the
-// radius is in gamut.
-__device__ __forceinline__ int4 channel_ranges(const TargetF32 T, const ChainF32 C, float r, int c,
-                                              int32_t hi_min, int need_high, int clip, float th0,
-                                              float inv_step, int H, float& lo_out) {
+// The bounds of channel c at radius r without the arc trigonometry: the
+// sinusoid (alpha, beta), the gamut ratio xg (|sin(j - j0)| <= xg inside the
+// gamut arc; >= 0.9999: every angle; < 0: no pair of the radius is in gamut)
+// and the low ratio xl (|sin(j - j0)| < xl: certainly not high; <= 0: no such
+// angle; >= 1: every angle, also when no enabled pattern needs the channel),
+// and the lower bound lo of lin_lower_bound.
+struct ArcChannel {
+    float alpha, beta, xg, xl, lo;
+};
+
+__device__ __forceinline__ ArcChannel channel_bounds(const TargetF32& T, const ChainF32& C, float r,
+                                                     int c, int32_t hi_min, bool need_high,
+                                                     bool clip) {
     const float U = r * 0.002f, V = r * 0.005f;
     const float Ui = U * 1.00001f, Vi = V * 1.00001f;
     const float ax = c == 0 ? C.Ax[0] : (c == 1 ? C.Ax[1] : C.Ax[2]);
     const float bz = c == 0 ? C.Bz[0] : (c == 1 ? C.Bz[1] : C.Bz[2]);
     const float l0 = c == 0 ? T.lin0[0] : (c == 1 ? T.lin0[1] : T.lin0[2]);
-    const float alpha = ax * U * (T.c2x + 0.75f * U * U);
-    const float beta = -bz * V * (T.c2z + 0.75f * V * V);
-    const float R2 = fmaxf(alpha * alpha + beta * beta, 1e-30f);
+    ArcChannel o;
+    o.alpha = ax * U * (T.c2x + 0.75f * U * U);
+    o.beta = -bz * V * (T.c2z + 0.75f * V * V);
+    const float R2 = fmaxf(o.alpha * o.alpha + o.beta * o.beta, 1e-30f);
     const float invR = rsqrtf(R2) * 1.00001f;  // 1/R, rounded up
     const float au = ax * Ui * Ui * Ui, bv = bz * Vi * Vi * Vi;
     const float e2 = fmaxf(au * au + bv * bv, 1e-36f);
     const float eps = 0.25f * e2 * rsqrtf(e2) * 1.0001f + 1e-7f;
-    float cidx = (atan2_arc(-beta, alpha) - th0) * inv_step;
-    cidx -= (float)H * floorf(cidx * (1.0f / (float)H));
-    int4 o;
-    if (clip) {
-        o.x = 0;
-        o.y = H;
-    } else {
+    o.xg = 2.0f;
+    if (!clip) {
         const float P = ax * T.c1x * U * U, Q = bz * T.c1z * V * V;
         const float G = fminf(l0 + fmaxf(P, Q) - kLinOutLo, kLinOutHi - l0 - fminf(P, Q)) + eps +
                         1e-5f;
-        const float x = G * invR * 1.0001f + 1e-6f;
-        const float half = (asin_arc(fminf(x, 0.9999f)) + kArcAngleMargin) * inv_step;
-        arc_range(cidx, x >= 0.9999f ? (float)H : half, H, o.x, o.y);
-        if (G < 0.0f) o.y = -1;
+        o.xg = G < 0.0f ? -1.0f : G * invR * 1.0001f + 1e-6f;
     }
     // the lower bound of lin_lower_bound, per channel
     const float xlo = -Ui * (T.c2x - Ui * (T.c1x - Ui)), xhi = Ui * (T.c2x + Ui * (T.c1x + Ui));
@@ -415,16 +415,24 @@ __device__ __forceinline__ int4 channel_ranges(const TargetF32 T, const ChainF32
     const float coupled = l0 - pq2 * rsqrtf(pq2) * 1.00001f + fminf(0.0f, ax * T.c1x) * Ui * Ui +
                           fminf(0.0f, bz * T.c1z) * Vi * Vi -
                           (fabsf(ax) * Ui * Ui * Ui + fabsf(bz) * Vi * Vi * Vi);
-    float lo = fmaxf(ends, coupled) - 1e-5f;
-    lo_out = lo;
-    if (!clip) lo = fmaxf(lo, kLinOutLo);
+    o.lo = fmaxf(ends, coupled) - 1e-5f;
+    const float lo = clip ? o.lo : fmaxf(o.lo, kLinOutLo);
     const float y = v_enc_fast(lo) + (float)hi_min - 1.02f;
     const float tau = (v_inv_fast(y) - lo) * 0.9999f - 3e-6f;
-    const float x = (0.5f * tau - eps) * invR * 0.9999f - 1e-6f;
-    const float half = (asin_arc(fminf(x, 0.9999f)) - kArcAngleMargin) * inv_step;
-    // no low arc where x <= 0; all slots where x >= 1 or the channel is not needed
-    const bool all_low = x >= 1.0f || !need_high;
-    arc_range(cidx, all_low ? (float)H : (x > 0.0f ? half : -1.0f), H, o.z, o.w);
+    o.xl = need_high ? (0.5f * tau - eps) * invR * 0.9999f - 1e-6f : 2.0f;
+    return o;
+}
+
+// The gamut and low arcs of one channel as circular slot ranges (gamut start,
+// len, low start, len).
+__device__ __forceinline__ int4 channel_arcs(const ArcChannel& a, float th0, float inv_step, int H) {
+    float cidx = (atan2_arc(-a.beta, a.alpha) - th0) * inv_step;
+    cidx -= (float)H * floorf(cidx * (1.0f / (float)H));
+    int4 o;
+    const float hg = (asin_arc(fminf(a.xg, 0.9999f)) + kArcAngleMargin) * inv_step;
+    arc_range(cidx, a.xg >= 0.9999f ? (float)H : hg, H, o.x, o.y);
+    const float hl = (asin_arc(fminf(a.xl, 0.9999f)) - kArcAngleMargin) * inv_step;
+    arc_range(cidx, a.xl >= 1.0f ? (float)H : (a.xl > 0.0f ? hl : -1.0f), H, o.z, o.w);
     return o;
 }
 
@@ -439,32 +447,35 @@ __device__ __forceinline__ int radius_ranges_body(const TargetF32& T, const Chai
                                                   int32_t hi_min, uint32_t chm, float th0,
                                                   float inv_step, int H, uint32_t* out,
                                                   int& total, bool& lin) {
-    int rs[6], rl[6];  // ranges 0..2: gamut arcs, 3..5: low arcs
-    bool empty = false;
+    ArcChannel ch[3];
     lin = false;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        float lo;
-        const int4 o = channel_ranges(T, C, r, c, hi_min, (chm >> (2 - c)) & 1u, CLIP ? 1 : 0, th0,
-                                      inv_step, H, lo);
-        lin |= !(lo > 0.0031308f + 1e-5f);
-        empty |= o.y < 0;
-        rs[c] = o.x;
-        rl[c] = max(o.y, 0);
-        rs[3 + c] = o.z;
-        rl[3 + c] = o.w;
+        ch[c] = channel_bounds(T, C, r, c, hi_min, (chm >> (2 - c)) & 1u, CLIP);
+        lin |= !(ch[c].lo > 0.0031308f + 1e-5f);
     }
     total = 0;
-    // no slot: a gamut arc is empty, or no channel can be high anywhere
-    if (empty || (rl[0] == 0 || rl[1] == 0 || rl[2] == 0) ||
-        (rl[3] == H && rl[4] == H && rl[5] == H))
+    // no slot: a channel leaves the gamut at every angle, or no channel can be high
+    if (ch[0].xg < 0.0f || ch[1].xg < 0.0f || ch[2].xg < 0.0f ||
+        (ch[0].xl >= 1.0f && ch[1].xl >= 1.0f && ch[2].xl >= 1.0f))
         return 0;
-    // every slot: all gamut arcs whole and some channel free of a low arc
-    if (rl[0] == H && rl[1] == H && rl[2] == H && (rl[3] == 0 || rl[4] == 0 || rl[5] == 0)) {
+    // every slot: in gamut at every angle and some channel free of a low arc
+    if (ch[0].xg >= 0.9999f && ch[1].xg >= 0.9999f && ch[2].xg >= 0.9999f &&
+        (ch[0].xl <= 0.0f || ch[1].xl <= 0.0f || ch[2].xl <= 0.0f)) {
         out[0] = (uint32_t)H << 16;
         total = H;
         return 1;
     }
+    int rs[6], rl[6];  // ranges 0..2: gamut arcs, 3..5: low arcs
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int4 o = channel_arcs(ch[c], th0, inv_step, H);
+        rs[c] = o.x;
+        rl[c] = o.y;
+        rs[3 + c] = o.z;
+        rl[3 + c] = o.w;
+    }
+    if (rl[0] == 0 || rl[1] == 0 || rl[2] == 0) return 0;
     // membership of slot 0, and the positions (> 0) where a range is entered or left
     constexpr int kSentinel = 0x7FFFFFFF;
     uint32_t state = 0;
