@@ -113,7 +113,8 @@ struct cvs_ctx {
     int64_t cap_arc = 0;
     unsigned long long* d_arc_probe = nullptr;
     unsigned long long* h_arc_probe = nullptr;
-    std::map<std::array<int64_t, 5>, bool> arc_choice;
+    std::map<std::array<int64_t, 6>, bool> arc_choice;
+    int search_kind = 0;  // kind of the current call, part of the choice's key
     // per-batch colour de-duplication of the image search (option "dedup")
     int dedup = 0;
     uint8_t* d_present = nullptr;   // 2^24 bytes
@@ -417,8 +418,8 @@ constexpr int64_t kArcProbeTargets = 4096;
 constexpr double kArcProbeRatio = 0.6;
 
 cvs_status arc_probe(cvs_ctx* c, const SearchArgs& a, int64_t n, cudaStream_t st,
-                     std::map<std::array<int64_t, 5>, bool>::iterator* it,
-                     const std::array<int64_t, 5>& key) {
+                     std::map<std::array<int64_t, 6>, bool>::iterator* it,
+                     const std::array<int64_t, 6>& key) {
     if (!c->d_arc_probe) {
         CVS_CUDA(cudaMalloc(&c->d_arc_probe, 2 * sizeof(unsigned long long)));
         CVS_CUDA(cudaMallocHost(&c->h_arc_probe, 2 * sizeof(unsigned long long)));
@@ -471,8 +472,9 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
         a.arc_ranges = c->arc_ranges;
         a.arc_cap = c->cap_arc;
         if (a.grid.arcs && !a.clip && c->angle_ranges == 2) {
-            const std::array<int64_t, 5> key = {c->grid_gen, a.hi_min, a.lo_max, a.mask2,
-                                                (int64_t)list_mode};
+            // per kind of call too: colours, images and the all-colour table differ
+            const std::array<int64_t, 6> key = {c->grid_gen, a.hi_min, a.lo_max, a.mask2,
+                                                (int64_t)list_mode, c->search_kind};
             auto it = c->arc_choice.find(key);
             if (it == c->arc_choice.end() && !capturing) {
                 cvs_status ps = arc_probe(c, a, n, st, &it, key);
@@ -806,6 +808,7 @@ cvs_status cvs_search_color(cvs_ctx* c, const uint8_t rgb[3], uint32_t target,
     CVS_CUDA(cudaMemcpyAsync(c->d_rgb1, rgb, 3, cudaMemcpyHostToDevice, st));
     CVS_CUDA(cudaMemsetAsync(c->dense, 0, sizeof(cvs_pair) * (size_t)nd, st));
     CVS_CUDA(launch_setup_colors(c->d_rgb1, 1, c->grid.rmax, c->tf, c->td, c->acc, st));
+    c->search_kind = 0;
     st0 = run_search(c, 1, thr, prec, 1, target, st);
     if (st0 != CVS_OK) return st0;
     CVS_CUDA(launch_compact_pairs(c->dense, nd, c->compact, c->counters + 3, st));
@@ -847,6 +850,7 @@ cvs_status cvs_search_colors_pairs(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     CVS_CUDA(grow(&c->d_count, &c->cap_count, n));
     CVS_CUDA(grow(&c->d_pmask, &c->cap_pmask, n));
     CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
+    c->search_kind = 0;
     st0 = run_search(c, n, thr, prec, 0, 0, st);
     if (st0 != CVS_OK) return st0;
     CVS_CUDA(launch_finalize_colors(c->acc, n, c->d_maxr, c->d_count, c->d_pmask, st));
@@ -877,6 +881,7 @@ cvs_status cvs_search_colors_pairs(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
         const int64_t b = n - t0 < batch ? n - t0 : batch;
         CVS_CUDA(cudaMemsetAsync(c->dense, 0, sizeof(cvs_pair) * (size_t)(b * kn), st));
         CVS_CUDA(launch_setup_colors(rgb_dev + 3 * t0, b, c->grid.rmax, c->tf, c->td, c->acc, st));
+        c->search_kind = 0;
         st0 = run_search(c, b, thr, prec, 1, (uint32_t)t0, st);
         if (st0 != CVS_OK) return st0;
         CVS_CUDA(launch_compact_pairs_batch(c->dense, kn, b, c->d_offs + t0, out_dev, st));
@@ -905,6 +910,7 @@ cvs_status cvs_search_colors(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, cons
     cudaStream_t st = (cudaStream_t)stream;
     auto enqueue = [&](cudaStream_t s, ImageDesc*) -> cvs_status {
         CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, s));
+        c->search_kind = 0;
         cvs_status r = run_search(c, n, thr, prec, 0, 0, s, s == c->cap);
         if (r != CVS_OK) return r;
         CVS_CUDA(launch_finalize_colors(c->acc, n, out->max_r, out->count, out->pmask, s));
@@ -1086,6 +1092,7 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
         CVS_CUDA(cudaStreamSynchronize(st));
         const int64_t nu = *c->h_unique;
         CVS_CUDA(launch_setup_colors(c->d_unique, nu, c->grid.rmax, c->tf, c->td, c->acc, st));
+        c->search_kind = 1;
         st0 = run_search(c, nu, thr, prec, 0, 0, st);
         if (st0 != CVS_OK) return st0;
         CVS_CUDA(launch_dedup_gather(c->d_imgs, n, total, c->d_index, c->acc, st));
@@ -1096,6 +1103,7 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
     cudaStream_t st = (cudaStream_t)stream;
     auto enqueue = [&](cudaStream_t s, ImageDesc* d_imgs) -> cvs_status {
         CVS_CUDA(launch_setup_images(d_imgs, n, total, c->grid.rmax, c->tf, c->td, c->acc, s));
+        c->search_kind = 1;
         cvs_status r = run_search(c, total, thr, prec, 0, 0, s, s == c->cap);
         if (r != CVS_OK) return r;
         CVS_CUDA(launch_finalize_images(c->acc, c->td, total, d_imgs, s));
@@ -1275,6 +1283,7 @@ cvs_status cvs_lut_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds*
         e = launch_rgb_iota(rgb, first, kChunk, st);
         if (e == cudaSuccess) e = launch_setup_colors(rgb, kChunk, c->grid.rmax, c->tf, c->td, c->acc, st);
         if (e != cudaSuccess) { st0 = fail(CVS_ERR_CUDA, "cvs_lut_build: %s", cudaGetErrorString(e)); break; }
+        c->search_kind = 2;
         st0 = run_search(c, kChunk, thr, prec, 0, 0, st);
         if (st0 != CVS_OK) break;
         e = launch_lut_pack(c->acc, kChunk, L->entry + first, L->pmask + first, st);
