@@ -175,14 +175,15 @@ def cpu_sample(n: int):
     return cube[idx]
 
 
-def time_oracle(n_colors: int):
-    """FP64 CPU oracle over a bounded, evenly spaced sample of the cube."""
+def time_oracle(n_colors: int, threads: int = 0):
+    """FP64 CPU oracle over a bounded, evenly spaced sample of the cube (all
+    host cores unless `threads` is given)."""
     import oracle
     from paper_2507_22901_gb300 import workloads as W
     radii, ang = W.grid(2)
     tt = oracle.trig_table(ang)
     rgb = cpu_sample(n_colors)
-    threads = oracle.max_threads()
+    threads = threads or oracle.max_threads()
     t0 = time.perf_counter()
     oracle.search_colors(rgb, radii, ang, 50.0, 0.5, threads=threads, trig_tab=tt)
     dt = time.perf_counter() - t0
@@ -690,10 +691,15 @@ def run_ours(args, world, rank, local):
     line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, threads, ccand, dt = time_oracle(args.cpu_sample)
+        n1 = max(8, args.cpu_sample // 32)  # one core: about 1/32 of the sample
+        v1, _, ccand1, dt1 = time_oracle(n1, threads=1)
         line["cpu_baseline"] = {
             "value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{args.cpu_sample} evenly spaced colours of the cube x 128 x 360 "
-                      f"({ccand:.3g} candidates, {dt:.1f} s)"}
+                      f"({ccand:.3g} candidates, {dt:.1f} s)",
+            "single_core": {"value": v1, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1} evenly spaced colours of the cube x 128 x 360 "
+                                      f"({ccand1:.3g} candidates, {dt1:.1f} s)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
