@@ -247,6 +247,15 @@ class Context:
         return self._h
 
     # -------------------------------------------------------------- options
+    def reserve(self, radii=None, angles_deg=None, max_targets=0, max_images=0):
+        """Allocate ahead of time what searches up to max_targets colours or
+        pixels (and batches of max_images images) on this grid need."""
+        g = None
+        if radii is not None:
+            g, keep = make_grid(radii, angles_deg)
+        check(lib().cvs_reserve(self._h, ctypes.byref(g) if g is not None else None,
+                                int(max_targets), int(max_images)), "cvs_reserve")
+
     def set_option(self, name: str, value: float):
         check(lib().cvs_set_option(self._h, name.encode(), float(value)), "cvs_set_option")
 

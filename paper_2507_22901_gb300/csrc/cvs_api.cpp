@@ -399,6 +399,10 @@ int64_t arc_entries(const cvs_ctx* c, int64_t n) {
 
 cvs_status ensure_arc_scratch(cvs_ctx* c, int64_t n) {
     if (!c->grid.arcs) return CVS_OK;
+    if (!c->d_arc_probe) {  // the probe's counts (allocated with the scratch, ahead of any search)
+        CVS_CUDA(cudaMalloc(&c->d_arc_probe, 2 * sizeof(unsigned long long)));
+        CVS_CUDA(cudaMallocHost(&c->h_arc_probe, 2 * sizeof(unsigned long long)));
+    }
     const int64_t need = arc_entries(c, n);
     if (c->cap_arc >= need) return CVS_OK;
     drop_graphs(c);  // captured graphs point at the buffer about to be replaced
@@ -420,10 +424,6 @@ constexpr double kArcProbeRatio = 0.6;
 cvs_status arc_probe(cvs_ctx* c, const SearchArgs& a, int64_t n, cudaStream_t st,
                      std::map<std::array<int64_t, 6>, bool>::iterator* it,
                      const std::array<int64_t, 6>& key) {
-    if (!c->d_arc_probe) {
-        CVS_CUDA(cudaMalloc(&c->d_arc_probe, 2 * sizeof(unsigned long long)));
-        CVS_CUDA(cudaMallocHost(&c->h_arc_probe, 2 * sizeof(unsigned long long)));
-    }
     int64_t nt = n < kArcProbeTargets ? n : kArcProbeTargets;
     if (nt * c->grid.K > a.arc_cap) nt = a.arc_cap / c->grid.K;
     const int64_t stride = nt > 0 ? n / nt : 1;  // evenly over the call's targets

@@ -207,3 +207,26 @@ def test_automatic_choice(ctx, torch_cuda):
     ctx.synchronize()
     st = ctx.stats()
     assert st["pruned"] < 0.45 * st["candidates"]
+
+
+def test_reserve_covers_the_ranges(torch_cuda):
+    """After cvs_reserve, a search within its limits (the first call of its
+    kind, so with the probe) allocates no device memory."""
+    torch = torch_cuda
+    c = cvs.Context(0)
+    try:
+        radii, ang = W.grid(2)
+        rgb = dev(torch, W.color_cube(8))
+        n = rgb.shape[0]
+        out = (torch.empty(n, dtype=torch.float32, device="cuda"),
+               torch.empty(n, dtype=torch.int32, device="cuda"),
+               torch.empty(n, dtype=torch.uint8, device="cuda"))
+        c.reserve(radii, ang, max_targets=n)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        c.search_colors(rgb, radii, ang, 50.0, 0.5, out=out)
+        c.synchronize()
+        assert c.stats()["ranges_ms"] > 0.0
+        assert abs(torch.cuda.mem_get_info()[0] - free0) < (1 << 20)
+    finally:
+        c.close()
