@@ -486,8 +486,9 @@ def run_serving(torch, device, W, cvs, n_table=600, n_search=24):
     """Workload 5: Poisson arrivals (seed 2, 120 frames/s) of 1920x1080 (60%),
     3840x2160 (30%) and 7680x4320 (10%) frames rendered as in workload 3, sent
     to the continuous-batching server; latency = submit -> maps resident.  With
-    the capacity table (all 600 requests) and with per-frame search (the first
-    n_search requests: the search alone cannot keep up with 120 frames/s)."""
+    the capacity table (all 600 requests) and with per-frame search, per pixel
+    and per distinct colour (the first n_search requests: the search alone
+    cannot keep up with 120 frames/s)."""
     import threading
     reqs = W.serving_requests(n_table, seed=2, rate=120.0)
     sizes = sorted({(w, h) for _, w, h, _ in reqs})
@@ -498,9 +499,10 @@ def run_serving(torch, device, W, cvs, n_table=600, n_search=24):
         frames.setdefault((w, h), []).append(img)
     r3, a3 = W.grid(3)
     out = {}
-    for mode, n in (("table", n_table), ("search", n_search)):
+    for mode, n in (("table", n_table), ("search", n_search), ("search_dedup", n_search)):
         srv = cvs.Server(r3, a3, 50.0, 0.5, max_inflight=4, max_pixels=7680 * 4320,
-                         mem_budget_bytes=6 << 30, use_table=(mode == "table"))
+                         mem_budget_bytes=6 << 30, use_table=(mode == "table"),
+                         dedup=(mode == "search_dedup"))
         tickets = []
         lock = threading.Lock()
         done_flag = [False]

@@ -349,7 +349,10 @@ typedef struct {
     int64_t max_pixels;          /* largest frame accepted (width * height) */
     int64_t mem_budget_bytes;    /* device arena for frames and maps (12 bytes per pixel) */
     int32_t use_table;           /* 1: answer from a capacity table built at creation */
-    int32_t reserved;
+    int32_t dedup;               /* per-frame search (use_table = 0): 1 = one search per
+                                    distinct colour of the frame (cvs_set_option "dedup");
+                                    its tables, about 130 MB per slot, are allocated at
+                                    creation too */
 } cvs_server_config;
 
 typedef enum {
@@ -497,7 +500,8 @@ cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const c
  *                   gathers the maps per pixel; the maps are identical.  The
  *                   call then synchronises `stream` once (to size the search)
  *                   and is not captured in a CUDA graph; the context keeps
- *                   about 130 MB of tables for it.  Default 0.
+ *                   about 130 MB of tables for it, allocated when the option
+ *                   is turned on.  Default 0.
  *   "angle_ranges"  the FP32 search in gamut-reject mode on a folded, evenly
  *                   spaced angle grid can first turn, per target and radius,
  *                   bounds on the pair's linear RGB (a sinusoid in the angle

@@ -82,7 +82,7 @@ class cvs_launch_shape(ctypes.Structure):
 class cvs_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
                 ("max_pixels", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_int64),
-                ("use_table", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("use_table", ctypes.c_int32), ("dedup", ctypes.c_int32)]
 
 
 class cvs_server_stats(ctypes.Structure):
@@ -581,11 +581,12 @@ class Server:
 
     def __init__(self, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0,
                  precision=PREC_FP32_RECHECK, device=0, max_inflight=2,
-                 max_pixels=7680 * 4320, mem_budget_bytes=4 << 30, use_table=False):
+                 max_pixels=7680 * 4320, mem_budget_bytes=4 << 30, use_table=False,
+                 dedup=False):
         g, self._keep = make_grid(radii, angles_deg)
         t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
         cfg = cvs_server_config(int(device), int(max_inflight), int(max_pixels),
-                                int(mem_budget_bytes), int(bool(use_table)), 0)
+                                int(mem_budget_bytes), int(bool(use_table)), int(bool(dedup)))
         self._h = ctypes.c_void_p()
         self._frames = {}
         check(lib().cvs_server_create(ctypes.byref(self._h), ctypes.byref(cfg), ctypes.byref(g),

@@ -265,6 +265,19 @@ void drop_graphs(cvs_ctx* c);
 
 cvs_status ensure_arc_scratch(cvs_ctx* c, int64_t n);
 
+// Tables of the per-batch colour de-duplication (option "dedup"): presence
+// map and index of all 2^24 colours, the distinct colours, scan sums.
+cvs_status ensure_dedup(cvs_ctx* c) {
+    if (c->d_present) return CVS_OK;
+    constexpr size_t kColours = size_t(1) << 24;
+    CVS_CUDA(cudaMalloc(&c->d_present, kColours));
+    CVS_CUDA(cudaMalloc(&c->d_index, sizeof(int32_t) * kColours));
+    CVS_CUDA(cudaMalloc(&c->d_unique, 3 * kColours));
+    CVS_CUDA(cudaMalloc(&c->d_scan, sizeof(int) * 1025));
+    CVS_CUDA(cudaMallocHost(&c->h_unique, sizeof(int)));
+    return CVS_OK;
+}
+
 cvs_status ensure_targets(cvs_ctx* c, int64_t n) {
     if (c->cap_tf < n || c->cap_td < n || c->cap_acc < n) {
         drop_graphs(c);  // captured graphs point at the buffers about to be replaced
@@ -698,6 +711,11 @@ cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
         if (!c->use_graphs) drop_graphs(c);
     } else if (!std::strcmp(name, "dedup")) {
         if (value != 0 && value != 1) return fail(CVS_ERR_INVALID_ARG, "dedup is 0 or 1");
+        if (value == 1) {  // its tables, now rather than inside a later search
+            CVS_CUDA(cudaSetDevice(c->device));
+            cvs_status ds = ensure_dedup(c);
+            if (ds != CVS_OK) return ds;
+        }
         c->dedup = (int)value;
     } else if (!std::strcmp(name, "angle_ranges")) {
         if (value != 0 && value != 1 && value != 2)
@@ -1073,13 +1091,8 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
         constexpr int64_t kColours = int64_t(1) << 24;
         if (st0 == CVS_OK) st0 = ensure_targets(c, total < kColours ? total : kColours);
         if (st0 != CVS_OK) return st0;
-        if (!c->d_present) {
-            CVS_CUDA(cudaMalloc(&c->d_present, (size_t)kColours));
-            CVS_CUDA(cudaMalloc(&c->d_index, sizeof(int32_t) * (size_t)kColours));
-            CVS_CUDA(cudaMalloc(&c->d_unique, 3 * (size_t)kColours));
-            CVS_CUDA(cudaMalloc(&c->d_scan, sizeof(int) * 1025));
-            CVS_CUDA(cudaMallocHost(&c->h_unique, sizeof(int)));
-        }
+        st0 = ensure_dedup(c);
+        if (st0 != CVS_OK) return st0;
         cudaStream_t st = (cudaStream_t)stream;
         CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, n));
         CVS_CUDA(cudaMemcpyAsync(c->d_imgs, h.data(), sizeof(ImageDesc) * n,

@@ -41,13 +41,14 @@ def same(a, b):
             np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2]))
 
 
-@pytest.mark.parametrize("use_table", [False, True])
-def test_alone_equals_mix_equals_direct(torch_cuda, use_table):
+@pytest.mark.parametrize("mode", ["search", "table", "search per distinct colour"])
+def test_alone_equals_mix_equals_direct(torch_cuda, mode):
     fr = frames(8)
     ref = direct(torch_cuda, fr)
     radii, ang = W.grid(3)
     srv = cvs.Server(radii, ang, 50, 0.5, max_inflight=3, max_pixels=1 << 20,
-                     mem_budget_bytes=64 << 20, use_table=use_table)
+                     mem_budget_bytes=64 << 20, use_table=(mode == "table"),
+                     dedup=(mode == "search per distinct colour"))
     alone = []
     for f in fr:  # one at a time
         t = srv.submit(f)
