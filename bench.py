@@ -43,7 +43,7 @@ LANES_PER_SM_CLK = 128
 # summarised in profiles/k_search_fp32_colour_cube_full.md (32,768-colour case
 # scaled by 8, traffic being proportional to the colours).  Valid only for the
 # kernel source it was taken from; otherwise the roofline reports null.
-TRAFFIC_CAPTURE = {"source_sha256_16": "201effb47032c95c", "bytes_per_launch": 8 * 36.6848e6}
+TRAFFIC_CAPTURE = {"source_sha256_16": "12deeb635e3014a7", "bytes_per_launch": 8 * 36.69632e6}
 
 
 def kernel_source_hash() -> str:

@@ -381,6 +381,7 @@ __device__ __forceinline__ void arc_range(float c, float half, int H, int& start
 // and the lower bound lo of lin_lower_bound.
 struct ArcChannel {
     float alpha, beta, xg, xl, lo;
+    float invR, eps, emid, ehalf, l0;  // E(j) = emid + ehalf cos 2j; the target's linear value
 };
 
 __device__ __forceinline__ ArcChannel channel_bounds(const TargetF32& T, const ChainF32& C, float r,
@@ -400,8 +401,13 @@ __device__ __forceinline__ ArcChannel channel_bounds(const TargetF32& T, const C
     const float e2 = fmaxf(au * au + bv * bv, 1e-36f);
     const float eps = 0.25f * e2 * rsqrtf(e2) * 1.0001f + 1e-7f;
     o.xg = 2.0f;
+    o.invR = invR;
+    o.eps = eps;
+    o.l0 = l0;
     if (!clip) {
         const float P = ax * T.c1x * U * U, Q = bz * T.c1z * V * V;
+        o.emid = 0.5f * (P + Q);
+        o.ehalf = 0.5f * (Q - P);
         const float G = fminf(l0 + fmaxf(P, Q) - kLinOutLo, kLinOutHi - l0 - fminf(P, Q)) + eps +
                         1e-5f;
         o.xg = G < 0.0f ? -1.0f : G * invR * 1.0001f + 1e-6f;
@@ -419,7 +425,8 @@ __device__ __forceinline__ ArcChannel channel_bounds(const TargetF32& T, const C
     const float lo = clip ? o.lo : fmaxf(o.lo, kLinOutLo);
     const float y = v_enc_fast(lo) + (float)hi_min - 1.02f;
     const float tau = (v_inv_fast(y) - lo) * 0.9999f - 3e-6f;
-    o.xl = need_high ? (0.5f * tau - eps) * invR * 0.9999f - 1e-6f : 2.0f;
+    const float ostar = 0.5f * tau;
+    o.xl = need_high ? (ostar - eps) * invR * 0.9999f - 1e-6f : 2.0f;
     return o;
 }
 
@@ -429,8 +436,33 @@ __device__ __forceinline__ int4 channel_arcs(const ArcChannel& a, float th0, flo
     float cidx = (atan2_arc(-a.beta, a.alpha) - th0) * inv_step;
     cidx -= (float)H * floorf(cidx * (1.0f / (float)H));
     int4 o;
-    const float hg = (asin_arc(fminf(a.xg, 0.9999f)) + kArcAngleMargin) * inv_step;
-    arc_range(cidx, a.xg >= 0.9999f ? (float)H : hg, H, o.x, o.y);
+    float xg = a.xg;
+    if (xg < 0.9999f) {
+        // E over the gamut arc only: the arc is j0 +- w with sin w = xg, and
+        // E = emid + ehalf cos 2j, cos 2j = 1 - 2 sin^2 j; cos 2j reaches 1
+        // inside it where |sin j0| <= sin w, -1 where |cos j0| <= sin w.  The
+        // arc from the narrower E lies inside this one, so the bound holds.
+        const float invr = rsqrtf(fmaxf(a.alpha * a.alpha + a.beta * a.beta, 1e-30f));
+        const float sj = -a.beta * invr, cj = a.alpha * invr;  // sin j0, cos j0
+        const float sw = xg, cw = sqrtf(fmaxf(1.0f - xg * xg, 0.0f));
+        const float s1 = sj * cw - cj * sw, s2 = sj * cw + cj * sw;
+        const float c1 = 1.0f - 2.0f * s1 * s1, c2 = 1.0f - 2.0f * s2 * s2;
+        const float cmax = fabsf(sj) <= sw + 1e-5f ? 1.0f : fminf(fmaxf(c1, c2) + 1e-5f, 1.0f);
+        const float cmin = fabsf(cj) <= sw + 1e-5f ? -1.0f : fmaxf(fminf(c1, c2) - 1e-5f, -1.0f);
+        const float e_a = a.ehalf * cmin, e_b = a.ehalf * cmax;
+        const float emin = a.emid + fminf(e_a, e_b) - 1e-7f, emax = a.emid + fmaxf(e_a, e_b) + 1e-7f;
+        const float G = fminf(a.l0 + emax - kLinOutLo, kLinOutHi - a.l0 - emin) + a.eps + 1e-5f;
+        xg = fminf(xg, G < 0.0f ? -1.0f : G * a.invR * 1.0001f + 1e-6f);
+    }
+    if (xg < 0.0f) {  // no angle of the radius keeps this channel in gamut
+        o.x = 0;
+        o.y = 0;
+        o.z = 0;
+        o.w = 0;
+        return o;
+    }
+    const float hg = (asin_arc(fminf(xg, 0.9999f)) + kArcAngleMargin) * inv_step;
+    arc_range(cidx, xg >= 0.9999f ? (float)H : hg, H, o.x, o.y);
     const float hl = (asin_arc(fminf(a.xl, 0.9999f)) - kArcAngleMargin) * inv_step;
     arc_range(cidx, a.xl >= 1.0f ? (float)H : (a.xl > 0.0f ? hl : -1.0f), H, o.z, o.w);
     return o;
