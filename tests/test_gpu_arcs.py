@@ -109,7 +109,8 @@ def test_4096_slots(ctx, torch_cuda):
 
 
 @pytest.mark.parametrize("thr", [(50.0, 0.5, 0x01), (50.0, 0.5, 0x40), (100.0, 0.25, 0x7F),
-                                 (150.0, 0.125, 0x2A), (20.0, 1.0, 0x7F)])
+                                 (150.0, 0.125, 0x2A), (20.0, 1.0, 0x7F), (0.0, 0.5, 0x7F),
+                                 (254.5, 0.125, 0x7F)])
 def test_masks_and_thresholds(ctx, torch_cuda, thr):
     v_th, r_novib, mask = thr
     radii, ang = W.grid(2)
