@@ -449,6 +449,37 @@ cvs_status arc_probe(cvs_ctx* c, const SearchArgs& a, int64_t n, cudaStream_t st
     return CVS_OK;
 }
 
+// The angle-range fields of a search of n targets: the scratch (grown unless
+// inside a capture, where the plain walk runs instead) and, with option
+// angle_ranges = 2, the probe's choice for this grid, thresholds and kind of
+// call (probed once, synchronously, outside captures).
+cvs_status prepare_arcs(cvs_ctx* c, SearchArgs& a, int64_t n, cvs_precision prec, int list_mode,
+                        cudaStream_t st, bool capturing) {
+    if (a.grid.arcs && prec == CVS_PREC_FP32_RECHECK) {
+        const int64_t need = arc_entries(c, n);
+        if (c->cap_arc < need && !capturing) {
+            cvs_status as = ensure_arc_scratch(c, n);
+            if (as != CVS_OK) return as;
+        }
+        if (c->cap_arc < need) a.grid.arcs = 0;  // (inside a capture) the plain walk
+        a.arc_ranges = c->arc_ranges;
+        a.arc_cap = c->cap_arc;
+        if (a.grid.arcs && !a.clip && c->angle_ranges == 2) {
+            // per kind of call too: colours, images and the all-colour table differ
+            const std::array<int64_t, 6> key = {c->grid_gen, a.hi_min, a.lo_max, a.mask2,
+                                                (int64_t)list_mode, c->search_kind};
+            auto it = c->arc_choice.find(key);
+            if (it == c->arc_choice.end() && !capturing) {
+                cvs_status ps = arc_probe(c, a, n, st, &it, key);
+                if (ps != CVS_OK) return ps;
+            }
+            if (it != c->arc_choice.end() && !it->second) a.grid.arcs = 0;
+        }
+    }
+    a.num_sms = c->num_sms;
+    return CVS_OK;
+}
+
 cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_precision prec,
                       int list_mode, uint32_t target_id, cudaStream_t st, bool capturing = false) {
     SearchArgs a{};
@@ -475,28 +506,10 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
     a.shape = c->shape;
     a.shape.kchunk = choose_kchunk(c, n, c->grid.K, c->grid.H);
     a.num_sms = c->num_sms;
-    if (a.grid.arcs && prec == CVS_PREC_FP32_RECHECK) {
-        const int64_t need = arc_entries(c, n);
-        if (c->cap_arc < need && !capturing) {
-            cvs_status as = ensure_arc_scratch(c, n);
-            if (as != CVS_OK) return as;
-        }
-        if (c->cap_arc < need) a.grid.arcs = 0;  // (inside a capture) the plain walk
-        a.arc_ranges = c->arc_ranges;
-        a.arc_cap = c->cap_arc;
-        if (a.grid.arcs && !a.clip && c->angle_ranges == 2) {
-            // per kind of call too: colours, images and the all-colour table differ
-            const std::array<int64_t, 6> key = {c->grid_gen, a.hi_min, a.lo_max, a.mask2,
-                                                (int64_t)list_mode, c->search_kind};
-            auto it = c->arc_choice.find(key);
-            if (it == c->arc_choice.end() && !capturing) {
-                cvs_status ps = arc_probe(c, a, n, st, &it, key);
-                if (ps != CVS_OK) return ps;
-            }
-            if (it != c->arc_choice.end() && !it->second) a.grid.arcs = 0;
-        }
+    {
+        cvs_status as = prepare_arcs(c, a, n, prec, list_mode, st, capturing);
+        if (as != CVS_OK) return as;
     }
-    a.num_sms = c->num_sms;
     // a tuned shape applies when the caller has not fixed the shape by hand
     if (c->shape.kchunk == 0 && c->shape.blocks_per_sm == 0 && c->shape.block == kSearchBlock) {
         const auto key = tune_key(c, n, (int)prec, a.clip, list_mode);
@@ -1242,6 +1255,9 @@ cvs_status cvs_autotune(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, const cvs
     a.half_w = (float)(0.5 - c->window);
     a.prec = (int32_t)prec;
     a.num_sms = c->num_sms;
+    c->search_kind = 0;
+    st0 = prepare_arcs(c, a, n, prec, 0, st, false);  // tune the walk the search will take
+    if (st0 != CVS_OK) return st0;
     LaunchShape sh;
     double ms = 0.0;
     st0 = tune_shape(c, a, st, &sh, &ms);
