@@ -231,3 +231,22 @@ def test_reserve_covers_the_ranges(torch_cuda):
         assert abs(torch.cuda.mem_get_info()[0] - free0) < (1 << 20)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_grids_match_plain_walk(ctx, torch_cuda, seed):
+    """Seeded random folded, evenly spaced grids (angle count, first angle),
+    radii (unsorted, radius 0 included), colours, thresholds and masks: the
+    range walk equals the plain walk bit for bit."""
+    rng = np.random.default_rng(1000 + seed)
+    n_ang = 2 * int(rng.integers(1, 361))
+    ang = float(rng.uniform(0.0, 360.0 / n_ang)) + np.arange(n_ang) * (360.0 / n_ang)
+    radii = rng.uniform(0.0, 32.0, int(rng.integers(1, 97)))
+    radii[0] = 0.0 if seed % 3 == 0 else radii[0]
+    rgb = rng.integers(0, 256, (int(rng.integers(1, 300)), 3)).astype(np.uint8)
+    v_th = float(rng.choice([0.0, 20.0, 50.0, 100.0, 150.0, 254.5]))
+    r_novib = float(rng.choice([0.125, 0.25, 0.5, 1.0]))
+    mask = int(rng.integers(1, 128))
+    res = both_walks(ctx, torch_cuda, rgb, radii, ang, v_th, r_novib, mask)
+    same(res[1][0], res[0][0], f"seed {seed}: {n_ang} angles, {len(radii)} radii")
+    assert res[1][1]["pruned"] >= res[0][1]["pruned"] or res[1][1]["ranges_ms"] == 0.0
