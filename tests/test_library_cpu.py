@@ -157,3 +157,38 @@ def test_workload_shapes():
     assert img.shape == (23, 37, 3) and img.dtype == np.uint8
     req = W.serving_requests()
     assert len(req) == 600 and all(req[i][0] < req[i + 1][0] for i in range(599))
+
+
+STRUCTS = ["cvs_grid", "cvs_thresholds", "cvs_pair", "cvs_capacity_map", "cvs_image", "cvs_stats",
+           "cvs_precision_report", "cvs_launch_shape", "cvs_server_config", "cvs_server_stats"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Size and field offsets of every public struct, as the C compiler lays
+    them out from include/cvsearch.h, equal the binding's ctypes layouts."""
+    import shutil
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cvsearch.h"', "int main(void) {"]
+    for name in STRUCTS:
+        st = getattr(binding, name)
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in st._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    include = str(Path(__file__).resolve().parent.parent / "include")
+    subprocess.run([gcc, "-std=c11", "-I", include, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for row in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if row:
+            name, key, val = row.split()
+            got[(name, key)] = int(val)
+    for name in STRUCTS:
+        st = getattr(binding, name)
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert got[(name, field)] == getattr(st, field).offset, (name, field)
