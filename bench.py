@@ -73,6 +73,10 @@ def parse_args():
     p.add_argument("--gather-profile", action="store_true",
                    help="only the table gathers (one 3840x2160 frame through the embedding "
                         "table, four images through the capacity table), for profiling")
+    p.add_argument("--frames-profile", action="store_true",
+                   help="only the per-pixel paths on one 1920x1080 frame (the image search, "
+                        "the same with one search per distinct colour, and the direct "
+                        "embedding), for profiling")
     p.add_argument("--cube-step", type=int, default=4, choices=[4, 8, 16],
                    help="channel step of the colour cube (4 = the 262,144-colour workload; "
                         "larger steps give the small cases used for profiling)")
@@ -753,10 +757,67 @@ def run_gather_profile(args):
                                 "gb_s": pxl * 21 / t_lut / 1e9}}))
 
 
+def run_frames_profile(args):
+    """The per-pixel kernels on one synthetic 1920x1080 frame (64 radii x 180
+    angles, V_th 50, R_novib 0.5): the persistent image search, the same with
+    one search per distinct colour (option dedup), and the direct embedding of
+    a 2D-code pattern map.  Each runs once untimed, then `args.steps` times
+    under CUDA events; prints one JSON line."""
+    import torch
+    import paper_2507_22901_gb300 as cvs
+    from paper_2507_22901_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    ctx = cvs.Context(0)
+    r3, a3 = W.grid(3)
+    w, h = 1920, 1080
+    terms = W.image_params(1, seed=21, sizes=[(w, h)])[0][2]
+    img = W.render_image_torch(w, h, terms, 21, device=dev)
+    pat = torch.from_numpy(W.code_pattern(h, w, module=16, seed=21)).to(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cand = w * h * len(r3) * len(a3)
+
+    def timed(fn):
+        fn()
+        ctx.synchronize()
+        torch.cuda.synchronize(dev)
+        ev0.record()
+        for _ in range(args.steps):
+            fn()
+        ev1.record()
+        ctx.synchronize()
+        torch.cuda.synchronize(dev)
+        return ev0.elapsed_time(ev1) / 1e3 / args.steps
+
+    out = {"workload": "one synthetic 1920x1080 frame (seed 21), 64 radii x 180 angles"}
+    maps = ctx.search_images([img], r3, a3, 50.0, 0.5)
+    t = timed(lambda: ctx.search_images([img], r3, a3, 50.0, 0.5, maps=maps))
+    st = ctx.stats()
+    out["search_images"] = {"seconds": t, "gcand_s": cand / t / 1e9,
+                            "angle_ranges": st["ranges_ms"] > 0,
+                            "pruned_fraction": st["pruned"] / cand,
+                            "skipped_fraction": st["skipped"] / cand}
+    ctx.set_option("dedup", 1)
+    maps_d = ctx.search_images([img], r3, a3, 50.0, 0.5)
+    t = timed(lambda: ctx.search_images([img], r3, a3, 50.0, 0.5, maps=maps_d))
+    n_distinct = ctx.stats()["targets"]
+    ctx.set_option("dedup", 0)
+    out["search_images_dedup"] = {
+        "seconds": t, "distinct_colours": n_distinct,
+        "maps_identical": all(torch.equal(a, b) for a, b in zip(maps[0], maps_d[0]))}
+    fa, fb, ch = ctx.embed_image(img, pat, r3, a3, 50.0, 0.5)
+    t = timed(lambda: ctx.embed_image(img, pat, r3, a3, 50.0, 0.5, frames=(fa, fb)))
+    out["embed_image"] = {"seconds": t, "pixels_requested": int((pat > 0).sum().item()),
+                          "pixels_embedded": int((ch >= 0).sum().item())}
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
     if args.gather_profile:
         return run_gather_profile(args)
+    if args.frames_profile:
+        return run_frames_profile(args)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
