@@ -23,8 +23,10 @@ arithmetic; the trig table against exact angles and libm; L*a*b* against the
 CIE closed form for greys and the published L*a*b* of the sRGB primaries; the
 inverse chain by round trip over all 2^24 colours and the forward / inverse
 identity; the decision rule by hand-worked cases; the search loops by brute
-force over tiny grids.  Agreement with the paper itself can only be soft: its
-one printed result (Table 2) is reported as a diagnostic, not a pin.
+force over tiny grids.  tests/test_oracle_mutants.py plants plausible mistakes
+in a copy of this package and checks that each one fails a pin.  Agreement with
+the paper itself can only be soft: its one printed result (Table 2) is reported
+as a diagnostic, not a pin.
 """
 from __future__ import annotations
 

@@ -75,6 +75,9 @@ CASES = [
     ((240, 100, 100), [15.5, 30.0], [10.0, 100.0, 190.0, 280.0]),
     ((100, 100, 240), [20.0, 25.0, 31.0], [45.0, 135.0, 225.0, 315.0]),
     ((12, 200, 33), [5.0, 28.0], [0.0, 60.0, 120.0, 180.0, 240.0, 300.0]),
+    # unsorted radii: the largest passing radius (22) comes before a smaller
+    # passing one (15.5), so max_r is not simply the last passing radius
+    ((240, 100, 100), [22.0, 30.0, 15.5], [10.0, 100.0, 190.0, 280.0]),
 ]
 
 
@@ -103,6 +106,11 @@ def test_search_colors_matches_brute_force(rgb, radii, angles):
 def test_some_brute_case_passes():
     # the tiny grids above must exercise passing candidates, not only rejections
     assert sum(len(_brute(*c, 50, 0.5)) for c in CASES) > 0
+    # and the unsorted case must pass at its largest radius before a smaller one
+    rgb, radii, angles = CASES[-1]
+    ks = [e[0] for e in _brute(rgb, radii, angles, 50, 0.5)]
+    best = max(ks, key=lambda k: radii[k])
+    assert any(k > best and radii[k] < radii[best] for k in ks)
 
 
 def test_radius_zero_gives_target_and_never_passes():
