@@ -77,6 +77,9 @@ def parse_args():
                    help="only the per-pixel paths on one 1920x1080 frame (the image search, "
                         "the same with one search per distinct colour, and the direct "
                         "embedding), for profiling")
+    p.add_argument("--sets-profile", action="store_true",
+                   help="only the multi-set pass (the cube under the 12 Table 1 threshold "
+                        "sets) and one embedding-table build, for profiling")
     p.add_argument("--cube-step", type=int, default=4, choices=[4, 8, 16],
                    help="channel step of the colour cube (4 = the 262,144-colour workload; "
                         "larger steps give the small cases used for profiling)")
@@ -812,12 +815,54 @@ def run_frames_profile(args):
     print(json.dumps(out))
 
 
+def run_sets_profile(args):
+    """The multi-set pass on its own: the colour cube (channel step
+    `args.cube_step`) x 128 radii x 360 angles under the 12 Table 1 threshold
+    sets, once untimed and then `args.steps` times under CUDA events; then one
+    embedding-table build (all 2^24 colours x 64 radii x 180 angles).  Prints
+    one JSON line."""
+    import torch
+    import paper_2507_22901_gb300 as cvs
+    from paper_2507_22901_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    ctx = cvs.Context(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cube = torch.from_numpy(W.color_cube(args.cube_step)).to(dev)
+    r2, a2 = W.grid(2)
+    sets = W.table1_threshold_sets()
+    res = ctx.search_colors_multi(cube, r2, a2, sets)
+    ctx.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        ctx.search_colors_multi(cube, r2, a2, sets, out=res)
+    ev1.record()
+    ctx.synchronize()
+    torch.cuda.synchronize(dev)
+    t_multi = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    cand = cube.shape[0] * len(r2) * len(a2)
+    r3, a3 = W.grid(3)
+    ev0.record()
+    etab = ctx.build_embed_table(r3, a3, 50.0, 0.5)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    t_etab = ev0.elapsed_time(ev1) / 1e3
+    etab.close()
+    ctx.close()
+    print(json.dumps({
+        "multi_set_pass": {"colours": int(cube.shape[0]), "sets": len(sets), "seconds": t_multi,
+                           "gdecisions_s": cand * len(sets) / t_multi / 1e9},
+        "embedding_table_build": {"colours": 1 << 24, "seconds": t_etab,
+                                  "gcand_s": (1 << 24) * len(r3) * len(a3) / t_etab / 1e9}}))
+
+
 def main():
     args = parse_args()
     if args.gather_profile:
         return run_gather_profile(args)
     if args.frames_profile:
         return run_frames_profile(args)
+    if args.sets_profile:
+        return run_sets_profile(args)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -11,9 +11,10 @@
 // item takes its radii in decreasing order, so a lane's first pass of a set is
 // its largest passing radius for that set: it is recorded once, in shared
 // memory, and the warp's maximum is taken at the end of the item.
-// Flagged slots are marked in a per-lane bitmap and decided after each
-// segment: bounds once, every set from them, FP64 codes when some set stays
-// open.
+// Flagged slots are marked in a per-lane bitmap; after each segment they are
+// queued per warp and decided 32 at a time, one per lane (so the long exact
+// path runs with full warps, seldom): bounds once, every set from them, FP64
+// codes when some set stays open.
 #include <cuda_runtime.h>
 
 #include "cvs_device.cuh"
@@ -27,6 +28,7 @@ namespace {
 constexpr int kMultiWords = 7;                  // flag words per lane per segment
 constexpr int kMultiSegIters = 32 * kMultiWords;  // < 256: byte counters cannot overflow
 constexpr int kMultiMaxChunk = 8192;            // radii per work item
+constexpr int kMultiQueue = 64;                 // flagged-slot queue entries per warp
 
 // Table entry of |d| = i: bit s set if set s calls the channel high (i >= hi_min[s]),
 // bit 16 + s if it calls it low (i <= lo_max[s]); i = 256 stands for out of range.
@@ -172,11 +174,27 @@ __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* 
     }
 }
 
+// Decide the first n (<= 32) queued flagged slots (rank | h << 16), one per lane.
+template <int PREC, bool FAST, bool CLIP, bool ALLMASK>
+__device__ __forceinline__ void drain_multi(const MultiArgs& A, const float2* r2s,
+                                            const float4* sc4s, const uint32_t* ts,
+                                            const TargetF32& T, const ChainF32& C,
+                                            const TargetF64& D, int64_t t, const uint32_t* pq,
+                                            int n, uint32_t setmask, unsigned long long& n_re) {
+    const unsigned lane = lane_id();
+    if ((int)lane < n) {
+        const uint32_t v = pq[lane];
+        multi_flagged<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t, (int)(v & 0xFFFFu),
+                                                 (int)(v >> 16), setmask, n_re);
+    }
+}
+
 // One work item: target t, radius ranks [kk0, kk1), taken in decreasing order.
 template <int PREC, bool FAST, bool CLIP, bool ALLMASK>
 __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s,
                                            const float4* sc4s, const uint32_t* ts, uint32_t* fb,
-                                           float* rmx, const TargetF32& T, const ChainF32& C,
+                                           float* rmx, uint32_t* pq, const TargetF32& T,
+                                           const ChainF32& C,
                                            const PairsC& PC, int64_t t, int kk0, int kk1,
                                            unsigned long long& n_flag,
                                            unsigned long long& n_re) {
@@ -194,6 +212,7 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
     for (int p = 0; p < 8; ++p) m.pm[p] = 0;
     m.cnt = 0;
     uint32_t seen = 0;  // sets this lane has seen pass (its largest radius is recorded)
+    int pq_n = 0;       // queued flagged slots (warp-uniform)
     for (int s = 0; s < NT; ++s) rmx[s * 32 + lane] = 0.0f;  // radius 0 never passes
     // slot i of the item is (rank kk1 - 1 - i / H, i % H); lanes step by 32
     const int q32 = 32 / H, r32 = 32 - q32 * H;
@@ -289,26 +308,43 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
             if (PREC == CVS_PREC_FP32_RECHECK) fb[w * 32 + lane] = bits;
         }
         flush_counts(m, NT);
-        if (PREC == CVS_PREC_FP32_RECHECK) {  // the segment's flagged slots
+        if (PREC == CVS_PREC_FP32_RECHECK) {  // queue the segment's flagged slots
             __syncwarp();
             const int nwords = (seg1 - seg0 + 31) >> 5;
             for (int w = 0; w < nwords; ++w) {
                 uint32_t bits = fb[w * 32 + lane];
-                while (__any_sync(0xFFFFFFFFu, bits != 0u)) {
-                    if (bits) {
+                while (true) {
+                    const bool has = bits != 0u;
+                    const unsigned ball = __ballot_sync(0xFFFFFFFFu, has);
+                    if (!ball) break;
+                    if (has) {
                         const int j = __ffs(bits) - 1;
                         bits &= bits - 1u;
                         const int i = (seg0 + 32 * w + j) * 32 + (int)lane;
                         const int dk = i / H;
+                        pq[pq_n + __popc(ball & ((1u << lane) - 1u))] =
+                            (uint32_t)(kk1 - 1 - dk) | ((uint32_t)(i - dk * H) << 16);
                         ++n_flag;
-                        multi_flagged<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t,
-                                                                 kk1 - 1 - dk, i - dk * H, setmask,
-                                                                 n_re);
+                    }
+                    pq_n += __popc(ball);  // below kMultiQueue: at most 31 + 32
+                    __syncwarp();
+                    if (pq_n >= 32) {
+                        drain_multi<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t, pq,
+                                                               32, setmask, n_re);
+                        const int rest = pq_n - 32;
+                        const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
+                        __syncwarp();
+                        if ((int)lane < rest) pq[lane] = mv;
+                        __syncwarp();
+                        pq_n = rest;
                     }
                 }
             }
         }
     }
+    if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0)
+        drain_multi<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t, pq, pq_n, setmask,
+                                               n_re);
     __syncwarp();
     // item totals: lane s publishes set s
     uint32_t pmask = 0;
@@ -340,8 +376,9 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
     uint32_t* ts = reinterpret_cast<uint32_t*>(smem + ((K * 8 + 15) & ~15) + H * 16);
     uint32_t* per_warp = ts + 260;  // 257 table entries, padded to 16 bytes
     const int warp = threadIdx.x >> 5;
-    uint32_t* fb = per_warp + warp * (kMultiWords * 32 + kMaxThresholdSets * 32);
+    uint32_t* fb = per_warp + warp * (kMultiWords * 32 + kMaxThresholdSets * 32 + kMultiQueue);
     float* rmx = reinterpret_cast<float*>(fb + kMultiWords * 32);
+    uint32_t* pq = fb + kMultiWords * 32 + kMaxThresholdSets * 32;
     build_set_table(ts, A);
     for (int i = threadIdx.x; i < K; i += blockDim.x) r2s[i] = dup(A.grid.r32[A.order[i]]);
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
@@ -373,11 +410,11 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
         TargetF32 T{};
         if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
         if (PREC == CVS_PREC_FP32_RECHECK && (T.flags & 1u))
-            multi_item<PREC, true, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, rmx, T, C, PC, t, k0, k1,
-                                                  n_flag, n_re);
+            multi_item<PREC, true, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t, k0,
+                                                  k1, n_flag, n_re);
         else
-            multi_item<PREC, false, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, rmx, T, C, PC, t, k0, k1,
-                                                   n_flag, n_re);
+            multi_item<PREC, false, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t, k0,
+                                                   k1, n_flag, n_re);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -403,7 +440,7 @@ __global__ void k_init_acc(Acc* __restrict__ acc, int64_t n) {
 
 int multi_smem_bytes(const GridDev& g, int block) {
     return ((g.K * 8 + 15) & ~15) + g.H * 16 + 260 * 4 +
-           (block / 32) * (kMultiWords * 32 + kMaxThresholdSets * 32) * 4;
+           (block / 32) * (kMultiWords * 32 + kMaxThresholdSets * 32 + kMultiQueue) * 4;
 }
 
 template <int PREC, bool CLIP, bool ALLMASK>
