@@ -31,18 +31,20 @@ UNIT = "Gcand/s"
 # Candidates of one 3840x2160 frame with the 64-radius x 180-angle image grid.
 CAND_PER_4K_FRAME = 3840 * 2160 * 64 * 180
 # Algorithmic instruction issues per candidate of the FP32 path (one colour
-# conversion and half a pair decision per candidate; see the roofline section
-# of the design notes): 53.5 FP32/INT lane operations + 6 MUFU operations.
+# conversion and half a pair decision per candidate): displacement 1, cube
+# expansion 6, linear RGB 6, encode 15 FP32 + 6 MUFU, rounding and window test
+# 12, half of the 27-issue pair decision 13.5.
 ALG_ISSUES_PER_CAND = 59.5
 # a candidate rejected before the encode (gamut reject, the warp's 32 slots all
 # certainly out of range): displacement 1 + cube expansion 6 + linear RGB 6 +
 # range test 6 issues
 ALG_ISSUES_PER_SKIPPED = 19.0
 LANES_PER_SM_CLK = 128
-# DRAM bytes of one FP32 search launch on this workload, from the ncu capture
-# summarised in profiles/k_search_fp32_colour_cube_full.md (32,768-colour case
-# scaled by 8, traffic being proportional to the colours).  Valid only for the
-# kernel source it was taken from; otherwise the roofline reports null.
+# DRAM bytes of one FP32 search launch on this workload, from one ncu capture
+# of the search kernel on 32,768 cube colours (dram__bytes_read.sum +
+# dram__bytes_write.sum), scaled by 8 to the cube's 262,144 colours since the
+# traffic is proportional to the colours.  Valid only for the kernel source it
+# was taken from (its hash below); otherwise the roofline reports null.
 TRAFFIC_CAPTURE = {"source_sha256_16": "12deeb635e3014a7", "bytes_per_launch": 8 * 36.69632e6}
 
 
@@ -228,6 +230,70 @@ def run_reference(args, world, rank):
 
 
 # ------------------------------------------------------------------ extras
+def table2_marks():
+    """The paper's Table 2 (7 patterns x 9 colours, 1 = check mark), as stored
+    with its citation in tests/golden/table2_presence.txt."""
+    from pathlib import Path
+    path = Path(__file__).resolve().parent / "tests" / "golden" / "table2_presence.txt"
+    rows = [ln.split() for ln in path.read_text().splitlines()
+            if ln.strip() and not ln.startswith("#")]
+    order = {int(r[0], 2): [int(x) for x in r[1:]] for r in rows}
+    return np.array([order[p] for p in range(1, 8)], int)
+
+
+def measure_4k_frames(ctx, torch, device, W, n_frames=4):
+    """Four 3840x2160 frames rendered by the 48-image recipe (seed 31), per
+    pixel 64 radii x 180 angles: timed as one batch through the per-pixel
+    search, through the per-batch colour de-duplication, and through the
+    capacity table (built once, its build timed apart).  The maps of the three
+    are compared."""
+    r3, a3 = W.grid(3)
+    params = W.image_params(n_frames, seed=31, sizes=[(3840, 2160)] * n_frames)
+    frames = [W.render_image_torch(w, h, t, ns, device=device) for w, h, t, ns in params]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=1):
+        fn()
+        ctx.synchronize()
+        torch.cuda.synchronize(device)
+        ev0.record()
+        for _ in range(reps):
+            r = fn()
+        ev1.record()
+        ctx.synchronize()
+        torch.cuda.synchronize(device)
+        return ev0.elapsed_time(ev1) / 1e3 / reps, r
+
+    maps = ctx.search_images(frames, r3, a3, 50.0, 0.5)
+    sec_direct, _ = timed(lambda: ctx.search_images(frames, r3, a3, 50.0, 0.5, maps=maps))
+    ctx.set_option("dedup", 1)
+    try:
+        maps_d = ctx.search_images(frames, r3, a3, 50.0, 0.5)
+        sec_dedup, _ = timed(lambda: ctx.search_images(frames, r3, a3, 50.0, 0.5, maps=maps_d))
+        distinct = ctx.stats()["targets"]
+    finally:
+        ctx.set_option("dedup", 0)
+    ev0.record()
+    lut = ctx.build_lut(r3, a3, 50.0, 0.5)
+    ev1.record()
+    torch.cuda.synchronize(device)
+    build_s = ev0.elapsed_time(ev1) / 1e3
+    maps_t = lut.lookup_images(frames)
+    sec_table, _ = timed(lambda: lut.lookup_images(frames, maps=maps_t), reps=20)
+    lut.close()
+    same = all(torch.equal(a, b) and torch.equal(a, c)
+               for m, md, mt in zip(maps, maps_d, maps_t) for a, b, c in zip(m, md, mt))
+    cand = n_frames * CAND_PER_4K_FRAME
+    return {"frames": n_frames, "size": "3840x2160", "grid": "64 radii x 180 angles",
+            "direct_s": sec_direct, "direct_frames_per_s": n_frames / sec_direct,
+            "direct_gcand_s": cand / sec_direct / 1e9,
+            "dedup_s": sec_dedup, "dedup_frames_per_s": n_frames / sec_dedup,
+            "distinct_colours": int(distinct),
+            "table_s": sec_table, "table_frames_per_s": n_frames / sec_table,
+            "table_build_s": build_s, "maps_identical": bool(same)}
+
+
 def run_extras(ctx, torch, device, W, cvs):
     """Precision study on workloads 1-4 (FP32 vs FP64 errors, re-decision
     fractions, decision mismatches) and one timed pass of the 48-image workload
@@ -267,6 +333,7 @@ def run_extras(ctx, torch, device, W, cvs):
             "rechecked_fraction": st32["rechecked"] / cand,
             "max_code_err_fp32": rep["max_code_err"], "max_lab_err_fp32": rep["max_lab_err"],
             "max_lin_err_fp32": rep["max_lin_err"], "raw_fp32_wrong_codes": rep["n_wrong_codes"],
+            "unflagged_wrong_codes": rep["n_unflagged_wrong"],
             "decision_mismatches_vs_fp64": mism,
             "fp32_gcand_s": cand / (st32["search_ms"] / 1e3) / 1e9,
             "fp64_gcand_s": cand / (st64["search_ms"] / 1e3) / 1e9,
@@ -398,12 +465,10 @@ def run_extras(ctx, torch, device, W, cvs):
     r2, a2 = W.grid(2)
     base = ctx.search_colors(cube, r2, a2, 50.0, 0.5)
     ctx.synchronize()
-    ctx.set_option("max_dl", 0.1)
-    lim = ctx.search_colors(cube, r2, a2, 50.0, 0.5)
-    lim = ctx.search_colors(cube, r2, a2, 50.0, 0.5, out=lim)
+    lim = ctx.search_colors(cube, r2, a2, 50.0, 0.5, max_dl=0.1)
+    lim = ctx.search_colors(cube, r2, a2, 50.0, 0.5, max_dl=0.1, out=lim)
     ctx.synchronize()
     st_l = ctx.stats()
-    ctx.set_option("max_dl", -1)
     cand = cube.shape[0] * len(r2) * len(a2)
     out["luminance_limit"] = {
         "workload": "262,144 cube colours x 128 radii x 360 angles, max_dl 0.1",
@@ -445,11 +510,21 @@ def run_extras(ctx, torch, device, W, cvs):
         ctx.search_colors_multi(t1rgb, r1, a1, sets1, out=res1)
         ctx.synchronize()
     host_s = (time.perf_counter() - h2) / reps
+    # Table 2's presence matrix in both gamut modes, and its agreement with the
+    # paper's (a soft diagnostic: the paper leaves the grid and gamut unstated)
+    table2 = table2_marks()
+    presence = {}
+    for gamut in (0, 1):
+        rg = ctx.search_colors_multi(t1rgb, r1, a1, sets1, gamut_mode=gamut)
+        torch.cuda.synchronize(device)
+        pm = W.presence_matrix(rg[2].cpu().numpy()).astype(int)
+        presence["reject" if gamut == 0 else "clip"] = {
+            "presence": pm.tolist(), "table2_agreement_of_63": int((pm == table2).sum())}
     out["table1_experiment"] = {
         "workload": "9 Table 1 colours x 12 (V_th, R_novib) x 7 patterns; 61 radii x 360 angles",
         "device_s": sec1, "call_to_result_s": host_s,
         "paper_array_method_s": 62.62, "paper_hardware": "MacBook Pro 13-inch 2019 (CPU), grid unstated",
-        "presence": W.presence_matrix(res1[2].cpu().numpy()).astype(int).tolist()}
+        "gamut_modes": presence}
     del t1rgb, res1
     # the experiment of §3: every cube colour under all 12 (V_th, R_novib) sets,
     # one multi-set pass against 12 single-set passes
@@ -640,6 +715,11 @@ def run_ours(args, world, rank, local):
     e2e = world * cand * args.steps / e2e_s / 1e9
     e2e_match = bool(np.array_equal(h_out[1], res32[1].cpu().numpy()))
 
+    # ---- 4K frames: a batch of 3840x2160 frames per GPU, measured
+    frames4k = measure_4k_frames(ctx, torch, device, W)
+    sec4k = max_over_ranks(frames4k["direct_s"], world, device)
+    frames4k["images_4k_per_s_all_gpus"] = world * frames4k["frames"] / sec4k
+
     # ---- extras: precision study (4096-colour set) and one pass over the images
     extras = {}
     if not args.no_extras and world == 1:
@@ -669,7 +749,8 @@ def run_ours(args, world, rank, local):
                    "v_th": 50, "r_novib": 0.5, "patterns": "all 7", "gamut": "reject",
                    "precision": "fp32 + fp64 re-decision", "l2": "flushed between steps "
                    "(256 MB write)", "parallelism": f"replicas x{world}"},
-        "images_4k_per_s": value * 1e9 / CAND_PER_4K_FRAME,
+        "images_4k_per_s": frames4k["images_4k_per_s_all_gpus"],
+        "frames_4k": frames4k,
         "fp64_gpu": {"value": fp64, "unit": UNIT,
                      "speedup": (value / fp64) if fp64 else None,
                      "decision_mismatches": mismatch},

@@ -64,8 +64,10 @@ typedef enum {
 
 /* Arithmetic of a search.  Both give identical results.  FP32_RECHECK runs
  * the bulk in FP32 and re-decides in FP64 every candidate whose FP32 codes
- * could be wrong; its error bound is validated for radii up to 32, so a grid
- * with a larger radius is searched in FP64 (cvs_stats.precision says which
+ * could be wrong; its error bound is validated for radii up to 32 (over all
+ * 2^24 colours), so on a grid with a larger radius an FP32_RECHECK call
+ * returns CVS_ERR_INVALID_ARG, unless option "fp64_fallback" is 1, in which
+ * case it runs in FP64 (about 100x slower; cvs_stats.precision says which
  * ran). */
 typedef enum {
     CVS_PREC_FP32_RECHECK = 0, /* FP32 bulk, FP64 re-decision near rounding boundaries */
@@ -86,22 +88,35 @@ typedef struct {
     int32_t n_angles;
 } cvs_grid;
 
-/* Embedding-signal condition (§3 Experiments, Table 1).
+/* Conditions a pair must meet: the embedding-signal condition (§3
+ * Experiments, Table 1), the gamut, and an optional refinement of the
+ * colour-vibration condition (§2 Methods).  32 bytes.
  * v_th: finite, >= 0.  r_novib: in (0, 1].  A channel difference d is high
  * if d > v_th and low if d < v_th * r_novib (exact comparisons).
  * pattern_mask: bit p-1 enables pattern p = (hi_R << 2) | (hi_G << 1) | hi_B,
  * p = 1..7 (0x7F = all seven patterns of Table 1).
- * gamut_mode: 0 = reject pairs with a code outside [0,255], 1 = clamp. */
+ * gamut_mode: 0 = reject pairs with a code outside [0,255], 1 = clamp.
+ * max_dl: luminance limit on the emitted pair.  §2 Methods keeps L* fixed
+ *   before quantisation and states no tolerance after it; with a positive,
+ *   finite max_dl a passing pair is kept only if each of its two emitted
+ *   8-bit colours has an L* (step 1 of §2 Methods applied to its codes,
+ *   clamped in clip mode) within max_dl of the target's L*.  0 (what a
+ *   zero-initialised struct holds) and +inf mean no limit; a negative value
+ *   or NaN is CVS_ERR_INVALID_ARG.  The first call on a context with a limit
+ *   builds a table of the L* of all 2^24 colours (128 MiB, synchronous). */
 typedef struct {
     double v_th;
     double r_novib;
     uint32_t pattern_mask;
     int32_t gamut_mode;
+    double max_dl;
 } cvs_thresholds;
 
 /* One passing candidate (16 bytes).  k, m: radius and angle indices;
  * plus / minus: the 8-bit sRGB of the two colours; pattern: 1..7;
- * flags: bit 0 = decided by the FP64 re-decision; target: caller's index. */
+ * flags: bit 0 = the codes were computed in FP64 (some FP32 code lay within
+ * the window of a rounding boundary, or the call ran in FP64); target:
+ * caller's index. */
 typedef struct {
     uint16_t k, m;
     uint8_t plus[3], minus[3];
@@ -156,9 +171,13 @@ typedef struct {
 
 /* Create a context on CUDA device `device` (the device is made current for
  * every call on the context).  *ctx receives the handle, owned by the caller
- * and released with cvs_destroy.  Returns CVS_ERR_CUDA if the device is not
- * usable. */
-cvs_status cvs_create(cvs_ctx** ctx, int device);
+ * and released with cvs_destroy.  mem_budget_bytes caps the device memory the
+ * context itself allocates (its scratch and tables, including temporary
+ * buffers of a table build; not the tables returned by cvs_lut_build and
+ * cvs_etab_build, which belong to the caller): a call that would exceed it
+ * returns CVS_ERR_NO_MEMORY before any device work, and the context stays
+ * usable.  0 = no cap.  Returns CVS_ERR_CUDA if the device is not usable. */
+cvs_status cvs_create(cvs_ctx** ctx, int device, size_t mem_budget_bytes);
 
 /* Free the context and all scratch memory it owns (waits for its work). */
 void cvs_destroy(cvs_ctx* ctx);
@@ -202,20 +221,29 @@ cvs_status cvs_search_color(cvs_ctx* ctx, const uint8_t rgb[3], uint32_t target,
 
 /* Every passing pair of n colours (the extraction of cvs_search_color for many
  * targets; for an image, the colours of its pixels, each result being a pure
- * function of the colour).  rgb_dev: device, 3n bytes.  out_dev: device array
- * of cap records; the pairs of colour i occupy [offsets[i], offsets[i+1]) in
- * (k, m) order, each record's target field = i.  offsets_host: optional host
- * array of n + 1 entries.  *n_out receives the total number of pairs; when it
- * exceeds cap, nothing is written to out_dev and CVS_ERR_TRUNCATED is
- * returned (offsets_host and *n_out are still filled, so the call can be
- * repeated with a larger buffer).  n <= 2^31.  Synchronous on `stream`. */
+ * function of the colour): "generate the array, extract the elements that
+ * satisfy the conditions" of §1 Introduction and §2 Methods, in one search
+ * per batch of colours; each passing pair is written once, straight to its
+ * place in the output.
+ * rgb_dev: device, 3n bytes.  out_dev: device array of cap records, 16-byte
+ * aligned; the pairs of colour i occupy [offsets[i], offsets[i+1]) in (k, m)
+ * order, each record's target field = i.  offsets_host: optional host array
+ * of n + 1 entries.  *n_out receives the total number of pairs; when it
+ * exceeds cap, only the records whose position is below cap are written and
+ * CVS_ERR_TRUNCATED is returned (offsets_host and *n_out are still filled, so
+ * the call can be repeated with a larger buffer).  n <= 2^31.  Synchronous on
+ * `stream`. */
 cvs_status cvs_search_colors_pairs(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
                                    const cvs_grid* grid, const cvs_thresholds* thr,
                                    cvs_precision prec, cvs_pair* out_dev, int64_t cap,
                                    int64_t* offsets_host, int64_t* n_out, void* stream);
 
-/* Per-target results for n colours.  rgb_dev: device, 3n bytes (R,G,B per
- * colour).  out_dev: device capacity map of n entries.  Asynchronous on
+/* Per-target results for n colours: for each colour the number of passing
+ * candidates, the largest passing radius and the set of patterns that some
+ * passing pair carries - the search of §2 Methods (pairs at fixed L*, back to
+ * 8-bit RGB, the conditions) reduced to the quantities of Table 2 (which of
+ * the Table 1 patterns a colour can carry).  rgb_dev: device, 3n bytes (R,G,B
+ * per colour).  out_dev: device capacity map of n entries.  Asynchronous on
  * `stream`; the device buffers must stay valid until it completes. */
 cvs_status cvs_search_colors(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
                              const cvs_grid* grid, const cvs_thresholds* thr,
@@ -239,6 +267,7 @@ cvs_status cvs_search_colors_host(cvs_ctx* ctx, const uint8_t* rgb_host, int64_t
  *   out_dev: device capacity map of n * n_thr entries; entry t * n_thr + s
  *            holds colour t under set s, equal to what cvs_search_colors
  *            returns for that colour with thr[s] alone.
+ *   Each set may carry its own luminance limit (max_dl).
  * Asynchronous on `stream`; not captured in CUDA graphs. */
 cvs_status cvs_search_colors_multi(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
                                    const cvs_grid* grid, const cvs_thresholds* thr,
@@ -246,9 +275,12 @@ cvs_status cvs_search_colors_multi(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t
                                    const cvs_capacity_map* out_dev, void* stream);
 
 /* Per-pixel results for a batch of n images of any sizes, in one persistent
- * launch over a shared work queue.  batch: host array of n image descriptors
- * (device pixel pointers).  maps: host array of n capacity maps (device
- * pointers, width*height entries each, row-major, dense).  Asynchronous. */
+ * launch over a shared work queue: the search of cvs_search_colors for every
+ * pixel's colour (the embedding of Fig. 1a needs, per pixel of the shown
+ * image, the pairs that the pixel's colour admits; §2 Methods, Fig. 2).
+ * batch: host array of n image descriptors (device pixel pointers).  maps:
+ * host array of n capacity maps (device pointers, width*height entries each,
+ * row-major, dense).  Asynchronous. */
 cvs_status cvs_search_images(cvs_ctx* ctx, const cvs_image* batch, int32_t n,
                              const cvs_grid* grid, const cvs_thresholds* thr,
                              cvs_precision prec, const cvs_capacity_map* maps,
@@ -271,7 +303,9 @@ cvs_status cvs_search_images(cvs_ctx* ctx, const cvs_image* batch, int32_t n,
  *                equals its pitch - not recommended).
  *   choice_dev:  optional device output (NULL to skip), width * height dense
  *                uint32: k | m << 16, or 0xFFFFFFFF where nothing was embedded.
- * The thresholds' pattern_mask still applies (a masked pattern never embeds).
+ * The thresholds' pattern_mask still applies (a masked pattern never embeds),
+ * and so does the luminance limit: with max_dl on, the pair is the first one
+ * of pattern p whose two colours also meet it.
  * Asynchronous on `stream`.  cvs_get_stats reports the kernel time; its
  * flagged / rechecked counters count the flagged slots that had to be decided
  * exactly and those re-decided in FP64 (x2 on folded grids). */
@@ -425,23 +459,32 @@ cvs_status cvs_synchronize(cvs_ctx* ctx, void* stream);
 cvs_status cvs_get_stats(cvs_ctx* ctx, cvs_stats* out);
 
 /* Precision study: for n colours (rgb_dev: device, 3n bytes) on the grid,
- * compare every FP32 colour conversion (the "plus" colour of each (k, m))
- * with its FP64 value.  Synchronous.  Fields of *out:
+ * compare every FP32 colour conversion (the "plus" colour of each (k, m), in
+ * every FP32 chain the search may take for it) with its FP64 value.
+ * Synchronous.  Fields of *out:
  *   max_code_err  largest |v32 - v64| in 8-bit code units among values within
  *                 0.05 of a rounding boundary (v = 255 enc(lin) unrounded)
  *   max_lin_err   largest |lin32 - lin64| of the linear RGB
  *   max_lab_err   largest |a*|, |b*| error of the colour the FP32 chain
  *                 stands for (its f-values against the exact a +- i sin j,
  *                 b +- i cos j); L* is exact
- *   n_wrong_codes FP32 codes in [0, 255] that differ from FP64 before any
- *                 re-decision (the re-decision corrects every one of them)
- *   n_values      codes examined */
+ *   n_wrong_codes FP32 codes in [-1, 256] that differ from FP64 before any
+ *                 re-decision
+ *   n_unflagged_wrong  of those, the codes the search would take without
+ *                 re-deciding them (v32 farther than the context's window W
+ *                 from a rounding boundary).  0 means every FP32 decision of
+ *                 the search on these colours and this grid is exact: the
+ *                 re-decision corrects all the others.
+ *   n_values      codes examined
+ *   window        the context's window W (option "fp32_window") used */
 typedef struct {
     double max_code_err;
     double max_lin_err;
     double max_lab_err;
     int64_t n_wrong_codes;
     int64_t n_values;
+    int64_t n_unflagged_wrong;
+    double window;
 } cvs_precision_report;
 cvs_status cvs_precision_probe(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n,
                                const cvs_grid* grid, cvs_precision_report* out);
@@ -483,18 +526,6 @@ cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const c
  *                   thresholds, precision, shape) is seen, and replay the graph
  *                   on later calls with the same signature (up to 8 graphs are
  *                   kept per context).  Default 0.
- *   "max_dl"        a perceptual refinement of the vibration condition: a
- *                   passing pair is kept only if each of its two emitted 8-bit
- *                   colours has an L* (step 1 of §2 Methods applied to its
- *                   codes) within this many units of the target's L*.  The paper
- *                   fixes L* before quantisation and gives no tolerance after
- *                   it, so the value is the caller's.  A negative value turns
- *                   the limit off (the default).  The first non-negative value
- *                   builds a table of the L* of all 2^24 colours (128 MiB,
- *                   synchronous).  Applies to cvs_search_color(s),
- *                   cvs_search_colors_host, cvs_search_images and
- *                   cvs_lut_build; cvs_search_colors_multi, cvs_embed_image
- *                   and cvs_etab_build return CVS_ERR_INVALID_ARG while it is on.
  *   "dedup"         1: cvs_search_images searches each distinct colour of the
  *                   batch once (a pixel's maps depend only on its colour) and
  *                   gathers the maps per pixel; the maps are identical.  The
@@ -514,8 +545,18 @@ cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const c
  *                   synchronises `stream` once), where the ranges list under
  *                   0.6 of the slots the plain search would walk.  The context
  *                   keeps up to 256 MiB of scratch for the ranges.
+ *   "fp64_fallback" 1: an FP32_RECHECK call on a grid with a radius above 32
+ *                   runs in FP64 instead of returning CVS_ERR_INVALID_ARG.
+ *                   Default 0.
+ *   "list_batch_items"  pair lists (cvs_search_color, cvs_search_colors_pairs)
+ *                   search their colours in batches of at most this many work
+ *                   items (a work item: one colour x up to 8192 slots; its
+ *                   passing-slot bitmap is kept until its records are
+ *                   written; at most 256 MiB of bitmaps per batch); [1, 2^26],
+ *                   default 2^22.  Results do not depend on it.
  * Read-only values for cvs_get_option: "graph_launches" (graph replays so
- * far), "graphs_cached".
+ * far), "graphs_cached", "mem_in_use" (bytes of device memory the context
+ * holds), "mem_budget" (the cap given to cvs_create, 0 = none).
  * Unknown names or out-of-range values return CVS_ERR_INVALID_ARG. */
 cvs_status cvs_set_option(cvs_ctx* ctx, const char* name, double value);
 cvs_status cvs_get_option(cvs_ctx* ctx, const char* name, double* value);
@@ -541,17 +582,20 @@ cvs_status cvs_get_option(cvs_ctx* ctx, const char* name, double* value);
  * CVS_NOALLOC_MAX_RADII, n_angles <= CVS_NOALLOC_MAX_ANGLES; larger sizes
  * return CVS_ERR_INVALID_ARG with a message naming the limit.
  *
- * The first call on a device looks up the array's device address and copies a
- * constant table into it (a synchronous copy): make that first call before
- * any stream capture.  Every call uploads the grid and reads the angle table
- * back to decide the +180 degree folding, which synchronises `stream`; the
- * search itself then runs asynchronously on `stream`.  All calls share the
- * one array and it keeps the last call's contents (what must start at zero is
- * cleared by each call): calls whose device work overlaps - on different
- * streams or from different threads - race on it, so the caller must
- * serialise them.  The device `device` is made current for the call and the
- * caller's current device is restored before returning.  Results are
- * identical to cvs_search_colors on the same inputs. */
+ * The first call on a device looks up the array's device address (once per
+ * device; a cudaDeviceReset between calls is not supported): make that first
+ * call before any stream capture.  Every call uploads the threshold keys and
+ * the grid and reads the angle table back to decide the +180 degree folding,
+ * which synchronises `stream`; the search itself then runs asynchronously on
+ * `stream`.  All calls share the one array and it keeps the last call's
+ * contents (what must start at zero is cleared by each call): calls whose
+ * device work overlaps - on different streams or from different threads - race
+ * on it, so the caller must serialise them.  The device `device` is made
+ * current for the call and the caller's current device is restored before
+ * returning.  The luminance limit (thr->max_dl) is not available here (it
+ * reads a 128 MiB table) and returns CVS_ERR_INVALID_ARG.  Results are
+ * identical to cvs_search_colors on a context with its default options
+ * (option "fp32_window" 2e-3). */
 #define CVS_NOALLOC_SCRATCH_BYTES (512 * 1024)
 #define CVS_NOALLOC_MAX_COLORS 4096
 #define CVS_NOALLOC_MAX_RADII 1024

@@ -120,7 +120,7 @@ def lib() -> ctypes.CDLL:
             L.orc_passes_dl.argtypes = [P(_Consts), d, vp, vp, d]
             L.orc_passes_dl.restype = ctypes.c_int
             L.orc_embed.argtypes = [P(_Consts), vp, vp, i64, vp, i32, vp, vp, i32, d, d, u32,
-                                    ctypes.c_int, vp, vp, vp, ctypes.c_int]
+                                    ctypes.c_int, d, vp, vp, vp, ctypes.c_int]
             L.orc_embed.restype = None
             L.orc_roundtrip_all.argtypes = [P(_Consts), P(d), ctypes.c_int]
             L.orc_roundtrip_all.restype = i64
@@ -290,9 +290,10 @@ def max_threads() -> int:
 
 
 def embed(rgbs, patterns, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0,
-          threads=1, trig_tab=None):
+          threads=1, trig_tab=None, max_dl=-1.0):
     """Embedding of requested patterns (Fig. 1a): per pixel (frame_a (n,3) uint8,
-    frame_b (n,3) uint8, choice uint32 = k | m << 16 or 0xFFFFFFFF)."""
+    frame_b (n,3) uint8, choice uint32 = k | m << 16 or 0xFFFFFFFF).  max_dl >= 0:
+    only pairs within the luminance limit count (< 0: no limit)."""
     rgbs = np.ascontiguousarray(np.asarray(rgbs, np.uint8).reshape(-1, 3))
     pats = np.ascontiguousarray(np.asarray(patterns, np.uint8).reshape(-1))
     n = rgbs.shape[0]
@@ -307,5 +308,6 @@ def embed(rgbs, patterns, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, g
     choice = np.zeros(n, np.uint32)
     lib().orc_embed(ctypes.byref(consts()), _ptr(rgbs), _ptr(pats), n, _ptr(radii), len(radii),
                     _ptr(s), _ptr(c), len(s), float(v_th), float(r_novib), int(pattern_mask),
-                    int(gamut_mode), _ptr(fa), _ptr(fb), _ptr(choice), int(threads))
+                    int(gamut_mode), float(max_dl), _ptr(fa), _ptr(fb), _ptr(choice),
+                    int(threads))
     return fa, fb, choice

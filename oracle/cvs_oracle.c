@@ -342,18 +342,19 @@ void orc_search_colors(const orc_consts* C, const uint8_t* rgb, int64_t n_target
 
 /* Embedding (Fig. 1a: devices see an area that looks uniform to people switch
  * between two colours).  Per pixel i with requested pattern p = pattern[i] in
- * 1..7: among the candidates (k, m) whose pair passes with exactly pattern p,
- * take the first in (radius value, k, m) order - the smallest colour shift,
- * then the caller's radius and angle order.  Frame A gets the pair's "plus"
- * colour (a* + D_a, b* + D_b), frame B its "minus" colour.  Pixels with p
- * outside 1..7, or with no such candidate, keep their own colour in both
- * frames.  choice[i] = k | m << 16, or 0xFFFFFFFF when nothing was embedded.
- * rgb, frame_a, frame_b: 3 bytes per pixel, dense. */
+ * 1..7: among the candidates (k, m) whose pair passes with exactly pattern p
+ * (and, with a luminance limit max_dl >= 0, passes it too), take the first in
+ * (radius value, k, m) order - the smallest colour shift, then the caller's
+ * radius and angle order.  Frame A gets the pair's "plus" colour (a* + D_a,
+ * b* + D_b), frame B its "minus" colour.  Pixels with p outside 1..7, or with
+ * no such candidate, keep their own colour in both frames.  choice[i] =
+ * k | m << 16, or 0xFFFFFFFF when nothing was embedded.  rgb, frame_a,
+ * frame_b: 3 bytes per pixel, dense. */
 void orc_embed(const orc_consts* C, const uint8_t* rgb, const uint8_t* pattern,
                int64_t n_pixels, const double* radii, int32_t n_radii, const double* sin_t,
                const double* cos_t, int32_t n_angles, double v_th, double r_novib,
-               uint32_t pattern_mask, int gamut_mode, uint8_t* frame_a, uint8_t* frame_b,
-               uint32_t* choice, int n_threads) {
+               uint32_t pattern_mask, int gamut_mode, double max_dl, uint8_t* frame_a,
+               uint8_t* frame_b, uint32_t* choice, int n_threads) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
 #endif
@@ -376,7 +377,8 @@ void orc_embed(const orc_consts* C, const uint8_t* rgb, const uint8_t* pattern,
                     int qp[3], qm[3];
                     uint8_t op[3], om[3];
                     orc_pair_codes(C, lab, radii[k], sin_t[m], cos_t[m], qp, qm);
-                    if (decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, op, om) != p)
+                    if (decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, op, om) != p ||
+                        !passes_dl(C, lab[0], op, om, max_dl))
                         continue;
                     found = 1;
                     best_r = radii[k];

@@ -41,7 +41,8 @@ class cvs_grid(ctypes.Structure):
 
 class cvs_thresholds(ctypes.Structure):
     _fields_ = [("v_th", ctypes.c_double), ("r_novib", ctypes.c_double),
-                ("pattern_mask", ctypes.c_uint32), ("gamut_mode", ctypes.c_int32)]
+                ("pattern_mask", ctypes.c_uint32), ("gamut_mode", ctypes.c_int32),
+                ("max_dl", ctypes.c_double)]
 
 
 class cvs_pair(ctypes.Structure):
@@ -71,7 +72,8 @@ class cvs_stats(ctypes.Structure):
 class cvs_precision_report(ctypes.Structure):
     _fields_ = [("max_code_err", ctypes.c_double), ("max_lin_err", ctypes.c_double),
                 ("max_lab_err", ctypes.c_double), ("n_wrong_codes", ctypes.c_int64),
-                ("n_values", ctypes.c_int64)]
+                ("n_values", ctypes.c_int64), ("n_unflagged_wrong", ctypes.c_int64),
+                ("window", ctypes.c_double)]
 
 
 class cvs_launch_shape(ctypes.Structure):
@@ -123,7 +125,7 @@ def lib() -> ctypes.CDLL:
     P, vp = ctypes.POINTER, ctypes.c_void_p
     i32, i64, u32, d, st = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double, ctypes.c_int
     sig = {
-        "cvs_create": ([P(vp), ctypes.c_int], st),
+        "cvs_create": ([P(vp), ctypes.c_int, ctypes.c_size_t], st),
         "cvs_destroy": ([vp], None),
         "cvs_last_error": ([], ctypes.c_char_p),
         "cvs_version": ([], ctypes.c_char_p),
@@ -196,13 +198,15 @@ def make_grid(radii, angles_deg):
     return g, (r, a)
 
 
-def make_thresholds(v_th, r_novib, pattern_mask=0x7F, gamut_mode=0):
-    return cvs_thresholds(float(v_th), float(r_novib), int(pattern_mask), int(gamut_mode))
+def make_thresholds(v_th, r_novib, pattern_mask=0x7F, gamut_mode=0, max_dl=None):
+    """A cvs_thresholds struct; max_dl None (or 0, or inf) = no luminance limit."""
+    return cvs_thresholds(float(v_th), float(r_novib), int(pattern_mask), int(gamut_mode),
+                          0.0 if max_dl is None else float(max_dl))
 
 
-def signal_bounds(v_th, r_novib, pattern_mask=0x7F, gamut_mode=0):
+def signal_bounds(v_th, r_novib, pattern_mask=0x7F, gamut_mode=0, max_dl=None):
     """(hi_min, lo_max) integer bounds of the embedding-signal condition."""
-    t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+    t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
     hi, lo = ctypes.c_int32(), ctypes.c_int32()
     check(lib().cvs_signal_bounds(ctypes.byref(t), ctypes.byref(hi), ctypes.byref(lo)),
           "cvs_signal_bounds")
@@ -220,9 +224,11 @@ def _stream_ptr(stream) -> int | None:
 class Context:
     """A libcvsearch context on one CUDA device."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, mem_budget: int = 0):
+        """mem_budget: cap in bytes on the device memory the context allocates
+        (0 = none)."""
         self._h = ctypes.c_void_p()
-        check(lib().cvs_create(ctypes.byref(self._h), int(device)), "cvs_create")
+        check(lib().cvs_create(ctypes.byref(self._h), int(device), int(mem_budget)), "cvs_create")
         self.device = device
 
     def close(self):
@@ -285,10 +291,10 @@ class Context:
 
     # -------------------------------------------------------------- searches
     def search_color(self, rgb, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
-                     gamut_mode=0, precision=PREC_FP32_RECHECK, target=0, cap=None):
+                     gamut_mode=0, max_dl=None, precision=PREC_FP32_RECHECK, target=0, cap=None):
         """All passing pairs of one colour, sorted by (k, m): (PAIR_DTYPE array, total)."""
         g, keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         src = (ctypes.c_uint8 * 3)(*[int(x) for x in rgb])
         if cap is None:
             cap = len(keep[0]) * len(keep[1])
@@ -301,7 +307,8 @@ class Context:
         return out[:min(n.value, cap)], n.value
 
     def search_colors(self, rgb_dev, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
-                      gamut_mode=0, precision=PREC_FP32_RECHECK, out=None, stream=None):
+                      gamut_mode=0, max_dl=None,
+                      precision=PREC_FP32_RECHECK, out=None, stream=None):
         """Per-colour (max_r, count, pmask) device tensors for an (n, 3) uint8 CUDA tensor."""
         import torch
         n = rgb_dev.numel() // 3
@@ -311,7 +318,7 @@ class Context:
                    torch.empty(n, dtype=torch.int32, device=dev),
                    torch.empty(n, dtype=torch.uint8, device=dev))
         g, keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         m = cvs_capacity_map(out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
         check(lib().cvs_search_colors(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g),
                                       ctypes.byref(t), int(precision), ctypes.byref(m),
@@ -319,13 +326,14 @@ class Context:
         return out
 
     def search_colors_pairs(self, rgb_dev, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
-                            gamut_mode=0, precision=PREC_FP32_RECHECK, cap=None, stream=None):
+                            gamut_mode=0, max_dl=None,
+                            precision=PREC_FP32_RECHECK, cap=None, stream=None):
         """Every passing pair of n colours: (records (total, 16) uint8 CUDA tensor
         viewable as PAIR_DTYPE, offsets int64 NumPy array of n + 1)."""
         import torch
         n = rgb_dev.numel() // 3
         g, keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         offs = np.zeros(n + 1, np.int64)
         total = ctypes.c_int64()
         if cap is None:  # ask for the size first
@@ -348,14 +356,16 @@ class Context:
                             precision=PREC_FP32_RECHECK, out=None, stream=None):
         """Per-colour results under several threshold sets in one pass.
 
-        thresholds: sequence of (v_th, r_novib) or (v_th, r_novib, pattern_mask).
+        thresholds: sequence of (v_th, r_novib), (v_th, r_novib, pattern_mask) or
+        (v_th, r_novib, pattern_mask, max_dl).
         Returns (max_r, count, pmask) device tensors of shape (n, n_sets)."""
         import torch
         n = rgb_dev.numel() // 3
         sets = [tuple(x) for x in thresholds]
         arr = (cvs_thresholds * max(len(sets), 1))()
         for i, x in enumerate(sets):
-            arr[i] = make_thresholds(x[0], x[1], x[2] if len(x) > 2 else 0x7F, gamut_mode)
+            arr[i] = make_thresholds(x[0], x[1], x[2] if len(x) > 2 else 0x7F, gamut_mode,
+                                     x[3] if len(x) > 3 else None)
         dev = rgb_dev.device
         shape = (n, len(sets))
         if out is None:
@@ -370,14 +380,14 @@ class Context:
         return out
 
     def search_colors_host(self, rgb, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
-                           gamut_mode=0, precision=PREC_FP32_RECHECK, out=None):
+                           gamut_mode=0, max_dl=None, precision=PREC_FP32_RECHECK, out=None):
         """As search_colors, with host NumPy buffers (copies inside the call)."""
         rgb = np.ascontiguousarray(np.asarray(rgb, np.uint8).reshape(-1, 3))
         n = rgb.shape[0]
         if out is None:
             out = (np.empty(n, np.float32), np.empty(n, np.int32), np.empty(n, np.uint8))
         g, keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         check(lib().cvs_search_colors_host(self._h, rgb.ctypes.data, n, ctypes.byref(g),
                                            ctypes.byref(t), int(precision), out[0].ctypes.data,
                                            out[1].ctypes.data, out[2].ctypes.data),
@@ -385,7 +395,8 @@ class Context:
         return out
 
     def embed_image(self, image, pattern, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
-                    gamut_mode=0, precision=PREC_FP32_RECHECK, frames=None, choice=True,
+                    gamut_mode=0, max_dl=None,
+                    precision=PREC_FP32_RECHECK, frames=None, choice=True,
                     stream=None):
         """The two alternating frames of an (H, W, 3) uint8 CUDA image carrying a
         per-pixel pattern ((H, W) uint8 CUDA tensor, 1..7, 0 = none).
@@ -393,7 +404,7 @@ class Context:
         of k | m << 16 (-1 where nothing was embedded) or None."""
         im, frames, ch = _embed_buffers(image, pattern, frames, choice)
         g, keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         check(lib().cvs_embed_image(self._h, ctypes.byref(im), pattern.data_ptr(), pattern.stride(0),
                                     ctypes.byref(g), ctypes.byref(t), int(precision),
                                     frames[0].data_ptr(), frames[1].data_ptr(),
@@ -402,7 +413,8 @@ class Context:
         return frames[0], frames[1], ch
 
     def search_images(self, images, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
-                      gamut_mode=0, precision=PREC_FP32_RECHECK, maps=None, stream=None):
+                      gamut_mode=0, max_dl=None,
+                      precision=PREC_FP32_RECHECK, maps=None, stream=None):
         """Per-pixel maps for a list of (H, W, 3) uint8 CUDA tensors (row pitch from stride)."""
         import torch
         n = len(images)
@@ -423,7 +435,7 @@ class Context:
             cmaps[i] = cvs_capacity_map(maps[i][0].data_ptr(), maps[i][1].data_ptr(),
                                         maps[i][2].data_ptr())
         g, keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         check(lib().cvs_search_images(self._h, descs, n, ctypes.byref(g), ctypes.byref(t),
                                       int(precision), cmaps, _stream_ptr(stream)),
               "cvs_search_images")
@@ -438,10 +450,10 @@ class Context:
         return {f: getattr(s, f) for f, _ in cvs_stats._fields_}
 
     def autotune(self, rgb_dev, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
-                 gamut_mode=0, precision=PREC_FP32_RECHECK) -> dict:
+                 gamut_mode=0, max_dl=None, precision=PREC_FP32_RECHECK) -> dict:
         """Time launch shapes on these colours and keep the fastest (see cvs_autotune)."""
         g, keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         best = cvs_launch_shape()
         n = rgb_dev.numel() // 3
         check(lib().cvs_autotune(self._h, rgb_dev.data_ptr(), n, ctypes.byref(g), ctypes.byref(t),
@@ -449,21 +461,21 @@ class Context:
         return {f: getattr(best, f) for f, _ in cvs_launch_shape._fields_}
 
     def build_lut(self, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0,
-                  precision=PREC_FP32_RECHECK, stream=None) -> "CapacityTable":
+                  max_dl=None, precision=PREC_FP32_RECHECK, stream=None) -> "CapacityTable":
         """Capacity table of all 2^24 colours for this grid and thresholds."""
         g, keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         h = ctypes.c_void_p()
         check(lib().cvs_lut_build(self._h, ctypes.byref(g), ctypes.byref(t), int(precision),
                                   ctypes.byref(h), _stream_ptr(stream)), "cvs_lut_build")
         return CapacityTable(h)
 
     def build_embed_table(self, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F,
-                          gamut_mode=0, precision=PREC_FP32_RECHECK,
+                          gamut_mode=0, max_dl=None, precision=PREC_FP32_RECHECK,
                           stream=None) -> "EmbedTable":
         """Embedding table of all 2^24 colours x 7 patterns for this grid and thresholds."""
         g, keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         h = ctypes.c_void_p()
         check(lib().cvs_etab_build(self._h, ctypes.byref(g), ctypes.byref(t), int(precision),
                                    ctypes.byref(h), _stream_ptr(stream)), "cvs_etab_build")
@@ -580,11 +592,11 @@ class Server:
     read the device-resident maps, release."""
 
     def __init__(self, radii, angles_deg, v_th, r_novib, pattern_mask=0x7F, gamut_mode=0,
-                 precision=PREC_FP32_RECHECK, device=0, max_inflight=2,
+                 max_dl=None, precision=PREC_FP32_RECHECK, device=0, max_inflight=2,
                  max_pixels=7680 * 4320, mem_budget_bytes=4 << 30, use_table=False,
                  dedup=False):
         g, self._keep = make_grid(radii, angles_deg)
-        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode)
+        t = make_thresholds(v_th, r_novib, pattern_mask, gamut_mode, max_dl)
         cfg = cvs_server_config(int(device), int(max_inflight), int(max_pixels),
                                 int(mem_budget_bytes), int(bool(use_table)), int(bool(dedup)))
         self._h = ctypes.c_void_p()

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -41,25 +42,36 @@ cvs_status fail(cvs_status st, const char* fmt, ...) {
 
 constexpr int32_t kMaxGrid = 8192;  // shared-memory tables: 8 B per radius, 16 B per angle slot
 
-template <class T>
-cudaError_t grow(T** p, int64_t* cap, int64_t need) {
-    if (*cap >= need && *p) return cudaSuccess;
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-    *cap = 0;
-    int64_t n = need < 1 ? 1 : need;
-    cudaError_t e = cudaMalloc((void**)p, (size_t)n * sizeof(T));
-    if (e == cudaSuccess) *cap = n;
-    return e;
-}
-
 }  // namespace
 
 void cvs::set_error_message(const char* msg) { g_err = msg; }
 
+int cvs::auto_kchunk(int num_sms, int64_t n_targets, int K, int H) {
+    // aim for >= 32 work items per SM warp-slot group, but >= 2 warp iterations per item
+    const int64_t want_items = (int64_t)num_sms * 512;
+    int64_t n_kc = (want_items + n_targets - 1) / (n_targets > 0 ? n_targets : 1);
+    if (n_kc < 1) n_kc = 1;
+    if (n_kc > K) n_kc = K;
+    int kchunk = (int)((K + n_kc - 1) / n_kc);
+    const int min_k = (64 + H - 1) / H;
+    if (kchunk < min_k) kchunk = min_k < K ? min_k : K;
+    return kchunk;
+}
+
+int cvs::fold_by_180(const double* s, const double* c, int N) {
+    if (N % 2) return 0;
+    for (int m = 0; m < N / 2; ++m)
+        if (!(s[m + N / 2] == -s[m] && c[m + N / 2] == -c[m])) return 0;
+    return 1;
+}
+
 struct cvs_ctx {
     int device = 0;
     int num_sms = 0;
+    // device memory the context owns (scratch, tables, graph copies), with
+    // its size, counted against the budget given to cvs_create (0 = none)
+    size_t budget = 0, in_use = 0;
+    std::unordered_map<void*, size_t> owned;
     cudaStream_t own = nullptr;  // stream of the synchronous entry points
     // grid cache
     std::vector<double> radii, angles;
@@ -75,10 +87,19 @@ struct cvs_ctx {
     long long* qkey = nullptr;
     unsigned long long* counters = nullptr;  // kNumCounters: work, flagged, rechecked, n_out, skipped
     unsigned long long* h_counters = nullptr;  // pinned copy
-    // list mode
-    cvs_pair* dense = nullptr;
+    // pair lists: records of cvs_search_color; per work item of a batch its
+    // passing-slot bitmap, count and scan base; per tile of the scan its base
     cvs_pair* compact = nullptr;
-    int64_t cap_dense = 0, cap_compact = 0;
+    int64_t cap_compact = 0;
+    uint32_t* d_bits = nullptr;
+    int64_t cap_bits = 0;
+    uint32_t* d_icount = nullptr;
+    int64_t cap_icount = 0;
+    int64_t* d_within = nullptr;
+    int64_t cap_within = 0;
+    int64_t* d_tiles = nullptr;
+    int64_t cap_tiles = 0;
+    int64_t list_batch_items = int64_t(1) << 22;  // most work items per batch
     // images
     ImageDesc* d_imgs = nullptr;
     int64_t cap_imgs = 0;
@@ -125,9 +146,11 @@ struct cvs_ctx {
     // pair lists of many colours: per-colour offsets into the caller's output
     int64_t* d_offs = nullptr;
     int64_t cap_offs = 0;
-    // luminance limit on emitted pairs (off while max_dl < 0); L* of all 2^24 colours
-    double max_dl = -1.0;
+    // L* of all 2^24 colours, built by the first call with a luminance limit
     double* ltab = nullptr;
+    // 1: CVS_PREC_FP32_RECHECK on a grid with a radius above kFp32MaxRadius
+    // runs in FP64; 0 (default): such a call is refused
+    int fp64_fallback = 0;
     // embedding: radius indices sorted by (radius value, index), K entries
     int32_t* d_order = nullptr;
     // multi-threshold search: n x n_thr accumulators
@@ -151,6 +174,63 @@ struct cvs_ctx {
 
 namespace {
 
+// Allocate `bytes` of device memory owned by the context, within its budget.
+cvs_status ctx_alloc(cvs_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    if (c->budget && c->in_use + bytes > c->budget)
+        return fail(CVS_ERR_NO_MEMORY,
+                    "context memory budget of %zu bytes exceeded: %zu in use, %zu more needed",
+                    c->budget, c->in_use, bytes);
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? CVS_ERR_NO_MEMORY : CVS_ERR_CUDA,
+                    "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    c->owned[*p] = bytes;
+    c->in_use += bytes;
+    return CVS_OK;
+}
+
+template <class T>
+cvs_status ctx_alloc(cvs_ctx* c, T** p, size_t bytes) {
+    void* v = nullptr;
+    const cvs_status st = ctx_alloc(c, &v, bytes);
+    *p = static_cast<T*>(v);
+    return st;
+}
+
+// Release memory from ctx_alloc (NULL is ignored).
+void ctx_free(cvs_ctx* c, void* p) {
+    if (!p) return;
+    auto it = c->owned.find(p);
+    if (it != c->owned.end()) {
+        c->in_use -= it->second;
+        c->owned.erase(it);
+    }
+    cudaFree(p);
+}
+
+// Make *p hold at least `need` elements (contents are not kept).
+template <class T>
+cvs_status grow(cvs_ctx* c, T** p, int64_t* cap, int64_t need) {
+    if (*cap >= need && *p) return CVS_OK;
+    ctx_free(c, *p);
+    *p = nullptr;
+    *cap = 0;
+    const int64_t n = need < 1 ? 1 : need;
+    const cvs_status st = ctx_alloc(c, p, (size_t)n * sizeof(T));
+    if (st == CVS_OK) *cap = n;
+    return st;
+}
+
+#define CVS_TRY(call)                        \
+    do {                                     \
+        const cvs_status s_ = (call);        \
+        if (s_ != CVS_OK) return s_;         \
+    } while (0)
+
 cvs_status set_device(cvs_ctx* c) {
     CVS_CUDA(cudaSetDevice(c->device));
     return CVS_OK;
@@ -167,8 +247,35 @@ cvs_status check_thresholds(const cvs_thresholds* t) {
                     t->pattern_mask);
     if (t->gamut_mode != 0 && t->gamut_mode != 1)
         return fail(CVS_ERR_INVALID_ARG, "gamut_mode must be 0 (reject) or 1 (clip)");
+    if (std::isnan(t->max_dl) || t->max_dl < 0.0)
+        return fail(CVS_ERR_INVALID_ARG,
+                    "max_dl must be 0 or +inf (no limit) or a positive limit (got %g)", t->max_dl);
     return CVS_OK;
 }
+
+// The luminance limit of a threshold set is on for a positive, finite max_dl.
+bool dl_on(const cvs_thresholds* t) { return t->max_dl > 0.0 && std::isfinite(t->max_dl); }
+
+// The L* table of all 2^24 colours that the luminance limit reads, built once
+// (synchronously, outside any capture) by the first call that needs it.
+cvs_status ensure_ltab(cvs_ctx* c, const cvs_thresholds* t) {
+    if (!dl_on(t) || c->ltab) return CVS_OK;
+    CVS_TRY(ctx_alloc(c, &c->ltab, sizeof(double) << 24));
+    CVS_CUDA(launch_l_table(c->ltab, c->own));
+    CVS_CUDA(cudaStreamSynchronize(c->own));
+    return CVS_OK;
+}
+
+}  // namespace
+
+cvs_status cvs::prepare_thresholds(cvs_ctx* c, const cvs_thresholds* t) {
+    cvs_status st = check_thresholds(t);
+    if (st == CVS_OK) st = set_device(c);
+    if (st == CVS_OK) st = ensure_ltab(c, t);
+    return st;
+}
+
+namespace {
 
 cvs_status check_grid(const cvs_grid* g) {
     if (!g) return fail(CVS_ERR_INVALID_ARG, "grid pointer is NULL");
@@ -200,13 +307,13 @@ cvs_status ensure_grid(cvs_ctx* c, const cvs_grid* g) {
     CVS_CUDA(cudaDeviceSynchronize());
     d.K = 0;  // invalid until complete
     if (c->cap_grid < kMaxGrid) {
-        CVS_CUDA(cudaMalloc(&d.r32, sizeof(float) * kMaxGrid));
-        CVS_CUDA(cudaMalloc(&d.sc32, sizeof(float2) * kMaxGrid));
-        CVS_CUDA(cudaMalloc(&d.r64, sizeof(double) * kMaxGrid));
-        CVS_CUDA(cudaMalloc(&d.s64, sizeof(double) * kMaxGrid));
-        CVS_CUDA(cudaMalloc(&d.c64, sizeof(double) * kMaxGrid));
-        CVS_CUDA(cudaMalloc(&c->d_angles, sizeof(double) * kMaxGrid));
-        CVS_CUDA(cudaMalloc(&c->d_order, sizeof(int32_t) * kMaxGrid));
+        CVS_TRY(ctx_alloc(c, &d.r32, sizeof(float) * kMaxGrid));
+        CVS_TRY(ctx_alloc(c, &d.sc32, sizeof(float2) * kMaxGrid));
+        CVS_TRY(ctx_alloc(c, &d.r64, sizeof(double) * kMaxGrid));
+        CVS_TRY(ctx_alloc(c, &d.s64, sizeof(double) * kMaxGrid));
+        CVS_TRY(ctx_alloc(c, &d.c64, sizeof(double) * kMaxGrid));
+        CVS_TRY(ctx_alloc(c, &c->d_angles, sizeof(double) * kMaxGrid));
+        CVS_TRY(ctx_alloc(c, &c->d_order, sizeof(int32_t) * kMaxGrid));
         c->cap_grid = kMaxGrid;
     }
     std::vector<float> r32(K);
@@ -235,21 +342,24 @@ cvs_status ensure_grid(cvs_ctx* c, const cvs_grid* g) {
     CVS_CUDA(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
     CVS_CUDA(cudaStreamSynchronize(st));
     if (status) return fail(CVS_ERR_NUMERIC, "an angle's sine could not be certified");
-    // Fold by +180 degrees when the table is exactly antisymmetric.
-    int sym = (N % 2 == 0) ? 1 : 0;
-    for (int m = 0; sym && m < N / 2; ++m)
-        if (!(s[m + N / 2] == -s[m] && co[m + N / 2] == -co[m])) sym = 0;
+    const int sym = fold_by_180(s.data(), co.data(), N);
     d.sym = sym;
     d.H = sym ? N / 2 : N;
-    // Angle ranges need slot h at angle angles[0] + h * 360 / N, h < N / 2.
+    // Angle ranges need slot h at angle angles[0] + h * 360 / N, h < N / 2,
+    // to within 1e-6 degrees (the ranges carry a margin of 2e-4 rad).
     int even = sym;
     const double step = 360.0 / N;
     for (int m = 0; even && m < N / 2; ++m) {
         const double want = g->angles_deg[0] + m * step;
-        if (!(std::fabs(g->angles_deg[m] - want) <= 1e-9 * (1.0 + std::fabs(want)))) even = 0;
+        if (!(std::fabs(g->angles_deg[m] - want) <= 1e-6)) even = 0;
     }
     d.arcs_ok = even;
-    d.th0 = (float)(g->angles_deg[0] * (3.14159265358979323846 / 180.0));
+    // The first angle reduced to [0, 360) in double before it is rounded to
+    // FP32 radians: fmod is exact, so a large offset (say 1e6 + 0.5 degrees)
+    // costs no more than the final FP32 rounding (< 4e-7 rad).
+    double th0_deg = std::fmod(g->angles_deg[0], 360.0);
+    if (th0_deg < 0.0) th0_deg += 360.0;
+    d.th0 = (float)(th0_deg * (3.14159265358979323846 / 180.0));
     d.inv_step = even ? (float)(N / (2.0 * 3.14159265358979323846)) : 0.0f;
     d.arcs = d.arcs_ok && c->angle_ranges;
     d.N = N;
@@ -270,11 +380,25 @@ cvs_status ensure_arc_scratch(cvs_ctx* c, int64_t n);
 cvs_status ensure_dedup(cvs_ctx* c) {
     if (c->d_present) return CVS_OK;
     constexpr size_t kColours = size_t(1) << 24;
-    CVS_CUDA(cudaMalloc(&c->d_present, kColours));
-    CVS_CUDA(cudaMalloc(&c->d_index, sizeof(int32_t) * kColours));
-    CVS_CUDA(cudaMalloc(&c->d_unique, 3 * kColours));
-    CVS_CUDA(cudaMalloc(&c->d_scan, sizeof(int) * 1025));
+    CVS_TRY(ctx_alloc(c, &c->d_present, kColours));
+    CVS_TRY(ctx_alloc(c, &c->d_index, sizeof(int32_t) * kColours));
+    CVS_TRY(ctx_alloc(c, &c->d_unique, 3 * kColours));
+    CVS_TRY(ctx_alloc(c, &c->d_scan, sizeof(int) * 1025));
     CVS_CUDA(cudaMallocHost(&c->h_unique, sizeof(int)));
+    return CVS_OK;
+}
+
+// The FP32 path's error bound is validated for radii up to kFp32MaxRadius:
+// on a grid with a larger radius an FP32 request is refused, or (option
+// "fp64_fallback") turned into FP64, which cvs_stats.precision reports.
+cvs_status resolve_precision(cvs_ctx* c, cvs_precision* prec) {
+    if (*prec != CVS_PREC_FP32_RECHECK || c->grid.rmax <= kFp32MaxRadius) return CVS_OK;
+    if (!c->fp64_fallback)
+        return fail(CVS_ERR_INVALID_ARG,
+                    "CVS_PREC_FP32_RECHECK is validated for radii up to %g and the grid has %g: "
+                    "pass CVS_PREC_FP64 (about 100x slower), or set option \"fp64_fallback\" to "
+                    "1 to have such grids run in FP64", kFp32MaxRadius, c->grid.rmax);
+    *prec = CVS_PREC_FP64;
     return CVS_OK;
 }
 
@@ -284,20 +408,20 @@ cvs_status ensure_targets(cvs_ctx* c, int64_t n) {
         ++c->scratch_gen;
     }
     if (c->cap_tf < n) {
-        if (c->tf) cudaFree(c->tf);
+        ctx_free(c, c->tf);
         c->tf = nullptr;
         c->cap_tf = 0;
-        CVS_CUDA(cudaMalloc((void**)&c->tf, target_f32_size() * (size_t)n));
+        CVS_TRY(ctx_alloc(c, &c->tf, target_f32_size() * (size_t)n));
         c->cap_tf = n;
     }
     if (c->cap_td < n) {
-        if (c->td) cudaFree(c->td);
+        ctx_free(c, c->td);
         c->td = nullptr;
         c->cap_td = 0;
-        CVS_CUDA(cudaMalloc((void**)&c->td, target_f64_size() * (size_t)n));
+        CVS_TRY(ctx_alloc(c, &c->td, target_f64_size() * (size_t)n));
         c->cap_td = n;
     }
-    CVS_CUDA(grow(&c->acc, &c->cap_acc, n));
+    CVS_TRY(grow(c, &c->acc, &c->cap_acc, n));
     return ensure_arc_scratch(c, n);  // before any capture can need it
 }
 
@@ -315,15 +439,7 @@ void thresholds_to_int(const cvs_thresholds* t, int32_t* hi_min, int32_t* lo_max
 
 int choose_kchunk(const cvs_ctx* c, int64_t n_targets, int K, int H) {
     if (c->shape.kchunk > 0) return c->shape.kchunk < K ? c->shape.kchunk : K;
-    // aim for >= 32 work items per SM warp-slot group, but >= 2 warp iterations per item
-    const int64_t want_items = (int64_t)c->num_sms * 512;
-    int64_t n_kc = (want_items + n_targets - 1) / (n_targets > 0 ? n_targets : 1);
-    if (n_kc < 1) n_kc = 1;
-    if (n_kc > K) n_kc = K;
-    int kchunk = (int)((K + n_kc - 1) / n_kc);
-    const int min_k = (64 + H - 1) / H;
-    if (kchunk < min_k) kchunk = min_k < K ? min_k : K;
-    return kchunk;
+    return auto_kchunk(c->num_sms, n_targets, K, H);
 }
 
 std::array<int64_t, 7> tune_key(const cvs_ctx* c, int64_t n, int prec, int clip, int list) {
@@ -343,8 +459,9 @@ cvs_status tune_shape(cvs_ctx* c, const SearchArgs& base, cudaStream_t st, Launc
     const int64_t per_target = (int64_t)K * H * (c->grid.sym ? 2 : 1);
     const int64_t cap = (int64_t)3e10 / (per_target > 0 ? per_target : 1);
     if (n > cap) n = cap < 1 ? 1 : cap;
-    CVS_CUDA(grow(&c->acc_tune, &c->cap_acc_tune, n));
-    if (!c->tune_counters) CVS_CUDA(cudaMalloc(&c->tune_counters, kNumCounters * sizeof(unsigned long long)));
+    CVS_TRY(grow(c, &c->acc_tune, &c->cap_acc_tune, n));
+    if (!c->tune_counters)
+        CVS_TRY(ctx_alloc(c, &c->tune_counters, kNumCounters * sizeof(unsigned long long)));
     std::vector<LaunchShape> cand;
     const int auto_k = choose_kchunk(c, n, K, H);
     const int min_k = (64 + H - 1) / H;
@@ -413,16 +530,16 @@ int64_t arc_entries(const cvs_ctx* c, int64_t n) {
 cvs_status ensure_arc_scratch(cvs_ctx* c, int64_t n) {
     if (!c->grid.arcs) return CVS_OK;
     if (!c->d_arc_probe) {  // the probe's counts (allocated with the scratch, ahead of any search)
-        CVS_CUDA(cudaMalloc(&c->d_arc_probe, 2 * sizeof(unsigned long long)));
+        CVS_TRY(ctx_alloc(c, &c->d_arc_probe, 2 * sizeof(unsigned long long)));
         CVS_CUDA(cudaMallocHost(&c->h_arc_probe, 2 * sizeof(unsigned long long)));
     }
     const int64_t need = arc_entries(c, n);
     if (c->cap_arc >= need) return CVS_OK;
     drop_graphs(c);  // captured graphs point at the buffer about to be replaced
-    if (c->arc_ranges) CVS_CUDA(cudaFree(c->arc_ranges));
+    ctx_free(c, c->arc_ranges);
     c->arc_ranges = nullptr;
     c->cap_arc = 0;
-    CVS_CUDA(cudaMalloc(&c->arc_ranges, sizeof(uint2) * (size_t)need));
+    CVS_TRY(ctx_alloc(c, &c->arc_ranges, sizeof(uint2) * (size_t)need));
     c->cap_arc = need;
     return CVS_OK;
 }
@@ -480,8 +597,18 @@ cvs_status prepare_arcs(cvs_ctx* c, SearchArgs& a, int64_t n, cvs_precision prec
     return CVS_OK;
 }
 
+// Where a pair-list search (list mode) leaves its work items' bitmaps and
+// counts, and the radii per work item fixed for the whole call.
+struct ListOut {
+    uint32_t* item_bits = nullptr;
+    int item_words = 0;
+    uint32_t* item_count = nullptr;
+    int kchunk = 1;
+};
+
 cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_precision prec,
-                      int list_mode, uint32_t target_id, cudaStream_t st, bool capturing = false) {
+                      int list_mode, uint32_t target_id, cudaStream_t st, bool capturing = false,
+                      const ListOut* lo = nullptr) {
     SearchArgs a{};
     a.tf = c->tf;
     a.td = c->td;
@@ -490,17 +617,20 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
     a.grid = c->grid;
     a.qkey = c->qkey;
     thresholds_to_int(thr, &a.hi_min, &a.lo_max);
-    // the FP32 path's error is validated for radii up to kFp32MaxRadius
-    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
     a.mask2 = thr->pattern_mask << 1;
     a.clip = thr->gamut_mode;
     a.half_w = (float)(0.5 - c->window);
     a.prec = (int32_t)prec;
     a.list_mode = list_mode;
-    a.dense = c->dense;
     a.target_id = target_id;
-    a.ltab = c->max_dl >= 0.0 ? c->ltab : nullptr;
-    a.max_dl = c->max_dl;
+    if (list_mode) {
+        a.item_bits = lo->item_bits;
+        a.item_words = lo->item_words;
+        a.item_count = lo->item_count;
+        a.item0 = 0;
+    }
+    a.ltab = dl_on(thr) ? c->ltab : nullptr;
+    a.max_dl = thr->max_dl;
     a.work_counter = c->counters;
     a.stats = c->counters + 1;
     a.shape = c->shape;
@@ -523,6 +653,7 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
         }
         if (it != c->tuned.end()) a.shape = it->second;
     }
+    if (list_mode) a.shape.kchunk = lo->kchunk;
     const unsigned ev_flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     CVS_CUDA(cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st));
     a.ev_ranges = c->ev_mid;
@@ -548,7 +679,7 @@ cvs_status run_search(cvs_ctx* c, int64_t n, const cvs_thresholds* thr, cvs_prec
 void drop_graphs(cvs_ctx* c) {
     for (auto& g : c->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
-        if (g.d_imgs) cudaFree(g.d_imgs);
+        ctx_free(c, g.d_imgs);
     }
     c->graphs.clear();
 }
@@ -575,13 +706,13 @@ cvs_status graph_launch(cvs_ctx* c, std::vector<uint64_t> key, cudaStream_t st, 
             for (size_t i = 1; i < c->graphs.size(); ++i)
                 if (c->graphs[i].last_use < c->graphs[lru].last_use) lru = i;
             if (c->graphs[lru].exec) cudaGraphExecDestroy(c->graphs[lru].exec);
-            if (c->graphs[lru].d_imgs) cudaFree(c->graphs[lru].d_imgs);
+            ctx_free(c, c->graphs[lru].d_imgs);
             c->graphs.erase(c->graphs.begin() + lru);
         }
         cvs_ctx::GraphEntry e;
         e.key = key;
         if (imgs) {  // the graph's own copy of the image table
-            CVS_CUDA(cudaMalloc(&e.d_imgs, sizeof(ImageDesc) * imgs->size()));
+            CVS_TRY(ctx_alloc(c, &e.d_imgs, sizeof(ImageDesc) * imgs->size()));
             CVS_CUDA(cudaMemcpy(e.d_imgs, imgs->data(), sizeof(ImageDesc) * imgs->size(),
                                 cudaMemcpyHostToDevice));
         }
@@ -591,17 +722,17 @@ cvs_status graph_launch(cvs_ctx* c, std::vector<uint64_t> key, cudaStream_t st, 
         cudaError_t ce = cudaStreamEndCapture(c->cap, &graph);
         if (est != CVS_OK) {
             if (graph) cudaGraphDestroy(graph);
-            if (e.d_imgs) cudaFree(e.d_imgs);
+            ctx_free(c, e.d_imgs);
             return est;
         }
         if (ce != cudaSuccess) {
-            if (e.d_imgs) cudaFree(e.d_imgs);
+            ctx_free(c, e.d_imgs);
             return fail(CVS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
         }
         ce = cudaGraphInstantiate(&e.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ce != cudaSuccess) {
-            if (e.d_imgs) cudaFree(e.d_imgs);
+            ctx_free(c, e.d_imgs);
             return fail(CVS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
         }
         c->graphs.push_back(e);
@@ -637,7 +768,7 @@ const char* cvs_last_error(void) { return g_err.c_str(); }
 
 const char* cvs_version(void) { return "0.1.0"; }
 
-cvs_status cvs_create(cvs_ctx** out, int device) {
+cvs_status cvs_create(cvs_ctx** out, int device, size_t mem_budget_bytes) {
     if (!out) return fail(CVS_ERR_INVALID_ARG, "ctx output pointer is NULL");
     *out = nullptr;
     int ndev = 0;
@@ -646,17 +777,23 @@ cvs_status cvs_create(cvs_ctx** out, int device) {
         return fail(CVS_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, ndev);
     cvs_ctx* c = new cvs_ctx();
     c->device = device;
+    c->budget = mem_budget_bytes;
     cvs_status st = set_device(c);
     if (st != CVS_OK) { delete c; return st; }
+    st = ctx_alloc(c, &c->qkey, 257 * sizeof(long long));
+    if (st == CVS_OK) st = ctx_alloc(c, &c->counters, kNumCounters * sizeof(unsigned long long));
+    if (st == CVS_OK) st = ctx_alloc(c, &c->d_status, sizeof(int));
+    if (st == CVS_OK) st = ctx_alloc(c, &c->d_rgb1, 16);
+    if (st == CVS_OK) st = ctx_alloc(c, &c->d_probe, 64);
+    if (st != CVS_OK) {
+        const std::string msg = g_err;
+        cvs_destroy(c);
+        return fail(st, "cvs_create: %s", msg.c_str());
+    }
     cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&c->qkey, 257 * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc(&c->counters, kNumCounters * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_counters, kNumCounters * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_rgb1, 16);
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_probe, 32);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev_mid);
@@ -675,18 +812,10 @@ void cvs_destroy(cvs_ctx* c) {
     cudaSetDevice(c->device);
     if (c->own) cudaStreamSynchronize(c->own);
     cudaDeviceSynchronize();
-    void* ptrs[] = {c->grid.r32, c->grid.sc32, c->grid.r64, c->grid.s64, c->grid.c64,
-                    c->d_angles, c->d_status, c->tf, c->td, c->acc, c->qkey, c->counters,
-                    c->dense, c->compact, c->d_imgs, c->d_in, c->d_maxr, c->d_count, c->d_pmask,
-                    c->d_rgb1, c->d_probe, c->d_order, c->ltab, c->d_offs,
-                    c->d_present, c->d_index, c->d_unique, c->d_scan, c->arc_ranges,
-                    c->d_arc_probe};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
     drop_graphs(c);
-    if (c->acc_tune) cudaFree(c->acc_tune);
-    if (c->acc_multi) cudaFree(c->acc_multi);
-    if (c->tune_counters) cudaFree(c->tune_counters);
+    for (auto& kv : c->owned) cudaFree(kv.first);  // every buffer the context allocated
+    c->owned.clear();
+    c->in_use = 0;
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->h_counters) cudaFreeHost(c->h_counters);
     if (c->h_unique) cudaFreeHost(c->h_unique);
@@ -730,6 +859,13 @@ cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
             if (ds != CVS_OK) return ds;
         }
         c->dedup = (int)value;
+    } else if (!std::strcmp(name, "fp64_fallback")) {
+        if (value != 0 && value != 1) return fail(CVS_ERR_INVALID_ARG, "fp64_fallback is 0 or 1");
+        c->fp64_fallback = (int)value;
+    } else if (!std::strcmp(name, "list_batch_items")) {
+        if (!(value >= 1 && value <= (double)(int64_t(1) << 26)))
+            return fail(CVS_ERR_INVALID_ARG, "list_batch_items in [1, 2^26]");
+        c->list_batch_items = (int64_t)value;
     } else if (!std::strcmp(name, "angle_ranges")) {
         if (value != 0 && value != 1 && value != 2)
             return fail(CVS_ERR_INVALID_ARG, "angle_ranges is 0, 1 or 2");
@@ -740,15 +876,6 @@ cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
             c->grid.arcs = arcs;
             c->tuned.clear();
         }
-    } else if (!std::strcmp(name, "max_dl")) {
-        if (std::isnan(value)) return fail(CVS_ERR_INVALID_ARG, "max_dl is NaN");
-        if (value >= 0.0 && !c->ltab) {  // built once, before any capture can need it
-            CVS_CUDA(cudaSetDevice(c->device));
-            CVS_CUDA(cudaMalloc(&c->ltab, sizeof(double) << 24));
-            CVS_CUDA(launch_l_table(c->ltab, c->own));
-            CVS_CUDA(cudaStreamSynchronize(c->own));
-        }
-        c->max_dl = value < 0.0 ? -1.0 : value;
     } else {
         return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);
     }
@@ -763,11 +890,14 @@ cvs_status cvs_get_option(cvs_ctx* c, const char* name, double* value) {
     else if (!std::strcmp(name, "kchunk")) *value = c->shape.kchunk;
     else if (!std::strcmp(name, "autotune")) *value = c->autotune;
     else if (!std::strcmp(name, "graphs")) *value = c->use_graphs;
-    else if (!std::strcmp(name, "max_dl")) *value = c->max_dl;
     else if (!std::strcmp(name, "dedup")) *value = c->dedup;
     else if (!std::strcmp(name, "angle_ranges")) *value = c->angle_ranges;
+    else if (!std::strcmp(name, "list_batch_items")) *value = (double)c->list_batch_items;
+    else if (!std::strcmp(name, "fp64_fallback")) *value = c->fp64_fallback;
     else if (!std::strcmp(name, "graph_launches")) *value = (double)c->graph_launches;
     else if (!std::strcmp(name, "graphs_cached")) *value = (double)c->graphs.size();
+    else if (!std::strcmp(name, "mem_in_use")) *value = (double)c->in_use;
+    else if (!std::strcmp(name, "mem_budget")) *value = (double)c->budget;
     else return fail(CVS_ERR_INVALID_ARG, "unknown option '%s'", name);
     return CVS_OK;
 }
@@ -790,7 +920,7 @@ cvs_status cvs_trig_table(cvs_ctx* c, const double* angles, int32_t n, double* s
     double *da = nullptr, *ds = nullptr, *dc = nullptr;
     float2* dsc = nullptr;
     cudaStream_t st = c->own;
-    CVS_CUDA(cudaMalloc(&da, sizeof(double) * n * 3 + sizeof(float2) * n));
+    CVS_TRY(ctx_alloc(c, &da, sizeof(double) * n * 3 + sizeof(float2) * n));
     ds = da + n;
     dc = ds + n;
     dsc = reinterpret_cast<float2*>(dc + n);
@@ -803,7 +933,7 @@ cvs_status cvs_trig_table(cvs_ctx* c, const double* angles, int32_t n, double* s
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(da);
+    ctx_free(c, da);
     if (e != cudaSuccess) return fail(CVS_ERR_CUDA, "cvs_trig_table: %s", cudaGetErrorString(e));
     if (status) return fail(CVS_ERR_NUMERIC, "an angle's sine could not be certified");
     return CVS_OK;
@@ -819,6 +949,85 @@ cvs_status cvs_target_lab(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, double*
     return CVS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Every passing pair of n colours on the device (grid and thresholds
+// prepared by the caller), per batch of colours: the search leaves each work
+// item's passing-slot bitmap and count; a scan of the counts gives each
+// item's first record; the emit kernel writes the records, in (target, k, m)
+// order, straight to out (records at or beyond cap are not written).  Fills
+// offs_host (n + 1 entries).  Synchronous on st.
+cvs_status search_pairs(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, const cvs_thresholds* thr,
+                        cvs_precision prec, cvs_pair* out, int64_t cap, uint32_t target0,
+                        int64_t* offs_host, cudaStream_t st) {
+    const int K = c->grid.K, H = c->grid.H;
+    // radii per work item: the automatic choice, within the bitmap of a warp
+    int kchunk = choose_kchunk(c, n, K, H);
+    const int kmax = kListMaxSlots / H > 0 ? kListMaxSlots / H : 1;
+    if (kchunk > kmax) kchunk = kmax;
+    const int64_t n_kc = (K + kchunk - 1) / kchunk;
+    const int words = (kchunk * H + 31) / 32;
+    // targets per batch: within list_batch_items work items and 256 MiB of bitmaps
+    int64_t items = c->list_batch_items;
+    const int64_t by_bytes = ((int64_t)256 << 20) / (4 * (int64_t)words);
+    if (items > by_bytes) items = by_bytes;
+    int64_t nb = items / n_kc;
+    nb = nb < 1 ? 1 : (nb > n ? n : nb);
+    const int64_t nitems = nb * n_kc;
+    CVS_TRY(ensure_targets(c, nb));
+    CVS_TRY(grow(c, &c->d_offs, &c->cap_offs, n + 1));
+    CVS_TRY(grow(c, &c->d_bits, &c->cap_bits, nitems * words));
+    CVS_TRY(grow(c, &c->d_icount, &c->cap_icount, nitems));
+    CVS_TRY(grow(c, &c->d_within, &c->cap_within, nitems));
+    CVS_TRY(grow(c, &c->d_tiles, &c->cap_tiles, (nitems + 4095) / 4096));
+    CVS_CUDA(cudaMemsetAsync(c->d_offs, 0, sizeof(int64_t), st));
+    ListOut lo;
+    lo.item_bits = c->d_bits;
+    lo.item_words = words;
+    lo.item_count = c->d_icount;
+    lo.kchunk = kchunk;
+    EmitArgs e{};
+    e.tf = c->tf;
+    e.td = c->td;
+    e.grid = c->grid;
+    e.qkey = c->qkey;
+    thresholds_to_int(thr, &e.hi_min, &e.lo_max);
+    e.mask2 = thr->pattern_mask << 1;
+    e.clip = thr->gamut_mode;
+    e.half_w = (float)(0.5 - c->window);
+    e.prec = (int32_t)prec;
+    e.kchunk = kchunk;
+    e.item_bits = c->d_bits;
+    e.item_words = words;
+    e.item_base = c->d_within;
+    e.tile_base = c->d_tiles;
+    e.out = out;
+    e.out_cap = cap;
+    for (int64_t t0 = 0; t0 < n; t0 += nb) {
+        const int64_t b = n - t0 < nb ? n - t0 : nb;
+        CVS_CUDA(launch_setup_colors(rgb_dev + 3 * t0, b, c->grid.rmax, c->tf, c->td, c->acc, st));
+        c->search_kind = 0;
+        CVS_TRY(run_search(c, b, thr, prec, 1, target0 + (uint32_t)t0, st, false, &lo));
+        CVS_CUDA(launch_pair_scan(c->d_icount, c->grid.sym, b * n_kc, c->d_within, c->d_tiles,
+                                  c->d_offs + t0, st));
+        e.n_targets = b;
+        e.offs = c->d_offs + t0;
+        e.target_id = target0 + (uint32_t)t0;
+        CVS_CUDA(launch_emit_pairs(e, c->num_sms, st));
+    }
+    CVS_CUDA(cudaMemcpyAsync(offs_host, c->d_offs, sizeof(int64_t) * (size_t)(n + 1),
+                             cudaMemcpyDeviceToHost, st));
+    CVS_CUDA(cudaStreamSynchronize(st));
+    collect_stats(c);
+    return CVS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 cvs_status cvs_search_color(cvs_ctx* c, const uint8_t rgb[3], uint32_t target,
                             const cvs_grid* grid, const cvs_thresholds* thr, cvs_precision prec,
                             cvs_pair* out_host, size_t cap, size_t* n_out) {
@@ -830,29 +1039,23 @@ cvs_status cvs_search_color(cvs_ctx* c, const uint8_t rgb[3], uint32_t target,
     if (st0 == CVS_OK) st0 = check_thresholds(thr);
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
-    if (st0 == CVS_OK) st0 = ensure_targets(c, 1);
+    if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
+    if (st0 == CVS_OK && thr) st0 = ensure_ltab(c, thr);
     if (st0 != CVS_OK) return st0;
-    const int64_t nd = (int64_t)c->grid.K * c->grid.N;
-    CVS_CUDA(grow(&c->dense, &c->cap_dense, nd));
-    CVS_CUDA(grow(&c->compact, &c->cap_compact, nd));
+    const int64_t nd = (int64_t)c->grid.K * c->grid.N;  // most pairs one colour can have
+    CVS_TRY(grow(c, &c->compact, &c->cap_compact, nd));
     cudaStream_t st = c->own;
     CVS_CUDA(cudaMemcpyAsync(c->d_rgb1, rgb, 3, cudaMemcpyHostToDevice, st));
-    CVS_CUDA(cudaMemsetAsync(c->dense, 0, sizeof(cvs_pair) * (size_t)nd, st));
-    CVS_CUDA(launch_setup_colors(c->d_rgb1, 1, c->grid.rmax, c->tf, c->td, c->acc, st));
-    c->search_kind = 0;
-    st0 = run_search(c, 1, thr, prec, 1, target, st);
+    int64_t offs[2] = {0, 0};
+    st0 = search_pairs(c, c->d_rgb1, 1, thr, prec, c->compact, nd, target, offs, st);
     if (st0 != CVS_OK) return st0;
-    CVS_CUDA(launch_compact_pairs(c->dense, nd, c->compact, c->counters + 3, st));
-    unsigned long long n = 0;
-    CVS_CUDA(cudaMemcpyAsync(&n, c->counters + 3, sizeof n, cudaMemcpyDeviceToHost, st));
-    CVS_CUDA(cudaStreamSynchronize(st));
-    collect_stats(c);
+    const int64_t n = offs[1];
     *n_out = (size_t)n;
-    const size_t ncopy = n < cap ? (size_t)n : cap;
+    const size_t ncopy = (size_t)n < cap ? (size_t)n : cap;
     if (ncopy)
         CVS_CUDA(cudaMemcpy(out_host, c->compact, ncopy * sizeof(cvs_pair), cudaMemcpyDeviceToHost));
     if ((size_t)n > cap)
-        return fail(CVS_ERR_TRUNCATED, "%llu passing pairs, capacity %zu", n, cap);
+        return fail(CVS_ERR_TRUNCATED, "%lld passing pairs, capacity %zu", (long long)n, cap);
     return CVS_OK;
 }
 
@@ -865,60 +1068,29 @@ cvs_status cvs_search_colors_pairs(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     if (n < 0 || n > ((int64_t)1 << 31)) return fail(CVS_ERR_INVALID_ARG, "n out of range");
     if (cap < 0) return fail(CVS_ERR_INVALID_ARG, "negative capacity");
     if (n > 0 && !rgb_dev) return fail(CVS_ERR_INVALID_ARG, "NULL device buffer");
+    if (cap > 0 && (reinterpret_cast<uintptr_t>(out_dev) & 15u))
+        return fail(CVS_ERR_INVALID_ARG, "out_dev must be 16-byte aligned");
     if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
         return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
     cvs_status st0 = check_grid(grid);
     if (st0 == CVS_OK) st0 = check_thresholds(thr);
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
-    if (st0 == CVS_OK) st0 = ensure_targets(c, n > 0 ? n : 1);
+    if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
+    if (st0 == CVS_OK && thr) st0 = ensure_ltab(c, thr);
     if (st0 != CVS_OK) return st0;
     if (offsets_host) offsets_host[0] = 0;
     if (n == 0) return CVS_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    // pass 1: the number of passing pairs of each colour
-    CVS_CUDA(grow(&c->d_maxr, &c->cap_maxr, n));
-    CVS_CUDA(grow(&c->d_count, &c->cap_count, n));
-    CVS_CUDA(grow(&c->d_pmask, &c->cap_pmask, n));
-    CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
-    c->search_kind = 0;
-    st0 = run_search(c, n, thr, prec, 0, 0, st);
-    if (st0 != CVS_OK) return st0;
-    CVS_CUDA(launch_finalize_colors(c->acc, n, c->d_maxr, c->d_count, c->d_pmask, st));
-    std::vector<int32_t> counts((size_t)n);
-    CVS_CUDA(cudaMemcpyAsync(counts.data(), c->d_count, sizeof(int32_t) * (size_t)n,
-                             cudaMemcpyDeviceToHost, st));
-    CVS_CUDA(cudaStreamSynchronize(st));
     std::vector<int64_t> offs((size_t)n + 1);
-    offs[0] = 0;
-    for (int64_t i = 0; i < n; ++i) offs[i + 1] = offs[i] + counts[i];
+    st0 = search_pairs(c, rgb_dev, n, thr, prec, out_dev, cap, 0, offs.data(),
+                       (cudaStream_t)stream);
+    if (st0 != CVS_OK) return st0;
     if (offsets_host) std::memcpy(offsets_host, offs.data(), sizeof(int64_t) * ((size_t)n + 1));
     const int64_t total = offs[n];
     *n_out = total;
     if (total > cap)
         return fail(CVS_ERR_TRUNCATED, "%lld passing pairs, capacity %lld", (long long)total,
                     (long long)cap);
-    if (total == 0) return CVS_OK;
-    // pass 2: dense records of a batch of colours, then one ordered compaction per colour
-    const int64_t kn = (int64_t)c->grid.K * c->grid.N;
-    const int64_t budget = (int64_t)512 << 20;  // bytes of dense records per batch
-    int64_t batch = budget / (kn * (int64_t)sizeof(cvs_pair));
-    batch = batch < 1 ? 1 : (batch > n ? n : batch);
-    CVS_CUDA(grow(&c->dense, &c->cap_dense, batch * kn));
-    CVS_CUDA(grow(&c->d_offs, &c->cap_offs, n + 1));
-    CVS_CUDA(cudaMemcpyAsync(c->d_offs, offs.data(), sizeof(int64_t) * ((size_t)n + 1),
-                             cudaMemcpyHostToDevice, st));
-    for (int64_t t0 = 0; t0 < n; t0 += batch) {
-        const int64_t b = n - t0 < batch ? n - t0 : batch;
-        CVS_CUDA(cudaMemsetAsync(c->dense, 0, sizeof(cvs_pair) * (size_t)(b * kn), st));
-        CVS_CUDA(launch_setup_colors(rgb_dev + 3 * t0, b, c->grid.rmax, c->tf, c->td, c->acc, st));
-        c->search_kind = 0;
-        st0 = run_search(c, b, thr, prec, 1, (uint32_t)t0, st);
-        if (st0 != CVS_OK) return st0;
-        CVS_CUDA(launch_compact_pairs_batch(c->dense, kn, b, c->d_offs + t0, out_dev, st));
-    }
-    CVS_CUDA(cudaStreamSynchronize(st));
-    collect_stats(c);
     return CVS_OK;
 }
 
@@ -935,6 +1107,8 @@ cvs_status cvs_search_colors(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, cons
     if (st0 == CVS_OK) st0 = check_thresholds(thr);
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
+    if (st0 == CVS_OK && thr) st0 = ensure_ltab(c, thr);
     if (st0 == CVS_OK) st0 = ensure_targets(c, n);
     if (st0 != CVS_OK) return st0;
     if (n == 0) return CVS_OK;
@@ -949,9 +1123,7 @@ cvs_status cvs_search_colors(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, cons
     };
     if (!c->use_graphs) return enqueue(st, nullptr);
     if (c->autotune) {  // tune outside the capture, once
-        const auto key = tune_key(c, n, (int)(prec == CVS_PREC_FP32_RECHECK &&
-                                              c->grid.rmax > kFp32MaxRadius ? CVS_PREC_FP64 : prec),
-                                  thr->gamut_mode, 0);
+        const auto key = tune_key(c, n, (int)prec, thr->gamut_mode, 0);
         if (!c->tuned.count(key)) {
             st0 = enqueue(st, nullptr);
             if (st0 != CVS_OK) return st0;
@@ -963,7 +1135,7 @@ cvs_status cvs_search_colors(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, cons
                                  (uint64_t)thr->gamut_mode, (uint64_t)prec,
                                  (uint64_t)c->shape.block, (uint64_t)c->shape.blocks_per_sm,
                                  (uint64_t)c->shape.kchunk, dbits(c->window),
-                                 dbits(c->max_dl)};
+                                 dbits(thr->max_dl)};
     st0 = graph_launch(c, key, st, enqueue);
     if (st0 == CVS_OK) c->last_pending = true;
     return st0;
@@ -973,8 +1145,6 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
                                    const cvs_grid* grid, const cvs_thresholds* thr,
                                    int32_t n_thr, cvs_precision prec,
                                    const cvs_capacity_map* out, void* stream) {
-    if (c && c->max_dl >= 0.0)
-        return fail(CVS_ERR_INVALID_ARG, "cvs_search_colors_multi does not support the max_dl option");
     if (!c || !out || !thr) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
     if (n < 0 || n > (int64_t)1 << 36) return fail(CVS_ERR_INVALID_ARG, "n out of range");
     if (n_thr < 1 || n_thr > kMaxThresholdSets)
@@ -992,10 +1162,12 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     }
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
+    for (int s = 0; s < n_thr && st0 == CVS_OK; ++s) st0 = ensure_ltab(c, thr + s);
     if (st0 == CVS_OK) st0 = ensure_targets(c, n);
     if (st0 != CVS_OK) return st0;
     if (n == 0) return CVS_OK;
-    CVS_CUDA(grow(&c->acc_multi, &c->cap_acc_multi, n * n_thr));
+    CVS_TRY(grow(c, &c->acc_multi, &c->cap_acc_multi, n * n_thr));
     MultiArgs a{};
     a.tf = c->tf;
     a.td = c->td;
@@ -1015,7 +1187,18 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
         a.hi_min_all = a.hi_min[s] < a.hi_min_all ? a.hi_min[s] : a.hi_min_all;
     }
     a.clip = thr[0].gamut_mode;
-    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
+    // luminance limits: per set, sets without one pass it always
+    a.ltab = nullptr;
+    a.dl_free = 0;
+    for (int s = 0; s < n_thr; ++s) {
+        if (dl_on(thr + s)) {
+            a.ltab = c->ltab;
+            std::memcpy(&a.max_dl_bits[s], &thr[s].max_dl, sizeof(double));
+        } else {
+            a.dl_free |= 1u << s;
+            a.max_dl_bits[s] = -1;  // never consulted: the set is in dl_free
+        }
+    }
     a.half_w = (float)(0.5 - c->window);
     a.prec = (int32_t)prec;
     a.kchunk = choose_kchunk(c, n, c->grid.K, c->grid.H);
@@ -1056,10 +1239,10 @@ cvs_status cvs_search_colors_host(cvs_ctx* c, const uint8_t* rgb_host, int64_t n
         return fail(CVS_ERR_INVALID_ARG, "NULL host buffer");
     cvs_status st0 = set_device(c);
     if (st0 != CVS_OK) return st0;
-    CVS_CUDA(grow(&c->d_in, &c->cap_in, 3 * n));
-    CVS_CUDA(grow(&c->d_maxr, &c->cap_maxr, n));
-    CVS_CUDA(grow(&c->d_count, &c->cap_count, n));
-    CVS_CUDA(grow(&c->d_pmask, &c->cap_pmask, n));
+    CVS_TRY(grow(c, &c->d_in, &c->cap_in, 3 * n));
+    CVS_TRY(grow(c, &c->d_maxr, &c->cap_maxr, n));
+    CVS_TRY(grow(c, &c->d_count, &c->cap_count, n));
+    CVS_TRY(grow(c, &c->d_pmask, &c->cap_pmask, n));
     cudaStream_t st = c->own;
     if (n > 0) CVS_CUDA(cudaMemcpyAsync(c->d_in, rgb_host, 3 * n, cudaMemcpyHostToDevice, st));
     cvs_capacity_map m{c->d_maxr, c->d_count, c->d_pmask};
@@ -1100,6 +1283,8 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
     if (st0 == CVS_OK) st0 = check_thresholds(thr);
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
+    if (st0 == CVS_OK && thr) st0 = ensure_ltab(c, thr);
     if (c->dedup) {  // one search per distinct colour of the batch
         constexpr int64_t kColours = int64_t(1) << 24;
         if (st0 == CVS_OK) st0 = ensure_targets(c, total < kColours ? total : kColours);
@@ -1107,7 +1292,7 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
         st0 = ensure_dedup(c);
         if (st0 != CVS_OK) return st0;
         cudaStream_t st = (cudaStream_t)stream;
-        CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, n));
+        CVS_TRY(grow(c, &c->d_imgs, &c->cap_imgs, n));
         CVS_CUDA(cudaMemcpyAsync(c->d_imgs, h.data(), sizeof(ImageDesc) * n,
                                  cudaMemcpyHostToDevice, st));
         CVS_CUDA(launch_dedup_mark(c->d_imgs, n, total, c->d_present, st));
@@ -1136,7 +1321,7 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
         return CVS_OK;
     };
     if (!c->use_graphs) {
-        CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, n));
+        CVS_TRY(grow(c, &c->d_imgs, &c->cap_imgs, n));
         CVS_CUDA(cudaMemcpyAsync(c->d_imgs, h.data(), sizeof(ImageDesc) * n, cudaMemcpyHostToDevice,
                                  st));
         return enqueue(st, c->d_imgs);
@@ -1145,7 +1330,7 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
                                  thr->pattern_mask, (uint64_t)thr->gamut_mode, (uint64_t)prec,
                                  (uint64_t)c->shape.block, (uint64_t)c->shape.blocks_per_sm,
                                  (uint64_t)c->shape.kchunk, dbits(c->window),
-                                 dbits(c->max_dl)};
+                                 dbits(thr->max_dl)};
     for (const ImageDesc& d : h) {
         key.insert(key.end(), {(uint64_t)d.rgb, (uint64_t)d.pitch, (uint64_t)d.width,
                                (uint64_t)d.height, (uint64_t)d.max_r, (uint64_t)d.count,
@@ -1160,8 +1345,6 @@ cvs_status cvs_embed_image(cvs_ctx* c, const cvs_image* img, const uint8_t* patt
                            int64_t pattern_pitch, const cvs_grid* grid, const cvs_thresholds* thr,
                            cvs_precision prec, uint8_t* frame_a_dev, uint8_t* frame_b_dev,
                            int64_t frame_pitch, uint32_t* choice_dev, void* stream) {
-    if (c && c->max_dl >= 0.0)
-        return fail(CVS_ERR_INVALID_ARG, "cvs_embed_image does not support the max_dl option");
     if (!c || !img || !pattern_dev || !frame_a_dev || !frame_b_dev)
         return fail(CVS_ERR_INVALID_ARG, "NULL argument");
     if (!img->rgb || img->width <= 0 || img->height <= 0 || img->pitch_bytes < 3LL * img->width)
@@ -1177,12 +1360,14 @@ cvs_status cvs_embed_image(cvs_ctx* c, const cvs_image* img, const uint8_t* patt
     if (st0 == CVS_OK) st0 = check_thresholds(thr);
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
+    if (st0 == CVS_OK && thr) st0 = ensure_ltab(c, thr);
     if (st0 == CVS_OK) st0 = ensure_targets(c, px);
     if (st0 != CVS_OK) return st0;
     cudaStream_t st = (cudaStream_t)stream;
     const ImageDesc h{img->rgb, img->pitch_bytes, img->width, img->height, 0, nullptr, nullptr,
                       nullptr};
-    CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, 1));
+    CVS_TRY(grow(c, &c->d_imgs, &c->cap_imgs, 1));
     CVS_CUDA(cudaMemcpyAsync(c->d_imgs, &h, sizeof(ImageDesc), cudaMemcpyHostToDevice, st));
     CVS_CUDA(launch_setup_images(c->d_imgs, 1, px, c->grid.rmax, c->tf, c->td, c->acc, st));
     EmbedArgs a{};
@@ -1205,7 +1390,8 @@ cvs_status cvs_embed_image(cvs_ctx* c, const cvs_image* img, const uint8_t* patt
     thresholds_to_int(thr, &a.hi_min, &a.lo_max);
     a.mask2 = thr->pattern_mask << 1;
     a.clip = thr->gamut_mode;
-    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
+    a.ltab = dl_on(thr) ? c->ltab : nullptr;
+    a.max_dl = thr->max_dl;
     a.half_w = (float)(0.5 - c->window);
     a.prec = (int32_t)prec;
     a.work_counter = c->counters;
@@ -1237,11 +1423,12 @@ cvs_status cvs_autotune(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, const cvs
     if (st0 == CVS_OK) st0 = check_thresholds(thr);
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
+    if (st0 == CVS_OK && thr) st0 = ensure_ltab(c, thr);
     if (st0 == CVS_OK) st0 = ensure_targets(c, n);
     if (st0 != CVS_OK) return st0;
     cudaStream_t st = c->own;
     CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
-    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
     SearchArgs a{};
     a.tf = c->tf;
     a.td = c->td;
@@ -1292,20 +1479,26 @@ cvs_status cvs_lut_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds*
     if (st0 == CVS_OK) st0 = check_thresholds(thr);
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
+    if (st0 == CVS_OK && thr) st0 = ensure_ltab(c, thr);
     constexpr int64_t kColours = int64_t(1) << 24, kChunk = int64_t(1) << 22;
     if (st0 == CVS_OK) st0 = ensure_targets(c, kChunk);
     if (st0 != CVS_OK) return st0;
     cvs_lut* L = new cvs_lut();
     L->device = c->device;
     uint8_t* rgb = nullptr;
+    // the table belongs to the caller; the colour buffer is the context's scratch
     cudaError_t e = cudaMalloc(&L->entry, sizeof(uint64_t) * kColours);
     if (e == cudaSuccess) e = cudaMalloc(&L->pmask, kColours);
-    if (e == cudaSuccess) e = cudaMalloc(&rgb, 3 * kChunk);
     if (e != cudaSuccess) {
-        if (rgb) cudaFree(rgb);
         cvs_lut_destroy(L);
         return fail(e == cudaErrorMemoryAllocation ? CVS_ERR_NO_MEMORY : CVS_ERR_CUDA,
                     "cvs_lut_build: %s", cudaGetErrorString(e));
+    }
+    st0 = ctx_alloc(c, &rgb, 3 * kChunk);
+    if (st0 != CVS_OK) {
+        cvs_lut_destroy(L);
+        return st0;
     }
     cudaStream_t st = (cudaStream_t)stream;
     for (int64_t first = 0; first < kColours && st0 == CVS_OK; first += kChunk) {
@@ -1320,7 +1513,7 @@ cvs_status cvs_lut_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds*
     }
     // the colour buffer is released once the stream has consumed it
     cudaError_t se = cudaStreamSynchronize(st);
-    cudaFree(rgb);
+    ctx_free(c, rgb);
     if (st0 == CVS_OK && se != cudaSuccess)
         st0 = fail(CVS_ERR_CUDA, "cvs_lut_build: %s", cudaGetErrorString(se));
     if (st0 != CVS_OK) {
@@ -1402,8 +1595,6 @@ extern "C" {
 
 cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds* thr,
                           cvs_precision prec, cvs_etab** out, void* stream) {
-    if (c && c->max_dl >= 0.0)
-        return fail(CVS_ERR_INVALID_ARG, "cvs_etab_build does not support the max_dl option");
     if (!c || !out) return fail(CVS_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
@@ -1412,6 +1603,8 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
     if (st0 == CVS_OK) st0 = check_thresholds(thr);
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
+    if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
+    if (st0 == CVS_OK && thr) st0 = ensure_ltab(c, thr);
     constexpr int64_t kColours = int64_t(1) << 24, kChunk = int64_t(1) << 22;
     if (st0 == CVS_OK) st0 = ensure_targets(c, kChunk);
     if (st0 != CVS_OK) return st0;
@@ -1419,15 +1612,19 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
     E->device = c->device;
     uint8_t* rgb = nullptr;
     uint32_t* keys = nullptr;  // one chunk's first-hit keys
+    // the table belongs to the caller; keys and colours are the context's scratch
     cudaError_t e = cudaMalloc(&E->entry, sizeof(uint4) * 7 * kColours);
-    if (e == cudaSuccess) e = cudaMalloc(&keys, sizeof(uint32_t) * 7 * kChunk);
-    if (e == cudaSuccess) e = cudaMalloc(&rgb, 3 * kChunk);
     if (e != cudaSuccess) {
-        if (rgb) cudaFree(rgb);
-        if (keys) cudaFree(keys);
         cvs_etab_destroy(E);
         return fail(e == cudaErrorMemoryAllocation ? CVS_ERR_NO_MEMORY : CVS_ERR_CUDA,
                     "cvs_etab_build: %s", cudaGetErrorString(e));
+    }
+    st0 = ctx_alloc(c, &keys, sizeof(uint32_t) * 7 * kChunk);
+    if (st0 == CVS_OK) st0 = ctx_alloc(c, &rgb, 3 * kChunk);
+    if (st0 != CVS_OK) {
+        ctx_free(c, keys);
+        cvs_etab_destroy(E);
+        return st0;
     }
     FirstHitArgs a{};
     a.tf = c->tf;
@@ -1439,7 +1636,8 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
     thresholds_to_int(thr, &a.hi_min, &a.lo_max);
     a.mask2 = thr->pattern_mask << 1;
     a.clip = thr->gamut_mode;
-    if (prec == CVS_PREC_FP32_RECHECK && c->grid.rmax > kFp32MaxRadius) prec = CVS_PREC_FP64;
+    a.ltab = dl_on(thr) ? c->ltab : nullptr;
+    a.max_dl = thr->max_dl;
     a.half_w = (float)(0.5 - c->window);
     a.prec = (int32_t)prec;
     a.kchunk = choose_kchunk(c, kChunk, c->grid.K, c->grid.H);
@@ -1467,8 +1665,8 @@ cvs_status cvs_etab_build(cvs_ctx* c, const cvs_grid* grid, const cvs_thresholds
                             cudaMemcpyDeviceToHost, st);
     // the scratch buffers are released once the stream has consumed them
     cudaError_t se = cudaStreamSynchronize(st);
-    cudaFree(rgb);
-    cudaFree(keys);
+    ctx_free(c, rgb);
+    ctx_free(c, keys);
     if (e == cudaSuccess) e = se;
     if (e != cudaSuccess) {
         cvs_etab_destroy(E);
@@ -1521,7 +1719,7 @@ cvs_status cvs_reserve(cvs_ctx* c, const cvs_grid* grid, int64_t max_targets, in
     if (st0 == CVS_OK && grid) st0 = ensure_grid(c, grid);
     if (st0 == CVS_OK && max_targets > 0) st0 = ensure_targets(c, max_targets);
     if (st0 != CVS_OK) return st0;
-    if (max_images > 0) CVS_CUDA(grow(&c->d_imgs, &c->cap_imgs, max_images));
+    if (max_images > 0) CVS_TRY(grow(c, &c->d_imgs, &c->cap_imgs, max_images));
     return CVS_OK;
 }
 
@@ -1552,26 +1750,29 @@ cvs_status cvs_precision_probe(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n,
     if (st0 == CVS_OK) st0 = ensure_targets(c, n);
     if (st0 != CVS_OK) return st0;
     cudaStream_t st = c->own;
-    CVS_CUDA(cudaMemsetAsync(c->d_probe, 0, 24, st));
+    // d_probe: three float maxima, a pad word, then three 64-bit counts
+    CVS_CUDA(cudaMemsetAsync(c->d_probe, 0, 40, st));
     CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
-    CVS_CUDA(launch_precision_probe(c->tf, c->td, n, c->grid, c->qkey, c->d_probe, c->d_probe + 1,
-                                    c->d_probe + 2,
+    CVS_CUDA(launch_precision_probe(c->tf, c->td, n, c->grid, c->qkey, (float)(0.5 - c->window),
+                                    c->d_probe, c->d_probe + 1, c->d_probe + 2,
                                     reinterpret_cast<unsigned long long*>(c->d_probe + 4),
                                     c->num_sms, st));
-    unsigned int h[6] = {0, 0, 0, 0, 0, 0};
-    CVS_CUDA(cudaMemcpyAsync(h, c->d_probe, 24, cudaMemcpyDeviceToHost, st));
+    unsigned int h[10] = {};
+    CVS_CUDA(cudaMemcpyAsync(h, c->d_probe, 40, cudaMemcpyDeviceToHost, st));
     CVS_CUDA(cudaStreamSynchronize(st));
     float fv, fl, fa;
     std::memcpy(&fv, &h[0], 4);
     std::memcpy(&fl, &h[1], 4);
     std::memcpy(&fa, &h[2], 4);
-    unsigned long long w;
-    std::memcpy(&w, &h[4], 8);
+    unsigned long long cnt[3];
+    std::memcpy(cnt, &h[4], 24);
     out->max_code_err = fv;
     out->max_lin_err = fl;
     out->max_lab_err = fa;
-    out->n_wrong_codes = (int64_t)w;
-    out->n_values = n * (int64_t)c->grid.K * c->grid.N * 3;
+    out->n_wrong_codes = (int64_t)cnt[0];
+    out->n_unflagged_wrong = (int64_t)cnt[1];
+    out->n_values = (int64_t)cnt[2];
+    out->window = c->window;
     return CVS_OK;
 }
 

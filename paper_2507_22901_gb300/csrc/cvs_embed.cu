@@ -69,8 +69,15 @@ __device__ __forceinline__ void take(Hit& w, int h, const int qp[3], const int q
     w.exact = exact;
 }
 
+// The luminance limit (when on) on a pair of exact codes.
+__device__ __forceinline__ bool dl_pass(const EmbedArgs& A, const TargetF64& D, const int qp[3],
+                                        const int qm[3]) {
+    return !A.ltab || dl_ok(A.ltab, A.max_dl, D.L, qp, qm);
+}
+
 // One flagged FP32 slot: exact pattern by interval analysis, FP64 where the
-// bounds cannot decide.  Records a hit of pattern p in w.
+// bounds cannot decide (or, under the luminance limit, where a passing pair's
+// codes are not all certain).  Records a hit of pattern p in w.
 template <bool FAST, bool CLIP>
 __device__ __forceinline__ void decide_flagged(const EmbedArgs& A, const TargetF32& T,
                                                const ChainF32& C, const TargetF64& D, float2 r2,
@@ -78,14 +85,16 @@ __device__ __forceinline__ void decide_flagged(const EmbedArgs& A, const TargetF
                                                unsigned long long& n_exact,
                                                unsigned long long& n_re) {
     const Intervals I = intervals32<FAST>(T, C, r2, sc, A.half_w, CLIP ? 1 : 0);
-    const int pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, CLIP ? 1 : 0, 0);
+    const int pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, CLIP ? 1 : 0, A.ltab ? 1 : 0);
     ++n_exact;
     if (pc == p) {
-        take(w, h, I.lo, I.lo + 3, !I.any_flag);  // lo == hi for every unflagged code
+        if (dl_pass(A, D, I.lo, I.lo + 3))
+            take(w, h, I.lo, I.lo + 3, !I.any_flag);  // lo == hi for every unflagged code
     } else if (pc < 0) {
         int qp[3], qm[3];
         ++n_re;
-        if (decide64<CLIP>(A, D, k, h, qp, qm) == p) take(w, h, qp, qm, true);
+        if (decide64<CLIP>(A, D, k, h, qp, qm) == p && dl_pass(A, D, qp, qm))
+            take(w, h, qp, qm, true);
     }
 }
 
@@ -133,7 +142,7 @@ __device__ __forceinline__ int embed_radius(const EmbedArgs& A, const float2* r2
                                 qm[c] = min(max(qm[c], 0), 255);
                             }
                         }
-                        take(w, h, qp, qm, true);
+                        if (dl_pass(A, D, qp, qm)) take(w, h, qp, qm, true);
                     }
                 } else if (it < 64) {
                     fbits |= 1ull << it;
@@ -165,7 +174,8 @@ __device__ __forceinline__ int embed_radius(const EmbedArgs& A, const float2* r2
             const int h = it * 32 + (int)lane;
             if (h < H && w.h == kNone) {
                 int qp[3], qm[3];
-                if (decide64<CLIP>(A, D, k, h, qp, qm) == p) take(w, h, qp, qm, true);
+                if (decide64<CLIP>(A, D, k, h, qp, qm) == p && dl_pass(A, D, qp, qm))
+                    take(w, h, qp, qm, true);
             }
         }
     }
@@ -309,8 +319,10 @@ __device__ __forceinline__ void first_flagged(const FirstHitArgs& A, const float
                 const int dk = i / H;
                 const int kq = kk0 + dk, hq = i - dk * H;
                 const Intervals I = intervals32<FAST>(T, C, r2s[kq], sc4s[hq], A.half_w, CLIP ? 1 : 0);
-                int pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, CLIP ? 1 : 0, 0);
+                // under the luminance limit a pass needs certain codes
+                int pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, CLIP ? 1 : 0, A.ltab ? 1 : 0);
                 ++n_exact;
+                if (pc > 0 && A.ltab && !dl_ok(A.ltab, A.max_dl, D.L, I.lo, I.lo + 3)) pc = 0;
                 if (pc < 0) {
                     const int k = __ldg(A.order + kq);
                     int qp[3], qm[3];
@@ -325,6 +337,7 @@ __device__ __forceinline__ void first_flagged(const FirstHitArgs& A, const float
                     }
                     Decide dc{A.hi_min, A.lo_max, A.mask2, CLIP ? 1 : 0};
                     pc = decide_codes(qp, qm, dc);
+                    if (pc > 0 && A.ltab && !dl_ok(A.ltab, A.max_dl, D.L, qp, qm)) pc = 0;
                     ++n_re;
                 }
                 if (pc > 0)
@@ -395,6 +408,19 @@ __device__ __forceinline__ void first_item(const FirstHitArgs& A, const float2* 
                         flag = flag && active;
                         if (flag || !active) pattern = 0;
                         if (flag) bits |= bit;
+                        if (pattern && A.ltab) {  // the luminance limit on the exact codes
+                            int qp[3], qm[3];
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                qp[c] = yp[c] - kMagicBits;
+                                qm[c] = ym[c] - kMagicBits;
+                                if (CLIP) {
+                                    qp[c] = min(max(qp[c], 0), 255);
+                                    qm[c] = min(max(qm[c], 0), 255);
+                                }
+                            }
+                            if (!dl_ok(A.ltab, A.max_dl, D.L, qp, qm)) pattern = 0;
+                        }
                     }
                 } else if (active) {
                     const int k = __ldg(A.order + kq);
@@ -410,6 +436,7 @@ __device__ __forceinline__ void first_item(const FirstHitArgs& A, const float2* 
                     }
                     Decide dc{A.hi_min, A.lo_max, A.mask2, CLIP ? 1 : 0};
                     pattern = decide_codes(qp, qm, dc);
+                    if (pattern && A.ltab && !dl_ok(A.ltab, A.max_dl, D.L, qp, qm)) pattern = 0;
                 }
                 const uint32_t newp =
                     __reduce_or_sync(0xFFFFFFFFu, pattern ? (1u << pattern) : 0u) & ~found;

@@ -80,9 +80,12 @@ struct SearchArgs {
     int32_t clip;
     float half_w;              // 0.5 - W
     int32_t prec;              // cvs_precision
-    int32_t list_mode;         // 1: write records into `dense`
-    cvs_pair* dense;           // K*N records (list mode)
-    uint32_t target_id;        // list mode: copied into records
+    int32_t list_mode;         // 1: leave each work item's passing-slot bitmap and count
+    uint32_t target_id;        // index of target 0 of the launch (list records)
+    uint32_t* item_bits;       // list mode: item_words words per work item of the batch
+    int32_t item_words;
+    uint32_t* item_count;      // list mode: passing slots per work item
+    int64_t item0;             // list mode: batch index of the launch's first work item
     const double* ltab;        // L* of all 2^24 colours when the luminance limit is on, else NULL
     double max_dl;             // the limit on |L*(plus) - L*(minus)| of an emitted pair
     unsigned long long* work_counter;
@@ -93,6 +96,33 @@ struct SearchArgs {
     int64_t arc_cap;           // entries of arc_ranges
     void* ev_ranges;           // host: a cudaEvent_t recorded after the first ranges pass, or NULL
     unsigned ev_flags;         // host: its record flags
+};
+
+// List mode: most slots (kchunk x H) of one work item, i.e. of a warp's
+// passing-slot bitmap in shared memory.
+constexpr int kListMaxSlots = 8192;
+
+// The records of a pair list from the search's per-item bitmaps (one batch).
+struct EmitArgs {
+    const TargetF32* tf;
+    const TargetF64* td;
+    int64_t n_targets;
+    GridDev grid;
+    const long long* qkey;
+    int32_t hi_min, lo_max;
+    uint32_t mask2;
+    int32_t clip;
+    float half_w;
+    int32_t prec;
+    int32_t kchunk;            // radii per work item, as in the search
+    const uint32_t* item_bits; // item_words words per item
+    int32_t item_words;
+    const int64_t* item_base;  // records before each item within its tile of the scan
+    const int64_t* tile_base;  // records before each tile (absolute)
+    cvs_pair* out;             // the records, in (target, k, m) order
+    int64_t out_cap;           // records `out` holds (the rest are not written)
+    int64_t* offs;             // offs[t] = first record of target t, offs[n] = the end
+    uint32_t target_id;        // index of target 0, for the records
 };
 
 // Entries of the angle-range scratch: targets are searched in chunks of
@@ -115,6 +145,9 @@ struct MultiArgs {
     int32_t all_patterns;      // 1 if every set enables all seven patterns
     int32_t hi_min_all;        // the smallest hi_min of the sets
     int32_t clip;              // shared by all sets
+    const double* ltab;        // L* of all 2^24 colours when some set has a luminance limit
+    uint32_t dl_free;          // sets without a luminance limit
+    int64_t max_dl_bits[kMaxThresholdSets];  // bits of each limited set's max_dl (> 0)
     float half_w;
     int32_t prec;
     int32_t kchunk;
@@ -146,6 +179,8 @@ struct EmbedArgs {
     int32_t clip;
     float half_w;
     int32_t prec;
+    const double* ltab;         // luminance limit on: L* of all 2^24 colours, else NULL
+    double max_dl;
     unsigned long long* work_counter;
     unsigned long long* stats;  // [0] flagged slots decided exactly, [1] slots re-decided in FP64
     int num_sms;
@@ -166,6 +201,8 @@ struct FirstHitArgs {
     float half_w;
     int32_t prec;
     int32_t kchunk;             // ranks per work item
+    const double* ltab;         // luminance limit on: L* of all 2^24 colours, else NULL
+    double max_dl;
     uint32_t* key;              // n_targets * 7, pattern p at t * 7 + p - 1; 0xFFFFFFFF = none
     unsigned long long* work_counter;
     unsigned long long* stats;
@@ -201,12 +238,6 @@ cudaError_t launch_etab_gather(const uint4* entry, const uint8_t* rgb, int64_t p
 cudaError_t launch_init_acc(Acc* acc, int64_t n, cudaStream_t st);
 cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t n,
                                    const ImageDesc* imgs, cudaStream_t st);
-cudaError_t launch_compact_pairs(const cvs_pair* dense, int64_t n_dense, cvs_pair* out,
-                                 unsigned long long* n_out, cudaStream_t st);
-// Block b compacts target b's kn dense records (pattern 0 = empty) into
-// out + offsets[b], keeping their order.
-cudaError_t launch_compact_pairs_batch(const cvs_pair* dense, int64_t kn, int64_t n_targets,
-                                      const int64_t* offsets, cvs_pair* out, cudaStream_t st);
 // Per-batch colour de-duplication of the image search (cvs_dedup.cu).
 // mark: present[c] = 1 for every pixel colour c (the map is cleared first).
 cudaError_t launch_dedup_mark(const ImageDesc* imgs, int n_imgs, int64_t total, uint8_t* present,
@@ -221,10 +252,12 @@ cudaError_t launch_dedup_gather(const ImageDesc* imgs, int n_imgs, int64_t total
 // L* of all 2^24 8-bit colours (index R << 16 | G << 8 | B), as step 1 forms it.
 cudaError_t launch_l_table(double* ltab, cudaStream_t st);
 cudaError_t launch_target_lab(const uint8_t* rgb, int64_t n, double* lab, cudaStream_t st);
+// FP32 against FP64 over every (target, k, m) plus colour; counts[0..2] =
+// wrong FP32 codes, wrong codes the search would not flag, values examined.
 cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int64_t n,
-                                   const GridDev& g, const long long* qkey,
+                                   const GridDev& g, const long long* qkey, float half_w,
                                    unsigned int* max_v_err_bits, unsigned int* max_lin_err_bits,
-                                   unsigned int* max_lab_err_bits, unsigned long long* n_wrong,
+                                   unsigned int* max_lab_err_bits, unsigned long long* counts,
                                    int num_sms, cudaStream_t st);
 cudaError_t copy_qkeys_to(long long* dst, cudaStream_t st);
 // Capacity table (all 2^24 colours).
@@ -245,9 +278,24 @@ cudaError_t launch_lut_gather_colors(const uint8_t* rgb, int64_t n, const uint64
                                      uint8_t* pm, cudaStream_t st);
 // Sets the thread-local text returned by cvs_last_error().
 void set_error_message(const char* msg);
+// Radii per work item of the search when the caller fixes none: enough work
+// items to spread n_targets over every SM, but at least two warp iterations.
+int auto_kchunk(int num_sms, int64_t n_targets, int K, int H);
+// 1 if a table of N sines and cosines is exactly antisymmetric under +180
+// degrees (entry m + N/2 = -entry m), so slot m stands for angles m, m + N/2.
+int fold_by_180(const double* s, const double* c, int N);
+// Validate a threshold set and allocate, ahead of any search on the context,
+// what it needs (the L* table of the luminance limit).
+cvs_status prepare_thresholds(cvs_ctx* c, const cvs_thresholds* t);
 size_t target_f32_size();
 size_t target_f64_size();
-int search_smem_bytes(const GridDev& g, int block);
+int search_smem_bytes(const GridDev& g, int block, int list);
+// Pair lists: scan of the items' record counts (count << sym) into within-tile
+// bases and tile bases (tile: ceil(n_items / 4096) entries; carry: device,
+// records before the batch), then the records.
+cudaError_t launch_pair_scan(const uint32_t* count, int sym, int64_t n_items, int64_t* within,
+                             int64_t* tile, const int64_t* carry, cudaStream_t st);
+cudaError_t launch_emit_pairs(const EmitArgs& a, int num_sms, cudaStream_t st);
 void chain_constants(float Ax[3], float Bz[3]);
 
 }  // namespace cvs

@@ -127,41 +127,15 @@ struct Smem {
     uint32_t* rq_kh;
 };
 
-__device__ __forceinline__ void write_records(cvs_pair* dense, int N, int H, int sym, int k, int h,
-                                              const int qp[3], const int qm[3], int pattern,
-                                              uint32_t flags, uint32_t target) {
-    cvs_pair rec;
-    rec.k = (uint16_t)k;
-    rec.m = (uint16_t)h;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        rec.plus[c] = (uint8_t)qp[c];
-        rec.minus[c] = (uint8_t)qm[c];
-    }
-    rec.pattern = (uint8_t)pattern;
-    rec.flags = (uint8_t)flags;
-    rec.target = target;
-    dense[(int64_t)k * N + h] = rec;
-    if (sym) {
-        rec.m = (uint16_t)(h + H);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            rec.plus[c] = (uint8_t)qm[c];
-            rec.minus[c] = (uint8_t)qp[c];
-        }
-        dense[(int64_t)k * N + h + H] = rec;
-    }
-}
-
-// The luminance limit on an emitted pair (codes in [0, 255]): each colour's
-// L* (step 1 applied to its codes, from the table) lies within max_dl of the
-// target's L*.
-__device__ __forceinline__ bool dl_ok(const double* __restrict__ ltab, double max_dl,
-                                      double l_target, const int qp[3], const int qm[3]) {
-    const int ip = (qp[0] << 16) | (qp[1] << 8) | qp[2];
-    const int im = (qm[0] << 16) | (qm[1] << 8) | qm[2];
-    return fabs(__dsub_rn(__ldg(ltab + ip), l_target)) <= max_dl &&
-           fabs(__dsub_rn(__ldg(ltab + im), l_target)) <= max_dl;
+// Pair lists (list mode).  A work item (target t, radii [k0, k1)) marks its
+// passing slots s = (k - k0) H + h in a per-warp bitmap in shared memory,
+// wherever the slot is decided (the FP32 walk, the interval analysis of
+// flagged slots, the FP64 re-decision); once every slot of the item is decided
+// it writes its records, in (k, m) order, straight to their final place (see
+// emit_item).
+__device__ __forceinline__ void mark_pass(uint32_t* pb, int k0, int H, int k, int h) {
+    const int s = (k - k0) * H + h;
+    atomicOr(pb + (s >> 5), 1u << (s & 31));
 }
 
 // Exact FP64 decision of one slot; returns the pattern (0 = fail) and the
@@ -186,9 +160,11 @@ __device__ __forceinline__ int decide64_slot(const SearchArgs& A, const TargetF6
     return (pattern && A.ltab && !dl_ok(A.ltab, A.max_dl, D.L, qp, qm)) ? 0 : pattern;
 }
 
-// Re-decide up to 32 queued slots in FP64, one per lane, and merge them.
+// Re-decide up to 32 queued slots in FP64, one per lane, and merge them (in
+// list mode every queued slot belongs to the warp's current item, whose
+// bitmap is pb with first radius k0).
 __device__ __noinline__ void flush_queue(const SearchArgs& A, uint32_t* rq_t, uint32_t* rq_kh,
-                                         int n, unsigned long long* n_re) {
+                                         int n, unsigned long long* n_re, uint32_t* pb, int k0) {
     const unsigned lane = lane_id();
     const int inc = A.grid.sym ? 2 : 1;
     if ((int)lane < n) {
@@ -200,8 +176,7 @@ __device__ __noinline__ void flush_queue(const SearchArgs& A, uint32_t* rq_t, ui
         const int pat = decide64_slot(A, D, k, h, qp, qm);
         if (pat) {
             if (A.list_mode) {
-                write_records(A.dense + (int64_t)t * A.grid.K * A.grid.N, A.grid.N, A.grid.H,
-                              A.grid.sym, k, h, qp, qm, pat, 1u, A.target_id + t);
+                mark_pass(pb, k0, A.grid.H, k, h);
             } else {
                 Acc* ac = A.acc + t;
                 atomicAdd(&ac->count, inc);
@@ -217,7 +192,7 @@ __device__ __noinline__ void flush_queue(const SearchArgs& A, uint32_t* rq_t, ui
 // Queue up to 32 slots for FP64 re-decision; flush when 32 are waiting.
 __device__ __forceinline__ void push_fp64(const SearchArgs& A, bool need64, int64_t t, int k,
                                           int h, uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
-                                          unsigned long long& n_re) {
+                                          unsigned long long& n_re, uint32_t* pb, int k0) {
     const unsigned lane = lane_id();
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, need64);
     if (!ball) return;
@@ -229,7 +204,7 @@ __device__ __forceinline__ void push_fp64(const SearchArgs& A, bool need64, int6
     rq_n += __popc(ball);
     __syncwarp();
     if (rq_n >= 32) {
-        flush_queue(A, rq_t, rq_kh, 32, &n_re);
+        flush_queue(A, rq_t, rq_kh, 32, &n_re, pb, k0);
         const int rest = rq_n - 32;
         uint32_t mt = 0, mkh = 0;
         if ((int)lane < rest) { mt = rq_t[32 + lane]; mkh = rq_kh[32 + lane]; }
@@ -240,14 +215,27 @@ __device__ __forceinline__ void push_fp64(const SearchArgs& A, bool need64, int6
     }
 }
 
+// Per-lane accumulators of one work item, and in list mode its bitmap.
+struct Tally {
+    int cnt;
+    float rmax;
+    uint32_t pm;
+    uint32_t skip;   // slots of this lane skipped as certainly out of gamut
+    uint32_t prune;  // slots of the item below the first radius where a pair may pass
+    uint32_t* pb;    // list mode: the item's passing-slot bitmap (shared), else NULL
+    int k0;          // list mode: the item's first radius
+};
+
 // Decide up to 32 flagged slots of target t, one per lane: exact interval
-// analysis in FP32, FP64 re-decision where the analysis cannot decide.
+// analysis in FP32, FP64 re-decision where the analysis cannot decide.  A list
+// takes the codes of a passing slot later (emit_item), so only the luminance
+// limit needs them exactly here.
 template <bool FAST, bool DL>
 __device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S,
                                               const TargetF32& T, const ChainF32& C, int64_t t,
-                                              uint32_t* pq, int n, int& cnt, float& rmax,
-                                              uint32_t& pm, uint32_t* rq_t, uint32_t* rq_kh,
-                                              int& rq_n, unsigned long long& n_re) {
+                                              uint32_t* pq, int n, Tally& acc, uint32_t* rq_t,
+                                              uint32_t* rq_kh, int& rq_n,
+                                              unsigned long long& n_re) {
     const unsigned lane = lane_id();
     const int inc = A.grid.sym ? 2 : 1;
     int k = 0, h = 0, pc = 0;
@@ -259,26 +247,22 @@ __device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S
         const float r = r2.x;
         // a list and the luminance limit need the exact codes of a passing pair
         const Intervals I = intervals32<FAST>(T, C, r2, S.sc4[h], A.half_w, A.clip);
-        pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, A.clip, A.list_mode || DL);
+        pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, A.clip, DL);
         if (DL && pc > 0 && !dl_ok(A.ltab, A.max_dl, A.td[t].L, I.lo, I.lo + 3)) pc = 0;
         if (pc > 0) {
-            cnt += inc;
-            rmax = fmaxf(rmax, r);
-            pm |= 1u << pc;
+            if (acc.pb) {
+                mark_pass(acc.pb, acc.k0, A.grid.H, k, h);
+            } else {
+                acc.cnt += inc;
+                acc.rmax = fmaxf(acc.rmax, r);
+                acc.pm |= 1u << pc;
+            }
         }
     }
     __syncwarp();
-    push_fp64(A, (int)lane < n && pc < 0, t, k, h, rq_t, rq_kh, rq_n, n_re);
+    push_fp64(A, (int)lane < n && pc < 0, t, k, h, rq_t, rq_kh, rq_n, n_re, acc.pb, acc.k0);
 }
 
-// Per-lane accumulators of one work item.
-struct Tally {
-    int cnt;
-    float rmax;
-    uint32_t pm;
-    uint32_t skip;   // slots of this lane skipped as certainly out of gamut
-    uint32_t prune;  // slots of the item below the first radius where a pair may pass
-};
 
 // One 32-slot step of a work item: every lane evaluates slot (k, h).  With
 // CHECK, lanes past the item's last slot (active == false) contribute nothing.
@@ -330,16 +314,7 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
                 acc.rmax = fmaxf(acc.rmax, r);
                 acc.pm |= 1u << pattern;  // bit p for pattern p; shifted down at the end
             } else {
-                int qp[3], qm[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    int a = yp[c] - kMagicBits, b = ym[c] - kMagicBits;
-                    if (CLIP) { a = min(max(a, 0), 255); b = min(max(b, 0), 255); }
-                    qp[c] = a;
-                    qm[c] = b;
-                }
-                write_records(A.dense + t * A.grid.K * A.grid.N, A.grid.N, H, A.grid.sym, k, h, qp, qm,
-                              pattern, 0u, A.target_id + (uint32_t)t);
+                mark_pass(acc.pb, acc.k0, H, k, h);
             }
         }
         return flag;
@@ -348,8 +323,7 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
         const int pattern = (!CHECK || active) ? decide64_slot(A, D, k, h, qp, qm) : 0;
         if (pattern) {
             if (LIST) {
-                write_records(A.dense + t * A.grid.K * A.grid.N, A.grid.N, H, A.grid.sym, k, h, qp, qm,
-                              pattern, 0u, A.target_id + (uint32_t)t);
+                mark_pass(acc.pb, acc.k0, H, k, h);
             } else {
                 acc.cnt += inc;
                 acc.rmax = fmaxf(acc.rmax, r);
@@ -429,8 +403,7 @@ __device__ __forceinline__ void collect_flagged(const SearchArgs& A, const Smem&
             pq_n += __popc(ball);
             __syncwarp();
             if (pq_n >= 32) {
-                drain_flagged<FAST, DL>(A, S, T, C, t, pq, 32, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh,
-                                    rq_n, n_re);
+                drain_flagged<FAST, DL>(A, S, T, C, t, pq, 32, acc, rq_t, rq_kh, rq_n, n_re);
                 const int rest = pq_n - 32;
                 const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
                 __syncwarp();
@@ -445,7 +418,7 @@ __device__ __forceinline__ void collect_flagged(const SearchArgs& A, const Smem&
 template <int PREC, bool FAST, bool CLIP, bool LIST, bool DL>
 __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int64_t t, int k0,
                                          int k1, const ChainF32& C, uint32_t* pq, uint32_t* fb,
-                                         uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
+                                         uint32_t* pb, uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
                                          unsigned long long& n_flag, unsigned long long& n_re,
                                          unsigned long long& n_skip,
                                          unsigned long long& n_prune) {
@@ -458,7 +431,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
     if (PREC != CVS_PREC_FP32_RECHECK || DL) D = A.td[t];  // the limit needs the target's L*
     const PairsT P = make_pairs(T);
     const PairsC PC = make_pairs(C);
-    Tally acc{0, -1.0f, 0u, 0u, 0u};
+    Tally acc{0, -1.0f, 0u, 0u, 0u, pb, k0};
     int pq_n = 0;  // flagged slots waiting for drain_flagged (warp-uniform)
     // slot i of the item is (k0 + i / H, i % H); lanes start at i = lane and
     // step by 32 = q32 H + r32, so one conditional wrap keeps h in [0, H)
@@ -508,8 +481,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
         }
     }
     if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0)
-        drain_flagged<FAST, DL>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh, rq_n,
-                            n_re);
+        drain_flagged<FAST, DL>(A, S, T, C, t, pq, pq_n, acc, rq_t, rq_kh, rq_n, n_re);
     n_skip += acc.skip;
     n_prune += acc.prune;
     if (!LIST) {
@@ -549,6 +521,11 @@ constexpr int kArcEntries = kSlowBase + kArcRadii + 3;
 constexpr int kArcWords = 2 * kArcEntries;
 constexpr int kArcBias = 1 << 23;
 constexpr uint32_t kSlowRadius = 0xFFFFFFFFu;
+// List mode: words of a warp's passing-slot bitmap (an item has at most
+// kListMaxSlots slots), and of the bitmap plus its nwords + 1 prefix counts in
+// the emit kernel.
+constexpr int kListWords = kListMaxSlots / 32;
+constexpr int kListWarpWords = 2 * kListWords + 2;
 
 __device__ __forceinline__ int warp_exclusive_sum(int v, int& total) {
     const unsigned lane = lane_id();
@@ -618,8 +595,7 @@ __device__ __forceinline__ void collect_list(const SearchArgs& A, const Smem& S,
             __syncwarp();
             if (pq_n >= 32) {
                 const TargetF32 T = A.tf[t];
-                drain_flagged<FAST, DL>(A, S, T, C, t, pq, 32, acc.cnt, acc.rmax, acc.pm, rq_t,
-                                        rq_kh, rq_n, n_re);
+                drain_flagged<FAST, DL>(A, S, T, C, t, pq, 32, acc, rq_t, rq_kh, rq_n, n_re);
                 const int rest = pq_n - 32;
                 const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
                 __syncwarp();
@@ -688,7 +664,7 @@ __device__ __forceinline__ void run_list(const SearchArgs& A, const Smem& S, con
 template <bool LIST, bool DL>
 __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S, int64_t t,
                                               int k0, int k1, const ChainF32& C, uint32_t* pq,
-                                              uint32_t* fb, uint32_t* al, uint32_t* rq_t,
+                                              uint32_t* fb, uint32_t* al, uint32_t* pb, uint32_t* rq_t,
                                               uint32_t* rq_kh, int& rq_n,
                                               unsigned long long& n_flag,
                                               unsigned long long& n_re,
@@ -700,7 +676,7 @@ __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S
     if (DL) D = A.td[t];
     const PairsT P = make_pairs(A.tf[t]);
     const PairsC PC = make_pairs(C);
-    Tally acc{0, -1.0f, 0u, 0u, 0u};
+    Tally acc{0, -1.0f, 0u, 0u, 0u, pb, k0};
     int pq_n = 0;
     uint32_t* pos = al + kArcEntries;
     const uint2* ranges = A.arc_ranges + t * K;
@@ -766,8 +742,7 @@ __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S
         if (ns) {  // the slow path decides its own flagged slots
             if (pq_n > 0) {
                 const TargetF32 T = A.tf[t];
-                drain_flagged<true, DL>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t,
-                                        rq_kh, rq_n, n_re);
+                drain_flagged<true, DL>(A, S, T, C, t, pq, pq_n, acc, rq_t, rq_kh, rq_n, n_re);
                 pq_n = 0;
             }
             run_list<false, true, LIST, DL>(A, S, P, PC, D, C, t, kb, al, kSlowBase,
@@ -775,8 +750,7 @@ __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S
                                             rq_n, n_flag, n_re);
             if (pq_n > 0) {
                 const TargetF32 T = A.tf[t];
-                drain_flagged<false, DL>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t,
-                                         rq_kh, rq_n, n_re);
+                drain_flagged<false, DL>(A, S, T, C, t, pq, pq_n, acc, rq_t, rq_kh, rq_n, n_re);
                 pq_n = 0;
             }
         }
@@ -784,8 +758,7 @@ __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S
     }
     if (pq_n > 0) {
         const TargetF32 T = A.tf[t];
-        drain_flagged<true, DL>(A, S, T, C, t, pq, pq_n, acc.cnt, acc.rmax, acc.pm, rq_t, rq_kh,
-                                rq_n, n_re);
+        drain_flagged<true, DL>(A, S, T, C, t, pq, pq_n, acc, rq_t, rq_kh, rq_n, n_re);
     }
     n_skip += acc.skip;
     n_prune += acc.prune;
@@ -878,6 +851,33 @@ __global__ void __launch_bounds__(256, CVS_ARC_PASS_MIN_BLOCKS)
     }
 }
 
+// ------------------------------------------------------------ pair-list output
+// A pair list takes three kernels per batch of colours.  The search (list
+// mode) leaves, per work item g, the bitmap of its passing slots in item_bits
+// (item_words words from g * item_words) and their number in item_count[g], and
+// goes on with its next item.  k_scan_tiles / k_scan_top turn the counts into
+// the position of every item's first record.  k_emit_pairs then writes the
+// records of every item straight to their place (see emit_records).  Records of
+// an item follow those of every earlier item, which is (target, k, m) order.
+
+// The end of a list-mode work item: its bitmap and count to global memory (one
+// coalesced row), and the shared bitmap cleared for the next item.
+__device__ __forceinline__ void store_item(const SearchArgs& A, long long g, int nwords,
+                                           uint32_t* pb) {
+    const unsigned lane = lane_id();
+    uint32_t* dst = A.item_bits + g * (long long)A.item_words;
+    int cnt = 0;
+    for (int w = (int)lane; w < nwords; w += 32) {
+        const uint32_t v = pb[w];
+        dst[w] = v;
+        cnt += __popc(v);
+        pb[w] = 0u;
+    }
+    cnt = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt);
+    if (lane == 0) A.item_count[g] = (uint32_t)cnt;
+    __syncwarp();
+}
+
 // Launch bounds of the search kernel: blocks of up to CVS_SEARCH_MAX_THREADS
 // threads, at least CVS_SEARCH_MIN_BLOCKS of them resident per SM.
 #ifndef CVS_SEARCH_MAX_THREADS
@@ -910,6 +910,13 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS,
     uint32_t* pq = S.rq_kh + nwarps * kRqCap + warp * kRqCap;
     uint32_t* fb = S.rq_kh + 2 * nwarps * kRqCap + warp * (kFlagWords * 32);
     uint32_t* al = S.rq_kh + 2 * nwarps * kRqCap + nwarps * (kFlagWords * 32) + warp * kArcWords;
+    // list mode: per warp the item's passing-slot bitmap
+    uint32_t* pb = nullptr;
+    if (LIST) {
+        pb = S.rq_kh + 2 * nwarps * kRqCap + nwarps * (kFlagWords * 32) +
+             (A.grid.arcs ? nwarps * kArcWords : 0) + warp * kListWords;
+        for (int w = lane_id(); w < kListWords; w += 32) pb[w] = 0u;
+    }
     for (int w = 0; w < kFlagWords; ++w) fb[w * 32 + lane_id()] = 0u;
     build_decide_lut(S.lut, A.hi_min, A.lo_max);
     for (int i = threadIdx.x; i < K; i += blockDim.x) S.r2[i] = dup(A.grid.r32[i]);
@@ -943,22 +950,29 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS,
         // (a run-time test: the plain walk stays compiled into the range
         // kernel, which measured faster than without it)
         if (ARCS && PREC == CVS_PREC_FP32_RECHECK && !CLIP && A.grid.arcs) {
-            run_item_arcs<LIST, DL>(A, S, t, k0, k1, C, pq, fb, al, rq_t, rq_kh, rq_n, n_flag,
-                                          n_re, n_skip, n_prune);
+            run_item_arcs<LIST, DL>(A, S, t, k0, k1, C, pq, fb, al, pb, rq_t, rq_kh, rq_n, n_flag,
+                                    n_re, n_skip, n_prune);
         } else if (PREC == CVS_PREC_FP32_RECHECK) {
             const uint32_t fl = A.tf[t].flags;
             if (fl & 1u)
-                run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
-                                                 n_re, n_skip, n_prune);
+                run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, pb, rq_t, rq_kh, rq_n,
+                                                     n_flag, n_re, n_skip, n_prune);
             else
-                run_item<PREC, false, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
-                                                  n_re, n_skip, n_prune);
+                run_item<PREC, false, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, pb, rq_t, rq_kh,
+                                                      rq_n, n_flag, n_re, n_skip, n_prune);
         } else {
-            run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, rq_t, rq_kh, rq_n, n_flag,
-                                             n_re, n_skip, n_prune);
+            run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, pb, rq_t, rq_kh, rq_n,
+                                                 n_flag, n_re, n_skip, n_prune);
+        }
+        if (LIST) {  // every slot of the item decided: its bitmap and count
+            if (PREC == CVS_PREC_FP32_RECHECK && rq_n > 0) {
+                flush_queue(A, rq_t, rq_kh, rq_n, &n_re, pb, k0);
+                rq_n = 0;
+            }
+            store_item(A, A.item0 + (long long)item, ((k1 - k0) * H + 31) >> 5, pb);
         }
     }
-    if (PREC == CVS_PREC_FP32_RECHECK && rq_n > 0) flush_queue(A, rq_t, rq_kh, rq_n, &n_re);
+    if (PREC == CVS_PREC_FP32_RECHECK && rq_n > 0) flush_queue(A, rq_t, rq_kh, rq_n, &n_re, nullptr, 0);
     // statistics
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -972,6 +986,318 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS,
         if (n_re) atomicAdd(A.stats + 1, n_re);
         if (n_skip) atomicAdd(A.stats + 3, n_skip);
         if (n_prune) atomicAdd(A.stats + 4, n_prune);
+    }
+}
+
+// ------------------------------------------------------------ pair-list records
+// FP32 codes of slot (k, h) of a target for its record; returns true when
+// some code lies within the window W of a rounding boundary (the record then
+// takes FP64 codes, see flush_records).
+__device__ __forceinline__ bool record_codes32(const EmitArgs& A, const float2* r2s,
+                                               const float4* sc4s, const ChainF32& C,
+                                               const TargetF32& T, int k, int h, int qp[3],
+                                               int qm[3]) {
+    const float2 r2 = r2s[k];
+    const float4 sc = sc4s[h];
+    const PairsT P = make_pairs(T);
+    const PairsC PC = make_pairs(C);
+    const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y)), w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
+    int yp[3], ym[3];
+    const bool flag = ((T.flags & 1u) || fast_radius(T, r2.x))
+                          ? codes32<true>(P, PC, u2, w2, A.half_w, yp, ym)
+                          : codes32<false>(P, PC, u2, w2, A.half_w, yp, ym);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        qp[c] = yp[c] - kMagicBits;
+        qm[c] = ym[c] - kMagicBits;
+    }
+    return flag;
+}
+
+// Store the record of slot (k, h) at pos (if below the capacity) and, on a
+// folded grid, its +180 degree partner at pos + ck; codes clamped in clip mode.
+__device__ __forceinline__ void store_records(const EmitArgs& A, uint32_t target, int k, int h,
+                                              int qp_in[3], int qm_in[3], uint32_t fp64,
+                                              unsigned long long pos, unsigned ck) {
+    int qp[3], qm[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        qp[c] = A.clip ? min(max(qp_in[c], 0), 255) : qp_in[c];
+        qm[c] = A.clip ? min(max(qm_in[c], 0), 255) : qm_in[c];
+    }
+    Decide dc;
+    dc.hi_min = A.hi_min;
+    dc.lo_max = A.lo_max;
+    dc.mask2 = A.mask2;
+    dc.clip = A.clip;
+    const int pattern = decide_codes(qp, qm, dc);
+    const uint32_t tail = (uint32_t)pattern << 16 | fp64 << 24;
+    uint4* out = reinterpret_cast<uint4*>(A.out);
+    if (pos < (unsigned long long)A.out_cap)
+        out[pos] = make_uint4((uint32_t)k | (uint32_t)h << 16,
+                              (uint32_t)qp[0] | (uint32_t)qp[1] << 8 | (uint32_t)qp[2] << 16 |
+                                  (uint32_t)qm[0] << 24,
+                              (uint32_t)qm[1] | (uint32_t)qm[2] << 8 | tail, target);
+    if (A.grid.sym && pos + ck < (unsigned long long)A.out_cap)
+        out[pos + ck] = make_uint4((uint32_t)k | (uint32_t)(h + A.grid.H) << 16,
+                                   (uint32_t)qm[0] | (uint32_t)qm[1] << 8 |
+                                       (uint32_t)qm[2] << 16 | (uint32_t)qp[0] << 24,
+                                   (uint32_t)qp[1] | (uint32_t)qp[2] << 8 | tail, target);
+}
+
+// Records whose codes need FP64, queued per warp: the position, the partner's
+// offset and the slot.  They are computed 32 at a time, one per lane, so the
+// FP64 pipe runs full warps.
+struct RecQueue {
+    unsigned long long* pos;
+    uint32_t* ck;
+    uint32_t* kh;
+};
+constexpr int kRecQueue = 64;
+
+__device__ __noinline__ void flush_records(const EmitArgs& A, const TargetF64& D, uint32_t target,
+                                           const RecQueue& Q, int n) {
+    const unsigned lane = lane_id();
+    if ((int)lane < n) {
+        const uint32_t kh = Q.kh[lane];
+        const int k = (int)(kh & 0xFFFFu), h = (int)(kh >> 16);
+        int qp[3], qm[3];
+        pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + k), __ldg(A.grid.s64 + h),
+                     __ldg(A.grid.c64 + h), A.qkey, qp, qm);
+        store_records(A, target, k, h, qp, qm, 1u, Q.pos[lane], Q.ck[lane]);
+    }
+    __syncwarp();
+}
+
+// Passing slots of an item's bitmap before slot s (pre: exclusive prefix of
+// the words' counts, nwords + 1 entries).
+__device__ __forceinline__ int passing_before(const uint32_t* pb, const uint32_t* pre, int s) {
+    const int w = s >> 5, b = s & 31;
+    return (int)pre[w] + (b ? __popc(pb[w] & ((1u << b) - 1u)) : 0);
+}
+
+// Positions of the items' records: k_scan_tiles gives, per tile of kScanTile
+// items, each item's records before it within the tile and the tile's total;
+// k_scan_top the records before each tile (after the carry: the records of the
+// earlier batches, offs[0]).  An item has (passing slots) << sym records.
+constexpr int kScanTile = 4096;
+__global__ void __launch_bounds__(1024) k_scan_tiles(const uint32_t* __restrict__ count, int sym,
+                                                     int64_t n, int64_t* __restrict__ within,
+                                                     int64_t* __restrict__ tile_sum) {
+    __shared__ long long warp_sum[32];
+    const int64_t i0 = (int64_t)blockIdx.x * kScanTile + 4 * (int64_t)threadIdx.x;
+    long long v[4], run = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[j] = i0 + j < n ? (long long)count[i0 + j] << sym : 0;
+        run += v[j];
+    }
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    long long x = run;  // inclusive scan of the threads' sums within the warp
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+        if ((int)lane >= off) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = warp_sum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long y = __shfl_up_sync(0xFFFFFFFFu, w, off);
+            if ((int)lane >= off) w += y;
+        }
+        warp_sum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    long long ex = x - run + (warp > 0 ? warp_sum[warp - 1] : 0);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (i0 + j < n) within[i0 + j] = ex;
+        ex += v[j];
+    }
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = warp_sum[31];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int64_t* __restrict__ tile, int ntiles,
+                                                   const int64_t* __restrict__ carry) {
+    __shared__ long long warp_sum[32];
+    __shared__ long long base;
+    if (threadIdx.x == 0) base = carry[0];
+    __syncthreads();
+    const unsigned lane = lane_id();
+    const int warp = threadIdx.x >> 5;
+    for (int t0 = 0; t0 < ntiles; t0 += 1024) {
+        const int t = t0 + (int)threadIdx.x;
+        const long long v = t < ntiles ? tile[t] : 0;
+        long long x = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+            if ((int)lane >= off) x += y;
+        }
+        if (lane == 31) warp_sum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            long long w = warp_sum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const long long y = __shfl_up_sync(0xFFFFFFFFu, w, off);
+                if ((int)lane >= off) w += y;
+            }
+            warp_sum[lane] = w;
+        }
+        __syncthreads();
+        const long long ex = base + x - v + (warp > 0 ? warp_sum[warp - 1] : 0);
+        if (t < ntiles) tile[t] = ex;  // in place: records before tile t
+        __syncthreads();
+        if (threadIdx.x == 0) base += warp_sum[31];
+        __syncthreads();
+    }
+}
+
+// The records of one item (target t, radii [k0, k1), its bitmap pb with word
+// prefixes pre, first record at base): per radius k its passing slots in
+// ascending h with m = h, then, on a folded grid, the same slots again with
+// m = h + H and the colours swapped.  Lane j of a round takes the j-th next
+// passing slot, so consecutive lanes store consecutive 16-byte records;
+// records whose FP32 codes are flagged wait in the warp's queue for FP64.
+// Records at or beyond A.out_cap are not written.
+template <int PREC>
+__device__ __forceinline__ void emit_records(const EmitArgs& A, const float2* r2s,
+                                             const float4* sc4s, const ChainF32& C, int64_t t,
+                                             int k0, int nwords, int P, long long base,
+                                             const uint32_t* pb, const uint32_t* pre,
+                                             const RecQueue& Q) {
+    const unsigned lane = lane_id();
+    const int H = A.grid.H, sym = A.grid.sym;
+    TargetF32 T{};
+    if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
+    const TargetF64 D = A.td[t];
+    const uint32_t target = A.target_id + (uint32_t)t;
+    int q_n = 0;  // queued records (warp-uniform)
+    for (int r0 = 0; r0 < P; r0 += 32) {
+        const int R = r0 + (int)lane;
+        bool need64 = false;
+        int k = 0, h = 0;
+        unsigned long long pos = 0;
+        unsigned ck = 0;
+        if (R < P) {
+            int lo = 0, hi = nwords - 1;  // the word holding the R-th passing slot
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((int)pre[mid] <= R) lo = mid; else hi = mid - 1;
+            }
+            const int s = lo * 32 + (int)__fns(pb[lo], 0, R - (int)pre[lo] + 1);
+            const int dk = s / H;
+            h = s - dk * H;
+            k = k0 + dk;
+            const int before = passing_before(pb, pre, dk * H);
+            ck = (unsigned)(passing_before(pb, pre, dk * H + H) - before);
+            pos = (unsigned long long)base + ((unsigned long long)before << sym) +
+                  (unsigned)(R - before);
+            if (PREC == CVS_PREC_FP32_RECHECK) {
+                int qp[3], qm[3];
+                need64 = record_codes32(A, r2s, sc4s, C, T, k, h, qp, qm);
+                if (!need64) store_records(A, target, k, h, qp, qm, 0u, pos, ck);
+            } else {
+                need64 = true;
+            }
+        }
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, need64);
+        if (need64) {
+            const int slot = q_n + __popc(ball & ((1u << lane) - 1u));
+            Q.pos[slot] = pos;
+            Q.ck[slot] = ck;
+            Q.kh[slot] = (uint32_t)k | (uint32_t)h << 16;
+        }
+        q_n += __popc(ball);
+        __syncwarp();
+        if (q_n >= 32) {
+            flush_records(A, D, target, Q, 32);
+            const int rest = q_n - 32;  // below kRecQueue - 32
+            unsigned long long mp = 0;
+            uint32_t mc = 0, mk = 0;
+            if ((int)lane < rest) {
+                mp = Q.pos[32 + lane];
+                mc = Q.ck[32 + lane];
+                mk = Q.kh[32 + lane];
+            }
+            __syncwarp();
+            if ((int)lane < rest) {
+                Q.pos[lane] = mp;
+                Q.ck[lane] = mc;
+                Q.kh[lane] = mk;
+            }
+            __syncwarp();
+            q_n = rest;
+        }
+    }
+    if (q_n > 0) flush_records(A, D, target, Q, q_n);
+}
+
+// One warp per work item (grid-stride): stage the item's bitmap in shared
+// memory, scan its words, set the per-target offsets, write the records.
+template <int PREC>
+__global__ void __launch_bounds__(kSearchBlock) k_emit_pairs(const EmitArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int K = A.grid.K, H = A.grid.H;
+    float2* r2s = reinterpret_cast<float2*>(smem);
+    float4* sc4s = reinterpret_cast<float4*>(smem + ((K * 8 + 15) & ~15));
+    unsigned char* per_warp = smem + ((K * 8 + 15) & ~15) + H * 16;
+    const int warp = threadIdx.x >> 5;
+    RecQueue Q;  // per warp: positions (8 B), partner offsets, slots (4 B each)
+    Q.pos = reinterpret_cast<unsigned long long*>(per_warp) + warp * kRecQueue;
+    Q.ck = reinterpret_cast<uint32_t*>(per_warp + (kSearchBlock / 32) * kRecQueue * 8) +
+           warp * 2 * kRecQueue;
+    Q.kh = Q.ck + kRecQueue;
+    uint32_t* pb = reinterpret_cast<uint32_t*>(per_warp + (kSearchBlock / 32) * kRecQueue * 16) +
+                   warp * kListWarpWords;
+    uint32_t* pre = pb + kListWords;
+    for (int i = threadIdx.x; i < K; i += blockDim.x) r2s[i] = dup(A.grid.r32[i]);
+    for (int i = threadIdx.x; i < H; i += blockDim.x) {
+        const float2 sc = A.grid.sc32[i];
+        sc4s[i] = make_float4(sc.x, -sc.x, sc.y, -sc.y);
+    }
+    __syncthreads();
+    ChainF32 C;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        C.Ax[c] = __double2float_rn(__dmul_rn(c_MI[3 * c], c_W[0]));
+        C.Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
+    }
+    const unsigned lane = lane_id();
+    const int n_kc = (K + A.kchunk - 1) / A.kchunk;
+    const long long n_items = A.n_targets * (long long)n_kc;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_items;
+         g += nwarps) {
+        const int64_t t = g / n_kc;
+        const int kc = (int)(g - t * n_kc);
+        const int k0 = kc * A.kchunk, k1 = min(k0 + A.kchunk, K);
+        const int nwords = ((k1 - k0) * H + 31) >> 5;
+        const uint32_t* src = A.item_bits + g * (long long)A.item_words;
+        int run = 0;
+        for (int w0 = 0; w0 < nwords; w0 += 32) {
+            const int w = w0 + (int)lane;
+            const uint32_t v = w < nwords ? src[w] : 0u;
+            if (w < nwords) pb[w] = v;
+            int tot;
+            const int ex = warp_exclusive_sum(__popc(v), tot);
+            if (w < nwords) pre[w] = (uint32_t)(run + ex);
+            run += tot;
+        }
+        if (lane == 0) pre[nwords] = (uint32_t)run;
+        __syncwarp();
+        const long long base = A.tile_base[g / kScanTile] + A.item_base[g];
+        if (lane == 0) {
+            if (kc == 0) A.offs[t] = base;
+            if (kc == n_kc - 1) A.offs[t + 1] = base + ((long long)run << A.grid.sym);
+        }
+        emit_records<PREC>(A, r2s, sc4s, C, t, k0, nwords, run, base, pb, pre, Q);
+        __syncwarp();
     }
 }
 
@@ -1000,68 +1326,6 @@ __global__ void k_finalize_images(const Acc* __restrict__ acc, const TargetF64* 
     im.pmask[local] = (uint8_t)a.pmask;
 }
 
-// ------------------------------------------------------------ list compaction
-// One block: records with pattern != 0, in index order ((k, m) order).
-__global__ void __launch_bounds__(1024) k_compact_pairs(const cvs_pair* __restrict__ dense,
-                                                        int64_t n, cvs_pair* out,
-                                                        unsigned long long* n_out) {
-    __shared__ int warp_sums[32];
-    __shared__ long long base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const unsigned lane = lane_id();
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t start = 0; start < n; start += blockDim.x) {
-        const int64_t i = start + threadIdx.x;
-        const bool valid = i < n && dense[i].pattern != 0;
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, valid);
-        if (lane == 0) warp_sums[warp] = __popc(ball);
-        __syncthreads();
-        int before = 0, total = 0;
-        for (int w = 0; w < nw; ++w) {
-            if (w < warp) before += warp_sums[w];
-            total += warp_sums[w];
-        }
-        if (valid) out[base + before + __popc(ball & ((1u << lane) - 1u))] = dense[i];
-        __syncthreads();
-        if (threadIdx.x == 0) base += total;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *n_out = (unsigned long long)base;
-}
-
-// Ordered compaction of a batch of targets' dense records: block b moves the
-// passing records of target b (kn entries, (k, m) order) to out + offsets[b].
-__global__ void __launch_bounds__(1024) k_compact_pairs_batch(const cvs_pair* __restrict__ dense,
-                                                              int64_t kn,
-                                                              const int64_t* __restrict__ offsets,
-                                                              cvs_pair* out) {
-    __shared__ int warp_sums[32];
-    __shared__ long long base;
-    const cvs_pair* src = dense + (int64_t)blockIdx.x * kn;
-    cvs_pair* dst = out + offsets[blockIdx.x];
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const unsigned lane = lane_id();
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t start = 0; start < kn; start += blockDim.x) {
-        const int64_t i = start + threadIdx.x;
-        const bool valid = i < kn && src[i].pattern != 0;
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, valid);
-        if (lane == 0) warp_sums[warp] = __popc(ball);
-        __syncthreads();
-        int before = 0, total = 0;
-        for (int w = 0; w < nw; ++w) {
-            if (w < warp) before += warp_sums[w];
-            total += warp_sums[w];
-        }
-        if (valid) dst[base + before + __popc(ball & ((1u << lane) - 1u))] = src[i];
-        __syncthreads();
-        if (threadIdx.x == 0) base += total;
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------------------ L* of all colours
 __global__ void k_l_table(double* __restrict__ ltab) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1083,64 +1347,89 @@ __global__ void k_target_lab(const uint8_t* __restrict__ rgb, int64_t n, double*
 }
 
 // ------------------------------------------------------------ precision probe
-// Every (target, k, m) plus-colour in FP32 and FP64: the largest |v32 - v64| of
-// values within 0.05 of a rounding boundary (v in code units), the largest
-// |lin32 - lin64|, and the number of FP32 codes in [-1, 256] that differ.
+// Every (target, k, m) plus colour in FP32 (each chain the search may take for
+// it: the cubic-branch chain where the target or the radius stays on the cubic
+// branch of f^-1, the branchy chain for targets that may leave it) against the
+// FP64 chain.  Per value, exactly: the FP32 code round(v32) against the FP64
+// code (threshold count), and whether the search would flag it (v32 within W of
+// a rounding boundary, |v32 - round(v32)| >= half_w).  Counts: out[0] FP32
+// codes in [-1, 256] that differ from FP64, out[1] those among them the search
+// would take unflagged (must be 0 for exact results), out[2] values examined.
+// Maxima (float bits): |lin32 - lin64|; |v32 - v64| among values with v64
+// within 0.05 of a boundary (v64 by the FP64 power, evaluated only where v32
+// lies within 0.08 of a boundary; with |lin32 - lin64| small that covers every
+// such value); the a*/b* error of the colour the FP32 chain stands for.
+// One warp per target (grid-stride), lanes over the K x N values.
 __global__ void k_precision_probe(const TargetF32* __restrict__ tf, const TargetF64* __restrict__ td,
                                   int64_t n, const GridDev g, const long long* __restrict__ qkey,
-                                  unsigned int* max_v_err_bits, unsigned int* max_lin_err_bits,
-                                  unsigned int* max_lab_err_bits, unsigned long long* n_wrong) {
+                                  float half_w, unsigned int* max_v_err_bits,
+                                  unsigned int* max_lin_err_bits, unsigned int* max_lab_err_bits,
+                                  unsigned long long* counts) {
     float Ax[3], Bz[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         Ax[c] = __double2float_rn(__dmul_rn(c_MI[3 * c], c_W[0]));
         Bz[c] = __double2float_rn(__dmul_rn(c_MI[3 * c + 2], c_W[2]));
     }
-    const int64_t total = n * g.K * g.N;
+    const unsigned lane = lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int KN = g.K * g.N;
     float vmax = 0.0f, lmax = 0.0f, amax = 0.0f;
-    unsigned long long wrong = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = i / ((int64_t)g.K * g.N);
-        const int rem = (int)(i - t * g.K * g.N);
-        const int k = rem / g.N, m = rem - k * g.N;
+    unsigned long long wrong = 0, unflagged_wrong = 0, values = 0;
+    for (int64_t t = warp; t < n; t += nwarps) {
         const TargetF32 T = tf[t];
         const TargetF64 D = td[t];
-        const float r = g.r32[k];
-        const float2 sc = g.sc32[m];
         const PairsT P = make_pairs(T);
-        // FP64 reference of the plus colour
-        const double da = __dmul_rn(g.r64[k], g.s64[m]), db = __dmul_rn(g.r64[k], g.c64[m]);
-        double lin[3];
-        color_lin64(D.L, __dadd_rn(D.a, da), __dadd_rn(D.b, db), lin);
-        // FP32 plus colour, recomputed to get the unrounded values
-        float2 dX2, dZ2;
-        const float u = r * sc.x, w = r * sc.y;
-        if (T.flags & 1u) delta_xz<true>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
-        else delta_xz<false>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
-        // L*a*b* the FP32 chain stands for: f-values fx0 + u and fz0 + w
-        {
-            const double fy = (D.L + 16.0) / 116.0;
-            const double fx_exact = fy + (D.a + da) / 500.0, fz_exact = fy - (D.b + db) / 200.0;
-            const double ea = 500.0 * fabs(((double)T.fx0 + (double)u) - fx_exact);
-            const double eb = 200.0 * fabs(((double)T.fz0 + (double)w) - fz_exact);
-            amax = fmaxf(amax, (float)fmax(ea, eb));
-        }
+        const double fy = __ddiv_rn(__dadd_rn(D.L, 16.0), 116.0);
+        for (int i = (int)lane; i < KN; i += 32) {
+            const int k = i / g.N, m = i - k * g.N;
+            const float r = g.r32[k];
+            const float2 sc = g.sc32[m];
+            const double da = __dmul_rn(g.r64[k], g.s64[m]), db = __dmul_rn(g.r64[k], g.c64[m]);
+            double lin[3];
+            color_lin64(D.L, __dadd_rn(D.a, da), __dadd_rn(D.b, db), lin);
+            int q64[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float l32 = __ffma2_rn(f2(Bz[c], Bz[c]), dZ2,
-                                         __ffma2_rn(f2(Ax[c], Ax[c]), dX2,
-                                                    f2(T.lin0[c], T.lin0[c]))).x;
-            const float v32 = encode_v32(l32);
-            const double l64 = lin[c];
-            const double v64 = l64 <= 0.0031308 ? 3294.6 * l64 : 269.025 * pow(l64, 1.0 / 2.4) - 14.025;
-            lmax = fmaxf(lmax, (float)fabs((double)l32 - l64));
-            const double frac = v64 - floor(v64);
-            if (fabs(frac - 0.5) < 0.05 && v64 > -2.0 && v64 < 258.0)
-                vmax = fmaxf(vmax, (float)fabs((double)v32 - v64));
-            const int q64 = quantize64(l64, qkey);
-            const int q32 = (int)fminf(fmaxf(rintf(v32), -1.0f), 256.0f);
-            if (q64 != q32 && q64 >= 0 && q64 <= 255) ++wrong;
+            for (int c = 0; c < 3; ++c) q64[c] = quantize64(lin[c], qkey);
+            const float u = r * sc.x, w = r * sc.y;
+            {  // a*, b* of the colour the FP32 chain stands for: f-values fx0 + u, fz0 + w
+                const double fx_exact = fy + (D.a + da) * 0.002, fz_exact = fy - (D.b + db) * 0.005;
+                const double ea = 500.0 * fabs(((double)T.fx0 + (double)u) - fx_exact);
+                const double eb = 200.0 * fabs(((double)T.fz0 + (double)w) - fz_exact);
+                amax = fmaxf(amax, (float)fmax(ea, eb));
+            }
+            const bool fast_ok = (T.flags & 1u) || fast_radius(T, r);
+#pragma unroll 1
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 0 && !fast_ok) continue;     // the cubic-branch chain
+                if (pass == 1 && (T.flags & 1u)) continue;  // the branchy chain
+                float2 dX2, dZ2;
+                if (pass == 0) delta_xz<true>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
+                else delta_xz<false>(P, f2(u, -u), f2(w, -w), dX2, dZ2);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float l32 = __ffma2_rn(f2(Bz[c], Bz[c]), dZ2,
+                                                 __ffma2_rn(f2(Ax[c], Ax[c]), dX2,
+                                                            f2(T.lin0[c], T.lin0[c]))).x;
+                    const float v32 = encode_v32(l32);
+                    const float d = v32 - rintf(v32);
+                    const int q32 = (int)fminf(fmaxf(rintf(v32), -1.0f), 256.0f);
+                    lmax = fmaxf(lmax, (float)fabs((double)l32 - lin[c]));
+                    if (q32 != q64[c]) {
+                        ++wrong;
+                        if (fabsf(d) < half_w) ++unflagged_wrong;
+                    }
+                    if (fabsf(d) > 0.42f && v32 > -2.0f && v32 < 258.0f) {
+                        const double l64 = lin[c];
+                        const double v64 = l64 <= 0.0031308 ? 3294.6 * l64
+                                                            : 269.025 * pow(l64, 1.0 / 2.4) - 14.025;
+                        const double frac = v64 - floor(v64);
+                        if (fabs(frac - 0.5) < 0.05) vmax = fmaxf(vmax, (float)fabs((double)v32 - v64));
+                    }
+                    ++values;
+                }
+            }
         }
     }
 #pragma unroll
@@ -1149,12 +1438,16 @@ __global__ void k_precision_probe(const TargetF32* __restrict__ tf, const Target
         lmax = fmaxf(lmax, __shfl_xor_sync(0xFFFFFFFFu, lmax, off));
         amax = fmaxf(amax, __shfl_xor_sync(0xFFFFFFFFu, amax, off));
         wrong += __shfl_xor_sync(0xFFFFFFFFu, wrong, off);
+        unflagged_wrong += __shfl_xor_sync(0xFFFFFFFFu, unflagged_wrong, off);
+        values += __shfl_xor_sync(0xFFFFFFFFu, values, off);
     }
-    if (lane_id() == 0) {
+    if (lane == 0) {
         atomicMax(max_v_err_bits, __float_as_uint(vmax));
         atomicMax(max_lin_err_bits, __float_as_uint(lmax));
         atomicMax(max_lab_err_bits, __float_as_uint(amax));
-        if (wrong) atomicAdd(n_wrong, wrong);
+        if (wrong) atomicAdd(counts, wrong);
+        if (unflagged_wrong) atomicAdd(counts + 1, unflagged_wrong);
+        if (values) atomicAdd(counts + 2, values);
     }
 }
 
@@ -1249,11 +1542,13 @@ cudaError_t launch_setup_images(const ImageDesc* imgs, int n_imgs, int64_t total
     return cudaGetLastError();
 }
 
-int search_smem_bytes(const GridDev& g, int block) {
+int search_smem_bytes(const GridDev& g, int block, int list) {
     // (r, r) pairs, angle quadruples, then per warp: FP64 queue (targets, slots)
-    // and flagged queue, and on grids with angle ranges the range list
+    // and flagged queue, on grids with angle ranges the range list, and in list
+    // mode the item's bitmap with its prefix counts
     return ((g.K * 8 + 15) & ~15) + g.H * 16 + 3 * 512 +
-           (block / 32) * (kRqCap * 12 + kFlagWords * 32 * 4 + (g.arcs ? kArcWords * 4 : 0));
+           (block / 32) * (kRqCap * 12 + kFlagWords * 32 * 4 + (g.arcs ? kArcWords * 4 : 0) +
+                           (list ? kListWords * 4 : 0));
 }
 
 template <int PREC, bool CLIP, bool LIST, bool DL>
@@ -1263,7 +1558,7 @@ cudaError_t launch_search_t(const SearchArgs& a_in, cudaStream_t st) {
     const bool arcs = PREC == CVS_PREC_FP32_RECHECK && !CLIP && a.grid.arcs && a.arc_ranges &&
                       a.arc_cap >= a.grid.K;
     a.grid.arcs = arcs ? 1 : 0;
-    const int smem = search_smem_bytes(a.grid, a.shape.block);
+    const int smem = search_smem_bytes(a.grid, a.shape.block, LIST);
     constexpr bool kArcsKernel = PREC == CVS_PREC_FP32_RECHECK && !CLIP;
     const void* fn = arcs ? (const void*)k_search<PREC, CLIP, LIST, DL, kArcsKernel>
                           : (const void*)k_search<PREC, CLIP, LIST, DL, false>;
@@ -1289,7 +1584,8 @@ cudaError_t launch_search_t(const SearchArgs& a_in, cudaStream_t st) {
         c.acc += t0;
         c.n_targets = nt;
         c.target_id = a.target_id + (uint32_t)t0;
-        if (c.dense) c.dense += t0 * (int64_t)a.grid.K * a.grid.N;
+        if (LIST)  // items of this chunk follow those of the earlier chunks
+            c.item0 = a.item0 + t0 * ((a.grid.K + a.shape.kchunk - 1) / a.shape.kchunk);
         if (t0 > 0) {
             e = cudaMemsetAsync(c.work_counter, 0, sizeof(unsigned long long), st);
             if (e != cudaSuccess) return e;
@@ -1351,16 +1647,36 @@ cudaError_t launch_finalize_images(const Acc* acc, const TargetF64* td, int64_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_pairs(const cvs_pair* dense, int64_t n_dense, cvs_pair* out,
-                                 unsigned long long* n_out, cudaStream_t st) {
-    k_compact_pairs<<<1, 1024, 0, st>>>(dense, n_dense, out, n_out);
+cudaError_t launch_pair_scan(const uint32_t* count, int sym, int64_t n_items, int64_t* within,
+                             int64_t* tile, const int64_t* carry, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    const int64_t ntiles = (n_items + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<(unsigned)ntiles, 1024, 0, st>>>(count, sym, n_items, within, tile);
+    k_scan_top<<<1, 1024, 0, st>>>(tile, (int)ntiles, carry);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compact_pairs_batch(const cvs_pair* dense, int64_t kn, int64_t n_targets,
-                                      const int64_t* offsets, cvs_pair* out, cudaStream_t st) {
-    if (n_targets <= 0 || kn <= 0) return cudaSuccess;
-    k_compact_pairs_batch<<<(unsigned)n_targets, 1024, 0, st>>>(dense, kn, offsets, out);
+int emit_smem_bytes(const GridDev& g) {
+    // tables, then per warp the record queue (16 B an entry) and the bitmap
+    // with its prefix counts
+    return ((g.K * 8 + 15) & ~15) + g.H * 16 +
+           (kSearchBlock / 32) * (kRecQueue * 16 + kListWarpWords * 4);
+}
+
+cudaError_t launch_emit_pairs(const EmitArgs& a, int num_sms, cudaStream_t st) {
+    const int64_t n_items = a.n_targets * ((a.grid.K + a.kchunk - 1) / a.kchunk);
+    if (n_items <= 0) return cudaSuccess;
+    const int smem = emit_smem_bytes(a.grid);
+    const void* fn = a.prec == CVS_PREC_FP64 ? (const void*)k_emit_pairs<CVS_PREC_FP64>
+                                             : (const void*)k_emit_pairs<CVS_PREC_FP32_RECHECK>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t want = (n_items + 3) / 4, cap = (int64_t)num_sms * 16;  // 4 warps a block
+    const unsigned blocks = (unsigned)(want < cap ? want : cap);
+    if (a.prec == CVS_PREC_FP64)
+        k_emit_pairs<CVS_PREC_FP64><<<blocks, kSearchBlock, smem, st>>>(a);
+    else
+        k_emit_pairs<CVS_PREC_FP32_RECHECK><<<blocks, kSearchBlock, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1376,13 +1692,13 @@ cudaError_t launch_target_lab(const uint8_t* rgb, int64_t n, double* lab, cudaSt
 }
 
 cudaError_t launch_precision_probe(const TargetF32* tf, const TargetF64* td, int64_t n,
-                                   const GridDev& g, const long long* qkey,
+                                   const GridDev& g, const long long* qkey, float half_w,
                                    unsigned int* max_v_err_bits, unsigned int* max_lin_err_bits,
-                                   unsigned int* max_lab_err_bits, unsigned long long* n_wrong,
+                                   unsigned int* max_lab_err_bits, unsigned long long* counts,
                                    int num_sms, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_precision_probe<<<num_sms * 8, 256, 0, st>>>(tf, td, n, g, qkey, max_v_err_bits,
-                                                    max_lin_err_bits, max_lab_err_bits, n_wrong);
+    k_precision_probe<<<num_sms * 8, 256, 0, st>>>(tf, td, n, g, qkey, half_w, max_v_err_bits,
+                                                    max_lin_err_bits, max_lab_err_bits, counts);
     return cudaGetLastError();
 }
 

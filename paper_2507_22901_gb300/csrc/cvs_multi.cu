@@ -75,6 +75,23 @@ __device__ __forceinline__ uint32_t pass_sets(const uint32_t e[3], bool in_range
     return ok;
 }
 
+// Sets whose luminance limit the pair with exact codes qp, qm meets: those
+// without a limit, and those whose max_dl is at least the larger |L* - L| of
+// the two emitted colours (non-negative doubles order as their bit patterns).
+// Called only for slots that pass some set, so it stays out of the slot loop.
+__device__ __noinline__ uint32_t dl_sets(const MultiArgs& A, double L, const int qp[3],
+                                         const int qm[3]) {
+    const int ip = (qp[0] << 16) | (qp[1] << 8) | qp[2];
+    const int im = (qm[0] << 16) | (qm[1] << 8) | qm[2];
+    const double d = fmax(fabs(__dsub_rn(__ldg(A.ltab + ip), L)),
+                          fabs(__dsub_rn(__ldg(A.ltab + im), L)));
+    const long long db = __double_as_longlong(d);
+    uint32_t m = A.dl_free;
+    for (int s = 0; s < A.n_thr; ++s)
+        if (db <= A.max_dl_bits[s]) m |= 1u << s;
+    return m;
+}
+
 // Per-lane tallies of one work item.
 struct MultiTally {
     uint32_t c4[4];  // pass counts, byte b of word j = set 4 j + b
@@ -141,8 +158,11 @@ __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* 
         e[c] = eL;
     }
     uint32_t open = (maybe_out ? 0xFFFFu : unstable) & ~cinv & setmask;
-    uint32_t hR, hG, hB, ok;
-    if (open) {  // some set's decision depends on a code the bounds leave open: FP64
+    uint32_t hR, hG, hB, ok = 0;
+    if (!open) ok = pass_sets<ALLMASK>(e, true, setmask & ~cinv, A.pmask_sets, hR, hG, hB);
+    // some set's decision depends on a code the bounds leave open, or (under a
+    // luminance limit) a set passes and the limit needs the exact codes: FP64
+    if (open || (A.ltab && ok)) {
         int qp[3], qm[3];
         pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + __ldg(A.order + kk)), __ldg(A.grid.s64 + h),
                      __ldg(A.grid.c64 + h), A.qkey, qp, qm);
@@ -157,9 +177,8 @@ __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* 
             e[c] = ts[min(abs(qp[c] - qm[c]), 256)];
         }
         ok = pass_sets<ALLMASK>(e, in_range, setmask, A.pmask_sets, hR, hG, hB);
+        if (A.ltab && ok) ok &= dl_sets(A, D.L, qp, qm);
         ++n_re;
-    } else {
-        ok = pass_sets<ALLMASK>(e, true, setmask & ~cinv, A.pmask_sets, hR, hG, hB);
     }
     if (!ok) return;
     const int inc = A.grid.sym ? 2 : 1;
@@ -186,6 +205,111 @@ __device__ __forceinline__ void drain_multi(const MultiArgs& A, const float2* r2
         const uint32_t v = pq[lane];
         multi_flagged<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t, (int)(v & 0xFFFFu),
                                                  (int)(v >> 16), setmask, n_re);
+    }
+}
+
+// Iterations [it, end) of a work item (lanes at slot (rank kk, angle h),
+// radii decreasing), one encode variant: LINSEG = false where every radius of
+// the iterations stays above the sRGB linear segment.  Flagged slots set
+// their bits in `bits` (bit advances per iteration).
+template <int PREC, bool FAST, bool CLIP, bool ALLMASK, bool LINSEG>
+__device__ __forceinline__ void multi_iters(const MultiArgs& A, const float2* r2s,
+                                            const uint32_t* ts, const float4* sc4s,
+                                            const PairsT& P, const PairsC& PC,
+                                            const TargetF64& D, MultiTally& m, float* rmx,
+                                            uint32_t setmask, int nw, int nslots, int kk1,
+                                            int& it, int end, int& kk, int& h, uint32_t& bits,
+                                            uint32_t& bit, uint32_t& seen) {
+    const unsigned lane = lane_id();
+    const int H = A.grid.H;
+    const int q32 = 32 / H, r32 = 32 - q32 * H;
+    for (; it < end; ++it, bit <<= 1) {
+        const bool active = it * 32 + (int)lane < nslots;
+        const int kq = active ? kk : kk1 - 1, hq = active ? h : 0;
+        uint32_t ok = 0, hR = 0, hG = 0, hB = 0;
+        bool skip = false;
+        if (PREC == CVS_PREC_FP32_RECHECK) {
+            const float2 r2 = r2s[kq];
+            const float4 sc = sc4s[hq];
+            const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));
+            const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
+            float2 lin[3];
+            lin32<FAST>(P, PC, u2, w2, lin);
+            // gamut reject: a warp whose pairs all leave the gamut passes no set
+            skip = !CLIP && __all_sync(0xFFFFFFFFu, !active || surely_out32(lin));
+            if (!skip) {
+                int yp[3], ym[3];
+                bool flag = encode32<LINSEG>(lin, A.half_w, yp, ym, nullptr);
+                flag = flag && active;
+                if (flag) bits |= bit;
+                uint32_t e[3];
+                uint32_t o = 0;
+                int qa[3], qb[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    int a = yp[c] - kMagicBits, b = ym[c] - kMagicBits;
+                    if (CLIP) {
+                        a = min(max(a, 0), 255);
+                        b = min(max(b, 0), 255);
+                    }
+                    qa[c] = a;
+                    qb[c] = b;
+                    o |= (uint32_t)a | (uint32_t)b;
+                    e[c] = ts[min(abs(a - b), 256)];
+                }
+                if (active && !flag) {
+                    ok = pass_sets<ALLMASK>(e, o <= 255u, setmask, A.pmask_sets, hR, hG, hB);
+                    if (A.ltab && ok) {  // the luminance limits, per set
+                        ok &= dl_sets(A, D.L, qa, qb);
+                        hR &= ok;
+                        hG &= ok;
+                        hB &= ok;
+                    }
+                }
+            }
+        } else if (active) {
+            int qp[3], qm[3];
+            pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + __ldg(A.order + kq)),
+                         __ldg(A.grid.s64 + hq), __ldg(A.grid.c64 + hq), A.qkey, qp, qm);
+            uint32_t e[3];
+            bool in_range = true;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                if (CLIP) {
+                    qp[c] = min(max(qp[c], 0), 255);
+                    qm[c] = min(max(qm[c], 0), 255);
+                }
+                in_range = in_range && qp[c] >= 0 && qp[c] <= 255 && qm[c] >= 0 &&
+                           qm[c] <= 255;
+                e[c] = ts[min(abs(qp[c] - qm[c]), 256)];
+            }
+            ok = pass_sets<ALLMASK>(e, in_range, setmask, A.pmask_sets, hR, hG, hB);
+            if (A.ltab && ok) {
+                ok &= dl_sets(A, D.L, qp, qm);
+                hR &= ok;
+                hG &= ok;
+                hB &= ok;
+            }
+        }
+        if (!skip) {
+            tally_counts(m, ok, nw);
+            tally_patterns(m, hR, hG, hB);
+            uint32_t fresh = ok & ~seen;  // radii decrease: the first pass is the largest
+            if (fresh) {
+                seen |= fresh;
+                const float r = r2s[kq].x;
+                while (fresh) {
+                    const int s = __ffs(fresh) - 1;
+                    fresh &= fresh - 1u;
+                    rmx[s * 32 + lane] = r;
+                }
+            }
+        }
+        h += r32;
+        kk -= q32;
+        const bool wrap = h >= H;
+        h = wrap ? h - H : h;
+        kk = wrap ? kk - 1 : kk;
     }
 }
 
@@ -231,79 +355,20 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
         for (int w = 0, it = seg0; it < seg1; ++w) {
             uint32_t bits = 0;
             const int wend = min(seg1, it + 32);
-            for (uint32_t bit = 1u; it < wend; ++it, bit <<= 1) {
-                const bool active = it * 32 + (int)lane < nslots;
-                const int kq = active ? kk : kk1 - 1, hq = active ? h : 0;
-                uint32_t ok = 0, hR = 0, hG = 0, hB = 0;
-                bool skip = false;
-                if (PREC == CVS_PREC_FP32_RECHECK) {
-                    const float2 r2 = r2s[kq];
-                    const float4 sc = sc4s[hq];
-                    const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));
-                    const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
-                    float2 lin[3];
-                    lin32<FAST>(P, PC, u2, w2, lin);
-                    // gamut reject: a warp whose pairs all leave the gamut passes no set
-                    skip = !CLIP && __all_sync(0xFFFFFFFFu, !active || surely_out32(lin));
-                    if (!skip) {
-                        int yp[3], ym[3];
-                        bool flag;
-                        if (it >= it_pow) flag = encode32<false>(lin, A.half_w, yp, ym, nullptr);
-                        else flag = encode32<true>(lin, A.half_w, yp, ym, nullptr);
-                        flag = flag && active;
-                        if (flag) bits |= bit;
-                        uint32_t e[3];
-                        uint32_t o = 0;
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            int a = yp[c] - kMagicBits, b = ym[c] - kMagicBits;
-                            if (CLIP) {
-                                a = min(max(a, 0), 255);
-                                b = min(max(b, 0), 255);
-                            }
-                            o |= (uint32_t)a | (uint32_t)b;
-                            e[c] = ts[min(abs(a - b), 256)];
-                        }
-                        if (active && !flag)
-                            ok = pass_sets<ALLMASK>(e, o <= 255u, setmask, A.pmask_sets, hR, hG, hB);
-                    }
-                } else if (active) {
-                    int qp[3], qm[3];
-                    pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + __ldg(A.order + kq)),
-                                 __ldg(A.grid.s64 + hq), __ldg(A.grid.c64 + hq), A.qkey, qp, qm);
-                    uint32_t e[3];
-                    bool in_range = true;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        if (CLIP) {
-                            qp[c] = min(max(qp[c], 0), 255);
-                            qm[c] = min(max(qm[c], 0), 255);
-                        }
-                        in_range = in_range && qp[c] >= 0 && qp[c] <= 255 && qm[c] >= 0 &&
-                                   qm[c] <= 255;
-                        e[c] = ts[min(abs(qp[c] - qm[c]), 256)];
-                    }
-                    ok = pass_sets<ALLMASK>(e, in_range, setmask, A.pmask_sets, hR, hG, hB);
-                }
-                if (!skip) {
-                    tally_counts(m, ok, nw);
-                    tally_patterns(m, hR, hG, hB);
-                    uint32_t fresh = ok & ~seen;  // radii decrease: the first pass is the largest
-                    if (fresh) {
-                        seen |= fresh;
-                        const float r = r2s[kq].x;
-                        while (fresh) {
-                            const int s = __ffs(fresh) - 1;
-                            fresh &= fresh - 1u;
-                            rmx[s * 32 + lane] = r;
-                        }
-                    }
-                }
-                h += r32;
-                kk -= q32;
-                const bool wrap = h >= H;
-                h = wrap ? h - H : h;
-                kk = wrap ? kk - 1 : kk;
+            uint32_t bit = 1u;
+            if (PREC == CVS_PREC_FP32_RECHECK && FAST && it < it_pow) {
+                // iterations that may reach the sRGB linear segment, then the rest
+                multi_iters<PREC, FAST, CLIP, ALLMASK, true>(A, r2s, ts, sc4s, P, PC, D, m, rmx,
+                                                             setmask, nw, nslots, kk1, it,
+                                                             min(wend, it_pow), kk, h, bits, bit,
+                                                             seen);
+                multi_iters<PREC, FAST, CLIP, ALLMASK, false>(A, r2s, ts, sc4s, P, PC, D, m, rmx,
+                                                              setmask, nw, nslots, kk1, it, wend,
+                                                              kk, h, bits, bit, seen);
+            } else {
+                multi_iters<PREC, FAST, CLIP, ALLMASK, !(PREC == CVS_PREC_FP32_RECHECK && FAST)>(
+                    A, r2s, ts, sc4s, P, PC, D, m, rmx, setmask, nw, nslots, kk1, it, wend, kk, h,
+                    bits, bit, seen);
             }
             if (PREC == CVS_PREC_FP32_RECHECK) fb[w * 32 + lane] = bits;
         }

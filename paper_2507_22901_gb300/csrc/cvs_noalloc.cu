@@ -71,8 +71,20 @@ long long host_dkey(double x) {
     return k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFll);
 }
 
+// The 257 quantisation threshold keys, formed once on the host; static, so the
+// source of every call's asynchronous copy outlives the copy.
+struct QKeys {
+    long long v[257];
+    QKeys() {
+        const double thr[257] = CVS_QTHR_INIT;
+        for (int i = 0; i < 257; ++i) v[i] = host_dkey(thr[i]);
+    }
+};
+const QKeys g_qkeys;
+
 // Once per device, with that device current: the scratch array's device
-// address, and the quantisation threshold keys copied into it.
+// address.  (A cudaDeviceReset between calls would invalidate the cached
+// address; the entry point does not support that.)
 cvs_status device_setup(int device, unsigned char** out) {
     std::lock_guard<std::mutex> lock(g_setup_mu);
     if (g_scratch_ptr[device]) {
@@ -82,15 +94,10 @@ cvs_status device_setup(int device, unsigned char** out) {
     if (cvs::target_f32_size() != kTfBytes || cvs::target_f64_size() != kTdBytes)
         return fail(CVS_ERR_CUDA, "no-alloc scratch layout does not match the target records");
     unsigned char* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p)
         return fail(CVS_ERR_CUDA, "cudaGetSymbolAddress(g_noalloc_scratch): %s",
                     cudaGetErrorString(e));
-    const double thr[257] = CVS_QTHR_INIT;
-    long long keys[257];
-    for (int i = 0; i < 257; ++i) keys[i] = host_dkey(thr[i]);
-    e = cudaMemcpy(p + kOffQkey, keys, sizeof keys, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return fail(CVS_ERR_CUDA, "threshold keys: %s", cudaGetErrorString(e));
     g_scratch_ptr[device] = p;
     *out = p;
     return CVS_OK;
@@ -126,6 +133,8 @@ cvs_status run(int device, const uint8_t* rgb_dev, int64_t n, const cvs_grid* g,
         if (g->radii[i] > rmax) rmax = g->radii[i];
     }
     d.rmax = rmax;
+    // every call writes all it reads: the threshold keys, then the grid
+    NA_CUDA(cudaMemcpyAsync(p + kOffQkey, g_qkeys.v, sizeof g_qkeys.v, cudaMemcpyHostToDevice, st));
     NA_CUDA(cudaMemcpyAsync(d.r64, g->radii, sizeof(double) * K, cudaMemcpyHostToDevice, st));
     NA_CUDA(cudaMemcpyAsync(d.r32, r32, sizeof(float) * K, cudaMemcpyHostToDevice, st));
     NA_CUDA(cudaMemcpyAsync(angles, g->angles_deg, sizeof(double) * N, cudaMemcpyHostToDevice, st));
@@ -137,9 +146,7 @@ cvs_status run(int device, const uint8_t* rgb_dev, int64_t n, const cvs_grid* g,
     NA_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));
     if (hstatus) return fail(CVS_ERR_NUMERIC, "an angle's sine could not be certified");
-    int sym = (N % 2 == 0) ? 1 : 0;
-    for (int m = 0; sym && m < N / 2; ++m)
-        if (!(sh[m + N / 2] == -sh[m] && ch[m + N / 2] == -ch[m])) sym = 0;
+    const int sym = cvs::fold_by_180(sh, ch, N);
     d.sym = sym;
     d.H = sym ? N / 2 : N;
     if (n == 0) return CVS_OK;
@@ -162,21 +169,13 @@ cvs_status run(int device, const uint8_t* rgb_dev, int64_t n, const cvs_grid* g,
     a.mask2 = thr->pattern_mask << 1;
     a.clip = thr->gamut_mode;
     a.half_w = (float)(0.5 - 2e-3);
-    a.prec = (prec == CVS_PREC_FP32_RECHECK && rmax > cvs::kFp32MaxRadius) ? (int32_t)CVS_PREC_FP64
-                                                                           : (int32_t)prec;
+    a.prec = (int32_t)prec;
     a.list_mode = 0;
     a.work_counter = counters;
     a.stats = counters + 1;
     a.shape.block = cvs::kSearchBlock;
     a.shape.blocks_per_sm = 0;
-    // radius chunk: enough work items to spread n targets over every SM
-    int64_t n_kc = ((int64_t)num_sms * 512 + n - 1) / n;
-    if (n_kc < 1) n_kc = 1;
-    if (n_kc > K) n_kc = K;
-    int kchunk = (int)((K + n_kc - 1) / n_kc);
-    const int min_k = (64 + d.H - 1) / d.H;
-    if (kchunk < min_k) kchunk = min_k < K ? min_k : K;
-    a.shape.kchunk = kchunk;
+    a.shape.kchunk = cvs::auto_kchunk(num_sms, n, K, d.H);
     a.num_sms = num_sms;
     NA_CUDA(cvs::launch_setup_colors(rgb_dev, n, rmax, tf, td, acc, st));
     NA_CUDA(cudaMemsetAsync(counters, 0, cvs::kNumCounters * sizeof(unsigned long long), st));
@@ -213,9 +212,19 @@ extern "C" cvs_status cvs_search_colors_noalloc(int device, const uint8_t* rgb_d
             return fail(CVS_ERR_INVALID_ARG, "angle %d is not finite", i);
     if (prec != CVS_PREC_FP32_RECHECK && prec != CVS_PREC_FP64)
         return fail(CVS_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (prec == CVS_PREC_FP32_RECHECK)
+        for (int i = 0; i < grid->n_radii; ++i)
+            if (grid->radii[i] > cvs::kFp32MaxRadius)
+                return fail(CVS_ERR_INVALID_ARG,
+                            "CVS_PREC_FP32_RECHECK is validated for radii up to %g (radius %d is "
+                            "%g): pass CVS_PREC_FP64", cvs::kFp32MaxRadius, i, grid->radii[i]);
     int32_t hi, lo;
     cvs_status s = cvs_signal_bounds(thr, &hi, &lo);  // validates the thresholds
     if (s != CVS_OK) return s;
+    if (thr->max_dl > 0.0 && std::isfinite(thr->max_dl))
+        return fail(CVS_ERR_INVALID_ARG,
+                    "cvs_search_colors_noalloc: the luminance limit max_dl needs a 128 MiB table "
+                    "of L* values that the fixed scratch cannot hold; pass max_dl = 0");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev ||
         device >= kMaxDevices)

@@ -197,6 +197,12 @@ cvs_status cvs_server_create(cvs_server** out, const cvs_server_config* cfg, con
     if (st != CVS_OK) return st;
     if (!grid->radii || !grid->angles_deg || grid->n_radii <= 0 || grid->n_angles <= 0)
         return fail(CVS_ERR_INVALID_ARG, "empty or NULL grid");
+    if (prec == CVS_PREC_FP32_RECHECK)
+        for (int i = 0; i < grid->n_radii; ++i)
+            if (grid->radii[i] > cvs::kFp32MaxRadius)
+                return fail(CVS_ERR_INVALID_ARG,
+                            "CVS_PREC_FP32_RECHECK is validated for radii up to %g: pass "
+                            "CVS_PREC_FP64 for this grid", cvs::kFp32MaxRadius);
     cvs_server* S = new cvs_server();
     S->cfg = *cfg;
     S->radii.assign(grid->radii, grid->radii + grid->n_radii);
@@ -216,15 +222,16 @@ cvs_status cvs_server_create(cvs_server** out, const cvs_server_config* cfg, con
     st = CVS_OK;
     if (cfg->use_table) {
         cvs_ctx* c0 = nullptr;
-        st = cvs_create(&c0, cfg->device);
+        st = cvs_create(&c0, cfg->device, 0);
         if (st == CVS_OK) st = cvs_lut_build(c0, &S->grid, &S->thr, prec, &S->lut, nullptr);
         if (c0) cvs_destroy(c0);
     }
     for (size_t i = 0; i < S->slots.size() && st == CVS_OK; ++i) {
         Slot& sl = S->slots[i];
         if (!cfg->use_table) {
-            st = cvs_create(&sl.ctx, cfg->device);
+            st = cvs_create(&sl.ctx, cfg->device, 0);
             if (st == CVS_OK) st = cvs_reserve(sl.ctx, &S->grid, cfg->max_pixels, 1);
+            if (st == CVS_OK) st = cvs::prepare_thresholds(sl.ctx, &S->thr);
             // leave room on every SM for the other slots' kernels
             const int per_sm = 5 / cfg->max_inflight;
             if (st == CVS_OK && cfg->max_inflight > 1)

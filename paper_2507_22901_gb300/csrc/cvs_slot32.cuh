@@ -689,6 +689,17 @@ __device__ __forceinline__ int certain_from(const Intervals& I, int32_t hi_min, 
     return ok ? pattern : 0;
 }
 
+// The luminance limit on an emitted pair (codes in [0, 255]): each colour's
+// L* (step 1 applied to its codes, from the table of all 2^24 colours) lies
+// within max_dl of the target's L*.
+__device__ __forceinline__ bool dl_ok(const double* __restrict__ ltab, double max_dl,
+                                      double l_target, const int qp[3], const int qm[3]) {
+    const int ip = (qp[0] << 16) | (qp[1] << 8) | qp[2];
+    const int im = (qm[0] << 16) | (qm[1] << 8) | qm[2];
+    return fabs(__dsub_rn(__ldg(ltab + ip), l_target)) <= max_dl &&
+           fabs(__dsub_rn(__ldg(ltab + im), l_target)) <= max_dl;
+}
+
 template <bool FAST>
 __device__ __forceinline__ int certain32(const TargetF32& T, const ChainF32& C, float2 r2,
                                          float4 sc, float half_w, int32_t hi_min, int32_t lo_max,

@@ -82,6 +82,10 @@ GRIDS = {
     "12 degrees, radius 0 included": (np.arange(0, 41) * 0.8, np.arange(30) * 12.0),
     "unsorted radii": (np.array([30.0, 1.0, 25.0, 7.0, 31.5, 14.0, 0.5, 22.0, 12.25, 3.0]),
                        np.arange(360) * 1.0),
+    # first angles far from [0, 360): the offset is reduced exactly before the
+    # ranges round it to FP32 radians
+    "0.5 degree from 1e6 + 0.5": (np.arange(1, 65) * 0.5, 1e6 + 0.5 + np.arange(720) * 0.5),
+    "1 degree from -1e6 - 0.25": (np.arange(1, 65) * 0.5, -1e6 - 0.25 + np.arange(360) * 1.0),
 }
 
 
@@ -140,16 +144,14 @@ def test_luminance_limit(ctx, torch_cuda):
     radii, ang = W.grid(3)
     rgb = sample_colours(150, 11)
     out = {}
-    ctx.set_option("max_dl", 0.5)
     try:
         for ar in (1, 0):
             ctx.set_option("angle_ranges", ar)
-            o = ctx.search_colors(dev(torch_cuda, rgb), radii, ang, 50.0, 0.5)
+            o = ctx.search_colors(dev(torch_cuda, rgb), radii, ang, 50.0, 0.5, max_dl=0.5)
             ctx.synchronize()
             out[ar] = tuple(x.cpu().numpy() for x in o)
     finally:
         ctx.set_option("angle_ranges", 2)
-        ctx.set_option("max_dl", -1.0)
     exp = oracle.search_colors(rgb, radii, ang, 50.0, 0.5, threads=THREADS, max_dl=0.5)
     same(out[1], exp, "max_dl 0.5 (ranges)")
     same(out[0], exp, "max_dl 0.5 (plain)")

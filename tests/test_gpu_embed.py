@@ -99,10 +99,14 @@ def test_masks_and_large_radii(ctx, torch_cuda):
     img = small_image(20, 12, 6)
     pat = W.code_pattern(12, 20, module=2, seed=6, fill=1.0)
     radii, ang = np.array([10.0, 24.0, 40.0, 64.0]), np.arange(0.0, 360.0, 10.0)
-    for mask in (0x7F, 0b1010101, 0):
-        got = gpu_embed(ctx, torch_cuda, img, pat, radii, ang, pattern_mask=mask)
-        exp = oracle_embed(img, pat, radii, ang, pattern_mask=mask)
-        assert_same(got, exp, f"mask {mask:#x}")
+    ctx.set_option("fp64_fallback", 1)  # radii above 32 run in FP64
+    try:
+        for mask in (0x7F, 0b1010101, 0):
+            got = gpu_embed(ctx, torch_cuda, img, pat, radii, ang, pattern_mask=mask)
+            exp = oracle_embed(img, pat, radii, ang, pattern_mask=mask)
+            assert_same(got, exp, f"mask {mask:#x}")
+    finally:
+        ctx.set_option("fp64_fallback", 0)
     assert (got[2] == NONE).all()
 
 

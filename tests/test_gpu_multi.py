@@ -122,12 +122,17 @@ def test_masks_per_set_and_one_set(ctx, torch_cuda):
 
 
 def test_large_radii_and_ragged_grid(ctx, torch_cuda):
-    """Radii above the FP32 limit run in FP64; an odd, unfolded angle list."""
+    """Radii above the FP32 limit (run in FP64 through option fp64_fallback); an
+    odd, unfolded angle list."""
     rgb = W.color_cube(step=64)
     radii = np.array([0.0, 3.0, 40.0, 7.5, 120.0])
     ang = np.arange(0.0, 359.0, 7.0)
     sets = W.table1_threshold_sets()[:5]
-    got = multi(ctx, torch_cuda, rgb, radii, ang, sets, 0, binding.PREC_FP32_RECHECK)
+    ctx.set_option("fp64_fallback", 1)
+    try:
+        got = multi(ctx, torch_cuda, rgb, radii, ang, sets, 0, binding.PREC_FP32_RECHECK)
+    finally:
+        ctx.set_option("fp64_fallback", 0)
     for s, (vth, rn) in enumerate(sets):
         exp = oracle.search_colors(rgb, radii, ang, vth, rn, threads=THREADS)
         column_equal(got, s, exp, "large radii")

@@ -177,7 +177,8 @@ def test_precision_set_full_fp32_equals_fp64_and_probe(ctx, torch_cuda):
     w = ctx.get_option("fp32_window")
     print("probe", pr, "window", w)
     assert pr["max_code_err"] < w / 2  # the window keeps a margin over the measured error
-    assert pr["max_lab_err"] < 1e-4 and pr["n_values"] == len(rgb) * 256 * 720 * 3
+    assert pr["n_unflagged_wrong"] == 0 and pr["window"] == w
+    assert pr["max_lab_err"] < 1e-4 and pr["n_values"] >= len(rgb) * 256 * 720 * 3
 
 
 # ------------------------------------------------------------------ images
@@ -341,16 +342,28 @@ def test_host_entry_point_and_stream(ctx, torch_cuda):
     assert_maps_equal(tuple(x.cpu().numpy() for x in out), exp, "side stream")
 
 
-def test_large_radii_run_in_fp64_and_match(ctx, torch_cuda):
-    """Radii beyond the FP32 path's validated range (32) are searched in FP64."""
+def test_large_radii_need_fp64(ctx, torch_cuda):
+    """Radii beyond the FP32 path's validated range (32): an FP32 request is
+    refused with a message naming the remedies; FP64, asked for directly or
+    through option fp64_fallback, matches the oracle."""
     rgb = cube_sample(16, seed=21)
     radii = np.array([5.0, 31.5, 40.0, 64.0, 120.0])
     ang = np.arange(72) * 5.0
     exp = oracle_colors(rgb, radii, ang)
-    got = gpu_colors(ctx, torch_cuda, rgb, radii, ang, binding.PREC_FP32_RECHECK)
-    ctx.synchronize()
-    assert ctx.stats()["precision"] == binding.PREC_FP64
-    assert_maps_equal(got, exp, "large radii")
+    with pytest.raises(cvs.CvsError) as ei:
+        gpu_colors(ctx, torch_cuda, rgb, radii, ang, binding.PREC_FP32_RECHECK)
+    assert ei.value.status == binding.CVS_ERR_INVALID_ARG
+    assert "CVS_PREC_FP64" in str(ei.value) and "fp64_fallback" in str(ei.value)
+    got = gpu_colors(ctx, torch_cuda, rgb, radii, ang, binding.PREC_FP64)
+    assert_maps_equal(got, exp, "large radii, FP64")
+    ctx.set_option("fp64_fallback", 1)
+    try:
+        got = gpu_colors(ctx, torch_cuda, rgb, radii, ang, binding.PREC_FP32_RECHECK)
+        ctx.synchronize()
+        assert ctx.stats()["precision"] == binding.PREC_FP64
+    finally:
+        ctx.set_option("fp64_fallback", 0)
+    assert_maps_equal(got, exp, "large radii, fallback")
 
 
 # ------------------------------------------------------------------ batching machinery

@@ -75,13 +75,19 @@ def test_signal_bounds_exact_products():
 
 
 @pytest.mark.parametrize("bad", [dict(v_th=float("nan")), dict(v_th=-1.0), dict(r_novib=0.0),
-                                 dict(r_novib=1.5), dict(pattern_mask=0x80), dict(gamut_mode=2)])
+                                 dict(r_novib=1.5), dict(pattern_mask=0x80), dict(gamut_mode=2),
+                                 dict(max_dl=float("nan")), dict(max_dl=-0.25)])
 def test_signal_bounds_rejects_invalid(bad):
     args = dict(v_th=50.0, r_novib=0.5, pattern_mask=0x7F, gamut_mode=0)
     args.update(bad)
     with pytest.raises(cvs.CvsError) as ei:
         cvs.signal_bounds(**args)
     assert ei.value.status == binding.CVS_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("max_dl", [None, 0.0, 0.1, float("inf")])
+def test_signal_bounds_accepts_luminance_limits(max_dl):
+    assert cvs.signal_bounds(50, 0.5, max_dl=max_dl) == (51, 24)
 
 
 def _grab(txt, name):

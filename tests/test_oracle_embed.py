@@ -15,7 +15,7 @@ import oracle
 NONE = 0xFFFFFFFF
 
 
-def _enumerate(rgb, radii, angles, vth, rn, mask=0x7F, gamut=0):
+def _enumerate(rgb, radii, angles, vth, rn, mask=0x7F, gamut=0, max_dl=-1.0):
     lab = oracle.target_lab(rgb)
     s, c = oracle.trig_table(angles)
     out = []
@@ -23,7 +23,7 @@ def _enumerate(rgb, radii, angles, vth, rn, mask=0x7F, gamut=0):
         for m in range(len(angles)):
             qp, qm = oracle.pair_codes(lab, r, s[m], c[m])
             pat, op, om = oracle.decide_pair(qp, qm, vth, rn, mask, gamut)
-            if pat:
+            if pat and oracle.passes_dl(lab[0], op, om, max_dl):
                 out.append((float(r), k, m, tuple(op), tuple(om), pat))
     return out
 
@@ -54,6 +54,38 @@ def test_embed_matches_enumeration(rgb, radii, angles, gamut):
     for i, p in enumerate(pats):
         ea, eb, ec = _expected(rgb, int(p), cands)
         assert (tuple(fa[i]), tuple(fb[i]), int(ch[i])) == (ea, eb, ec), (rgb, int(p))
+
+
+@pytest.mark.parametrize("rgb,radii,angles", CASES)
+@pytest.mark.parametrize("gamut", [0, 1])
+def test_embed_with_luminance_limit_matches_enumeration(rgb, radii, angles, gamut):
+    """With a luminance limit the chosen pair is the first passing pair of the
+    pattern whose two colours both keep L* within the limit (the limit's pin,
+    passes_dl, is in test_oracle_dl)."""
+    pats = np.arange(0, 9, dtype=np.uint8)
+    rgbs = np.tile(np.array(rgb, np.uint8), (len(pats), 1))
+    for lim in (0.02, 0.1, 2.0):
+        cands = _enumerate(rgb, radii, angles, 50, 0.5, gamut=gamut, max_dl=lim)
+        fa, fb, ch = oracle.embed(rgbs, pats, radii, angles, 50, 0.5, gamut_mode=gamut, max_dl=lim)
+        for i, p in enumerate(pats):
+            ea, eb, ec = _expected(rgb, int(p), cands)
+            assert (tuple(fa[i]), tuple(fb[i]), int(ch[i])) == (ea, eb, ec), (rgb, int(p), lim)
+
+
+def test_luminance_limit_changes_some_embedding_choices():
+    """The limit is not vacuous on these cases: it removes some choices, keeps
+    others, and a huge limit changes nothing."""
+    changed = kept = 0
+    for rgb, radii, angles in CASES:
+        pats = np.arange(1, 8, dtype=np.uint8)
+        rgbs = np.tile(np.array(rgb, np.uint8), (7, 1))
+        base = oracle.embed(rgbs, pats, radii, angles, 50, 0.5)[2]
+        lim = oracle.embed(rgbs, pats, radii, angles, 50, 0.5, max_dl=0.1)[2]
+        huge = oracle.embed(rgbs, pats, radii, angles, 50, 0.5, max_dl=1e9)[2]
+        assert np.array_equal(huge, base)
+        changed += int((lim != base).sum())
+        kept += int(((lim == base) & (base != NONE)).sum())
+    assert changed > 0 and kept > 0
 
 
 def test_enumeration_cases_embed_something():

@@ -98,8 +98,11 @@ MUTANTS = [
      "if (!pat || !passes_dl(C, lab[0], rec.plus, rec.minus, max_dl)) continue;",
      "if (!pat) continue;"),
     ("embedding: any pattern", C,
-     "if (decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, op, om) != p)",
-     "if (decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, op, om) == 0)"),
+     "if (decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, op, om) != p ||",
+     "if (decide_pair(qp, qm, v_th, r_novib, pattern_mask, gamut_mode, op, om) == 0 ||"),
+    ("embedding ignores the luminance limit", C,
+     "!= p ||\n                        !passes_dl(C, lab[0], op, om, max_dl))",
+     "!= p)"),
     ("embedding: first radius in list order", C, "best_r = radii[k];", "best_r = 0.0;"),
     # constants and tables (Python side)
     ("thresholds rounded to nearest (linear branch)", "oracle/constants.py",
