@@ -82,6 +82,9 @@ def parse_args():
     p.add_argument("--sets-profile", action="store_true",
                    help="only the multi-set pass (the cube under the 12 Table 1 threshold "
                         "sets) and one embedding-table build, for profiling")
+    p.add_argument("--pairs-profile", action="store_true",
+                   help="only the pair lists (the 4096-colour precision set on the 64 x 180 "
+                        "grid, and a slice of the cube on the 128 x 360 grid), for profiling")
     p.add_argument("--cube-step", type=int, default=4, choices=[4, 8, 16],
                    help="channel step of the colour cube (4 = the 262,144-colour workload; "
                         "larger steps give the small cases used for profiling)")
@@ -936,12 +939,47 @@ def run_sets_profile(args):
                                   "gcand_s": (1 << 24) * len(r3) * len(a3) / t_etab / 1e9}}))
 
 
+def run_pairs_profile(args):
+    """The pair lists on their own: every passing pair of the 4096-colour
+    precision set on the 64-radius x 180-angle grid (the bench's pair-list
+    workload), and of every 16th cube colour on the 128 x 360 grid; each once
+    to size the output, then `args.steps` times under CUDA events.  Prints one
+    JSON line (call-to-result times: the calls are synchronous)."""
+    import torch
+    import paper_2507_22901_gb300 as cvs
+    from paper_2507_22901_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    ctx = cvs.Context(0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    cases = {"precision_set_64x180": (W.precision_colors(), W.grid(3)),
+             "cube_every_16th_128x360": (W.color_cube()[::16].copy(), W.grid(2))}
+    for name, (rgb_h, (radii, ang)) in cases.items():
+        rgb = torch.from_numpy(rgb_h).to(dev)
+        recs, offs = ctx.search_colors_pairs(rgb, radii, ang, 50.0, 0.5)
+        cap = int(offs[-1])
+        ev0.record()
+        for _ in range(args.steps):
+            recs, offs = ctx.search_colors_pairs(rgb, radii, ang, 50.0, 0.5, cap=cap)
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        sec = ev0.elapsed_time(ev1) / 1e3 / args.steps
+        cand = len(rgb_h) * len(radii) * len(ang)
+        out[name] = {"colours": len(rgb_h), "candidates": cand, "pairs": cap, "seconds": sec,
+                     "gcand_s": cand / sec / 1e9, "record_gb_s": cap * 16 / sec / 1e9}
+        del recs, rgb
+    ctx.close()
+    print(json.dumps({"pair_lists": out}))
+
+
 def main():
     args = parse_args()
     if args.gather_profile:
         return run_gather_profile(args)
     if args.frames_profile:
         return run_frames_profile(args)
+    if args.pairs_profile:
+        return run_pairs_profile(args)
     if args.sets_profile:
         return run_sets_profile(args)
     world, rank, local = dist_setup()

@@ -963,10 +963,15 @@ cvs_status search_pairs(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n, const cvs
                         cvs_precision prec, cvs_pair* out, int64_t cap, uint32_t target0,
                         int64_t* offs_host, cudaStream_t st) {
     const int K = c->grid.K, H = c->grid.H;
-    // radii per work item: the automatic choice, within the bitmap of a warp
+    // radii per work item: the automatic choice, at least 1024 slots (an item
+    // has a fixed cost in the search and in the emit kernel), and within the
+    // bitmap of a warp
     int kchunk = choose_kchunk(c, n, K, H);
+    if (c->shape.kchunk == 0 && kchunk * H < 1024) kchunk = (1024 + H - 1) / H;
+    if (kchunk > K) kchunk = K;
     const int kmax = kListMaxSlots / H > 0 ? kListMaxSlots / H : 1;
     if (kchunk > kmax) kchunk = kmax;
+    if (kchunk > kListMaxRadii) kchunk = kListMaxRadii;
     const int64_t n_kc = (K + kchunk - 1) / kchunk;
     const int words = (kchunk * H + 31) / 32;
     // targets per batch: within list_batch_items work items and 256 MiB of bitmaps

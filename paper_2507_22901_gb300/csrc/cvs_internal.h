@@ -101,6 +101,7 @@ struct SearchArgs {
 // List mode: most slots (kchunk x H) of one work item, i.e. of a warp's
 // passing-slot bitmap in shared memory.
 constexpr int kListMaxSlots = 8192;
+constexpr int kListMaxRadii = 256;  // and at most this many radii
 
 // The records of a pair list from the search's per-item bitmaps (one batch).
 struct EmitArgs {

@@ -160,11 +160,32 @@ __device__ __forceinline__ int decide64_slot(const SearchArgs& A, const TargetF6
     return (pattern && A.ltab && !dl_ok(A.ltab, A.max_dl, D.L, qp, qm)) ? 0 : pattern;
 }
 
-// Re-decide up to 32 queued slots in FP64, one per lane, and merge them (in
-// list mode every queued slot belongs to the warp's current item, whose
-// bitmap is pb with first radius k0).
+// The warp's current work item in list mode: its bitmap in shared memory (pb,
+// NULL when there is none), target and radii [k0, k1).
+struct ItemRef {
+    uint32_t* pb;
+    int64_t t;
+    int k0, k1;
+};
+
+// A passing slot of an earlier, already stored item (list mode): straight
+// into that item's bitmap and count in global memory.
+__device__ __forceinline__ void mark_stored(const SearchArgs& A, int64_t t, int k, int h) {
+    const int kchunk = A.shape.kchunk;
+    const int n_kc = (A.grid.K + kchunk - 1) / kchunk;
+    const int kc = k / kchunk;
+    const long long g = A.item0 + t * (long long)n_kc + kc;
+    const int s = (k - kc * kchunk) * A.grid.H + h;
+    atomicOr(A.item_bits + g * (long long)A.item_words + (s >> 5), 1u << (s & 31));
+    atomicAdd(A.item_count + g, 1u);
+}
+
+// Re-decide up to 32 queued slots in FP64, one per lane, and merge them.  The
+// queue runs across work items; in list mode a slot of the current item goes
+// to its bitmap in shared memory, a slot of an earlier item to global memory.
 __device__ __noinline__ void flush_queue(const SearchArgs& A, uint32_t* rq_t, uint32_t* rq_kh,
-                                         int n, unsigned long long* n_re, uint32_t* pb, int k0) {
+                                         int n, unsigned long long* n_re, uint32_t* cur_pb,
+                                         int64_t cur_t, int cur_k0, int cur_k1) {
     const unsigned lane = lane_id();
     const int inc = A.grid.sym ? 2 : 1;
     if ((int)lane < n) {
@@ -176,7 +197,10 @@ __device__ __noinline__ void flush_queue(const SearchArgs& A, uint32_t* rq_t, ui
         const int pat = decide64_slot(A, D, k, h, qp, qm);
         if (pat) {
             if (A.list_mode) {
-                mark_pass(pb, k0, A.grid.H, k, h);
+                if (cur_pb && (int64_t)t == cur_t && k >= cur_k0 && k < cur_k1)
+                    mark_pass(cur_pb, cur_k0, A.grid.H, k, h);
+                else
+                    mark_stored(A, (int64_t)t, k, h);
             } else {
                 Acc* ac = A.acc + t;
                 atomicAdd(&ac->count, inc);
@@ -192,7 +216,7 @@ __device__ __noinline__ void flush_queue(const SearchArgs& A, uint32_t* rq_t, ui
 // Queue up to 32 slots for FP64 re-decision; flush when 32 are waiting.
 __device__ __forceinline__ void push_fp64(const SearchArgs& A, bool need64, int64_t t, int k,
                                           int h, uint32_t* rq_t, uint32_t* rq_kh, int& rq_n,
-                                          unsigned long long& n_re, uint32_t* pb, int k0) {
+                                          unsigned long long& n_re, const ItemRef& cur) {
     const unsigned lane = lane_id();
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, need64);
     if (!ball) return;
@@ -204,7 +228,7 @@ __device__ __forceinline__ void push_fp64(const SearchArgs& A, bool need64, int6
     rq_n += __popc(ball);
     __syncwarp();
     if (rq_n >= 32) {
-        flush_queue(A, rq_t, rq_kh, 32, &n_re, pb, k0);
+        flush_queue(A, rq_t, rq_kh, 32, &n_re, cur.pb, cur.t, cur.k0, cur.k1);
         const int rest = rq_n - 32;
         uint32_t mt = 0, mkh = 0;
         if ((int)lane < rest) { mt = rq_t[32 + lane]; mkh = rq_kh[32 + lane]; }
@@ -222,8 +246,7 @@ struct Tally {
     uint32_t pm;
     uint32_t skip;   // slots of this lane skipped as certainly out of gamut
     uint32_t prune;  // slots of the item below the first radius where a pair may pass
-    uint32_t* pb;    // list mode: the item's passing-slot bitmap (shared), else NULL
-    int k0;          // list mode: the item's first radius
+    ItemRef item;    // list mode: the current item (its bitmap in shared memory), else pb NULL
 };
 
 // Decide up to 32 flagged slots of target t, one per lane: exact interval
@@ -250,8 +273,8 @@ __device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S
         pc = certain_from(I, A.hi_min, A.lo_max, A.mask2, A.clip, DL);
         if (DL && pc > 0 && !dl_ok(A.ltab, A.max_dl, A.td[t].L, I.lo, I.lo + 3)) pc = 0;
         if (pc > 0) {
-            if (acc.pb) {
-                mark_pass(acc.pb, acc.k0, A.grid.H, k, h);
+            if (acc.item.pb) {
+                mark_pass(acc.item.pb, acc.item.k0, A.grid.H, k, h);
             } else {
                 acc.cnt += inc;
                 acc.rmax = fmaxf(acc.rmax, r);
@@ -260,7 +283,7 @@ __device__ __forceinline__ void drain_flagged(const SearchArgs& A, const Smem& S
         }
     }
     __syncwarp();
-    push_fp64(A, (int)lane < n && pc < 0, t, k, h, rq_t, rq_kh, rq_n, n_re, acc.pb, acc.k0);
+    push_fp64(A, (int)lane < n && pc < 0, t, k, h, rq_t, rq_kh, rq_n, n_re, acc.item);
 }
 
 
@@ -314,7 +337,7 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
                 acc.rmax = fmaxf(acc.rmax, r);
                 acc.pm |= 1u << pattern;  // bit p for pattern p; shifted down at the end
             } else {
-                mark_pass(acc.pb, acc.k0, H, k, h);
+                mark_pass(acc.item.pb, acc.item.k0, H, k, h);
             }
         }
         return flag;
@@ -323,7 +346,7 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
         const int pattern = (!CHECK || active) ? decide64_slot(A, D, k, h, qp, qm) : 0;
         if (pattern) {
             if (LIST) {
-                mark_pass(acc.pb, acc.k0, H, k, h);
+                mark_pass(acc.item.pb, acc.item.k0, H, k, h);
             } else {
                 acc.cnt += inc;
                 acc.rmax = fmaxf(acc.rmax, r);
@@ -431,7 +454,7 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
     if (PREC != CVS_PREC_FP32_RECHECK || DL) D = A.td[t];  // the limit needs the target's L*
     const PairsT P = make_pairs(T);
     const PairsC PC = make_pairs(C);
-    Tally acc{0, -1.0f, 0u, 0u, 0u, pb, k0};
+    Tally acc{0, -1.0f, 0u, 0u, 0u, ItemRef{pb, t, k0, k1}};
     int pq_n = 0;  // flagged slots waiting for drain_flagged (warp-uniform)
     // slot i of the item is (k0 + i / H, i % H); lanes start at i = lane and
     // step by 32 = q32 H + r32, so one conditional wrap keeps h in [0, H)
@@ -525,7 +548,7 @@ constexpr uint32_t kSlowRadius = 0xFFFFFFFFu;
 // kListMaxSlots slots), and of the bitmap plus its nwords + 1 prefix counts in
 // the emit kernel.
 constexpr int kListWords = kListMaxSlots / 32;
-constexpr int kListWarpWords = 2 * kListWords + 2;
+constexpr int kListWarpWords = 2 * kListWords + 2 + 2 * kListMaxRadii;
 
 __device__ __forceinline__ int warp_exclusive_sum(int v, int& total) {
     const unsigned lane = lane_id();
@@ -676,7 +699,7 @@ __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S
     if (DL) D = A.td[t];
     const PairsT P = make_pairs(A.tf[t]);
     const PairsC PC = make_pairs(C);
-    Tally acc{0, -1.0f, 0u, 0u, 0u, pb, k0};
+    Tally acc{0, -1.0f, 0u, 0u, 0u, ItemRef{pb, t, k0, k1}};
     int pq_n = 0;
     uint32_t* pos = al + kArcEntries;
     const uint2* ranges = A.arc_ranges + t * K;
@@ -964,15 +987,12 @@ __global__ void __launch_bounds__(CVS_SEARCH_MAX_THREADS,
             run_item<PREC, true, CLIP, LIST, DL>(A, S, t, k0, k1, C, pq, fb, pb, rq_t, rq_kh, rq_n,
                                                  n_flag, n_re, n_skip, n_prune);
         }
-        if (LIST) {  // every slot of the item decided: its bitmap and count
-            if (PREC == CVS_PREC_FP32_RECHECK && rq_n > 0) {
-                flush_queue(A, rq_t, rq_kh, rq_n, &n_re, pb, k0);
-                rq_n = 0;
-            }
-            store_item(A, A.item0 + (long long)item, ((k1 - k0) * H + 31) >> 5, pb);
-        }
+        // list mode: the item's bitmap and count (slots still queued for FP64
+        // reach them in global memory when the queue is flushed)
+        if (LIST) store_item(A, A.item0 + (long long)item, ((k1 - k0) * H + 31) >> 5, pb);
     }
-    if (PREC == CVS_PREC_FP32_RECHECK && rq_n > 0) flush_queue(A, rq_t, rq_kh, rq_n, &n_re, nullptr, 0);
+    if (PREC == CVS_PREC_FP32_RECHECK && rq_n > 0)
+        flush_queue(A, rq_t, rq_kh, rq_n, &n_re, nullptr, -1, 0, 0);
     // statistics
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -1052,19 +1072,21 @@ struct RecQueue {
     unsigned long long* pos;
     uint32_t* ck;
     uint32_t* kh;
+    uint32_t* t;  // the target (index within the batch)
+    int n;        // queued entries (warp-uniform); the queue runs across items
 };
 constexpr int kRecQueue = 64;
 
-__device__ __noinline__ void flush_records(const EmitArgs& A, const TargetF64& D, uint32_t target,
-                                           const RecQueue& Q, int n) {
+__device__ __noinline__ void flush_records(const EmitArgs& A, const RecQueue& Q, int n) {
     const unsigned lane = lane_id();
     if ((int)lane < n) {
-        const uint32_t kh = Q.kh[lane];
+        const uint32_t kh = Q.kh[lane], t = Q.t[lane];
         const int k = (int)(kh & 0xFFFFu), h = (int)(kh >> 16);
+        const TargetF64 D = A.td[t];
         int qp[3], qm[3];
         pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + k), __ldg(A.grid.s64 + h),
                      __ldg(A.grid.c64 + h), A.qkey, qp, qm);
-        store_records(A, target, k, h, qp, qm, 1u, Q.pos[lane], Q.ck[lane]);
+        store_records(A, A.target_id + t, k, h, qp, qm, 1u, Q.pos[lane], Q.ck[lane]);
     }
     __syncwarp();
 }
@@ -1170,14 +1192,12 @@ __device__ __forceinline__ void emit_records(const EmitArgs& A, const float2* r2
                                              const float4* sc4s, const ChainF32& C, int64_t t,
                                              int k0, int nwords, int P, long long base,
                                              const uint32_t* pb, const uint32_t* pre,
-                                             const RecQueue& Q) {
+                                             const uint32_t* rad, RecQueue& Q) {
     const unsigned lane = lane_id();
     const int H = A.grid.H, sym = A.grid.sym;
     TargetF32 T{};
     if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
-    const TargetF64 D = A.td[t];
     const uint32_t target = A.target_id + (uint32_t)t;
-    int q_n = 0;  // queued records (warp-uniform)
     for (int r0 = 0; r0 < P; r0 += 32) {
         const int R = r0 + (int)lane;
         bool need64 = false;
@@ -1194,8 +1214,8 @@ __device__ __forceinline__ void emit_records(const EmitArgs& A, const float2* r2
             const int dk = s / H;
             h = s - dk * H;
             k = k0 + dk;
-            const int before = passing_before(pb, pre, dk * H);
-            ck = (unsigned)(passing_before(pb, pre, dk * H + H) - before);
+            const int before = (int)rad[2 * dk];  // passing slots of earlier radii, this one's
+            ck = rad[2 * dk + 1];
             pos = (unsigned long long)base + ((unsigned long long)before << sym) +
                   (unsigned)(R - before);
             if (PREC == CVS_PREC_FP32_RECHECK) {
@@ -1208,34 +1228,36 @@ __device__ __forceinline__ void emit_records(const EmitArgs& A, const float2* r2
         }
         const unsigned ball = __ballot_sync(0xFFFFFFFFu, need64);
         if (need64) {
-            const int slot = q_n + __popc(ball & ((1u << lane) - 1u));
+            const int slot = Q.n + __popc(ball & ((1u << lane) - 1u));
             Q.pos[slot] = pos;
             Q.ck[slot] = ck;
             Q.kh[slot] = (uint32_t)k | (uint32_t)h << 16;
+            Q.t[slot] = (uint32_t)t;
         }
-        q_n += __popc(ball);
+        Q.n += __popc(ball);
         __syncwarp();
-        if (q_n >= 32) {
-            flush_records(A, D, target, Q, 32);
-            const int rest = q_n - 32;  // below kRecQueue - 32
+        if (Q.n >= 32) {
+            flush_records(A, Q, 32);
+            const int rest = Q.n - 32;  // below kRecQueue - 32
             unsigned long long mp = 0;
-            uint32_t mc = 0, mk = 0;
+            uint32_t mc = 0, mk = 0, mt = 0;
             if ((int)lane < rest) {
                 mp = Q.pos[32 + lane];
                 mc = Q.ck[32 + lane];
                 mk = Q.kh[32 + lane];
+                mt = Q.t[32 + lane];
             }
             __syncwarp();
             if ((int)lane < rest) {
                 Q.pos[lane] = mp;
                 Q.ck[lane] = mc;
                 Q.kh[lane] = mk;
+                Q.t[lane] = mt;
             }
             __syncwarp();
-            q_n = rest;
+            Q.n = rest;
         }
     }
-    if (q_n > 0) flush_records(A, D, target, Q, q_n);
 }
 
 // One warp per work item (grid-stride): stage the item's bitmap in shared
@@ -1248,14 +1270,17 @@ __global__ void __launch_bounds__(kSearchBlock) k_emit_pairs(const EmitArgs A) {
     float4* sc4s = reinterpret_cast<float4*>(smem + ((K * 8 + 15) & ~15));
     unsigned char* per_warp = smem + ((K * 8 + 15) & ~15) + H * 16;
     const int warp = threadIdx.x >> 5;
-    RecQueue Q;  // per warp: positions (8 B), partner offsets, slots (4 B each)
+    RecQueue Q;  // per warp: positions (8 B), partner offsets, slots, targets (4 B each)
     Q.pos = reinterpret_cast<unsigned long long*>(per_warp) + warp * kRecQueue;
     Q.ck = reinterpret_cast<uint32_t*>(per_warp + (kSearchBlock / 32) * kRecQueue * 8) +
-           warp * 2 * kRecQueue;
+           warp * 3 * kRecQueue;
     Q.kh = Q.ck + kRecQueue;
-    uint32_t* pb = reinterpret_cast<uint32_t*>(per_warp + (kSearchBlock / 32) * kRecQueue * 16) +
+    Q.t = Q.kh + kRecQueue;
+    Q.n = 0;
+    uint32_t* pb = reinterpret_cast<uint32_t*>(per_warp + (kSearchBlock / 32) * kRecQueue * 20) +
                    warp * kListWarpWords;
     uint32_t* pre = pb + kListWords;
+    uint32_t* rad = pre + kListWords + 2;  // per radius of the item: (passing before, count)
     for (int i = threadIdx.x; i < K; i += blockDim.x) r2s[i] = dup(A.grid.r32[i]);
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
         const float2 sc = A.grid.sc32[i];
@@ -1291,14 +1316,21 @@ __global__ void __launch_bounds__(kSearchBlock) k_emit_pairs(const EmitArgs A) {
         }
         if (lane == 0) pre[nwords] = (uint32_t)run;
         __syncwarp();
+        for (int dk = (int)lane; dk < k1 - k0; dk += 32) {  // per radius: passing before, count
+            const int b0 = passing_before(pb, pre, dk * H);
+            rad[2 * dk] = (uint32_t)b0;
+            rad[2 * dk + 1] = (uint32_t)(passing_before(pb, pre, dk * H + H) - b0);
+        }
+        __syncwarp();
         const long long base = A.tile_base[g / kScanTile] + A.item_base[g];
         if (lane == 0) {
             if (kc == 0) A.offs[t] = base;
             if (kc == n_kc - 1) A.offs[t + 1] = base + ((long long)run << A.grid.sym);
         }
-        emit_records<PREC>(A, r2s, sc4s, C, t, k0, nwords, run, base, pb, pre, Q);
+        emit_records<PREC>(A, r2s, sc4s, C, t, k0, nwords, run, base, pb, pre, rad, Q);
         __syncwarp();
     }
+    if (Q.n > 0) flush_records(A, Q, Q.n);
 }
 
 // ------------------------------------------------------------ finalize
@@ -1660,7 +1692,7 @@ int emit_smem_bytes(const GridDev& g) {
     // tables, then per warp the record queue (16 B an entry) and the bitmap
     // with its prefix counts
     return ((g.K * 8 + 15) & ~15) + g.H * 16 +
-           (kSearchBlock / 32) * (kRecQueue * 16 + kListWarpWords * 4);
+           (kSearchBlock / 32) * (kRecQueue * 20 + kListWarpWords * 4);
 }
 
 cudaError_t launch_emit_pairs(const EmitArgs& a, int num_sms, cudaStream_t st) {

@@ -129,7 +129,7 @@ __device__ __forceinline__ void flush_counts(MultiTally& m, int NT) {
 
 // Exact decision of one flagged slot against every set; passes go straight to
 // the accumulators (rare).
-template <int PREC, bool FAST, bool CLIP, bool ALLMASK>
+template <int PREC, bool FAST, bool CLIP, bool ALLMASK, bool DL>
 __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* r2s,
                                               const float4* sc4s, const uint32_t* ts,
                                               const TargetF32& T, const ChainF32& C,
@@ -162,7 +162,7 @@ __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* 
     if (!open) ok = pass_sets<ALLMASK>(e, true, setmask & ~cinv, A.pmask_sets, hR, hG, hB);
     // some set's decision depends on a code the bounds leave open, or (under a
     // luminance limit) a set passes and the limit needs the exact codes: FP64
-    if (open || (A.ltab && ok)) {
+    if (open || (DL && ok)) {
         int qp[3], qm[3];
         pair_codes64(D.L, D.a, D.b, __ldg(A.grid.r64 + __ldg(A.order + kk)), __ldg(A.grid.s64 + h),
                      __ldg(A.grid.c64 + h), A.qkey, qp, qm);
@@ -177,7 +177,7 @@ __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* 
             e[c] = ts[min(abs(qp[c] - qm[c]), 256)];
         }
         ok = pass_sets<ALLMASK>(e, in_range, setmask, A.pmask_sets, hR, hG, hB);
-        if (A.ltab && ok) ok &= dl_sets(A, D.L, qp, qm);
+        if (DL && ok) ok &= dl_sets(A, D.L, qp, qm);
         ++n_re;
     }
     if (!ok) return;
@@ -194,7 +194,7 @@ __device__ __forceinline__ void multi_flagged(const MultiArgs& A, const float2* 
 }
 
 // Decide the first n (<= 32) queued flagged slots (rank | h << 16), one per lane.
-template <int PREC, bool FAST, bool CLIP, bool ALLMASK>
+template <int PREC, bool FAST, bool CLIP, bool ALLMASK, bool DL>
 __device__ __forceinline__ void drain_multi(const MultiArgs& A, const float2* r2s,
                                             const float4* sc4s, const uint32_t* ts,
                                             const TargetF32& T, const ChainF32& C,
@@ -203,23 +203,25 @@ __device__ __forceinline__ void drain_multi(const MultiArgs& A, const float2* r2
     const unsigned lane = lane_id();
     if ((int)lane < n) {
         const uint32_t v = pq[lane];
-        multi_flagged<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t, (int)(v & 0xFFFFu),
+        multi_flagged<PREC, FAST, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t, (int)(v & 0xFFFFu),
                                                  (int)(v >> 16), setmask, n_re);
     }
 }
 
 // Iterations [it, end) of a work item (lanes at slot (rank kk, angle h),
-// radii decreasing), one encode variant: LINSEG = false where every radius of
-// the iterations stays above the sRGB linear segment.  Flagged slots set
-// their bits in `bits` (bit advances per iteration).
-template <int PREC, bool FAST, bool CLIP, bool ALLMASK, bool LINSEG>
+// radii decreasing); from it_pow on, every radius stays above the sRGB linear
+// segment and the encode skips its select.  (Splitting the range at it_pow
+// into two loops of one variant each, as k_search does, measured slower
+// here: 26.5 against 23.7 ms for the 12 Table 1 sets on the cube.)  Flagged
+// slots set their bits in `bits` (bit advances per iteration).
+template <int PREC, bool FAST, bool CLIP, bool ALLMASK, bool DL>
 __device__ __forceinline__ void multi_iters(const MultiArgs& A, const float2* r2s,
                                             const uint32_t* ts, const float4* sc4s,
                                             const PairsT& P, const PairsC& PC,
                                             const TargetF64& D, MultiTally& m, float* rmx,
                                             uint32_t setmask, int nw, int nslots, int kk1,
                                             int& it, int end, int& kk, int& h, uint32_t& bits,
-                                            uint32_t& bit, uint32_t& seen) {
+                                            uint32_t& bit, uint32_t& seen, int it_pow) {
     const unsigned lane = lane_id();
     const int H = A.grid.H;
     const int q32 = 32 / H, r32 = 32 - q32 * H;
@@ -239,7 +241,9 @@ __device__ __forceinline__ void multi_iters(const MultiArgs& A, const float2* r2
             skip = !CLIP && __all_sync(0xFFFFFFFFu, !active || surely_out32(lin));
             if (!skip) {
                 int yp[3], ym[3];
-                bool flag = encode32<LINSEG>(lin, A.half_w, yp, ym, nullptr);
+                bool flag;
+                if (it >= it_pow) flag = encode32<false>(lin, A.half_w, yp, ym, nullptr);
+                else flag = encode32<true>(lin, A.half_w, yp, ym, nullptr);
                 flag = flag && active;
                 if (flag) bits |= bit;
                 uint32_t e[3];
@@ -259,7 +263,7 @@ __device__ __forceinline__ void multi_iters(const MultiArgs& A, const float2* r2
                 }
                 if (active && !flag) {
                     ok = pass_sets<ALLMASK>(e, o <= 255u, setmask, A.pmask_sets, hR, hG, hB);
-                    if (A.ltab && ok) {  // the luminance limits, per set
+                    if (DL && ok) {  // the luminance limits, per set
                         ok &= dl_sets(A, D.L, qa, qb);
                         hR &= ok;
                         hG &= ok;
@@ -284,7 +288,7 @@ __device__ __forceinline__ void multi_iters(const MultiArgs& A, const float2* r2
                 e[c] = ts[min(abs(qp[c] - qm[c]), 256)];
             }
             ok = pass_sets<ALLMASK>(e, in_range, setmask, A.pmask_sets, hR, hG, hB);
-            if (A.ltab && ok) {
+            if (DL && ok) {
                 ok &= dl_sets(A, D.L, qp, qm);
                 hR &= ok;
                 hG &= ok;
@@ -314,7 +318,7 @@ __device__ __forceinline__ void multi_iters(const MultiArgs& A, const float2* r2
 }
 
 // One work item: target t, radius ranks [kk0, kk1), taken in decreasing order.
-template <int PREC, bool FAST, bool CLIP, bool ALLMASK>
+template <int PREC, bool FAST, bool CLIP, bool ALLMASK, bool DL>
 __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s,
                                            const float4* sc4s, const uint32_t* ts, uint32_t* fb,
                                            float* rmx, uint32_t* pq, const TargetF32& T,
@@ -356,20 +360,9 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
             uint32_t bits = 0;
             const int wend = min(seg1, it + 32);
             uint32_t bit = 1u;
-            if (PREC == CVS_PREC_FP32_RECHECK && FAST && it < it_pow) {
-                // iterations that may reach the sRGB linear segment, then the rest
-                multi_iters<PREC, FAST, CLIP, ALLMASK, true>(A, r2s, ts, sc4s, P, PC, D, m, rmx,
-                                                             setmask, nw, nslots, kk1, it,
-                                                             min(wend, it_pow), kk, h, bits, bit,
-                                                             seen);
-                multi_iters<PREC, FAST, CLIP, ALLMASK, false>(A, r2s, ts, sc4s, P, PC, D, m, rmx,
-                                                              setmask, nw, nslots, kk1, it, wend,
-                                                              kk, h, bits, bit, seen);
-            } else {
-                multi_iters<PREC, FAST, CLIP, ALLMASK, !(PREC == CVS_PREC_FP32_RECHECK && FAST)>(
-                    A, r2s, ts, sc4s, P, PC, D, m, rmx, setmask, nw, nslots, kk1, it, wend, kk, h,
-                    bits, bit, seen);
-            }
+            multi_iters<PREC, FAST, CLIP, ALLMASK, DL>(A, r2s, ts, sc4s, P, PC, D, m, rmx, setmask,
+                                                       nw, nslots, kk1, it, wend, kk, h, bits, bit,
+                                                       seen, it_pow);
             if (PREC == CVS_PREC_FP32_RECHECK) fb[w * 32 + lane] = bits;
         }
         flush_counts(m, NT);
@@ -394,7 +387,7 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
                     pq_n += __popc(ball);  // below kMultiQueue: at most 31 + 32
                     __syncwarp();
                     if (pq_n >= 32) {
-                        drain_multi<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t, pq,
+                        drain_multi<PREC, FAST, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t, pq,
                                                                32, setmask, n_re);
                         const int rest = pq_n - 32;
                         const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
@@ -408,7 +401,7 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
         }
     }
     if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0)
-        drain_multi<PREC, FAST, CLIP, ALLMASK>(A, r2s, sc4s, ts, T, C, D, t, pq, pq_n, setmask,
+        drain_multi<PREC, FAST, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t, pq, pq_n, setmask,
                                                n_re);
     __syncwarp();
     // item totals: lane s publishes set s
@@ -432,7 +425,7 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
     }
 }
 
-template <int PREC, bool CLIP, bool ALLMASK>
+template <int PREC, bool CLIP, bool ALLMASK, bool DL>
 __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = A.grid.K, H = A.grid.H;
@@ -475,10 +468,10 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
         TargetF32 T{};
         if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
         if (PREC == CVS_PREC_FP32_RECHECK && (T.flags & 1u))
-            multi_item<PREC, true, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t, k0,
+            multi_item<PREC, true, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t, k0,
                                                   k1, n_flag, n_re);
         else
-            multi_item<PREC, false, CLIP, ALLMASK>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t, k0,
+            multi_item<PREC, false, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t, k0,
                                                    k1, n_flag, n_re);
     }
 #pragma unroll
@@ -508,28 +501,35 @@ int multi_smem_bytes(const GridDev& g, int block) {
            (block / 32) * (kMultiWords * 32 + kMaxThresholdSets * 32 + kMultiQueue) * 4;
 }
 
-template <int PREC, bool CLIP, bool ALLMASK>
+template <int PREC, bool CLIP, bool ALLMASK, bool DL>
 cudaError_t launch_multi_t(const MultiArgs& a, cudaStream_t st) {
     const int block = kSearchBlock;
     const int smem = multi_smem_bytes(a.grid, block);
-    const void* fn = (const void*)k_search_multi<PREC, CLIP, ALLMASK>;
+    const void* fn = (const void*)k_search_multi<PREC, CLIP, ALLMASK, DL>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    k_search_multi<PREC, CLIP, ALLMASK><<<a.num_sms * per_sm, block, smem, st>>>(a);
+    k_search_multi<PREC, CLIP, ALLMASK, DL><<<a.num_sms * per_sm, block, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+template <int PREC, bool DL>
+cudaError_t launch_multi_d(const MultiArgs& a, cudaStream_t st) {
+    if (a.clip)
+        return a.all_patterns ? launch_multi_t<PREC, true, true, DL>(a, st)
+                              : launch_multi_t<PREC, true, false, DL>(a, st);
+    return a.all_patterns ? launch_multi_t<PREC, false, true, DL>(a, st)
+                          : launch_multi_t<PREC, false, false, DL>(a, st);
+}
+
+// DL: some set carries a luminance limit (a separate instantiation, so that
+// the sets without one run the loop without it)
 template <int PREC>
 cudaError_t launch_multi_p(const MultiArgs& a, cudaStream_t st) {
-    if (a.clip)
-        return a.all_patterns ? launch_multi_t<PREC, true, true>(a, st)
-                              : launch_multi_t<PREC, true, false>(a, st);
-    return a.all_patterns ? launch_multi_t<PREC, false, true>(a, st)
-                          : launch_multi_t<PREC, false, false>(a, st);
+    return a.ltab ? launch_multi_d<PREC, true>(a, st) : launch_multi_d<PREC, false>(a, st);
 }
 
 }  // namespace
