@@ -39,13 +39,16 @@ ALG_ISSUES_PER_CAND = 59.5
 # certainly out of range): displacement 1 + cube expansion 6 + linear RGB 6 +
 # range test 6 issues
 ALG_ISSUES_PER_SKIPPED = 19.0
+# A coarser count per fully evaluated candidate, for comparison: 38 FMA-pipe
+# + 6 MUFU + 12 integer operations.
+ALG_ISSUES_COARSE = 56.0
 LANES_PER_SM_CLK = 128
 # DRAM bytes of one FP32 search launch on this workload, from one ncu capture
 # of the search kernel on 32,768 cube colours (dram__bytes_read.sum +
 # dram__bytes_write.sum), scaled by 8 to the cube's 262,144 colours since the
 # traffic is proportional to the colours.  Valid only for the kernel source it
 # was taken from (its hash below); otherwise the roofline reports null.
-TRAFFIC_CAPTURE = {"source_sha256_16": "12deeb635e3014a7", "bytes_per_launch": 8 * 36.69632e6}
+TRAFFIC_CAPTURE = {"source_sha256_16": "597018404689dc6c", "bytes_per_launch": 8 * 36.917024e6}
 
 
 def kernel_source_hash() -> str:
@@ -82,6 +85,9 @@ def parse_args():
     p.add_argument("--sets-profile", action="store_true",
                    help="only the multi-set pass (the cube under the 12 Table 1 threshold "
                         "sets) and one embedding-table build, for profiling")
+    p.add_argument("--no-frames", action="store_true",
+                   help="skip the 4K-frame measurement (images_4k_per_s is then null), for "
+                        "profiling runs")
     p.add_argument("--pairs-profile", action="store_true",
                    help="only the pair lists (the 4096-colour precision set on the 64 x 180 "
                         "grid, and a slice of the cube on the 128 x 360 grid), for profiling")
@@ -246,10 +252,10 @@ def table2_marks():
 
 def measure_4k_frames(ctx, torch, device, W, n_frames=4):
     """Four 3840x2160 frames rendered by the 48-image recipe (seed 31), per
-    pixel 64 radii x 180 angles: timed as one batch through the per-pixel
-    search, through the per-batch colour de-duplication, and through the
-    capacity table (built once, its build timed apart).  The maps of the three
-    are compared."""
+    pixel 64 radii x 180 angles: timed as one batch through cvs_search_images
+    with its defaults, with every pixel searched (option dedup 0), with one
+    search per distinct colour (dedup 1), and through the capacity table (built
+    once, its build timed apart).  The maps of the four are compared."""
     r3, a3 = W.grid(3)
     params = W.image_params(n_frames, seed=31, sizes=[(3840, 2160)] * n_frames)
     frames = [W.render_image_torch(w, h, t, ns, device=device) for w, h, t, ns in params]
@@ -268,15 +274,18 @@ def measure_4k_frames(ctx, torch, device, W, n_frames=4):
         torch.cuda.synchronize(device)
         return ev0.elapsed_time(ev1) / 1e3 / reps, r
 
-    maps = ctx.search_images(frames, r3, a3, 50.0, 0.5)
-    sec_direct, _ = timed(lambda: ctx.search_images(frames, r3, a3, 50.0, 0.5, maps=maps))
-    ctx.set_option("dedup", 1)
+    ctx.set_option("dedup", 0)  # every pixel searched
     try:
+        maps = ctx.search_images(frames, r3, a3, 50.0, 0.5)
+        sec_direct, _ = timed(lambda: ctx.search_images(frames, r3, a3, 50.0, 0.5, maps=maps))
+        ctx.set_option("dedup", 1)
         maps_d = ctx.search_images(frames, r3, a3, 50.0, 0.5)
         sec_dedup, _ = timed(lambda: ctx.search_images(frames, r3, a3, 50.0, 0.5, maps=maps_d))
         distinct = ctx.stats()["targets"]
     finally:
-        ctx.set_option("dedup", 0)
+        ctx.set_option("dedup", 2)  # the default: automatic
+    maps_a = ctx.search_images(frames, r3, a3, 50.0, 0.5)
+    sec_default, _ = timed(lambda: ctx.search_images(frames, r3, a3, 50.0, 0.5, maps=maps_a))
     ev0.record()
     lut = ctx.build_lut(r3, a3, 50.0, 0.5)
     ev1.record()
@@ -285,10 +294,14 @@ def measure_4k_frames(ctx, torch, device, W, n_frames=4):
     maps_t = lut.lookup_images(frames)
     sec_table, _ = timed(lambda: lut.lookup_images(frames, maps=maps_t), reps=20)
     lut.close()
-    same = all(torch.equal(a, b) and torch.equal(a, c)
-               for m, md, mt in zip(maps, maps_d, maps_t) for a, b, c in zip(m, md, mt))
+    same = all(torch.equal(a, b) and torch.equal(a, c) and torch.equal(a, d)
+               for m, md, mt, ma in zip(maps, maps_d, maps_t, maps_a)
+               for a, b, c, d in zip(m, md, mt, ma))
     cand = n_frames * CAND_PER_4K_FRAME
     return {"frames": n_frames, "size": "3840x2160", "grid": "64 radii x 180 angles",
+            "default_s": sec_default, "default_frames_per_s": n_frames / sec_default,
+            "default_path": "cvs_search_images with its default options (per-batch "
+                            "colour de-duplication for batches of 2^20 pixels or more)",
             "direct_s": sec_direct, "direct_frames_per_s": n_frames / sec_direct,
             "direct_gcand_s": cand / sec_direct / 1e9,
             "dedup_s": sec_dedup, "dedup_frames_per_s": n_frames / sec_dedup,
@@ -345,6 +358,7 @@ def run_extras(ctx, torch, device, W, cvs):
     # one pass over the 48 full-size synthetic images
     r3, a3 = W.grid(3)
     px = sum(im.shape[0] * im.shape[1] for im in imgs)
+    ctx.set_option("dedup", 0)  # every pixel searched
     maps = ctx.search_images(imgs, r3, a3, 50.0, 0.5)
     ctx.synchronize()
     torch.cuda.synchronize(device)
@@ -369,7 +383,7 @@ def run_extras(ctx, torch, device, W, cvs):
     torch.cuda.synchronize(device)
     sec_d = t0.elapsed_time(t1) / 1e3
     n_distinct = ctx.stats()["targets"]
-    ctx.set_option("dedup", 0)
+    ctx.set_option("dedup", 2)
     same_d = all(torch.equal(a, b) for m, m2 in zip(maps, maps_d) for a, b in zip(m, m2))
     del maps_d
     out["images_dedup"] = {"seconds": sec_d, "distinct_colours": n_distinct,
@@ -719,9 +733,11 @@ def run_ours(args, world, rank, local):
     e2e_match = bool(np.array_equal(h_out[1], res32[1].cpu().numpy()))
 
     # ---- 4K frames: a batch of 3840x2160 frames per GPU, measured
-    frames4k = measure_4k_frames(ctx, torch, device, W)
-    sec4k = max_over_ranks(frames4k["direct_s"], world, device)
-    frames4k["images_4k_per_s_all_gpus"] = world * frames4k["frames"] / sec4k
+    frames4k = {"images_4k_per_s_all_gpus": None}
+    if not args.no_frames:
+        frames4k = measure_4k_frames(ctx, torch, device, W)
+        sec4k = max_over_ranks(frames4k["default_s"], world, device)
+        frames4k["images_4k_per_s_all_gpus"] = world * frames4k["frames"] / sec4k
 
     # ---- extras: precision study (4096-colour set) and one pass over the images
     extras = {}
@@ -739,6 +755,8 @@ def run_ours(args, world, rank, local):
     prune_c = pruned / args.steps  # rejected by the per-radius bound: no per-candidate work
     alg_ops = ALG_ISSUES_PER_CAND * (cand - skip_c - prune_c) + ALG_ISSUES_PER_SKIPPED * skip_c
     achieved = alg_ops / kern_avg_s / 1e12
+    alg_ops56 = ALG_ISSUES_COARSE * (cand - skip_c - prune_c) + ALG_ISSUES_PER_SKIPPED * skip_c
+    with_pass_s = kern_avg_s + ranges_avg_ms / 1e3
     num_sms = torch.cuda.get_device_properties(device).multi_processor_count
     peak = num_sms * LANES_PER_SM_CLK * f_mhz * 1e6 / 1e12
 
@@ -771,6 +789,9 @@ def run_ours(args, world, rank, local):
                                  and args.cube_step == 4 else None),
                      "peak_basis": f"{num_sms} SMs x {LANES_PER_SM_CLK} lanes x "
                                    f"{f_mhz:.0f} MHz median SM clock under load",
+                     "frac_incl_ranges_pass": alg_ops / with_pass_s / 1e12 / peak,
+                     "frac_56_issue_model": alg_ops56 / kern_avg_s / 1e12 / peak,
+                     "frac_56_issue_model_incl_ranges_pass": alg_ops56 / with_pass_s / 1e12 / peak,
                      "ops_per_candidate": ALG_ISSUES_PER_CAND,
                      "ops_per_skipped_candidate": ALG_ISSUES_PER_SKIPPED,
                      "skipped_fraction": skip_c / cand,
@@ -876,6 +897,7 @@ def run_frames_profile(args):
         return ev0.elapsed_time(ev1) / 1e3 / args.steps
 
     out = {"workload": "one synthetic 1920x1080 frame (seed 21), 64 radii x 180 angles"}
+    ctx.set_option("dedup", 0)  # every pixel searched
     maps = ctx.search_images([img], r3, a3, 50.0, 0.5)
     t = timed(lambda: ctx.search_images([img], r3, a3, 50.0, 0.5, maps=maps))
     st = ctx.stats()
@@ -887,7 +909,7 @@ def run_frames_profile(args):
     maps_d = ctx.search_images([img], r3, a3, 50.0, 0.5)
     t = timed(lambda: ctx.search_images([img], r3, a3, 50.0, 0.5, maps=maps_d))
     n_distinct = ctx.stats()["targets"]
-    ctx.set_option("dedup", 0)
+    ctx.set_option("dedup", 2)
     out["search_images_dedup"] = {
         "seconds": t, "distinct_colours": n_distinct,
         "maps_identical": all(torch.equal(a, b) for a, b in zip(maps[0], maps_d[0]))}

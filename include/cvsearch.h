@@ -526,13 +526,19 @@ cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const c
  *                   thresholds, precision, shape) is seen, and replay the graph
  *                   on later calls with the same signature (up to 8 graphs are
  *                   kept per context).  Default 0.
- *   "dedup"         1: cvs_search_images searches each distinct colour of the
+ *   "dedup"         cvs_search_images searching each distinct colour of the
  *                   batch once (a pixel's maps depend only on its colour) and
- *                   gathers the maps per pixel; the maps are identical.  The
+ *                   gathering the maps per pixel; the maps are identical.  The
  *                   call then synchronises `stream` once (to size the search)
  *                   and is not captured in a CUDA graph; the context keeps
- *                   about 130 MB of tables for it, allocated when the option
- *                   is turned on.  Default 0.
+ *                   about 130 MB of tables for it.  0: never; 1: always (the
+ *                   tables are allocated when the option is set); 2 (default):
+ *                   for batches of at least 2^20 pixels while option "graphs"
+ *                   is 0, when the tables and the search of the distinct
+ *                   colours fit the context's memory budget (else the batch
+ *                   is searched per pixel and the tables are freed);
+ *                   cvs_reserve with max_targets >= 2^20 allocates them if
+ *                   they fit.
  *   "angle_ranges"  the FP32 search in gamut-reject mode on a folded, evenly
  *                   spaced angle grid can first turn, per target and radius,
  *                   bounds on the pair's linear RGB (a sinusoid in the angle

@@ -136,8 +136,9 @@ struct cvs_ctx {
     unsigned long long* h_arc_probe = nullptr;
     std::map<std::array<int64_t, 6>, bool> arc_choice;
     int search_kind = 0;  // kind of the current call, part of the choice's key
-    // per-batch colour de-duplication of the image search (option "dedup")
-    int dedup = 0;
+    // per-batch colour de-duplication of the image search (option "dedup":
+    // 0 never, 1 always, 2 automatic)
+    int dedup = 2;
     uint8_t* d_present = nullptr;   // 2^24 bytes
     int32_t* d_index = nullptr;     // 2^24 colour -> distinct-colour index
     uint8_t* d_unique = nullptr;    // 3 x 2^24 distinct colours
@@ -376,17 +377,35 @@ void drop_graphs(cvs_ctx* c);
 cvs_status ensure_arc_scratch(cvs_ctx* c, int64_t n);
 
 // Tables of the per-batch colour de-duplication (option "dedup"): presence
-// map and index of all 2^24 colours, the distinct colours, scan sums.
+// map and index of all 2^24 colours, the distinct colours, scan sums (each
+// allocated if missing, so a refused allocation can be retried).
 cvs_status ensure_dedup(cvs_ctx* c) {
-    if (c->d_present) return CVS_OK;
     constexpr size_t kColours = size_t(1) << 24;
-    CVS_TRY(ctx_alloc(c, &c->d_present, kColours));
-    CVS_TRY(ctx_alloc(c, &c->d_index, sizeof(int32_t) * kColours));
-    CVS_TRY(ctx_alloc(c, &c->d_unique, 3 * kColours));
-    CVS_TRY(ctx_alloc(c, &c->d_scan, sizeof(int) * 1025));
-    CVS_CUDA(cudaMallocHost(&c->h_unique, sizeof(int)));
+    if (!c->d_present) CVS_TRY(ctx_alloc(c, &c->d_present, kColours));
+    if (!c->d_index) CVS_TRY(ctx_alloc(c, &c->d_index, sizeof(int32_t) * kColours));
+    if (!c->d_unique) CVS_TRY(ctx_alloc(c, &c->d_unique, 3 * kColours));
+    if (!c->d_scan) CVS_TRY(ctx_alloc(c, &c->d_scan, sizeof(int) * 1025));
+    if (!c->h_unique) CVS_CUDA(cudaMallocHost(&c->h_unique, sizeof(int)));
     return CVS_OK;
 }
+
+// Frees the de-duplication tables (after a refused allocation of the automatic
+// mode, so that a partial set does not hold budget the per-pixel search needs).
+void drop_dedup(cvs_ctx* c) {
+    ctx_free(c, c->d_present);
+    ctx_free(c, c->d_index);
+    ctx_free(c, c->d_unique);
+    ctx_free(c, c->d_scan);
+    c->d_present = nullptr;
+    c->d_index = nullptr;
+    c->d_unique = nullptr;
+    c->d_scan = nullptr;
+}
+
+// Option "dedup" = 2 (the default): batches of at least this many pixels are
+// searched once per distinct colour, when CUDA graphs are off and the tables
+// fit the context's memory budget.
+constexpr int64_t kDedupAutoPixels = int64_t(1) << 20;
 
 // The FP32 path's error bound is validated for radii up to kFp32MaxRadius:
 // on a grid with a larger radius an FP32 request is refused, or (option
@@ -852,7 +871,8 @@ cvs_status cvs_set_option(cvs_ctx* c, const char* name, double value) {
         c->use_graphs = (int)value;
         if (!c->use_graphs) drop_graphs(c);
     } else if (!std::strcmp(name, "dedup")) {
-        if (value != 0 && value != 1) return fail(CVS_ERR_INVALID_ARG, "dedup is 0 or 1");
+        if (value != 0 && value != 1 && value != 2)
+            return fail(CVS_ERR_INVALID_ARG, "dedup is 0, 1 or 2");
         if (value == 1) {  // its tables, now rather than inside a later search
             CVS_CUDA(cudaSetDevice(c->device));
             cvs_status ds = ensure_dedup(c);
@@ -1290,12 +1310,13 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
     if (st0 == CVS_OK) st0 = ensure_grid(c, grid);
     if (st0 == CVS_OK) st0 = resolve_precision(c, &prec);
     if (st0 == CVS_OK && thr) st0 = ensure_ltab(c, thr);
-    if (c->dedup) {  // one search per distinct colour of the batch
-        constexpr int64_t kColours = int64_t(1) << 24;
-        if (st0 == CVS_OK) st0 = ensure_targets(c, total < kColours ? total : kColours);
-        if (st0 != CVS_OK) return st0;
-        st0 = ensure_dedup(c);
-        if (st0 != CVS_OK) return st0;
+    if (st0 != CVS_OK) return st0;
+    const bool auto_dedup =
+        c->dedup == 2 && !c->use_graphs && total >= kDedupAutoPixels;
+    // One search per distinct colour of the batch.  Every allocation comes
+    // before the gather, the only write to the maps.
+    auto search_distinct = [&]() -> cvs_status {
+        CVS_TRY(ensure_dedup(c));
         cudaStream_t st = (cudaStream_t)stream;
         CVS_TRY(grow(c, &c->d_imgs, &c->cap_imgs, n));
         CVS_CUDA(cudaMemcpyAsync(c->d_imgs, h.data(), sizeof(ImageDesc) * n,
@@ -1307,14 +1328,22 @@ cvs_status cvs_search_images(cvs_ctx* c, const cvs_image* batch, int32_t n, cons
                                  cudaMemcpyDeviceToHost, st));
         CVS_CUDA(cudaStreamSynchronize(st));
         const int64_t nu = *c->h_unique;
+        CVS_TRY(ensure_targets(c, nu));  // the search covers the distinct colours only
         CVS_CUDA(launch_setup_colors(c->d_unique, nu, c->grid.rmax, c->tf, c->td, c->acc, st));
         c->search_kind = 1;
         st0 = run_search(c, nu, thr, prec, 0, 0, st);
         if (st0 != CVS_OK) return st0;
         CVS_CUDA(launch_dedup_gather(c->d_imgs, n, total, c->d_index, c->acc, st));
         return CVS_OK;
+    };
+    if (c->dedup == 1) return search_distinct();
+    if (auto_dedup) {
+        st0 = search_distinct();
+        if (st0 != CVS_ERR_NO_MEMORY) return st0;
+        drop_dedup(c);  // memory the budget refused: the per-pixel search, tables freed
+        g_err.clear();
     }
-    if (st0 == CVS_OK) st0 = ensure_targets(c, total);
+    st0 = ensure_targets(c, total);
     if (st0 != CVS_OK) return st0;
     cudaStream_t st = (cudaStream_t)stream;
     auto enqueue = [&](cudaStream_t s, ImageDesc* d_imgs) -> cvs_status {
@@ -1723,6 +1752,12 @@ cvs_status cvs_reserve(cvs_ctx* c, const cvs_grid* grid, int64_t max_targets, in
     if (st0 == CVS_OK) st0 = set_device(c);
     if (st0 == CVS_OK && grid) st0 = ensure_grid(c, grid);
     if (st0 == CVS_OK && max_targets > 0) st0 = ensure_targets(c, max_targets);
+    // an image batch this large may take the per-batch de-duplication
+    if (st0 == CVS_OK && c->dedup == 2 && max_targets >= kDedupAutoPixels &&
+        ensure_dedup(c) != CVS_OK) {  // beyond the budget: such batches search per pixel
+        drop_dedup(c);
+        g_err.clear();
+    }
     if (st0 != CVS_OK) return st0;
     if (max_images > 0) CVS_TRY(grow(c, &c->d_imgs, &c->cap_imgs, max_images));
     return CVS_OK;

@@ -236,7 +236,9 @@ cvs_status cvs_server_create(cvs_server** out, const cvs_server_config* cfg, con
             const int per_sm = 5 / cfg->max_inflight;
             if (st == CVS_OK && cfg->max_inflight > 1)
                 st = cvs_set_option(sl.ctx, "blocks_per_sm", per_sm < 1 ? 1 : per_sm);
-            if (st == CVS_OK && cfg->dedup) st = cvs_set_option(sl.ctx, "dedup", 1);
+            // de-duplicate per frame or not, fixed at creation (no table is
+            // allocated while serving)
+            if (st == CVS_OK) st = cvs_set_option(sl.ctx, "dedup", cfg->dedup ? 1 : 0);
         }
         if (st != CVS_OK) break;
         e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);

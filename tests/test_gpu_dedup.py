@@ -70,3 +70,59 @@ def test_small_ragged_images_match_oracle(torch_cuda):
         assert np.array_equal(g[1].reshape(-1), ec) and np.array_equal(g[2].reshape(-1), ep)
         assert np.array_equal(g[0].reshape(-1).view(np.uint32), em.view(np.uint32))
     ctx.close()
+
+
+def same_maps(a, b):
+    for x, y in zip(a, b):
+        assert np.array_equal(x[0].view(np.uint32), y[0].view(np.uint32))
+        assert np.array_equal(x[1], y[1]) and np.array_equal(x[2], y[2])
+
+
+def test_automatic_dedup(torch_cuda):
+    """The default (dedup 2) searches each distinct colour once for batches of
+    at least 2^20 pixels, unless CUDA graphs are on; the maps never change."""
+    torch = torch_cuda
+    ctx = cvs.Context(0)
+    assert ctx.get_option("dedup") == 2
+    radii, ang = W.grid(3)
+    (w, h, t, s), = W.image_params(1, seed=9, sizes=[(1024, 1024)])
+    img = W.render_image_torch(w, h, t, s, device="cuda")
+    n_distinct = len(torch.unique((img[..., 0].long() << 16) | (img[..., 1].long() << 8)
+                                  | img[..., 2].long()))
+    direct, st = maps_of(ctx, torch, [img], radii, ang, 0)
+    assert st["targets"] == 1 << 20
+    auto, st = maps_of(ctx, torch, [img], radii, ang, 2)
+    assert st["targets"] == n_distinct < 1 << 20
+    same_maps(direct, auto)
+    below, st = maps_of(ctx, torch, [img[:1023]], radii, ang, 2)  # one row short
+    assert st["targets"] == 1023 * 1024
+    same_maps([tuple(x[:1023] for x in direct[0])], below)
+    ctx.set_option("graphs", 1)
+    try:
+        graphed, st = maps_of(ctx, torch, [img], radii, ang, 2)
+        assert st["targets"] == 1 << 20
+        same_maps(direct, graphed)
+    finally:
+        ctx.set_option("graphs", 0)
+    ctx.close()
+
+
+def test_automatic_dedup_within_budget(torch_cuda):
+    """A budget that holds the per-pixel search of a 2^20-pixel batch never
+    makes the automatic mode fail: tables that do not fit leave the search
+    per pixel, with the same maps, and the context stays within its budget."""
+    torch = torch_cuda
+    radii, ang = W.grid(3)
+    (w, h, t, s), = W.image_params(1, seed=9, sizes=[(1024, 1024)])
+    img = W.render_image_torch(w, h, t, s, device="cuda")
+    probe = cvs.Context(0)
+    direct, _ = maps_of(probe, torch, [img], radii, ang, 0)
+    need = probe.get_option("mem_in_use")
+    probe.close()
+    for budget in (need, need + (64 << 20), need + (256 << 20)):
+        ctx = cvs.Context(0, mem_budget=budget)
+        got, st = maps_of(ctx, torch, [img], radii, ang, 2)
+        same_maps(direct, got)
+        assert ctx.get_option("mem_in_use") <= budget
+        assert st["targets"] <= 1 << 20
+        ctx.close()

@@ -101,7 +101,7 @@ def test_batch_image_in_full(ctx, torch_cuda, dedup):
         maps = ctx.search_images([dev(torch, img)], radii, ang, 50.0, 0.5)
         torch.cuda.synchronize()
     finally:
-        ctx.set_option("dedup", 0)
+        ctx.set_option("dedup", 2)
     got = tuple(x.cpu().numpy().reshape(-1) for x in maps[0])
     key = (img[..., 0].astype(np.uint32) << 16) | (img[..., 1].astype(np.uint32) << 8) | img[..., 2]
     uniq, inv = np.unique(key.reshape(-1), return_inverse=True)
