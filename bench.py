@@ -945,6 +945,19 @@ def run_sets_profile(args):
     ctx.synchronize()
     torch.cuda.synchronize(dev)
     t_multi = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    ranges_ms = ctx.stats()["ranges_ms"]
+    ctx.set_option("angle_ranges", 0)  # the plain walk, for comparison
+    plain = ctx.search_colors_multi(cube, r2, a2, sets)
+    ctx.synchronize()
+    ev0.record()
+    for _ in range(args.steps):
+        ctx.search_colors_multi(cube, r2, a2, sets, out=plain)
+    ev1.record()
+    ctx.synchronize()
+    torch.cuda.synchronize(dev)
+    t_plain = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    ctx.set_option("angle_ranges", 2)
+    same = all(torch.equal(a, b) for a, b in zip(res, plain))
     cand = cube.shape[0] * len(r2) * len(a2)
     r3, a3 = W.grid(3)
     ev0.record()
@@ -956,7 +969,9 @@ def run_sets_profile(args):
     ctx.close()
     print(json.dumps({
         "multi_set_pass": {"colours": int(cube.shape[0]), "sets": len(sets), "seconds": t_multi,
-                           "gdecisions_s": cand * len(sets) / t_multi / 1e9},
+                           "gdecisions_s": cand * len(sets) / t_multi / 1e9,
+                           "ranges_pass_ms": ranges_ms,
+                           "plain_walk_seconds": t_plain, "same_as_plain_walk": same},
         "embedding_table_build": {"colours": 1 << 24, "seconds": t_etab,
                                   "gcand_s": (1 << 24) * len(r3) * len(a3) / t_etab / 1e9}}))
 

@@ -616,6 +616,9 @@ cvs_status prepare_arcs(cvs_ctx* c, SearchArgs& a, int64_t n, cvs_precision prec
     return CVS_OK;
 }
 
+// The probe's key for the multi-threshold search (in place of a list mode).
+constexpr int kMultiArcKey = 2;
+
 // Where a pair-list search (list mode) leaves its work items' bitmaps and
 // counts, and the radii per work item fixed for the whole call.
 struct ListOut {
@@ -1233,9 +1236,33 @@ cvs_status cvs_search_colors_multi(cvs_ctx* c, const uint8_t* rgb_dev, int64_t n
     a.num_sms = c->num_sms;
     cudaStream_t st = (cudaStream_t)stream;
     CVS_CUDA(launch_setup_colors(rgb_dev, n, c->grid.rmax, c->tf, c->td, c->acc, st));
+    // angle ranges of the union of the sets (the smallest hi_min, every
+    // enabled pattern): a superset of the slots that pass any set
+    a.arc_ranges = nullptr;
+    a.arc_cap = 0;
+    a.ev_ranges = nullptr;
+    if (prec == CVS_PREC_FP32_RECHECK && !a.clip && c->grid.arcs) {
+        SearchArgs pa{};
+        pa.tf = c->tf;
+        pa.td = c->td;
+        pa.grid = c->grid;
+        pa.hi_min = a.hi_min_all;
+        pa.lo_max = -1;
+        for (int p = 1; p <= 7; ++p)
+            if (a.pmask_sets[p]) pa.mask2 |= 1u << p;
+        pa.num_sms = c->num_sms;
+        c->search_kind = 0;
+        CVS_TRY(prepare_arcs(c, pa, n, prec, kMultiArcKey, st, false));
+        if (pa.grid.arcs && pa.arc_ranges && pa.arc_cap >= c->grid.K) {
+            a.arc_ranges = pa.arc_ranges;
+            a.arc_cap = pa.arc_cap;
+            a.ev_ranges = c->ev_mid;
+            a.ev_flags = cudaEventRecordDefault;
+        }
+    }
     CVS_CUDA(launch_init_acc(c->acc_multi, n * n_thr, st));
     CVS_CUDA(cudaMemsetAsync(c->counters, 0, kNumCounters * sizeof(unsigned long long), st));
-    c->last_arcs = false;
+    c->last_arcs = a.arc_ranges != nullptr;
     CVS_CUDA(cudaEventRecord(c->ev0, st));
     CVS_CUDA(launch_search_multi(a, st));
     CVS_CUDA(cudaEventRecord(c->ev1, st));

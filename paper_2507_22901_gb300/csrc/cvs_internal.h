@@ -155,6 +155,13 @@ struct MultiArgs {
     unsigned long long* work_counter;
     unsigned long long* stats;
     int num_sms;
+    // angle ranges of the union of the sets (FP32, gamut reject, a grid with
+    // angle ranges), or NULL for the plain walk: per chunk of arc_cap / K
+    // targets the range pass fills arc_ranges, then the search walks the lists
+    uint2* arc_ranges;
+    int64_t arc_cap;
+    void* ev_ranges;           // host: a cudaEvent_t recorded after the first ranges pass, or NULL
+    unsigned ev_flags;         // host: its record flags
 };
 
 // The embedding step: per pixel the first passing pair of the requested
@@ -223,6 +230,9 @@ cudaError_t launch_search(const SearchArgs& a, cudaStream_t st);
 // walk searches.
 cudaError_t launch_arc_probe(const SearchArgs& a, int64_t nt, int64_t stride,
                              unsigned long long* counts, cudaStream_t st);
+// The angle-range pass alone (k_arc_ranges) for the nt targets at a.tf, with
+// a.hi_min and the patterns of a.mask2, into out (nt * K entries).
+cudaError_t launch_arc_pass(const SearchArgs& a, int64_t nt, uint2* out, cudaStream_t st);
 cudaError_t launch_finalize_colors(const Acc* acc, int64_t n, float* max_r, int32_t* count,
                                    uint8_t* pmask, cudaStream_t st);
 cudaError_t launch_search_multi(const MultiArgs& a, cudaStream_t st);

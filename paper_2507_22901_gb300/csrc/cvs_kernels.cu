@@ -364,6 +364,7 @@ __device__ __forceinline__ bool slot_step(const SearchArgs& A, const Smem& S, co
 // branch for flagged slots; collect_flagged compacts them after each segment.
 constexpr int kFlagWords = 8;
 constexpr int kSegIters = 32 * kFlagWords;
+static_assert(kSegIters <= kArcMaskWords, "a segment's start mask must fit its buffer");
 
 // Iterations [it, end) of an item (within one segment starting at seg0), with
 // lanes at slot (k, h); flagged slots set their bits in fb.
@@ -526,58 +527,11 @@ __device__ __forceinline__ void run_item(const SearchArgs& A, const Smem& S, int
     }
 }
 
-// ------------------------------------------------------------ angle-range items
-// k_arc_ranges writes, per (target, radius) of a chunk, up to two slot ranges
-// (start | len << 16; a third or more merged into the second, a superset) with
-// bit 31 of the first word set where the radius may reach the sRGB linear
-// segment, or kSlowRadius for a radius on the slow path (searched whole).
-// run_item_arcs concatenates, per warp, the ranges of up to kArcRadii radii
-// into a list and evaluates only the listed slots, 32 at a time whatever
-// radius they belong to; the rest certainly fail.  List entry j: al[j] =
-// radius offset (bits 0..6) | linear-segment bit (bit 7) | (first slot - first
-// position + kArcBias) << 8, and its first position pos[j] = al[kArcEntries
-// + j].  Fast-path radii's entries start at index 0, slow-path radii's (whole
-// radii) at kSlowBase; each region ends with a sentinel position.
-constexpr int kArcRadii = 128;
-constexpr int kSlowBase = kArcRadii * 2 + 1;
-constexpr int kArcEntries = kSlowBase + kArcRadii + 3;
-constexpr int kArcWords = 2 * kArcEntries;
-constexpr int kArcBias = 1 << 23;
-constexpr uint32_t kSlowRadius = 0xFFFFFFFFu;
 // List mode: words of a warp's passing-slot bitmap (an item has at most
 // kListMaxSlots slots), and of the bitmap plus its nwords + 1 prefix counts in
 // the emit kernel.
 constexpr int kListWords = kListMaxSlots / 32;
 constexpr int kListWarpWords = 2 * kListWords + 2 + 2 * kListMaxRadii;
-
-__device__ __forceinline__ int warp_exclusive_sum(int v, int& total) {
-    const unsigned lane = lane_id();
-    int x = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xFFFFFFFFu, x, off);
-        if ((int)lane >= off) x += y;
-    }
-    total = __shfl_sync(0xFFFFFFFFu, x, 31);
-    return x - v;
-}
-
-// The slot of position p of a list region (entries up to jend, whose
-// sentinel position is pos[jend]): j0 is the entry holding position b - 1
-// (jbeg - 1 before the region), so the entries starting in [b, b + 31] are
-// among j0 + 1 .. j0 + 32, one per lane; a lane's entry is j0 plus the starts
-// at or before it.  Returns the entry word and advances j0 to the entry
-// holding b + 31.
-__device__ __forceinline__ uint32_t list_step(const uint32_t* al, int jend, int b, int& j0) {
-    const unsigned lane = lane_id();
-    const uint32_t* pos = al + kArcEntries;
-    const int ji = j0 + 1 + (int)lane;
-    const int d = ji <= jend ? (int)pos[ji] - b : 64;
-    const uint32_t starts = __reduce_or_sync(0xFFFFFFFFu, d < 32 ? 1u << d : 0u);
-    const int jj = j0 + __popc(starts & ((2u << lane) - 1u));
-    j0 += __popc(starts);
-    return al[jj];
-}
 
 // Queue the flagged slots of one segment of a list region (words [0, nwords)
 // of fb; bit i of word w of lane l = position seg + 32 (32 w + i) + l) into
@@ -637,7 +591,7 @@ __device__ __forceinline__ void collect_list(const SearchArgs& A, const Smem& S,
 template <bool FAST, bool LINSEG, bool LIST, bool DL>
 __device__ __forceinline__ void run_list(const SearchArgs& A, const Smem& S, const PairsT& P,
                                          const PairsC& PC, const TargetF64& D, const ChainF32& C,
-                                         int64_t t, int kg, const uint32_t* al, int jbeg, int jend,
+                                         int64_t t, int kg, uint32_t* al, int jbeg, int jend,
                                          int pbeg, int pend, Tally& acc, uint32_t* fb,
                                          uint32_t* pq, int& pq_n, uint32_t* rq_t, uint32_t* rq_kh,
                                          int& rq_n, unsigned long long& n_flag,
@@ -646,8 +600,10 @@ __device__ __forceinline__ void run_list(const SearchArgs& A, const Smem& S, con
     const unsigned lane = lane_id();
     const int pfull = pbeg + ((pend - pbeg) & ~31);  // start of the partial step
     int j0 = jbeg - 1;
+    const uint32_t* msk = al + 2 * kArcEntries;
     for (int seg = pbeg; seg < pend; seg += 32 * kSegIters) {
         const int seg_end = min(pend, seg + 32 * kSegIters);
+        list_mask(al, jend, seg, (seg_end - seg + 31) >> 5, j0);
         int b = seg;
         while (b < seg_end) {
             const int q = (b - seg) >> 5;  // step index within the segment
@@ -656,7 +612,7 @@ __device__ __forceinline__ void run_list(const SearchArgs& A, const Smem& S, con
             uint32_t bits = 0, bit = 1u << (q & 31);
             for (; b < min(wend, pfull); b += 32) {
                 const int p = b + (int)lane;
-                const uint32_t e = list_step(al, jend, b, j0);
+                const uint32_t e = list_step(al, msk[(b - seg) >> 5], j0);
                 const int k = kg + (int)(e & 127u), h = p + (int)(e >> 8) - kArcBias;
                 if (slot_step<PREC, FAST, false, false, LIST, LINSEG, DL>(A, S, P, PC, D, t, k, h,
                                                                           true, acc))
@@ -666,7 +622,7 @@ __device__ __forceinline__ void run_list(const SearchArgs& A, const Smem& S, con
             if (b < wend) {  // the partial step
                 const int p = b + (int)lane;
                 const bool active = p < pend;
-                const uint32_t e = list_step(al, jend, b, j0);
+                const uint32_t e = list_step(al, msk[(b - seg) >> 5], j0);
                 const int k = kg + (int)(e & 127u), h = p + (int)(e >> 8) - kArcBias;
                 if (slot_step<PREC, FAST, true, false, LIST, LINSEG, DL>(A, S, P, PC, D, t, k, h,
                                                                          active, acc))
@@ -1657,6 +1613,14 @@ cudaError_t launch_arc_probe(const SearchArgs& a, int64_t nt, int64_t stride,
     const int64_t want = (nt + 7) / 8, cap = (int64_t)a.num_sms * 16;
     k_arc_ranges<false><<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(a, nt, a.arc_ranges,
                                                                             counts, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_arc_pass(const SearchArgs& a, int64_t nt, uint2* out, cudaStream_t st) {
+    if (nt <= 0) return cudaSuccess;
+    const int64_t want = (nt + 7) / 8, cap = (int64_t)a.num_sms * 16;  // 8 warps a block
+    k_arc_ranges<false><<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(a, nt, out, nullptr,
+                                                                            1);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,10 @@
 // queued per warp and decided 32 at a time, one per lane (so the long exact
 // path runs with full warps, seldom): bounds once, every set from them, FP64
 // codes when some set stays open.
+// On a grid with angle ranges (FP32, gamut reject) a fast-path target's item
+// walks only the slots listed by the range pass run for the union of the sets
+// (the smallest hi_min and every enabled pattern), a superset of the slots
+// that pass any set.
 #include <cuda_runtime.h>
 
 #include "cvs_device.cuh"
@@ -27,8 +31,11 @@ namespace {
 
 constexpr int kMultiWords = 7;                  // flag words per lane per segment
 constexpr int kMultiSegIters = 32 * kMultiWords;  // < 256: byte counters cannot overflow
+static_assert(kMultiSegIters <= kArcMaskWords, "a segment's start mask must fit its buffer");
 constexpr int kMultiMaxChunk = 8192;            // radii per work item
 constexpr int kMultiQueue = 64;                 // flagged-slot queue entries per warp
+// per warp in shared memory: flag words, largest radius per set, queue
+constexpr int kMultiWarpWords = kMultiWords * 32 + kMaxThresholdSets * 32 + kMultiQueue;
 
 // Table entry of |d| = i: bit s set if set s calls the channel high (i >= hi_min[s]),
 // bit 16 + s if it calls it low (i <= lo_max[s]); i = 256 stands for out of range.
@@ -110,10 +117,10 @@ __device__ __forceinline__ void tally_patterns(MultiTally& m, uint32_t hR, uint3
     m.pm[7] |= hR & hG & hB;
 }
 
-__device__ __forceinline__ void tally_counts(MultiTally& m, uint32_t ok, int nw) {
+// (all four words whatever the number of sets: branch-free measured 2% faster)
+__device__ __forceinline__ void tally_counts(MultiTally& m, uint32_t ok) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (j < nw) m.c4[j] += (((ok >> (4 * j)) & 15u) * 0x00204081u) & 0x01010101u;
+    for (int j = 0; j < 4; ++j) m.c4[j] += (((ok >> (4 * j)) & 15u) * 0x00204081u) & 0x01010101u;
 }
 
 // Byte counters -> lane s's 32-bit count of set s.
@@ -208,6 +215,33 @@ __device__ __forceinline__ void drain_multi(const MultiArgs& A, const float2* r2
     }
 }
 
+// Item totals: lane s publishes set s (count, largest passing radius, patterns).
+__device__ __forceinline__ void publish_item(const MultiArgs& A, const MultiTally& m,
+                                             const float* rmx, int64_t t) {
+    const unsigned lane = lane_id();
+    const int NT = A.n_thr;
+    const int inc = A.grid.sym ? 2 : 1;
+    __syncwarp();
+    uint32_t pmask = 0;
+#pragma unroll
+    for (int p = 1; p <= 7; ++p) {
+        const uint32_t wp = __reduce_or_sync(0xFFFFFFFFu, m.pm[p]);
+        if ((wp >> lane) & 1u) pmask |= 1u << (p - 1);
+    }
+    int rbits_mine = __float_as_int(-1.0f);
+    for (int s = 0; s < NT; ++s) {
+        const uint32_t b = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(rmx[s * 32 + lane]));
+        if ((int)lane == s && b != 0u) rbits_mine = (int)b;
+    }
+    __syncwarp();
+    if ((int)lane < NT && m.cnt) {
+        Acc* ac = A.acc + t * NT + lane;
+        atomicAdd(&ac->count, (int)m.cnt * inc);
+        atomicMax(&ac->rmax_bits, rbits_mine);
+        atomicOr(&ac->pmask, pmask);
+    }
+}
+
 // Iterations [it, end) of a work item (lanes at slot (rank kk, angle h),
 // radii decreasing); from it_pow on, every radius stays above the sRGB linear
 // segment and the encode skips its select.  (Splitting the range at it_pow
@@ -219,7 +253,7 @@ __device__ __forceinline__ void multi_iters(const MultiArgs& A, const float2* r2
                                             const uint32_t* ts, const float4* sc4s,
                                             const PairsT& P, const PairsC& PC,
                                             const TargetF64& D, MultiTally& m, float* rmx,
-                                            uint32_t setmask, int nw, int nslots, int kk1,
+                                            uint32_t setmask, int nslots, int kk1,
                                             int& it, int end, int& kk, int& h, uint32_t& bits,
                                             uint32_t& bit, uint32_t& seen, int it_pow) {
     const unsigned lane = lane_id();
@@ -296,7 +330,7 @@ __device__ __forceinline__ void multi_iters(const MultiArgs& A, const float2* r2
             }
         }
         if (!skip) {
-            tally_counts(m, ok, nw);
+            tally_counts(m, ok);
             tally_patterns(m, hR, hG, hB);
             uint32_t fresh = ok & ~seen;  // radii decrease: the first pass is the largest
             if (fresh) {
@@ -328,9 +362,7 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
                                            unsigned long long& n_re) {
     const unsigned lane = lane_id();
     const int H = A.grid.H, NT = A.n_thr;
-    const int inc = A.grid.sym ? 2 : 1;
     const uint32_t setmask = (1u << NT) - 1u;
-    const int nw = (NT + 3) >> 2;
     const TargetF64 D = A.td[t];
     const PairsT P = make_pairs(T);
     MultiTally m;
@@ -343,7 +375,6 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
     int pq_n = 0;       // queued flagged slots (warp-uniform)
     for (int s = 0; s < NT; ++s) rmx[s * 32 + lane] = 0.0f;  // radius 0 never passes
     // slot i of the item is (rank kk1 - 1 - i / H, i % H); lanes step by 32
-    const int q32 = 32 / H, r32 = 32 - q32 * H;
     int kk = kk1 - 1 - (int)lane / H, h = (int)lane % H;
     int klo = kk0;      // ranks below klo certainly fail for every set
     int it_pow = 1 << 30;  // iterations from here on never reach the sRGB linear segment
@@ -361,7 +392,7 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
             const int wend = min(seg1, it + 32);
             uint32_t bit = 1u;
             multi_iters<PREC, FAST, CLIP, ALLMASK, DL>(A, r2s, ts, sc4s, P, PC, D, m, rmx, setmask,
-                                                       nw, nslots, kk1, it, wend, kk, h, bits, bit,
+                                                       nslots, kk1, it, wend, kk, h, bits, bit,
                                                        seen, it_pow);
             if (PREC == CVS_PREC_FP32_RECHECK) fb[w * 32 + lane] = bits;
         }
@@ -403,29 +434,202 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
     if (PREC == CVS_PREC_FP32_RECHECK && pq_n > 0)
         drain_multi<PREC, FAST, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t, pq, pq_n, setmask,
                                                n_re);
-    __syncwarp();
-    // item totals: lane s publishes set s
-    uint32_t pmask = 0;
+    publish_item(A, m, rmx, t);
+}
+
+// Steps [b, bend) of a list walk (lane at position b + lane of the list in
+// al, whose start mask covers the segment from seg; positions from pend on
+// inactive): as multi_iters,
+// with each lane's (rank, angle) from its list entry.  The encode keeps the
+// sRGB linear-segment select throughout: the loop body stays one variant (a
+// choice per step, or two loops split at the last radius that may reach the
+// segment, measured 2.5% and 6% slower: the kernel waits on instruction
+// fetch, and both make the loop longer).
+template <bool ALLMASK, bool DL>
+__device__ __forceinline__ void multi_list_iters(const MultiArgs& A, const float2* r2s,
+                                                 const uint32_t* ts, const float4* sc4s,
+                                                 const PairsT& P, const PairsC& PC,
+                                                 const TargetF64& D, MultiTally& m, float* rmx,
+                                                 uint32_t setmask, const uint32_t* al,
+                                                 int kb, int pend, int seg, int& b,
+                                                 int bend, int& j0, uint32_t& bits,
+                                                 uint32_t& seen) {
+    const unsigned lane = lane_id();
+    const uint32_t* msk = al + 2 * kArcEntries;
+    uint32_t bit = 1u;
+    for (; b < bend; b += 32, bit <<= 1) {
+        const int p = b + (int)lane;
+        const bool active = p < pend;
+        const uint32_t e = list_step(al, msk[(b - seg) >> 5], j0);
+        const int kq = active ? kb + (int)(e & 127u) : kb;
+        const int hq = active ? p + (int)(e >> 8) - kArcBias : 0;
+        const float2 r2 = r2s[kq];
+        const float4 sc = sc4s[hq];
+        const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));
+        const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
+        float2 lin[3];
+        lin32<true>(P, PC, u2, w2, lin);
+        // gamut reject: a warp whose pairs all leave the gamut passes no set
+        if (__all_sync(0xFFFFFFFFu, !active || surely_out32(lin))) continue;
+        int yp[3], ym[3];
+        bool flag;
+        flag = encode32<true>(lin, A.half_w, yp, ym, nullptr);
+        flag = flag && active;
+        if (flag) bits |= bit;
+        uint32_t e3[3];
+        uint32_t o = 0;
+        int qa[3], qb[3];
 #pragma unroll
-    for (int p = 1; p <= 7; ++p) {
-        const uint32_t wp = __reduce_or_sync(0xFFFFFFFFu, m.pm[p]);
-        if ((wp >> lane) & 1u) pmask |= 1u << (p - 1);
-    }
-    int rbits_mine = __float_as_int(-1.0f);
-    for (int s = 0; s < NT; ++s) {
-        const uint32_t b = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(rmx[s * 32 + lane]));
-        if ((int)lane == s && b != 0u) rbits_mine = (int)b;
-    }
-    __syncwarp();
-    if ((int)lane < NT && m.cnt) {
-        Acc* ac = A.acc + t * NT + lane;
-        atomicAdd(&ac->count, (int)m.cnt * inc);
-        atomicMax(&ac->rmax_bits, rbits_mine);
-        atomicOr(&ac->pmask, pmask);
+        for (int c = 0; c < 3; ++c) {
+            const int a = yp[c] - kMagicBits, bq = ym[c] - kMagicBits;
+            qa[c] = a;
+            qb[c] = bq;
+            o |= (uint32_t)a | (uint32_t)bq;
+            e3[c] = ts[min(abs(a - bq), 256)];
+        }
+        uint32_t ok = 0, hR = 0, hG = 0, hB = 0;
+        if (active && !flag) {
+            ok = pass_sets<ALLMASK>(e3, o <= 255u, setmask, A.pmask_sets, hR, hG, hB);
+            if (DL && ok) {  // the luminance limits, per set
+                ok &= dl_sets(A, D.L, qa, qb);
+                hR &= ok;
+                hG &= ok;
+                hB &= ok;
+            }
+        }
+        tally_counts(m, ok);
+        tally_patterns(m, hR, hG, hB);
+        uint32_t fresh = ok & ~seen;  // ranks decrease along a lane: the first pass is the largest
+        if (fresh) {
+            seen |= fresh;
+            const float r = r2.x;
+            while (fresh) {
+                const int s = __ffs(fresh) - 1;
+                fresh &= fresh - 1u;
+                rmx[s * 32 + lane] = r;
+            }
+        }
     }
 }
 
-template <int PREC, bool CLIP, bool ALLMASK, bool DL>
+// A work item of a fast-path target (FP32, gamut reject) on a grid with angle
+// ranges: ranks [kk0, kk1) in blocks of kArcRadii from the top, each block's
+// ranges listed in decreasing rank (so that a lane meets its radii in
+// decreasing order, as in multi_item) and walked 32 positions a step; flagged
+// slots are found again in the list and queued as in multi_item.
+template <bool ALLMASK, bool DL>
+__device__ __forceinline__ void multi_item_arcs(const MultiArgs& A, const float2* r2s,
+                                                const float4* sc4s, const uint32_t* ts,
+                                                uint32_t* fb, float* rmx, uint32_t* pq,
+                                                uint32_t* al, const TargetF32& T,
+                                                const ChainF32& C, const PairsC& PC, int64_t t,
+                                                int kk0, int kk1, unsigned long long& n_flag,
+                                                unsigned long long& n_re) {
+    constexpr int PREC = CVS_PREC_FP32_RECHECK;
+    const unsigned lane = lane_id();
+    const int K = A.grid.K, NT = A.n_thr;
+    const uint32_t setmask = (1u << NT) - 1u;
+    const TargetF64 D = A.td[t];
+    const PairsT P = make_pairs(T);
+    MultiTally m;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) m.c4[j] = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) m.pm[p] = 0;
+    m.cnt = 0;
+    uint32_t seen = 0;
+    int pq_n = 0;
+    for (int s = 0; s < NT; ++s) rmx[s * 32 + lane] = 0.0f;
+    uint32_t* pos = al + kArcEntries;
+    const uint2* ranges = A.arc_ranges + t * K;
+    for (int kb1 = kk1; kb1 > kk0; kb1 -= kArcRadii) {
+        const int kb = max(kk0, kb1 - kArcRadii);
+        int nf = 0, pf = 0;  // the list's entries and positions
+        for (int kg = kb1 - 1; kg >= kb; kg -= 32) {
+            const int kk = kg - (int)lane;
+            const uint2 o =
+                kk >= kb ? __ldg(ranges + __ldg(A.order + kk)) : make_uint2(0u, 0u);
+            const uint32_t w0 = o.x & 0x7FFFFFFFu, w1 = o.y;
+            const int l0 = (int)(w0 >> 16), l1 = (int)(w1 >> 16);
+            const int n = (l0 > 0 ? 1 : 0) + (l1 > 0 ? 1 : 0);
+            int nr, pr;
+            const int eoff = nf + warp_exclusive_sum(n, nr);
+            const int poff = pf + warp_exclusive_sum(l0 + l1, pr);
+            const uint32_t koff = (uint32_t)(kk - kb);
+            int e = eoff, q = poff;
+            if (l0 > 0) {
+                al[e] = koff | ((uint32_t)((int)(w0 & 0xFFFFu) - q + kArcBias) << 8);
+                pos[e] = (uint32_t)q;
+                ++e;
+                q += l0;
+            }
+            if (l1 > 0) {
+                al[e] = koff | ((uint32_t)((int)(w1 & 0xFFFFu) - q + kArcBias) << 8);
+                pos[e] = (uint32_t)q;
+            }
+            nf += nr;
+            pf += pr;
+        }
+        if (lane == 0) pos[nf] = (uint32_t)pf;
+        __syncwarp();
+        int j0 = -1;
+        for (int seg = 0; seg < pf; seg += 32 * kMultiSegIters) {
+            const int seg_end = min(pf, seg + 32 * kMultiSegIters);
+            list_mask(al, nf, seg, (seg_end - seg + 31) >> 5, j0);
+            int b = seg;
+            for (int w = 0; b < seg_end; ++w) {
+                uint32_t bits = 0;
+                multi_list_iters<ALLMASK, DL>(A, r2s, ts, sc4s, P, PC, D, m, rmx, setmask, al,
+                                              kb, pf, seg, b, min(seg_end, b + 32 * 32), j0,
+                                              bits, seen);
+                fb[w * 32 + lane] = bits;
+            }
+            flush_counts(m, NT);
+            __syncwarp();
+            // queue the segment's flagged slots
+            const int nwords = (((seg_end - seg + 31) >> 5) + 31) >> 5;
+            for (int w = 0; w < nwords; ++w) {
+                uint32_t bits = fb[w * 32 + lane];
+                while (true) {
+                    const bool has = bits != 0u;
+                    const unsigned ball = __ballot_sync(0xFFFFFFFFu, has);
+                    if (!ball) break;
+                    if (has) {
+                        const int i = __ffs(bits) - 1;
+                        bits &= bits - 1u;
+                        const int p = seg + 32 * (32 * w + i) + (int)lane;
+                        const uint32_t e = list_entry(al, 0, nf, p);
+                        const uint32_t kk = (uint32_t)kb + (e & 127u);
+                        const uint32_t h = (uint32_t)(p + (int)(e >> 8) - kArcBias);
+                        pq[pq_n + __popc(ball & ((1u << lane) - 1u))] = kk | (h << 16);
+                        ++n_flag;
+                    }
+                    pq_n += __popc(ball);  // below kMultiQueue: at most 31 + 32
+                    __syncwarp();
+                    if (pq_n >= 32) {
+                        drain_multi<PREC, true, false, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t,
+                                                                    pq, 32, setmask, n_re);
+                        const int rest = pq_n - 32;
+                        const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
+                        __syncwarp();
+                        if ((int)lane < rest) pq[lane] = mv;
+                        __syncwarp();
+                        pq_n = rest;
+                    }
+                }
+            }
+        }
+        __syncwarp();  // the list is rebuilt for the next block of radii
+    }
+    if (pq_n > 0)
+        drain_multi<PREC, true, false, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t, pq, pq_n, setmask,
+                                                    n_re);
+    publish_item(A, m, rmx, t);
+}
+
+// ARCS: the kernel with the angle-range walk (FP32, gamut reject), a separate
+// instantiation so that the plain walk's code and registers stay as they are.
+template <int PREC, bool CLIP, bool ALLMASK, bool DL, bool ARCS>
 __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = A.grid.K, H = A.grid.H;
@@ -434,9 +638,11 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
     uint32_t* ts = reinterpret_cast<uint32_t*>(smem + ((K * 8 + 15) & ~15) + H * 16);
     uint32_t* per_warp = ts + 260;  // 257 table entries, padded to 16 bytes
     const int warp = threadIdx.x >> 5;
-    uint32_t* fb = per_warp + warp * (kMultiWords * 32 + kMaxThresholdSets * 32 + kMultiQueue);
+    uint32_t* fb = per_warp + warp * kMultiWarpWords;
     float* rmx = reinterpret_cast<float*>(fb + kMultiWords * 32);
     uint32_t* pq = fb + kMultiWords * 32 + kMaxThresholdSets * 32;
+    uint32_t* al = ARCS ? per_warp + (blockDim.x >> 5) * kMultiWarpWords + warp * kArcWords
+                        : nullptr;
     build_set_table(ts, A);
     for (int i = threadIdx.x; i < K; i += blockDim.x) r2s[i] = dup(A.grid.r32[A.order[i]]);
     for (int i = threadIdx.x; i < H; i += blockDim.x) {
@@ -467,7 +673,10 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
         const int k0 = kc * kchunk, k1 = min(k0 + kchunk, K);
         TargetF32 T{};
         if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
-        if (PREC == CVS_PREC_FP32_RECHECK && (T.flags & 1u))
+        if (ARCS && (T.flags & 1u))
+            multi_item_arcs<ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, al, T, C, PC, t, k0, k1,
+                                         n_flag, n_re);
+        else if (!ARCS && PREC == CVS_PREC_FP32_RECHECK && (T.flags & 1u))
             multi_item<PREC, true, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t, k0,
                                                   k1, n_flag, n_re);
         else
@@ -496,24 +705,62 @@ __global__ void k_init_acc(Acc* __restrict__ acc, int64_t n) {
     acc[i] = z;
 }
 
-int multi_smem_bytes(const GridDev& g, int block) {
+int multi_smem_bytes(const GridDev& g, int block, bool arcs) {
     return ((g.K * 8 + 15) & ~15) + g.H * 16 + 260 * 4 +
-           (block / 32) * (kMultiWords * 32 + kMaxThresholdSets * 32 + kMultiQueue) * 4;
+           (block / 32) * (kMultiWarpWords + (arcs ? kArcWords : 0)) * 4;
 }
 
 template <int PREC, bool CLIP, bool ALLMASK, bool DL>
 cudaError_t launch_multi_t(const MultiArgs& a, cudaStream_t st) {
     const int block = kSearchBlock;
-    const int smem = multi_smem_bytes(a.grid, block);
-    const void* fn = (const void*)k_search_multi<PREC, CLIP, ALLMASK, DL>;
+    constexpr bool kArcsKernel = PREC == CVS_PREC_FP32_RECHECK && !CLIP;
+    const bool arcs = kArcsKernel && a.arc_ranges && a.arc_cap >= a.grid.K;
+    const int smem = multi_smem_bytes(a.grid, block, arcs);
+    const void* fn = arcs ? (const void*)k_search_multi<PREC, CLIP, ALLMASK, DL, kArcsKernel>
+                          : (const void*)k_search_multi<PREC, CLIP, ALLMASK, DL, false>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    k_search_multi<PREC, CLIP, ALLMASK, DL><<<a.num_sms * per_sm, block, smem, st>>>(a);
-    return cudaGetLastError();
+    if (!arcs) {
+        k_search_multi<PREC, CLIP, ALLMASK, DL, false><<<a.num_sms * per_sm, block, smem, st>>>(a);
+        return cudaGetLastError();
+    }
+    // per chunk of targets: the range pass for the union of the sets (the
+    // smallest hi_min, every enabled pattern), then the search
+    SearchArgs pass{};
+    pass.grid = a.grid;
+    pass.hi_min = a.hi_min_all;
+    for (int p = 1; p <= 7; ++p)
+        if (a.pmask_sets[p]) pass.mask2 |= 1u << p;
+    pass.num_sms = a.num_sms;
+    const int64_t chunk = a.arc_cap / a.grid.K;
+    for (int64_t t0 = 0; t0 < a.n_targets; t0 += chunk) {
+        const int64_t nt = a.n_targets - t0 < chunk ? a.n_targets - t0 : chunk;
+        MultiArgs c = a;
+        c.tf += t0;
+        c.td += t0;
+        c.acc += t0 * a.n_thr;
+        c.n_targets = nt;
+        if (t0 > 0) {
+            e = cudaMemsetAsync(c.work_counter, 0, sizeof(unsigned long long), st);
+            if (e != cudaSuccess) return e;
+        }
+        pass.tf = c.tf;
+        e = launch_arc_pass(pass, nt, a.arc_ranges, st);
+        if (e != cudaSuccess) return e;
+        if (t0 == 0 && a.ev_ranges) {
+            e = cudaEventRecordWithFlags((cudaEvent_t)a.ev_ranges, st, a.ev_flags);
+            if (e != cudaSuccess) return e;
+        }
+        k_search_multi<PREC, CLIP, ALLMASK, DL, kArcsKernel><<<a.num_sms * per_sm, block, smem, st>>>(
+            c);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <int PREC, bool DL>

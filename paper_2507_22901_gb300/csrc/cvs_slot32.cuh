@@ -708,5 +708,85 @@ __device__ __forceinline__ int certain32(const TargetF32& T, const ChainF32& C, 
     return certain_from(I, hi_min, lo_max, mask2, clip, list_mode);
 }
 
+
+// ------------------------------------------------------------ angle-range items
+// k_arc_ranges writes, per (target, radius) of a chunk, up to two slot ranges
+// (start | len << 16; a third or more merged into the second, a superset) with
+// bit 31 of the first word set where the radius may reach the sRGB linear
+// segment, or kSlowRadius for a radius on the slow path (searched whole).
+// The search kernels concatenate, per warp, the ranges of up to kArcRadii
+// radii into a list and evaluate only the listed slots, 32 at a time whatever
+// radius they belong to; the rest certainly fail (k_search in increasing
+// radius order, k_search_multi in decreasing radius rank).  List entry j:
+// al[j] = radius offset (bits 0..6) | linear-segment bit (bit 7) | (first slot
+// - first position + kArcBias) << 8, and its first position pos[j] =
+// al[kArcEntries + j].  Fast-path radii's entries start at index 0, slow-path
+// radii's (whole radii) at kSlowBase; each region ends with a sentinel
+// position.  After the list, al holds the start mask of the segment being
+// walked (list_mask).
+constexpr int kArcRadii = 128;
+constexpr int kSlowBase = kArcRadii * 2 + 1;
+constexpr int kArcEntries = kSlowBase + kArcRadii + 3;
+constexpr int kArcMaskWords = 256;  // steps of 32 positions per segment, at most
+constexpr int kArcWords = 2 * kArcEntries + kArcMaskWords;
+constexpr int kArcBias = 1 << 23;
+constexpr uint32_t kSlowRadius = 0xFFFFFFFFu;
+
+__device__ __forceinline__ int warp_exclusive_sum(int v, int& total) {
+    const unsigned lane = lane_id();
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+        if ((int)lane >= off) x += y;
+    }
+    total = __shfl_sync(0xFFFFFFFFu, x, 31);
+    return x - v;
+}
+
+// The start mask of the positions [seg, seg + 32 nsteps) of a list region
+// (entries below jend; nsteps <= kArcMaskWords), at al + 2 kArcEntries: bit l
+// of word q is set where an entry starts at position seg + 32 q + l.  j0 is
+// the entry holding position seg - 1 (jbeg - 1 before the region), so the
+// entries from j0 + 1 on start at or after seg, in order.
+__device__ __forceinline__ void list_mask(uint32_t* al, int jend, int seg, int nsteps, int j0) {
+    const unsigned lane = lane_id();
+    const uint32_t* pos = al + kArcEntries;
+    uint32_t* msk = al + 2 * kArcEntries;
+    for (int q = (int)lane; q < nsteps; q += 32) msk[q] = 0u;
+    __syncwarp();
+    const int end = seg + 32 * nsteps;
+    for (int j = j0 + 1 + (int)lane;; j += 32) {
+        const int pj = j < jend ? (int)pos[j] : end;
+        const bool in = pj < end;
+        if (in) atomicOr(msk + ((pj - seg) >> 5), 1u << ((pj - seg) & 31));
+        if (!(__ballot_sync(0xFFFFFFFFu, in) >> 31)) break;  // later entries start later
+    }
+    __syncwarp();
+}
+
+// The slot of position b + lane of a list region, given `starts`, word
+// (b - seg) / 32 of the segment's start mask: j0 is the entry holding position
+// b - 1, and a lane's entry is j0 plus the starts at or before it.  Returns the
+// entry word and advances j0 to the entry holding b + 31.
+__device__ __forceinline__ uint32_t list_step(const uint32_t* al, uint32_t starts, int& j0) {
+    const unsigned lane = lane_id();
+    const int jj = j0 + __popc(starts & ((2u << lane) - 1u));
+    j0 += __popc(starts);
+    return al[jj];
+}
+
+// The entry of a list region [jbeg, jend) holding position p (the last one
+// starting at or before p), by bisection over the start positions.
+__device__ __forceinline__ uint32_t list_entry(const uint32_t* al, int jbeg, int jend, int p) {
+    const uint32_t* pos = al + kArcEntries;
+    int lo = jbeg, hi = jend - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int)pos[mid] <= p) lo = mid; else hi = mid - 1;
+    }
+    return al[lo];
+}
+
 }  // namespace
 }  // namespace cvs

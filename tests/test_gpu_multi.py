@@ -152,3 +152,48 @@ def test_invalid_sets_rejected(ctx, torch_cuda):
     out = ctx.search_colors_multi(dev(torch_cuda, np.zeros((0, 3), np.uint8)), radii, ang,
                                   [(50.0, 0.5)])
     assert out[0].shape == (0, 1)
+
+
+@pytest.mark.parametrize("walk", [1, 0])
+def test_angle_range_walk_matches_oracle(ctx, torch_cuda, walk):
+    """The multi-set pass on the angle-range walk (option angle_ranges = 1:
+    ranges of the union of the sets) and on the plain walk (0): every set
+    equals the single-set entry point, and four sets the oracle.  The grids
+    cover one and several blocks of 128 radii, unsorted radii, radius chunks
+    per work item, per-set masks and luminance limits."""
+    torch = torch_cuda
+    cube = W.color_cube()
+    rng = np.random.default_rng(23)
+    rgb = np.concatenate([cube[rng.choice(len(cube), 96, replace=False)],
+                          np.array([[0, 0, 0], [252, 252, 252], [4, 200, 4]], np.uint8)])
+    r2, a2 = W.grid(2)
+    grids = [(r2, a2),
+             (np.linspace(0.2, 30.0, 200), np.arange(0.0, 360.0, 3.0)),
+             (rng.permutation(np.linspace(0.5, 24.0, 70)), np.arange(0.0, 360.0, 4.0))]
+    sets = [(50.0, 0.5, 0x7F, None), (100.0, 0.25, 0x7F, None), (150.0, 0.125, 0b0101010, 0.2),
+            (60.0, 0.5, 0b1000001, None), (200.0, 0.5, 0x7F, 0.05)]
+    ctx.set_option("angle_ranges", walk)
+    try:
+        for gi, (radii, ang) in enumerate(grids):
+            for kchunk in (0, 37):
+                ctx.set_option("kchunk", kchunk)
+                out = ctx.search_colors_multi(dev(torch, rgb), radii, ang, sets, 0)
+                ctx.synchronize()
+                got = tuple(x.cpu().numpy() for x in out)
+                st = ctx.stats()
+                assert (st["ranges_ms"] > 0.0) == (walk == 1), st
+                for s, (vth, rn, mask, lim) in enumerate(sets):
+                    one = ctx.search_colors(dev(torch, rgb), radii, ang, vth, rn, mask, 0,
+                                            max_dl=lim)
+                    torch.cuda.synchronize()
+                    column_equal(got, s, tuple(x.cpu().numpy() for x in one),
+                                 f"grid {gi} kchunk {kchunk}")
+            for s in (0, 2, 3, 4):
+                vth, rn, mask, lim = sets[s]
+                exp = oracle.search_colors(rgb, radii, ang, vth, rn, mask, 0, threads=THREADS,
+                                           max_dl=-1.0 if lim is None else lim)
+                column_equal(got, s, exp, f"grid {gi} vs oracle")
+            assert got[1].sum() > 0
+    finally:
+        ctx.set_option("kchunk", 0)
+        ctx.set_option("angle_ranges", 2)
