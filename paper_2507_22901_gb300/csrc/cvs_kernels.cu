@@ -585,10 +585,14 @@ __device__ __forceinline__ void collect_list(const SearchArgs& A, const Smem& S,
 }
 
 // Positions [pbeg, pend) of a list region (entries jbeg .. jend - 1, entry
-// jbeg starting at pbeg), 32 per step, in one slot variant (LINSEG fixed by
-// the caller); the last, partial step is peeled.  Flagged slots set their
-// bits in fb and are collected after each segment of kSegIters steps.
-template <bool FAST, bool LINSEG, bool LIST, bool DL>
+// jbeg starting at pbeg), 32 per step; the last, partial step is peeled.
+// Flagged slots set their bits in fb and are collected after each segment of
+// kSegIters steps.  The encode keeps its sRGB linear-segment select for every
+// radius: one loop for the whole region.  (Two loops, split at the first
+// radius that may reach the segment so that the radii below it skip the
+// select, ran 2.3% slower: the kernel is bound by instruction issue and fetch,
+// and the second loop doubled the hot code.)
+template <bool FAST, bool LIST, bool DL>
 __device__ __forceinline__ void run_list(const SearchArgs& A, const Smem& S, const PairsT& P,
                                          const PairsC& PC, const TargetF64& D, const ChainF32& C,
                                          int64_t t, int kg, uint32_t* al, int jbeg, int jend,
@@ -614,8 +618,8 @@ __device__ __forceinline__ void run_list(const SearchArgs& A, const Smem& S, con
                 const int p = b + (int)lane;
                 const uint32_t e = list_step(al, msk[(b - seg) >> 5], j0);
                 const int k = kg + (int)(e & 127u), h = p + (int)(e >> 8) - kArcBias;
-                if (slot_step<PREC, FAST, false, false, LIST, LINSEG, DL>(A, S, P, PC, D, t, k, h,
-                                                                          true, acc))
+                if (slot_step<PREC, FAST, false, false, LIST, true, DL>(A, S, P, PC, D, t, k, h,
+                                                                        true, acc))
                     bits |= bit;
                 bit <<= 1;
             }
@@ -624,8 +628,8 @@ __device__ __forceinline__ void run_list(const SearchArgs& A, const Smem& S, con
                 const bool active = p < pend;
                 const uint32_t e = list_step(al, msk[(b - seg) >> 5], j0);
                 const int k = kg + (int)(e & 127u), h = p + (int)(e >> 8) - kArcBias;
-                if (slot_step<PREC, FAST, true, false, LIST, LINSEG, DL>(A, S, P, PC, D, t, k, h,
-                                                                         active, acc))
+                if (slot_step<PREC, FAST, true, false, LIST, true, DL>(A, S, P, PC, D, t, k, h,
+                                                                       active, acc))
                     bits |= bit;
                 b = wend;
             }
@@ -661,43 +665,35 @@ __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S
     const uint2* ranges = A.arc_ranges + t * K;
     for (int kb = k0; kb < k1; kb += kArcRadii) {
         const int kb1 = min(k1, kb + kArcRadii);
-        int nf = 0, pf = 0, ns = 0, ps = 0, jlin = -1, plin = 0;
+        int nf = 0, pf = 0, ns = 0, ps = 0;
         for (int kg = kb; kg < kb1; kg += 32) {
             const int k = kg + (int)lane;
             const uint2 o = k < kb1 ? ranges[k] : make_uint2(0u, 0u);
             const int slow = o.x == kSlowRadius ? 1 : 0;
-            const uint32_t w0 = slow ? 0u : (o.x & 0x7FFFFFFFu), w1 = slow ? 0u : o.y;
+            const uint32_t w0 = slow ? 0u : o.x, w1 = slow ? 0u : o.y;
             const int l0 = (int)(w0 >> 16), l1 = (int)(w1 >> 16);
             const int n = (l0 > 0 ? 1 : 0) + (l1 > 0 ? 1 : 0);
             const int tot = l0 + l1;
-            const uint32_t linbit = (slow || (o.x >> 31)) ? (1u << 7) : 0u;
             if (k < kb1 && !slow) acc.prune += (uint32_t)(H - tot);
             int nr, pr, nsr, psr;
             const int eoff = nf + warp_exclusive_sum(n, nr);
             const int poff = pf + warp_exclusive_sum(tot, pr);
             const int soff = ns + warp_exclusive_sum(slow, nsr);
             const int spoff = ps + warp_exclusive_sum(slow ? H : 0, psr);
-            // entries before the first one that may reach the linear segment skip its select
-            const unsigned lin_lanes = __ballot_sync(0xFFFFFFFFu, n > 0 && linbit);
-            if (jlin < 0 && lin_lanes) {
-                const int ll = __ffs(lin_lanes) - 1;
-                jlin = __shfl_sync(0xFFFFFFFFu, eoff, ll);
-                plin = __shfl_sync(0xFFFFFFFFu, poff, ll);
-            }
             const uint32_t koff = (uint32_t)(k - kb);
             int e = eoff, q = poff;
             if (l0 > 0) {
-                al[e] = koff | linbit | ((uint32_t)((int)(w0 & 0xFFFFu) - q + kArcBias) << 8);
+                al[e] = koff | ((uint32_t)((int)(w0 & 0xFFFFu) - q + kArcBias) << 8);
                 pos[e] = (uint32_t)q;
                 ++e;
                 q += l0;
             }
             if (l1 > 0) {
-                al[e] = koff | linbit | ((uint32_t)((int)(w1 & 0xFFFFu) - q + kArcBias) << 8);
+                al[e] = koff | ((uint32_t)((int)(w1 & 0xFFFFu) - q + kArcBias) << 8);
                 pos[e] = (uint32_t)q;
             }
             if (slow) {
-                al[kSlowBase + soff] = koff | (1u << 7) | ((uint32_t)(kArcBias - spoff) << 8);
+                al[kSlowBase + soff] = koff | ((uint32_t)(kArcBias - spoff) << 8);
                 pos[kSlowBase + soff] = (uint32_t)spoff;
             }
             nf += nr;
@@ -705,28 +701,21 @@ __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S
             ns += nsr;
             ps += psr;
         }
-        if (jlin < 0) {
-            jlin = nf;
-            plin = pf;
-        }
         if (lane == 0) {
             pos[nf] = (uint32_t)pf;
             pos[kSlowBase + ns] = (uint32_t)ps;
         }
         __syncwarp();
-        run_list<true, false, LIST, DL>(A, S, P, PC, D, C, t, kb, al, 0, jlin, 0, plin, acc, fb,
-                                        pq, pq_n, rq_t, rq_kh, rq_n, n_flag, n_re);
-        run_list<true, true, LIST, DL>(A, S, P, PC, D, C, t, kb, al, jlin, nf, plin, pf, acc, fb,
-                                       pq, pq_n, rq_t, rq_kh, rq_n, n_flag, n_re);
+        run_list<true, LIST, DL>(A, S, P, PC, D, C, t, kb, al, 0, nf, 0, pf, acc, fb, pq, pq_n,
+                                 rq_t, rq_kh, rq_n, n_flag, n_re);
         if (ns) {  // the slow path decides its own flagged slots
             if (pq_n > 0) {
                 const TargetF32 T = A.tf[t];
                 drain_flagged<true, DL>(A, S, T, C, t, pq, pq_n, acc, rq_t, rq_kh, rq_n, n_re);
                 pq_n = 0;
             }
-            run_list<false, true, LIST, DL>(A, S, P, PC, D, C, t, kb, al, kSlowBase,
-                                            kSlowBase + ns, 0, ps, acc, fb, pq, pq_n, rq_t, rq_kh,
-                                            rq_n, n_flag, n_re);
+            run_list<false, LIST, DL>(A, S, P, PC, D, C, t, kb, al, kSlowBase, kSlowBase + ns, 0,
+                                      ps, acc, fb, pq, pq_n, rq_t, rq_kh, rq_n, n_flag, n_re);
             if (pq_n > 0) {
                 const TargetF32 T = A.tf[t];
                 drain_flagged<false, DL>(A, S, T, C, t, pq, pq_n, acc, rq_t, rq_kh, rq_n, n_re);
@@ -797,9 +786,8 @@ __global__ void __launch_bounds__(256, CVS_ARC_PASS_MIN_BLOCKS)
             } else {
                 uint32_t rr[kMaxArcRanges];
                 int tot = 0;
-                bool lin = true;
                 const int n = radius_ranges_body<CLIP>(T, C, r, A.hi_min, chm, A.grid.th0,
-                                                       A.grid.inv_step, H, rr, tot, lin);
+                                                       A.grid.inv_step, H, rr, tot);
                 o.x = n > 0 ? rr[0] : 0u;
                 o.y = 0u;
                 if (n == 2) o.y = rr[1];
@@ -808,7 +796,6 @@ __global__ void __launch_bounds__(256, CVS_ARC_PASS_MIN_BLOCKS)
                     const uint32_t e = (last & 0xFFFFu) + (last >> 16);
                     o.y = s1 | ((e - s1) << 16);
                 }
-                if (lin) o.x |= 1u << 31;
                 if (probe) {
                     covered += tot;
                     plain += certain_fail_radius(T, C, r, A.hi_min) ? 0 : H;
@@ -866,7 +853,7 @@ __device__ __forceinline__ void store_item(const SearchArgs& A, long long g, int
 #define CVS_SEARCH_MIN_BLOCKS 6
 #endif
 #ifndef CVS_ARCS_MIN_BLOCKS
-#define CVS_ARCS_MIN_BLOCKS 6
+#define CVS_ARCS_MIN_BLOCKS 7  // 6 measured 2.9% slower, 8 (with halved segments to fit) 7%
 #endif
 
 // ARCS: the angle-range walk (FP32, gamut reject, a grid with angle ranges),

@@ -470,22 +470,17 @@ __device__ __forceinline__ int4 channel_arcs(const ArcChannel& a, float th0, flo
 
 // Feasible slot ranges of radius r for a fast-path target: writes up to
 // kMaxArcRanges entries (start | len << 16), disjoint and ascending, to out
-// and returns their number; total = slots covered; lin = some candidate may
-// reach the sRGB linear segment (its lower bound, as in pow_branch_only, is
-// not above the segment by 2e-5).  chm: channels an enabled pattern needs
-// high (bit 2 - c for channel c).
+// and returns their number; total = slots covered.  chm: channels an enabled
+// pattern needs high (bit 2 - c for channel c).
 template <bool CLIP>
 __device__ __forceinline__ int radius_ranges_body(const TargetF32& T, const ChainF32& C, float r,
                                                   int32_t hi_min, uint32_t chm, float th0,
                                                   float inv_step, int H, uint32_t* out,
-                                                  int& total, bool& lin) {
+                                                  int& total) {
     ArcChannel ch[3];
-    lin = false;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 3; ++c)
         ch[c] = channel_bounds(T, C, r, c, hi_min, (chm >> (2 - c)) & 1u, CLIP);
-        lin |= !(ch[c].lo > 0.0031308f + 1e-5f);
-    }
     total = 0;
     // no slot: a channel leaves the gamut at every angle, or no channel can be high
     if (ch[0].xg < 0.0f || ch[1].xg < 0.0f || ch[2].xg < 0.0f ||
@@ -711,15 +706,14 @@ __device__ __forceinline__ int certain32(const TargetF32& T, const ChainF32& C, 
 
 // ------------------------------------------------------------ angle-range items
 // k_arc_ranges writes, per (target, radius) of a chunk, up to two slot ranges
-// (start | len << 16; a third or more merged into the second, a superset) with
-// bit 31 of the first word set where the radius may reach the sRGB linear
-// segment, or kSlowRadius for a radius on the slow path (searched whole).
+// (start | len << 16; a third or more merged into the second, a superset), or
+// kSlowRadius for a radius on the slow path (searched whole).
 // The search kernels concatenate, per warp, the ranges of up to kArcRadii
 // radii into a list and evaluate only the listed slots, 32 at a time whatever
 // radius they belong to; the rest certainly fail (k_search in increasing
 // radius order, k_search_multi in decreasing radius rank).  List entry j:
-// al[j] = radius offset (bits 0..6) | linear-segment bit (bit 7) | (first slot
-// - first position + kArcBias) << 8, and its first position pos[j] =
+// al[j] = radius offset (bits 0..6) | (first slot - first position +
+// kArcBias) << 8, and its first position pos[j] =
 // al[kArcEntries + j].  Fast-path radii's entries start at index 0, slow-path
 // radii's (whole radii) at kSlowBase; each region ends with a sentinel
 // position.  After the list, al holds the start mask of the segment being
