@@ -215,6 +215,19 @@ __device__ __forceinline__ void drain_multi(const MultiArgs& A, const float2* r2
     }
 }
 
+// The first rank in [kk0, kk1) whose radius leaves the cubic branch of f^-1
+// for target T (kk1 if none): fast_radius only falls as the radius grows.
+__device__ __forceinline__ int first_slow_rank(const TargetF32& T, const float2* r2s, int kk0,
+                                               int kk1) {
+    if (T.flags & 1u) return kk1;
+    int lo = kk0, hi = kk1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (fast_radius(T, r2s[mid].x)) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
 // Item totals: lane s publishes set s (count, largest passing radius, patterns).
 __device__ __forceinline__ void publish_item(const MultiArgs& A, const MultiTally& m,
                                              const float* rmx, int64_t t) {
@@ -512,8 +525,9 @@ __device__ __forceinline__ void multi_list_iters(const MultiArgs& A, const float
     }
 }
 
-// A work item of a fast-path target (FP32, gamut reject) on a grid with angle
-// ranges: ranks [kk0, kk1) in blocks of kArcRadii from the top, each block's
+// A work item (FP32, gamut reject) on a grid with angle ranges: the listed
+// slots of ranks [kk0, kk1) (none on a slow-path radius), in blocks of
+// kArcRadii from the top, each block's
 // ranges listed in decreasing rank (so that a lane meets its radii in
 // decreasing order, as in multi_item) and walked 32 positions a step; flagged
 // slots are found again in the list and queued as in multi_item.
@@ -547,8 +561,8 @@ __device__ __forceinline__ void multi_item_arcs(const MultiArgs& A, const float2
         int nf = 0, pf = 0;  // the list's entries and positions
         for (int kg = kb1 - 1; kg >= kb; kg -= 32) {
             const int kk = kg - (int)lane;
-            const uint2 o =
-                kk >= kb ? __ldg(ranges + __ldg(A.order + kk)) : make_uint2(0u, 0u);
+            uint2 o = kk >= kb ? __ldg(ranges + __ldg(A.order + kk)) : make_uint2(0u, 0u);
+            if (o.x == kSlowRadius) o = make_uint2(0u, 0u);  // walked by the plain kernel
             const uint32_t w0 = o.x, w1 = o.y;
             const int l0 = (int)(w0 >> 16), l1 = (int)(w1 >> 16);
             const int n = (l0 > 0 ? 1 : 0) + (l1 > 0 ? 1 : 0);
@@ -627,9 +641,10 @@ __device__ __forceinline__ void multi_item_arcs(const MultiArgs& A, const float2
     publish_item(A, m, rmx, t);
 }
 
-// ARCS: the kernel with the angle-range walk (FP32, gamut reject) of the
-// fast-path targets; a second launch of the plain kernel (skip_fast) takes the
-// slow-path targets.  Keeping their plain walk out of the range-walk kernel
+// ARCS: the kernel with the angle-range walk (FP32, gamut reject) of every
+// target's fast-path radii (the range pass lists no slot of a slow-path
+// radius); a second launch of the plain kernel (skip_fast) walks the
+// slow-path radii.  Keeping the plain walk out of the range-walk kernel
 // measured 13% faster (17.5 to 15.3 ms for the 12 Table 1 sets on the cube):
 // the kernel waits on instruction fetch, and warps running the two walks at
 // once double its hot code.
@@ -677,17 +692,22 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
         const int k0 = kc * kchunk, k1 = min(k0 + kchunk, K);
         TargetF32 T{};
         if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
-        if (ARCS) {  // fast-path targets only: the plain-walk kernel takes the others
-            if (T.flags & 1u)
-                multi_item_arcs<ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, al, T, C, PC, t, k0, k1,
-                                             n_flag, n_re);
+        if (ARCS) {  // the fast-path radii: the plain-walk kernel takes the others
+            multi_item_arcs<ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, al, T, C, PC, t, k0, k1,
+                                         n_flag, n_re);
         } else if (PREC == CVS_PREC_FP32_RECHECK && (T.flags & 1u)) {
             if (!A.skip_fast)
                 multi_item<PREC, true, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t,
                                                       k0, k1, n_flag, n_re);
-        } else
-            multi_item<PREC, false, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t, k0,
-                                                   k1, n_flag, n_re);
+        } else {
+            // after the range walk, only the slow-path radii are left: the
+            // ranks from the first radius off the cubic branch of f^-1 on
+            const int ks = (PREC == CVS_PREC_FP32_RECHECK && A.skip_fast)
+                               ? first_slow_rank(T, r2s, k0, k1) : k0;
+            if (ks < k1)
+                multi_item<PREC, false, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC,
+                                                       t, ks, k1, n_flag, n_re);
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

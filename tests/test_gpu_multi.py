@@ -160,12 +160,16 @@ def test_angle_range_walk_matches_oracle(ctx, torch_cuda, walk):
     ranges of the union of the sets) and on the plain walk (0): every set
     equals the single-set entry point, and four sets the oracle.  The grids
     cover one and several blocks of 128 radii, unsorted radii, radius chunks
-    per work item, per-set masks and luminance limits."""
+    per work item, per-set masks and luminance limits; the colours include dark
+    ones whose larger radii take the slow path (walked by the plain kernel)."""
     torch = torch_cuda
     cube = W.color_cube()
     rng = np.random.default_rng(23)
-    rgb = np.concatenate([cube[rng.choice(len(cube), 96, replace=False)],
-                          np.array([[0, 0, 0], [252, 252, 252], [4, 200, 4]], np.uint8)])
+    # dark colours leave the cubic branch of f^-1 part of the way up the radii
+    dark = np.array([[0, 0, 0], [28, 28, 28], [40, 40, 40], [60, 20, 20], [10, 40, 60],
+                     [48, 36, 80]], np.uint8)
+    rgb = np.concatenate([cube[rng.choice(len(cube), 96, replace=False)], dark,
+                          np.array([[252, 252, 252], [4, 200, 4]], np.uint8)])
     r2, a2 = W.grid(2)
     grids = [(r2, a2),
              (np.linspace(0.2, 30.0, 200), np.arange(0.0, 360.0, 3.0)),
