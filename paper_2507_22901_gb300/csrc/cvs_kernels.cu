@@ -665,57 +665,54 @@ __device__ __forceinline__ void run_item_arcs(const SearchArgs& A, const Smem& S
     const uint2* ranges = A.arc_ranges + t * K;
     for (int kb = k0; kb < k1; kb += kArcRadii) {
         const int kb1 = min(k1, kb + kArcRadii);
-        int nf = 0, pf = 0, ns = 0, ps = 0;
-        for (int kg = kb; kg < kb1; kg += 32) {
-            const int k = kg + (int)lane;
-            const uint2 o = k < kb1 ? ranges[k] : make_uint2(0u, 0u);
-            const int slow = o.x == kSlowRadius ? 1 : 0;
-            const uint32_t w0 = slow ? 0u : o.x, w1 = slow ? 0u : o.y;
-            const int l0 = (int)(w0 >> 16), l1 = (int)(w1 >> 16);
-            const int n = (l0 > 0 ? 1 : 0) + (l1 > 0 ? 1 : 0);
-            const int tot = l0 + l1;
-            if (k < kb1 && !slow) acc.prune += (uint32_t)(H - tot);
-            int nr, pr, nsr, psr;
-            const int eoff = nf + warp_exclusive_sum(n, nr);
-            const int poff = pf + warp_exclusive_sum(tot, pr);
-            const int soff = ns + warp_exclusive_sum(slow, nsr);
-            const int spoff = ps + warp_exclusive_sum(slow ? H : 0, psr);
-            const uint32_t koff = (uint32_t)(k - kb);
-            int e = eoff, q = poff;
-            if (l0 > 0) {
-                al[e] = koff | ((uint32_t)((int)(w0 & 0xFFFFu) - q + kArcBias) << 8);
-                pos[e] = (uint32_t)q;
-                ++e;
-                q += l0;
+        // the list: the fast-path radii's ranges (entries [0, js), positions
+        // [0, ps)), then the slow-path radii's (to nf and pf)
+        int nf = 0, pf = 0, js = 0, ps = 0;
+        for (int region = 0; region < 2; ++region) {
+            for (int kg = kb; kg < kb1; kg += 32) {
+                const int k = kg + (int)lane;
+                const uint2 o = k < kb1 ? ranges[k] : make_uint2(0u, 0u);
+                const bool take = k < kb1 && ((o.x & kSlowRadius) != 0u) == (region == 1);
+                const uint32_t w0 = take ? (o.x & ~kSlowRadius) : 0u, w1 = take ? o.y : 0u;
+                const int l0 = (int)(w0 >> 16), l1 = (int)(w1 >> 16);
+                const int n = (l0 > 0 ? 1 : 0) + (l1 > 0 ? 1 : 0);
+                const int tot = l0 + l1;
+                if (take) acc.prune += (uint32_t)(H - tot);
+                int nr, pr;
+                const int eoff = nf + warp_exclusive_sum(n, nr);
+                const int poff = pf + warp_exclusive_sum(tot, pr);
+                const uint32_t koff = (uint32_t)(k - kb);
+                int e = eoff, q = poff;
+                if (l0 > 0) {
+                    al[e] = koff | ((uint32_t)((int)(w0 & 0xFFFFu) - q + kArcBias) << 8);
+                    pos[e] = (uint32_t)q;
+                    ++e;
+                    q += l0;
+                }
+                if (l1 > 0) {
+                    al[e] = koff | ((uint32_t)((int)(w1 & 0xFFFFu) - q + kArcBias) << 8);
+                    pos[e] = (uint32_t)q;
+                }
+                nf += nr;
+                pf += pr;
             }
-            if (l1 > 0) {
-                al[e] = koff | ((uint32_t)((int)(w1 & 0xFFFFu) - q + kArcBias) << 8);
-                pos[e] = (uint32_t)q;
+            if (region == 0) {
+                js = nf;
+                ps = pf;
             }
-            if (slow) {
-                al[kSlowBase + soff] = koff | ((uint32_t)(kArcBias - spoff) << 8);
-                pos[kSlowBase + soff] = (uint32_t)spoff;
-            }
-            nf += nr;
-            pf += pr;
-            ns += nsr;
-            ps += psr;
         }
-        if (lane == 0) {
-            pos[nf] = (uint32_t)pf;
-            pos[kSlowBase + ns] = (uint32_t)ps;
-        }
+        if (lane == 0) pos[nf] = (uint32_t)pf;  // (pos[js] = ps: the first slow entry or this)
         __syncwarp();
-        run_list<true, LIST, DL>(A, S, P, PC, D, C, t, kb, al, 0, nf, 0, pf, acc, fb, pq, pq_n,
+        run_list<true, LIST, DL>(A, S, P, PC, D, C, t, kb, al, 0, js, 0, ps, acc, fb, pq, pq_n,
                                  rq_t, rq_kh, rq_n, n_flag, n_re);
-        if (ns) {  // the slow path decides its own flagged slots
+        if (nf > js) {  // the slow path decides its own flagged slots
             if (pq_n > 0) {
                 const TargetF32 T = A.tf[t];
                 drain_flagged<true, DL>(A, S, T, C, t, pq, pq_n, acc, rq_t, rq_kh, rq_n, n_re);
                 pq_n = 0;
             }
-            run_list<false, LIST, DL>(A, S, P, PC, D, C, t, kb, al, kSlowBase, kSlowBase + ns, 0,
-                                      ps, acc, fb, pq, pq_n, rq_t, rq_kh, rq_n, n_flag, n_re);
+            run_list<false, LIST, DL>(A, S, P, PC, D, C, t, kb, al, js, nf, ps, pf, acc, fb, pq,
+                                      pq_n, rq_t, rq_kh, rq_n, n_flag, n_re);
             if (pq_n > 0) {
                 const TargetF32 T = A.tf[t];
                 drain_flagged<false, DL>(A, S, T, C, t, pq, pq_n, acc, rq_t, rq_kh, rq_n, n_re);
@@ -776,30 +773,24 @@ __global__ void __launch_bounds__(256, CVS_ARC_PASS_MIN_BLOCKS)
         const TargetF32 T = A.tf[t * stride];
         for (int k = (int)lane; k < K; k += 32) {
             const float r = __ldg(A.grid.r32 + k);
+            const bool slow = !((T.flags & 1u) || fast_radius(T, r));
             uint2 o;
-            if (!((T.flags & 1u) || fast_radius(T, r))) {
-                o = make_uint2(kSlowRadius, 0u);
-                if (probe) {
-                    covered += H;
-                    plain += H;
-                }
-            } else {
-                uint32_t rr[kMaxArcRanges];
-                int tot = 0;
-                const int n = radius_ranges_body<CLIP>(T, C, r, A.hi_min, chm, A.grid.th0,
-                                                       A.grid.inv_step, H, rr, tot);
-                o.x = n > 0 ? rr[0] : 0u;
-                o.y = 0u;
-                if (n == 2) o.y = rr[1];
-                if (n > 2) {  // cover the second to the last range with one
-                    const uint32_t s1 = rr[1] & 0xFFFFu, last = rr[n - 1];
-                    const uint32_t e = (last & 0xFFFFu) + (last >> 16);
-                    o.y = s1 | ((e - s1) << 16);
-                }
-                if (probe) {
-                    covered += tot;
-                    plain += certain_fail_radius(T, C, r, A.hi_min) ? 0 : H;
-                }
+            uint32_t rr[kMaxArcRanges];
+            int tot = 0;
+            const int n = radius_ranges_body<CLIP>(T, C, r, A.hi_min, chm, A.grid.th0,
+                                                   A.grid.inv_step, H, rr, tot);
+            o.x = n > 0 ? rr[0] : 0u;
+            o.y = 0u;
+            if (n == 2) o.y = rr[1];
+            if (n > 2) {  // cover the second to the last range with one
+                const uint32_t s1 = rr[1] & 0xFFFFu, last = rr[n - 1];
+                const uint32_t e = (last & 0xFFFFu) + (last >> 16);
+                o.y = s1 | ((e - s1) << 16);
+            }
+            if (slow) o.x |= kSlowRadius;
+            if (probe) {  // the plain walk searches a slow-path radius whole
+                covered += tot;
+                plain += (!slow && certain_fail_radius(T, C, r, A.hi_min)) ? 0 : H;
             }
             out[t * K + k] = o;
         }

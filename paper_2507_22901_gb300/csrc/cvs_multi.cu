@@ -562,7 +562,7 @@ __device__ __forceinline__ void multi_item_arcs(const MultiArgs& A, const float2
         for (int kg = kb1 - 1; kg >= kb; kg -= 32) {
             const int kk = kg - (int)lane;
             uint2 o = kk >= kb ? __ldg(ranges + __ldg(A.order + kk)) : make_uint2(0u, 0u);
-            if (o.x == kSlowRadius) o = make_uint2(0u, 0u);  // walked by the plain kernel
+            if (o.x & kSlowRadius) o = make_uint2(0u, 0u);  // walked by the plain kernel
             const uint32_t w0 = o.x, w1 = o.y;
             const int l0 = (int)(w0 >> 16), l1 = (int)(w1 >> 16);
             const int n = (l0 > 0 ? 1 : 0) + (l1 > 0 ? 1 : 0);

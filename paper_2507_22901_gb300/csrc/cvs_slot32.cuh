@@ -293,7 +293,17 @@ __device__ __forceinline__ int first_linseg_radius(const TargetF32& T, const Cha
 //   high_possible needs 2|O| >= tau = v^-1(v(lo) + hi_min - 1) - lo: outside
 //   the arc |sin(j - j0)| < (tau/2 - eps)/R about j0.
 // A slot can pass only inside every gamut arc and outside the "low" arc of at
-// least one channel that an enabled pattern needs high.  radius_ranges_body turns
+// least one channel that an enabled pattern needs high.
+// On a slow-path radius some f-values fall below delta = 6/29, where f^-1 is
+// not the cube but its tangent line at delta: f^-1(f) = f^3 + e(f) with
+// e(f) = -(delta - f)^2 (f + 2 delta) below delta and 0 above.  So each colour
+// adds Ax (e(fx0 +- u) - e(fx0)) + Bz (e(fz0 +- w) - e(fz0)) to the cubic
+// form, a departure D within [Dlo, Dhi] (finv_departure: e is non-positive
+// and its size only grows as f falls, over the f-values of real colours at
+// radii up to 32).  The bounds then widen by it: G by Dhi - lo_out and hi_out
+// - Dlo on its two sides, lo by Dlo, and tau by Dhi - Dlo, since
+// lin+ - lin- = 2 O + D+ - D-.  On a fast-path radius D is exactly 0 and the
+// bounds are those above.  radius_ranges_body turns
 // these arcs into slot-index ranges of a folded, evenly spaced grid (slot h
 // at th0 + h pi/H) and intersects them by a sweep over their end points.
 // Every bound carries margins far above its FP32 rounding: arguments of asin
@@ -382,11 +392,33 @@ __device__ __forceinline__ void arc_range(float c, float half, int H, int& start
 struct ArcChannel {
     float alpha, beta, xg, xl, lo;
     float invR, eps, emid, ehalf, l0;  // E(j) = emid + ehalf cos 2j; the target's linear value
+    float dlo, dhi;                    // the departure from the cubic, [Dlo, Dhi]
 };
+
+// Range [lo, hi] of e(f0 + d) - e(f0) over |d| <= Di (Di with its margin,
+// as fast_radius takes it): exactly 0 where f0 - Di stays above delta.
+struct FinvDeparture {
+    float xlo, xhi, zlo, zhi;
+};
+
+__device__ __forceinline__ void finv_departure(float f0, float Di, float& lo, float& hi) {
+    const float dl = (float)kFinvBreak;
+    const float fmin = f0 - Di;
+    if (fmin > dl * 1.00001f + 1e-6f) {
+        lo = 0.0f;
+        hi = 0.0f;
+        return;
+    }
+    const float tm = fmaxf(dl - fmin, 0.0f), t0 = fmaxf(dl - f0, 0.0f);
+    const float emax = tm * tm * (fmin + 2.0f * dl) * 1.0001f + 1e-7f;  // |e| at the lowest f
+    const float e0 = t0 * t0 * (f0 + 2.0f * dl);                        // |e(f0)|
+    lo = -emax + e0 * 0.9999f - 1e-7f;
+    hi = e0 * 1.0001f + 1e-7f;
+}
 
 __device__ __forceinline__ ArcChannel channel_bounds(const TargetF32& T, const ChainF32& C, float r,
                                                      int c, int32_t hi_min, bool need_high,
-                                                     bool clip) {
+                                                     bool clip, const FinvDeparture& dep) {
     const float U = r * 0.002f, V = r * 0.005f;
     const float Ui = U * 1.00001f, Vi = V * 1.00001f;
     const float ax = c == 0 ? C.Ax[0] : (c == 1 ? C.Ax[1] : C.Ax[2]);
@@ -404,12 +436,14 @@ __device__ __forceinline__ ArcChannel channel_bounds(const TargetF32& T, const C
     o.invR = invR;
     o.eps = eps;
     o.l0 = l0;
+    o.dlo = fminf(ax * dep.xlo, ax * dep.xhi) + fminf(bz * dep.zlo, bz * dep.zhi);
+    o.dhi = fmaxf(ax * dep.xlo, ax * dep.xhi) + fmaxf(bz * dep.zlo, bz * dep.zhi);
     if (!clip) {
         const float P = ax * T.c1x * U * U, Q = bz * T.c1z * V * V;
         o.emid = 0.5f * (P + Q);
         o.ehalf = 0.5f * (Q - P);
-        const float G = fminf(l0 + fmaxf(P, Q) - kLinOutLo, kLinOutHi - l0 - fminf(P, Q)) + eps +
-                        1e-5f;
+        const float G = fminf(l0 + fmaxf(P, Q) + o.dhi - kLinOutLo,
+                              kLinOutHi - l0 - fminf(P, Q) - o.dlo) + eps + 1e-5f;
         o.xg = G < 0.0f ? -1.0f : G * invR * 1.0001f + 1e-6f;
     }
     // the lower bound of lin_lower_bound, per channel
@@ -421,11 +455,11 @@ __device__ __forceinline__ ArcChannel channel_bounds(const TargetF32& T, const C
     const float coupled = l0 - pq2 * rsqrtf(pq2) * 1.00001f + fminf(0.0f, ax * T.c1x) * Ui * Ui +
                           fminf(0.0f, bz * T.c1z) * Vi * Vi -
                           (fabsf(ax) * Ui * Ui * Ui + fabsf(bz) * Vi * Vi * Vi);
-    o.lo = fmaxf(ends, coupled) - 1e-5f;
+    o.lo = fmaxf(ends, coupled) - 1e-5f + o.dlo;
     const float lo = clip ? o.lo : fmaxf(o.lo, kLinOutLo);
     const float y = v_enc_fast(lo) + (float)hi_min - 1.02f;
     const float tau = (v_inv_fast(y) - lo) * 0.9999f - 3e-6f;
-    const float ostar = 0.5f * tau;
+    const float ostar = 0.5f * (tau - (o.dhi - o.dlo));
     o.xl = need_high ? (ostar - eps) * invR * 0.9999f - 1e-6f : 2.0f;
     return o;
 }
@@ -451,7 +485,8 @@ __device__ __forceinline__ int4 channel_arcs(const ArcChannel& a, float th0, flo
         const float cmin = fabsf(cj) <= sw + 1e-5f ? -1.0f : fmaxf(fminf(c1, c2) - 1e-5f, -1.0f);
         const float e_a = a.ehalf * cmin, e_b = a.ehalf * cmax;
         const float emin = a.emid + fminf(e_a, e_b) - 1e-7f, emax = a.emid + fmaxf(e_a, e_b) + 1e-7f;
-        const float G = fminf(a.l0 + emax - kLinOutLo, kLinOutHi - a.l0 - emin) + a.eps + 1e-5f;
+        const float G = fminf(a.l0 + emax + a.dhi - kLinOutLo, kLinOutHi - a.l0 - emin - a.dlo) +
+                        a.eps + 1e-5f;
         xg = fminf(xg, G < 0.0f ? -1.0f : G * a.invR * 1.0001f + 1e-6f);
     }
     if (xg < 0.0f) {  // no angle of the radius keeps this channel in gamut
@@ -468,7 +503,8 @@ __device__ __forceinline__ int4 channel_arcs(const ArcChannel& a, float th0, flo
     return o;
 }
 
-// Feasible slot ranges of radius r for a fast-path target: writes up to
+// Feasible slot ranges of radius r for any target (on a slow-path radius
+// with the bounds widened by the departure of f^-1 from its cubic): writes up to
 // kMaxArcRanges entries (start | len << 16), disjoint and ascending, to out
 // and returns their number; total = slots covered.  chm: channels an enabled
 // pattern needs high (bit 2 - c for channel c).
@@ -477,10 +513,13 @@ __device__ __forceinline__ int radius_ranges_body(const TargetF32& T, const Chai
                                                   int32_t hi_min, uint32_t chm, float th0,
                                                   float inv_step, int H, uint32_t* out,
                                                   int& total) {
+    FinvDeparture dep;
+    finv_departure(T.fx0, r * 0.002f * 1.00001f, dep.xlo, dep.xhi);
+    finv_departure(T.fz0, r * 0.005f * 1.00001f, dep.zlo, dep.zhi);
     ArcChannel ch[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-        ch[c] = channel_bounds(T, C, r, c, hi_min, (chm >> (2 - c)) & 1u, CLIP);
+        ch[c] = channel_bounds(T, C, r, c, hi_min, (chm >> (2 - c)) & 1u, CLIP, dep);
     total = 0;
     // no slot: a channel leaves the gamut at every angle, or no channel can be high
     if (ch[0].xg < 0.0f || ch[1].xg < 0.0f || ch[2].xg < 0.0f ||
@@ -706,25 +745,26 @@ __device__ __forceinline__ int certain32(const TargetF32& T, const ChainF32& C, 
 
 // ------------------------------------------------------------ angle-range items
 // k_arc_ranges writes, per (target, radius) of a chunk, up to two slot ranges
-// (start | len << 16; a third or more merged into the second, a superset), or
-// kSlowRadius for a radius on the slow path (searched whole).
+// (start | len << 16; a third or more merged into the second, a superset),
+// with bit 31 of the first word (kSlowRadius) set on a slow-path radius, whose
+// slots the search evaluates with the slow chain.
 // The search kernels concatenate, per warp, the ranges of up to kArcRadii
 // radii into a list and evaluate only the listed slots, 32 at a time whatever
 // radius they belong to; the rest certainly fail (k_search in increasing
 // radius order, k_search_multi in decreasing radius rank).  List entry j:
 // al[j] = radius offset (bits 0..6) | (first slot - first position +
 // kArcBias) << 8, and its first position pos[j] =
-// al[kArcEntries + j].  Fast-path radii's entries start at index 0, slow-path
-// radii's (whole radii) at kSlowBase; each region ends with a sentinel
-// position.  After the list, al holds the start mask of the segment being
-// walked (list_mask).
+// al[kArcEntries + j].  k_search lists the fast-path radii's entries first and
+// the slow-path radii's after them, so that each region is walked by one chain
+// variant; the first slow entry's position ends the fast region and a sentinel
+// position ends the list.  After the list, al holds the start mask of the
+// segment being walked (list_mask).
 constexpr int kArcRadii = 128;
-constexpr int kSlowBase = kArcRadii * 2 + 1;
-constexpr int kArcEntries = kSlowBase + kArcRadii + 3;
+constexpr int kArcEntries = 2 * kArcRadii + 2;
 constexpr int kArcMaskWords = 256;  // steps of 32 positions per segment, at most
 constexpr int kArcWords = 2 * kArcEntries + kArcMaskWords;
 constexpr int kArcBias = 1 << 23;
-constexpr uint32_t kSlowRadius = 0xFFFFFFFFu;
+constexpr uint32_t kSlowRadius = 1u << 31;
 
 __device__ __forceinline__ int warp_exclusive_sum(int v, int& total) {
     const unsigned lane = lane_id();

@@ -102,6 +102,29 @@ def test_grids_match_oracle_and_plain_walk(ctx, torch_cuda, name):
     assert res[1][1]["pruned"] >= res[0][1]["pruned"]
 
 
+@pytest.mark.parametrize("grid", [2, 3])
+def test_dark_colours_on_slow_radii(ctx, torch_cuda, grid):
+    """Dark colours, whose larger radii leave the cubic branch of f^-1: on
+    those radii the ranges come from bounds widened by the departure of the
+    piecewise f^-1 from its cube, and the slots they list are evaluated with
+    the slow chain.  Every cube colour with channels up to 88 (step 8), and
+    the darkest of each hue, against the oracle and the plain walk; the
+    ranges must also prune slow-path radii (more slots than the radius bound
+    alone removes)."""
+    radii, ang = W.grid(grid)
+    q = np.arange(0, 89, 8)
+    dark = np.stack(np.meshgrid(q, q, q, indexing="ij"), -1).reshape(-1, 3).astype(np.uint8)
+    hues = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [0, 1, 1], [1, 0, 1],
+                     [2, 1, 0], [0, 2, 1]], np.uint8)
+    rgb = np.concatenate([dark, hues, hues * 3])
+    res = both_walks(ctx, torch_cuda, rgb, radii, ang)
+    exp = oracle.search_colors(rgb, radii, ang, 50.0, 0.5, threads=THREADS)
+    same(res[1][0], exp, f"dark colours, grid {grid} (ranges)")
+    same(res[0][0], exp, f"dark colours, grid {grid} (plain)")
+    assert exp[1].sum() > 0
+    assert res[1][1]["pruned"] > res[0][1]["pruned"]
+
+
 def test_4096_slots(ctx, torch_cuda):
     radii = np.array([2.0, 9.5, 17.0, 24.5, 32.0])
     ang = np.arange(8192) * (360.0 / 8192)
