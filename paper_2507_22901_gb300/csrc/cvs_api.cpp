@@ -589,8 +589,16 @@ cvs_status arc_probe(cvs_ctx* c, const SearchArgs& a, int64_t n, cudaStream_t st
 // inside a capture, where the plain walk runs instead) and, with option
 // angle_ranges = 2, the probe's choice for this grid, thresholds and kind of
 // call (probed once, synchronously, outside captures).
+// With the automatic choice, a call of fewer (target, radius) pairs than
+// this keeps the plain walk: on work that does not fill the GPU the range
+// pass and its extra launches cost more than they save (the paper's Table 1
+// experiment, 9 colours x 61 radii under 12 sets: 58 us on the plain walk, 77
+// us with the ranges).
+constexpr int64_t kArcMinPairs = int64_t(1) << 13;
+
 cvs_status prepare_arcs(cvs_ctx* c, SearchArgs& a, int64_t n, cvs_precision prec, int list_mode,
                         cudaStream_t st, bool capturing) {
+    if (c->angle_ranges == 2 && n * (int64_t)c->grid.K < kArcMinPairs) a.grid.arcs = 0;
     if (a.grid.arcs && prec == CVS_PREC_FP32_RECHECK) {
         const int64_t need = arc_entries(c, n);
         if (c->cap_arc < need && !capturing) {

@@ -250,6 +250,16 @@ def test_automatic_choice(ctx, torch_cuda):
         assert auto["ranges_ms"] > 0.0 and auto["pruned"] == forced[1]["pruned"]
     elif ratio > 0.7:
         assert auto["ranges_ms"] == 0.0 and auto["pruned"] == forced[0]["pruned"]
+    # a call too small to fill the GPU (the Table 1 colours, 61 radii) keeps
+    # the plain walk, single-set and multi-set alike
+    t1 = dev(torch, np.array(list(W.TABLE1_COLORS.values()), np.uint8))
+    r1, a1 = W.grid(1)
+    ctx.search_colors(t1, r1, a1, 50.0, 0.5)
+    ctx.synchronize()
+    assert ctx.stats()["ranges_ms"] == 0.0
+    ctx.search_colors_multi(t1, r1, a1, W.table1_threshold_sets())
+    ctx.synchronize()
+    assert ctx.stats()["ranges_ms"] == 0.0
 
 
 def test_reserve_covers_the_ranges(torch_cuda):
