@@ -544,10 +544,13 @@ cvs_status cvs_autotune(cvs_ctx* ctx, const uint8_t* rgb_dev, int64_t n, const c
  *                   bounds on the pair's linear RGB (a sinusoid in the angle
  *                   plus a bounded rest) into the angle slots where a pair can
  *                   stay in gamut with a channel able to read high, and then
- *                   search only those slots; results are identical.  0: never;
- *                   1: always; 2 (default): decided per grid, thresholds and kind
- *                   of call (colours, images, the all-colour table) by
- *                   a probe of 4096 targets spread over the first call (which
+ *                   search only those slots; results are identical.  The
+ *                   multi-threshold search uses the ranges of the union of its
+ *                   sets.  0: never; 1: always; 2 (default): not for calls of
+ *                   fewer than 8192 (target, radius) pairs, else decided per
+ *                   grid, thresholds and kind of call (colours, images, the
+ *                   all-colour table, several threshold sets) by a probe of
+ *                   4096 targets spread over the first call (which
  *                   synchronises `stream` once), where the ranges list under
  *                   0.6 of the slots the plain search would walk.  The context
  *                   keeps up to 256 MiB of scratch for the ranges.
