@@ -162,7 +162,6 @@ struct MultiArgs {
     int64_t arc_cap;
     void* ev_ranges;           // host: a cudaEvent_t recorded after the first ranges pass, or NULL
     unsigned ev_flags;         // host: its record flags
-    int32_t skip_fast;         // the plain-walk kernel leaves fast-path targets to the range walk
 };
 
 // The embedding step: per pixel the first passing pair of the requested

@@ -215,19 +215,6 @@ __device__ __forceinline__ void drain_multi(const MultiArgs& A, const float2* r2
     }
 }
 
-// The first rank in [kk0, kk1) whose radius leaves the cubic branch of f^-1
-// for target T (kk1 if none): fast_radius only falls as the radius grows.
-__device__ __forceinline__ int first_slow_rank(const TargetF32& T, const float2* r2s, int kk0,
-                                               int kk1) {
-    if (T.flags & 1u) return kk1;
-    int lo = kk0, hi = kk1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (fast_radius(T, r2s[mid].x)) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
 // Item totals: lane s publishes set s (count, largest passing radius, patterns).
 __device__ __forceinline__ void publish_item(const MultiArgs& A, const MultiTally& m,
                                              const float* rmx, int64_t t) {
@@ -452,13 +439,13 @@ __device__ __forceinline__ void multi_item(const MultiArgs& A, const float2* r2s
 
 // Steps [b, bend) of a list walk (lane at position b + lane of the list in
 // al, whose start mask covers the segment from seg; positions from pend on
-// inactive): as multi_iters,
-// with each lane's (rank, angle) from its list entry.  The encode keeps the
+// inactive): as multi_iters, in the chain variant FAST, with each lane's
+// (rank, angle) from its list entry.  The encode keeps the
 // sRGB linear-segment select throughout: the loop body stays one variant (a
 // choice per step, or two loops split at the last radius that may reach the
 // segment, measured 2.5% and 6% slower: the kernel waits on instruction
 // fetch, and both make the loop longer).
-template <bool ALLMASK, bool DL>
+template <bool FAST, bool ALLMASK, bool DL>
 __device__ __forceinline__ void multi_list_iters(const MultiArgs& A, const float2* r2s,
                                                  const uint32_t* ts, const float4* sc4s,
                                                  const PairsT& P, const PairsC& PC,
@@ -481,7 +468,7 @@ __device__ __forceinline__ void multi_list_iters(const MultiArgs& A, const float
         const float2 u2 = __fmul2_rn(r2, f2(sc.x, sc.y));
         const float2 w2 = __fmul2_rn(r2, f2(sc.z, sc.w));
         float2 lin[3];
-        lin32<true>(P, PC, u2, w2, lin);
+        lin32<FAST>(P, PC, u2, w2, lin);
         // gamut reject: a warp whose pairs all leave the gamut passes no set
         if (__all_sync(0xFFFFFFFFu, !active || surely_out32(lin))) continue;
         int yp[3], ym[3];
@@ -526,12 +513,12 @@ __device__ __forceinline__ void multi_list_iters(const MultiArgs& A, const float
 }
 
 // A work item (FP32, gamut reject) on a grid with angle ranges: the listed
-// slots of ranks [kk0, kk1) (none on a slow-path radius), in blocks of
-// kArcRadii from the top, each block's
+// slots of ranks [kk0, kk1), of the fast-path radii (FAST) or of the
+// slow-path ones, in blocks of kArcRadii from the top, each block's
 // ranges listed in decreasing rank (so that a lane meets its radii in
 // decreasing order, as in multi_item) and walked 32 positions a step; flagged
 // slots are found again in the list and queued as in multi_item.
-template <bool ALLMASK, bool DL>
+template <bool FAST, bool ALLMASK, bool DL>
 __device__ __forceinline__ void multi_item_arcs(const MultiArgs& A, const float2* r2s,
                                                 const float4* sc4s, const uint32_t* ts,
                                                 uint32_t* fb, float* rmx, uint32_t* pq,
@@ -562,7 +549,8 @@ __device__ __forceinline__ void multi_item_arcs(const MultiArgs& A, const float2
         for (int kg = kb1 - 1; kg >= kb; kg -= 32) {
             const int kk = kg - (int)lane;
             uint2 o = kk >= kb ? __ldg(ranges + __ldg(A.order + kk)) : make_uint2(0u, 0u);
-            if (o.x & kSlowRadius) o = make_uint2(0u, 0u);  // walked by the plain kernel
+            if (((o.x & kSlowRadius) != 0u) == FAST) o = make_uint2(0u, 0u);  // the other walk's
+            o.x &= ~kSlowRadius;
             const uint32_t w0 = o.x, w1 = o.y;
             const int l0 = (int)(w0 >> 16), l1 = (int)(w1 >> 16);
             const int n = (l0 > 0 ? 1 : 0) + (l1 > 0 ? 1 : 0);
@@ -593,7 +581,7 @@ __device__ __forceinline__ void multi_item_arcs(const MultiArgs& A, const float2
             int b = seg;
             for (int w = 0; b < seg_end; ++w) {
                 uint32_t bits = 0;
-                multi_list_iters<ALLMASK, DL>(A, r2s, ts, sc4s, P, PC, D, m, rmx, setmask, al,
+                multi_list_iters<FAST, ALLMASK, DL>(A, r2s, ts, sc4s, P, PC, D, m, rmx, setmask, al,
                                               kb, pf, seg, b, min(seg_end, b + 32 * 32), j0,
                                               bits, seen);
                 fb[w * 32 + lane] = bits;
@@ -621,7 +609,7 @@ __device__ __forceinline__ void multi_item_arcs(const MultiArgs& A, const float2
                     pq_n += __popc(ball);  // below kMultiQueue: at most 31 + 32
                     __syncwarp();
                     if (pq_n >= 32) {
-                        drain_multi<PREC, true, false, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t,
+                        drain_multi<PREC, FAST, false, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t,
                                                                     pq, 32, setmask, n_re);
                         const int rest = pq_n - 32;
                         const uint32_t mv = (int)lane < rest ? pq[32 + lane] : 0u;
@@ -636,19 +624,18 @@ __device__ __forceinline__ void multi_item_arcs(const MultiArgs& A, const float2
         __syncwarp();  // the list is rebuilt for the next block of radii
     }
     if (pq_n > 0)
-        drain_multi<PREC, true, false, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t, pq, pq_n, setmask,
+        drain_multi<PREC, FAST, false, ALLMASK, DL>(A, r2s, sc4s, ts, T, C, D, t, pq, pq_n, setmask,
                                                     n_re);
     publish_item(A, m, rmx, t);
 }
 
-// ARCS: the kernel with the angle-range walk (FP32, gamut reject) of every
-// target's fast-path radii (the range pass lists no slot of a slow-path
-// radius); a second launch of the plain kernel (skip_fast) walks the
-// slow-path radii.  Keeping the plain walk out of the range-walk kernel
-// measured 13% faster (17.5 to 15.3 ms for the 12 Table 1 sets on the cube):
-// the kernel waits on instruction fetch, and warps running the two walks at
-// once double its hot code.
-template <int PREC, bool CLIP, bool ALLMASK, bool DL, bool ARCS>
+// ARCS (FP32, gamut reject, a grid with angle ranges): 1 = the range walk of
+// every target's fast-path radii, 2 = that of the slow-path radii of the
+// targets that have some (a second launch, with the slow chain); 0 = the plain
+// walk.  One chain variant per kernel: walking both in one kernel measured 13%
+// slower (17.5 against 15.3 ms for the 12 Table 1 sets on the cube), as the
+// kernel waits on instruction fetch and two walks at once double its hot code.
+template <int PREC, bool CLIP, bool ALLMASK, bool DL, int ARCS>
 __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = A.grid.K, H = A.grid.H;
@@ -692,21 +679,19 @@ __global__ void __launch_bounds__(kSearchBlock) k_search_multi(const MultiArgs A
         const int k0 = kc * kchunk, k1 = min(k0 + kchunk, K);
         TargetF32 T{};
         if (PREC == CVS_PREC_FP32_RECHECK) T = A.tf[t];
-        if (ARCS) {  // the fast-path radii: the plain-walk kernel takes the others
-            multi_item_arcs<ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, al, T, C, PC, t, k0, k1,
-                                         n_flag, n_re);
+        if (ARCS == 1) {
+            multi_item_arcs<true, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, al, T, C, PC, t, k0,
+                                               k1, n_flag, n_re);
+        } else if (ARCS == 2) {  // a fast-path target has no slow-path radius
+            if (!(T.flags & 1u))
+                multi_item_arcs<false, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, al, T, C, PC, t,
+                                                    k0, k1, n_flag, n_re);
         } else if (PREC == CVS_PREC_FP32_RECHECK && (T.flags & 1u)) {
-            if (!A.skip_fast)
-                multi_item<PREC, true, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t,
-                                                      k0, k1, n_flag, n_re);
+            multi_item<PREC, true, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t,
+                                                  k0, k1, n_flag, n_re);
         } else {
-            // after the range walk, only the slow-path radii are left: the
-            // ranks from the first radius off the cubic branch of f^-1 on
-            const int ks = (PREC == CVS_PREC_FP32_RECHECK && A.skip_fast)
-                               ? first_slow_rank(T, r2s, k0, k1) : k0;
-            if (ks < k1)
-                multi_item<PREC, false, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC,
-                                                       t, ks, k1, n_flag, n_re);
+            multi_item<PREC, false, CLIP, ALLMASK, DL>(A, r2s, sc4s, ts, fb, rmx, pq, T, C, PC, t,
+                                                   k0, k1, n_flag, n_re);
         }
     }
 #pragma unroll
@@ -743,7 +728,7 @@ cudaError_t launch_multi_t(const MultiArgs& a, cudaStream_t st) {
     const bool arcs = kArcsKernel && a.arc_ranges && a.arc_cap >= a.grid.K;
     const int smem = multi_smem_bytes(a.grid, block, arcs);
     const void* fn = arcs ? (const void*)k_search_multi<PREC, CLIP, ALLMASK, DL, kArcsKernel>
-                          : (const void*)k_search_multi<PREC, CLIP, ALLMASK, DL, false>;
+                          : (const void*)k_search_multi<PREC, CLIP, ALLMASK, DL, 0>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -751,18 +736,17 @@ cudaError_t launch_multi_t(const MultiArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (!arcs) {
-        k_search_multi<PREC, CLIP, ALLMASK, DL, false><<<a.num_sms * per_sm, block, smem, st>>>(a);
+        k_search_multi<PREC, CLIP, ALLMASK, DL, 0><<<a.num_sms * per_sm, block, smem, st>>>(a);
         return cudaGetLastError();
     }
-    // the plain-walk kernel for the slow-path targets of each chunk
-    const int smem_plain = multi_smem_bytes(a.grid, block, false);
-    const void* fn_plain = (const void*)k_search_multi<PREC, CLIP, ALLMASK, DL, false>;
-    e = cudaFuncSetAttribute(fn_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_plain);
+    // the range walk of the slow-path radii (slow chain), launched after each chunk's
+    const void* fn_slow = (const void*)k_search_multi<PREC, CLIP, ALLMASK, DL, kArcsKernel ? 2 : 0>;
+    e = cudaFuncSetAttribute(fn_slow, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    int per_sm_plain = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_plain, fn_plain, block, smem_plain);
+    int per_sm_slow = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_slow, fn_slow, block, smem);
     if (e != cudaSuccess) return e;
-    if (per_sm_plain < 1) per_sm_plain = 1;
+    if (per_sm_slow < 1) per_sm_slow = 1;
     // per chunk of targets: the range pass for the union of the sets (the
     // smallest hi_min, every enabled pattern), then the search
     SearchArgs pass{};
@@ -796,9 +780,8 @@ cudaError_t launch_multi_t(const MultiArgs& a, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         e = cudaMemsetAsync(c.work_counter, 0, sizeof(unsigned long long), st);
         if (e != cudaSuccess) return e;
-        c.skip_fast = 1;
-        k_search_multi<PREC, CLIP, ALLMASK, DL, false>
-            <<<a.num_sms * per_sm_plain, block, smem_plain, st>>>(c);
+        k_search_multi<PREC, CLIP, ALLMASK, DL, kArcsKernel ? 2 : 0>
+            <<<a.num_sms * per_sm_slow, block, smem, st>>>(c);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
